@@ -1,0 +1,290 @@
+"""LeCo CPU oracle: ctypes wrapper around ``leco_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY. The product path (the CUDA library and its Python binding) never imports
+this package; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+do. It shares no code with the CUDA path: the C source restates the algorithm from the paper
+(Liu, Zeng & Zhang, LeCo, §3.1-§3.3) in plain loops, compiled with ``-ffp-contract=off``.
+
+Arrays are numpy; values are passed as ``uint64`` (32-bit columns zero-extended).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "leco_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+MODEL_CONSTANT = 0
+MODEL_LINEAR = 1
+METRIC_TILDE = 0
+METRIC_DELTA = 1
+SM_BITS = 256  # model size S_M: one 32-byte record
+DEFAULT_CAP = 1 << 24
+DEFAULT_CHUNK = 1 << 16
+
+RECORD_DTYPE = np.dtype(
+    [("theta0", "<f8"), ("theta1", "<f8"), ("start", "<u8"), ("word3", "<u8")]
+)
+assert RECORD_DTYPE.itemsize == 32
+
+
+class _Fit(ctypes.Structure):
+    _fields_ = [
+        ("theta0", ctypes.c_double),
+        ("theta1", ctypes.c_double),
+        ("A", ctypes.c_int64),
+        ("B", ctypes.c_int64),
+        ("s", ctypes.c_int32),
+        ("exact", ctypes.c_int32),
+        ("b", ctypes.c_int32),
+        ("fallback", ctypes.c_int32),
+        ("shift", ctypes.c_int64),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (
+        not force
+        and os.path.exists(_SO)
+        and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)
+    ):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = [
+        "gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+        "-fPIC", "-shared", _SRC, "-o", tmp, "-lm",
+    ]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    L = ctypes.CDLL(build())
+    u64, i64, i32, dbl, vp = (
+        ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+    )
+    sig = {
+        "orc_clamp_floor": (i64, [dbl]),
+        "orc_predict": (i64, [dbl, dbl, u64]),
+        "orc_fit_partition": (None, [vp, u64, i32, ctypes.POINTER(_Fit)]),
+        "orc_partition_size_bits": (u64, [vp, u64, i32]),
+        "orc_words_for_bits": (u64, [u64]),
+        "orc_encode": (u64, [vp, u64, vp, u64, i32, vp, vp, u64]),
+        "orc_decode": (None, [vp, u64, vp, u64, i32, vp]),
+        "orc_lookup": (u64, [vp, u64, vp, u64, ctypes.c_uint32, i32, vp, u64, vp]),
+        "orc_filter_sum": (None, [vp, u64, vp, u64, i32, u64, u64, vp]),
+        "orc_delta_tilde": (i32, [vp, u64, u64]),
+        "orc_delta_bits": (i32, [vp, u64, u64]),
+        "orc_split_cost": (i64, [vp, u64, u64, i32]),
+        "orc_var_split": (u64, [vp, u64, dbl, u64, u64, u64, i32, vp]),
+        "orc_var_merge_seq": (u64, [vp, vp, u64, i32, u64, u64, vp]),
+        "orc_var_merge_round": (u64, [vp, vp, u64, i32, u64, u64, vp]),
+        "orc_splitmix64": (u64, [u64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _u64(a) -> np.ndarray:
+    if not isinstance(a, np.ndarray):
+        a = np.array(a, dtype=np.uint64)
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.uint64:
+        a = a.astype(np.uint64)
+    return a
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+
+
+# ------------------------------------------------------------------ prediction (§3.3)
+
+def clamp_floor(y: float) -> int:
+    return int(lib().orc_clamp_floor(float(y)))
+
+
+def predict(theta0: float, theta1: float, x: int) -> int:
+    """pred(i') = clamp_floor(fl(fl(theta1 * i') + theta0)) in binary64 without FMA."""
+    return int(lib().orc_predict(float(theta0), float(theta1), int(x)))
+
+
+# ------------------------------------------------------------------ regressor (§3.1)
+
+def fit(values, model: int = MODEL_LINEAR) -> dict:
+    v = _u64(values)
+    f = _Fit()
+    lib().orc_fit_partition(_p(v), v.size, model, ctypes.byref(f))
+    return {k: getattr(f, k) for k, _ in _Fit._fields_}
+
+
+def partition_size_bits(values, model: int = MODEL_LINEAR) -> int:
+    v = _u64(values)
+    return int(lib().orc_partition_size_bits(_p(v), v.size, model))
+
+
+# ------------------------------------------------------------------ partitions (§3.2)
+
+def fixed_starts(n: int, L: int) -> np.ndarray:
+    """Fixed-length partitioning (§3.2.1): partition j covers [jL, min((j+1)L, n))."""
+    if L < 1:
+        raise ValueError("partition size must be >= 1")
+    m = (n + L - 1) // L
+    s = np.arange(m + 1, dtype=np.uint64) * np.uint64(L)
+    s[-1] = n
+    return s
+
+
+def var_split(values, tau: float = 0.1, sm_bits: int = SM_BITS, cap: int = DEFAULT_CAP,
+              chunk: int = DEFAULT_CHUNK, metric: int = METRIC_TILDE) -> np.ndarray:
+    v = _u64(values)
+    out = np.zeros(v.size + 1, dtype=np.uint64)
+    m = lib().orc_var_split(_p(v), v.size, float(tau), sm_bits, cap, chunk, metric, _p(out))
+    return out[: m + 1].copy()
+
+
+def var_merge_seq(values, starts, model: int = MODEL_LINEAR, sm_bits: int = SM_BITS,
+                  cap: int = DEFAULT_CAP):
+    v = _u64(values)
+    st = _u64(starts).copy()
+    passes = ctypes.c_uint64(0)
+    m = lib().orc_var_merge_seq(_p(v), _p(st), max(st.size - 1, 0), model, sm_bits, cap,
+                                ctypes.byref(passes))
+    return st[: m + 1].copy(), int(passes.value)
+
+
+def var_merge_round(values, starts, model: int = MODEL_LINEAR, sm_bits: int = SM_BITS,
+                    cap: int = DEFAULT_CAP):
+    v = _u64(values)
+    st = _u64(starts).copy()
+    rounds = ctypes.c_uint64(0)
+    m = lib().orc_var_merge_round(_p(v), _p(st), max(st.size - 1, 0), model, sm_bits, cap,
+                                  ctypes.byref(rounds))
+    return st[: m + 1].copy(), int(rounds.value)
+
+
+def var_partition(values, tau: float = 0.1, model: int = MODEL_LINEAR, variant: str = "round",
+                  cap: int = DEFAULT_CAP, chunk: int = DEFAULT_CHUNK) -> np.ndarray:
+    """Split then merge (§3.2.2). variant 'round' uses chunked split + round merge; 'seq' the
+    paper's literal single sweep + sequential merge passes."""
+    if variant == "round":
+        st = var_split(values, tau, SM_BITS, cap, chunk)
+        st, _ = var_merge_round(values, st, model, SM_BITS, cap)
+    elif variant == "seq":
+        st = var_split(values, tau, SM_BITS, cap, 0)
+        st, _ = var_merge_seq(values, st, model, SM_BITS, cap)
+    else:
+        raise ValueError(variant)
+    return st
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(int(x)))
+
+
+def delta_tilde(values, i: int, j: int) -> int:
+    v = _u64(values)
+    return int(lib().orc_delta_tilde(_p(v), i, j))
+
+
+def delta_bits(values, i: int, j: int) -> int:
+    v = _u64(values)
+    return int(lib().orc_delta_bits(_p(v), i, j))
+
+
+def split_cost(values, i: int, j: int, metric: int = METRIC_TILDE) -> int:
+    v = _u64(values)
+    return int(lib().orc_split_cost(_p(v), i, j, metric))
+
+
+# ------------------------------------------------------------------ encoder / decoder (§3.3)
+
+def words_for_bits(total_bits: int) -> int:
+    return int(lib().orc_words_for_bits(total_bits))
+
+
+def encode(values, starts, model: int = MODEL_LINEAR):
+    """Fit and pack every partition [starts[p], starts[p+1]). Returns (records, words)."""
+    v = _u64(values)
+    st = _u64(starts)
+    m = max(st.size - 1, 0)
+    rec = np.zeros(m, dtype=RECORD_DTYPE)
+    cap = words_for_bits(64 * v.size)
+    words = np.zeros(cap, dtype=np.uint64)
+    nw = lib().orc_encode(_p(v), v.size, _p(st), m, model, _p(rec), _p(words), cap)
+    if nw == 0:
+        raise RuntimeError("oracle encode: word buffer too small")
+    return rec, words[:nw].copy()
+
+
+def encode_fixed(values, L: int, model: int = MODEL_LINEAR):
+    return encode(values, fixed_starts(len(values), L), model)
+
+
+def decode(records, words, n: int, dtype_bits: int = 64) -> np.ndarray:
+    rec = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
+    w = _u64(words)
+    out = np.zeros(n, dtype=np.uint64)
+    lib().orc_decode(_p(rec), rec.size, _p(w), n, dtype_bits, _p(out))
+    return out
+
+
+def lookup(records, words, n: int, idx, L: int = 0, dtype_bits: int = 64):
+    """Point lookups; L > 0 fixed partitions, L == 0 variable. Returns (values, n_out_of_range)."""
+    rec = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
+    w = _u64(words)
+    ix = _u64(idx)
+    out = np.zeros(ix.size, dtype=np.uint64)
+    bad = lib().orc_lookup(_p(rec), rec.size, _p(w), n, L, dtype_bits, _p(ix), ix.size, _p(out))
+    return out, int(bad)
+
+
+def filter_sum(records, words, n: int, lo: int, hi: int, dtype_bits: int = 64):
+    """(count, sum) over lo <= v <= hi (unsigned); sum is a Python int, exact mod 2^128."""
+    rec = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
+    w = _u64(words)
+    out = np.zeros(3, dtype=np.uint64)
+    lib().orc_filter_sum(_p(rec), rec.size, _p(w), n, dtype_bits, int(lo), int(hi), _p(out))
+    return int(out[0]), int(out[1]) | (int(out[2]) << 64)
+
+
+# ------------------------------------------------------------------ record fields (format R6)
+
+def rec_offset(word3) -> np.ndarray:
+    return np.asarray(word3, dtype=np.uint64) & np.uint64((1 << 48) - 1)
+
+
+def rec_width(word3) -> np.ndarray:
+    return (np.asarray(word3, dtype=np.uint64) >> np.uint64(48)) & np.uint64(0x7F)
+
+
+def rec_grid(word3) -> np.ndarray:
+    s = ((np.asarray(word3, dtype=np.uint64) >> np.uint64(55)) & np.uint64(0x7F)).astype(np.int64)
+    return np.where(s >= 64, s - 128, s)
+
+
+def rec_exact(word3) -> np.ndarray:
+    return (np.asarray(word3, dtype=np.uint64) >> np.uint64(62)) & np.uint64(1)
+
+
+def compressed_bytes(records, words) -> int:
+    return 32 * len(records) + 8 * len(words)
