@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""LeCo hot-path benchmark on GB300.
+
+Workload: three 200M-value uint64 columns, fixed partitions of 4096, linear model, seeded and
+synthetic (linear + bounded noise; sorted Normal(2^40, 2^36); sorted 1e9 * LogNormal(0, 2)).
+Each column is encoded once (encode throughput is reported separately); the timed step then runs,
+for every column, the three query paths of the library: full decode, the fused filter-sum at ~1%
+selectivity, and 10M uniform random lookups. All inputs are resident in HBM and larger than L2.
+
+value = algorithmic bytes of one step / step time (GB/s); per-op figures follow in "ops".
+Algorithmic bytes, C = compressed bytes (32 per record + 8 per residual word):
+  decode  C + 8 n          filter-sum  C + 24          lookups  k * (8 idx + 8 out + 32 sector)
+
+--impl reference times the CPU oracle (one thread) on a bounded sample of the same columns: every
+100th partition, so the sample's encoding is exactly those partitions of the full encoding.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DISTS = ("a", "b", "c")
+L = 4096
+METRIC = "LeCo decode GB/s & %HBM roofline; random-access Mlookups/s; serving p50/p99"
+WORKLOAD = "LeCo-fix L=4096 linear, 3 x 200M uint64 (linear+noise, sorted normal, sorted lognormal)"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["leco", "reference"], default="leco")
+    ap.add_argument("--n", type=int, default=200_000_000)
+    ap.add_argument("--lookups", type=int, default=10_000_000)
+    ap.add_argument("--sample-every", type=int, default=100, help="CPU sample: every k-th partition")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sample_partitions(v, every: int):
+    """Every `every`-th partition of L values (a bounded, representative CPU sample)."""
+    import numpy as np
+
+    m = (len(v) + L - 1) // L
+    parts = np.arange(0, m, every)
+    parts = parts[parts * L + L <= len(v)]
+    idx = (parts[:, None] * L + np.arange(L)[None, :]).ravel()
+    return v[idx]
+
+
+def step_bytes(comp_bytes, n, k):
+    dec = comp_bytes + 8 * n
+    filt = comp_bytes + 24
+    look = k * (8 + 8 + 32)
+    return dec, filt, look
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+
+def cpu_oracle_run(cols, lookups_frac, reps=1):
+    """Time the oracle (one thread) on prepared samples; returns (bytes, seconds)."""
+    import oracle
+
+    total_b, total_t = 0, 0.0
+    for s in cols:
+        v, rec, words, idx, lo, hi = s["v"], s["rec"], s["words"], s["idx"], s["lo"], s["hi"]
+        comp = oracle.compressed_bytes(rec, words)
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            d = oracle.decode(rec, words, len(v))
+            oracle.filter_sum(rec, words, len(v), lo, hi)
+            oracle.lookup(rec, words, len(v), idx, L=L)
+            total_t += time.perf_counter() - t0
+            dec, filt, look = step_bytes(comp, len(v), len(idx))
+            total_b += dec + filt + look
+            assert (d == v).all()
+    return total_b, total_t
+
+
+def prepare_cpu_samples(columns, every, lookups, n):
+    import oracle
+    import workloads as W
+
+    out = []
+    for d, v in columns.items():
+        s = sample_partitions(v, every)
+        rec, words = oracle.encode_fixed(s, L, oracle.MODEL_LINEAR)
+        k = max(1, int(lookups * len(s) / n))
+        lo, hi = W.filter_bounds(v)
+        out.append(dict(v=s, rec=rec, words=words, idx=W.uniform_indices(k, len(s), seed=7), lo=lo, hi=hi))
+    return out
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import oracle
+    import workloads as W
+
+    oracle.build()
+    columns = {d: W.cfg2(d, args.n) for d in DISTS}
+    samples = prepare_cpu_samples(columns, args.sample_every, args.lookups, args.n)
+    del columns
+    for _ in range(args.warmup):
+        cpu_oracle_run(samples, None)
+    b, t = cpu_oracle_run(samples, None, reps=args.steps)
+    value = b / t / 1e9
+    nsamp = sum(len(s["v"]) for s in samples)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"every {args.sample_every}th partition"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{nsamp} values: every {args.sample_every}th 4096-value partition of each column"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_leco(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    import paper_2306_15374_gb300 as pkg
+
+    if rank == 0:
+        pkg.build()
+    if world > 1:
+        dist.barrier()
+    pkg.build()
+    from paper_2306_15374_gb300 import leco
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    columns = {d: W.cfg2(d, args.n) for d in DISTS}
+    n = args.n
+    k = args.lookups
+    cols, comp, bounds, idxs = {}, {}, {}, {}
+    enc_ms = []
+    for d, v in columns.items():
+        dv = torch.from_numpy(v.view(np.int64)).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(2):  # second encode is the timed one (pools warm)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c = leco.leco_encode(dv, leco.fixed(L), leco.LECO_MODEL_LINEAR)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep == 0:
+                c.free()
+        enc_ms.append(e0.elapsed_time(e1))
+        cols[d] = c
+        st = c.stats()
+        comp[d] = st["record_bytes"] + st["residual_bytes"]
+        bounds[d] = W.filter_bounds(v)
+        idxs[d] = torch.from_numpy(W.uniform_indices(k, n, seed=ord(d)).view(np.int64)).to(dev)
+        del dv
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    outk = torch.empty(k, dtype=torch.int64, device=dev)
+    res = torch.zeros(3, dtype=torch.int64, device=dev)
+
+    ops = ("decode", "filter", "lookup")
+    ev = {(d, o): [] for d in DISTS for o in ops}
+
+    def step(record):
+        for d in DISTS:
+            c = cols[d]
+            marks = []
+            if record:
+                marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                marks[0].record(stream)
+            leco.leco_decode_all(c, out)
+            if record:
+                marks[1].record(stream)
+            leco.leco_filter_sum(c, bounds[d][0], bounds[d][1], res)
+            if record:
+                marks[2].record(stream)
+            leco.leco_random_access(c, idxs[d], outk)
+            if record:
+                marks[3].record(stream)
+                for j, o in enumerate(ops):
+                    ev[(d, o)].append((marks[j], marks[j + 1]))
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    per = {}
+    dec_b = filt_b = look_b = 0
+    for d in DISTS:
+        db, fb, lb = step_bytes(comp[d], n, k)
+        dec_b += db
+        filt_b += fb
+        look_b += lb
+    step_b = dec_b + filt_b + look_b
+    for o in ops:
+        tms = sum(a.elapsed_time(b) for d in DISTS for a, b in ev[(d, o)]) / args.steps
+        per[o] = tms
+    peak, peak_kind = measured_peaks()
+    dec_gbs = dec_b / (per["decode"] * 1e-3) / 1e9
+    ops_out = {
+        "decode": {"gbs": dec_gbs, "ms": per["decode"], "frac_hbm": dec_gbs / peak},
+        "filter_sum": {"gbs": filt_b / (per["filter"] * 1e-3) / 1e9, "ms": per["filter"],
+                       "frac_hbm": filt_b / (per["filter"] * 1e-3) / 1e9 / peak},
+        "random_access": {"mlookups_s": 3 * k / (per["lookup"] * 1e-3) / 1e6, "ms": per["lookup"],
+                          "gbs": look_b / (per["lookup"] * 1e-3) / 1e9},
+        "encode": {"gbs": sum(8 * n + comp[d] for d in DISTS) / (sum(enc_ms) * 1e-3) / 1e9,
+                   "ms": sum(enc_ms)},
+        "compressed_bytes": {d: comp[d] for d in DISTS},
+        "ratio": {d: comp[d] / (8 * n) for d in DISTS},
+    }
+    roofline = {"bound": "hbm", "kernel": "k_decode<uint64_t>", "achieved": dec_gbs, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": dec_gbs / peak, "traffic": None,
+                "bytes_per_launch": dec_b / 3}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        samples = prepare_cpu_samples(columns, args.sample_every, args.lookups, n)
+        b, t = cpu_oracle_run(samples, None)
+        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sum(len(s['v']) for s in samples)} values: every {args.sample_every}th "
+                         f"4096-value partition of each column; decode + filter-sum + proportional lookups"}
+
+    value = world * step_b / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_per_column": n, "partition_size": L, "lookups_per_column": k,
+                   "l2": "inputs larger than L2 (compressed columns 0.3-0.7 GB, decoded 1.6 GB)",
+                   "parallelism": f"replicas x{world}"},
+        "ops": ops_out, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": 9 * args.steps, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in cols.values():
+        c.free()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
+    """Same step through the public API with host buffers: lookup indices copied in from pinned
+    memory, decoded columns, lookup results and sums copied back to pinned memory."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+
+    h_idx = {d: torch.from_numpy(W.uniform_indices(k, n, seed=ord(d)).view(np.int64)).pin_memory() for d in DISTS}
+    h_out = torch.empty(n, dtype=torch.int64).pin_memory()
+    h_outk = torch.empty(k, dtype=torch.int64).pin_memory()
+    h_res = torch.empty(3, dtype=torch.int64).pin_memory()
+    d_idx = torch.empty(k, dtype=torch.int64, device=dev)
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    outk = torch.empty(k, dtype=torch.int64, device=dev)
+    res = torch.zeros(3, dtype=torch.int64, device=dev)
+
+    def step():
+        for d in DISTS:
+            d_idx.copy_(h_idx[d], non_blocking=True)
+            leco.leco_decode_all(cols[d], out)
+            leco.leco_filter_sum(cols[d], bounds[d][0], bounds[d][1], res)
+            leco.leco_random_access(cols[d], d_idx, outk)
+            h_out.copy_(out, non_blocking=True)
+            h_outk.copy_(outk, non_blocking=True)
+            h_res.copy_(res, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    steps = max(1, min(args.steps, 5))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    return {"value": step_b / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": 3 * 8 * k, "d2h_bytes_per_step": 3 * (8 * n + 8 * k + 24)}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_leco(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * leco.h — C ABI of the GB300 LeCo library (libleco.so).
+ *
+ * LeCo (Liu, Zeng & Zhang, "LeCo: Lightweight Compression via Learning Serial Correlations")
+ * compresses an integer column by splitting it into partitions (§3.2), fitting one regression
+ * model per partition (§3.1: constant = FOR, or linear) and bit-packing the residuals ("deltas")
+ * at a fixed width per partition (§3.3). This library runs encode, full decode, range decode,
+ * batched point lookups and a fused filter + sum scan on one CUDA GPU (sm_103a).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; host_* are host pointers.
+ *    The caller owns every buffer it passes in or out. The library owns the column (records,
+ *    residual words, partition starts, decode table and status word), allocated on the device
+ *    that is current when the column is created.
+ *  - Calls are stream-ordered on `stream` (a cudaStream_t; NULL = the legacy default stream) and
+ *    return before the GPU work completes, unless documented otherwise. Argument errors that the
+ *    host can see are returned synchronously and then nothing is enqueued.
+ *  - Device-side errors (an index >= n in a lookup) do not fail the call: the affected output
+ *    slot gets 0 and the column's status word records the error; leco_sync() reports it.
+ *  - A column is immutable after creation, so concurrent reads on different streams are safe.
+ *  - n = 0 is valid: an empty column; decodes write nothing and sums are zero.
+ *  - Values are unsigned 32- or 64-bit integers. Filter bounds compare as unsigned.
+ *
+ * Stored format (§3.3 storage format, with this library's readings):
+ *  - One 32-byte record per partition: {double theta0, double theta1, uint64 start, uint64 word3}
+ *    with word3 = bit offset (bits 0..47) | width b (48..54) | grid exponent s (55..61, two's
+ *    complement) | exact flag (62) | 0 (63).
+ *  - Residuals: zigzag-coded, b bits each, packed LSB-first into one stream of little-endian
+ *    64-bit words shared by all partitions; partition p starts at its bit offset, offsets dense.
+ *    The stream carries at least two zero padding words and is a multiple of 16 bytes.
+ *  - Value at local index i' of a partition: pred(i') + unzigzag(field) mod 2^64 (truncated to
+ *    32 bits for 32-bit columns), with pred(i') = floor(fl(fl(theta1 * i') + theta0)) in IEEE
+ *    binary64, one rounding per operation (no FMA), NaN -> 0 and saturation to int64 (§3.3
+ *    decoder). When the exact flag is set the encoder guarantees that this equals
+ *    (A + B i') >> s with the integers A = theta0 * 2^s, B = theta1 * 2^s (s < 0: no shift), which
+ *    is what the device evaluates.
+ */
+#ifndef LECO_H
+#define LECO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* leco_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  LECO_OK = 0,
+  LECO_ERR_INVALID_ARG = 1, /* a NULL, size or enum argument the call cannot accept */
+  LECO_ERR_OOM = 2,         /* device or host allocation failed */
+  LECO_ERR_INDEX_RANGE = 3, /* a lookup index was >= n (reported by leco_sync) */
+  LECO_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  LECO_ERR_CORRUPT = 5,     /* a serialized blob failed validation */
+  LECO_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  LECO_ERR_BUDGET = 7       /* a server admission would exceed its memory budget */
+} leco_status;
+
+typedef enum { LECO_U32 = 0, LECO_U64 = 1 } leco_dtype;
+
+/* §3.1 model family members built here: constant (FOR, §2) and linear. */
+typedef enum { LECO_MODEL_CONSTANT = 0, LECO_MODEL_LINEAR = 1 } leco_model;
+
+typedef enum { LECO_PART_FIXED = 0, LECO_PART_VAR = 1 } leco_part_kind;
+
+/* Partition policy (§3.2). Fixed: partition j = positions [j L, (j+1) L) (§3.2.1), part_size = L
+ * (1 .. 2^24). Variable: split + merge (§3.2.2); part_size caps a partition's length (1 .. 2^24,
+ * 0 = 2^24); tau in [0, 1] is the split threshold coefficient (C <= tau * S_M with S_M = 256 bits,
+ * one record). */
+typedef struct {
+  int32_t kind;       /* leco_part_kind */
+  uint32_t part_size; /* fixed: L; variable: length cap */
+  double tau;         /* variable only */
+} leco_partition_policy;
+
+typedef struct leco_column leco_column; /* opaque, device resident, immutable */
+
+/* count and sum of the selected values; the sum is exact modulo 2^128 */
+typedef struct {
+  uint64_t count;
+  uint64_t sum_lo;
+  uint64_t sum_hi;
+} leco_sum_result;
+
+typedef struct {
+  uint64_t n;              /* values */
+  uint64_t partitions;     /* m */
+  uint64_t record_bytes;   /* 32 m */
+  uint64_t residual_bytes; /* 8 * padded word count */
+  uint64_t total_bytes;    /* record_bytes + residual_bytes (+ 8 (m+1) start index for var) */
+  double ratio;            /* total_bytes / (n * value bytes); 0 for n = 0 */
+  int32_t dtype;           /* leco_dtype */
+  int32_t kind;            /* leco_part_kind */
+  int32_t model;           /* leco_model */
+  uint32_t part_size;      /* fixed L (0 for variable) */
+  uint64_t residual_bits;  /* sum over partitions of len * b */
+  uint64_t device_bytes;   /* bytes the column holds on the device */
+} leco_stats;
+
+/* Filter flags. LECO_FILTER_PRUNE skips partitions whose value bounds (from the model and the
+ * residual width, §5.1 pruning) lie outside [lo, hi]; the result is identical. */
+#define LECO_FILTER_PRUNE 1u
+
+/* ------------------------------------------------------------------------------------------ */
+/* Library */
+
+/* Human-readable name of a status code; never NULL. */
+const char* leco_status_string(leco_status s);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+uint32_t leco_version(void);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Encode (§3: Partitioner -> Regressor -> Encoder)
+ *
+ * d_values: n values of `dtype` (4 or 8 bytes each, contiguous) on the device, caller-owned, read
+ * only. policy: fixed or variable partitions. model: constant or linear. On success *out receives
+ * a new column (free with leco_column_free). The call synchronizes `stream` once (to size the
+ * residual stream) and returns with the column's encode enqueued on `stream`.
+ * Errors: INVALID_ARG (NULL out, NULL d_values with n > 0, part_size out of range, tau outside
+ * [0,1], bad enum), OOM, CUDA. */
+leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
+                        leco_partition_policy policy, leco_model model, leco_stream_t stream,
+                        leco_column** out);
+
+/* Variable-length partitioning only (§3.2.2): split + merge on the device. d_starts_out receives
+ * m+1 uint64 partition starts (the last is n) and must hold n+1 entries; *m_out = m. Synchronizes
+ * `stream` once per merge round. Errors as leco_encode. */
+leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtype,
+                               leco_partition_policy policy, leco_model model,
+                               uint64_t* d_starts_out, uint64_t* m_out, leco_stream_t stream);
+
+/* Encode with caller-chosen partition starts (d_starts: m+1 uint64 on the device, starts[0] = 0,
+ * starts[m] = n, strictly increasing, each partition at most 2^24 long). The column is a variable
+ * partition column. Errors as leco_encode. */
+leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype dtype,
+                                    const uint64_t* d_starts, uint64_t m, leco_model model,
+                                    leco_stream_t stream, leco_column** out);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Decode (§3.3 Decoder)
+ *
+ * Full decompression: d_out receives all n values (n * value bytes, caller-owned, device). */
+leco_status leco_decode_all(const leco_column* col, void* d_out, leco_stream_t stream);
+
+/* Range decompression of positions [begin, begin + count): d_out receives count values.
+ * Errors: INVALID_ARG if begin + count > n. */
+leco_status leco_decode_range(const leco_column* col, uint64_t begin, uint64_t count, void* d_out,
+                              leco_stream_t stream);
+
+/* Batched point lookups: d_out[q] = value at position d_idx[q] for q < k (input order, duplicates
+ * allowed). Fixed partitions use j = i / L; variable partitions a search over the starts. An
+ * index >= n writes 0 and sets LECO_ERR_INDEX_RANGE in the column status (see leco_sync). */
+leco_status leco_random_access(const leco_column* col, const uint64_t* d_idx, uint64_t k,
+                               void* d_out, leco_stream_t stream);
+
+/* Fused filter + aggregate: count and sum of the values v with lo <= v <= hi (unsigned,
+ * inclusive), never materialising the decoded column. d_out: one leco_sum_result on the device,
+ * overwritten. lo > hi gives {0, 0, 0}. flags: 0 or LECO_FILTER_PRUNE. */
+leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, uint32_t flags,
+                            leco_sum_result* d_out, leco_stream_t stream);
+
+/* Synchronize `stream`, then return the first device-side error recorded on the column since the
+ * last leco_sync (and clear it), else LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
+leco_status leco_sync(const leco_column* col, leco_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Column metadata and lifetime */
+
+leco_status leco_stats_get(const leco_column* col, leco_stats* out);
+
+/* Copy the column's m records (32 bytes each) and padded residual words to host buffers of at
+ * least 32 m and 8 * (padded words) bytes (either may be NULL to skip); synchronous. */
+leco_status leco_column_export(const leco_column* col, void* host_records, void* host_words,
+                               void* host_starts);
+
+/* Serialize to a self-describing host blob (header + records + starts (variable only) + words +
+ * CRC-32). host_buf == NULL: *bytes = the size needed. cap too small: INVALID_ARG with *bytes
+ * set. Synchronous (waits for the column's encode). */
+leco_status leco_serialize(const leco_column* col, void* host_buf, uint64_t cap, uint64_t* bytes);
+
+/* Rebuild a column from a blob (validated: magic, version, sizes, CRC, record consistency).
+ * Errors: CORRUPT, INVALID_ARG, OOM, CUDA. */
+leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t stream,
+                             leco_column** out);
+
+/* Release a column: waits for the device to finish, then frees. NULL is ignored. */
+void leco_column_free(leco_column* col);
+
+/* Release a column in stream order: the memory is returned after the work already enqueued on
+ * `stream` completes; the caller guarantees that no other stream still uses the column. */
+void leco_column_free_async(leco_column* col, leco_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LECO_H */

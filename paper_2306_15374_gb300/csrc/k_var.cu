@@ -1,0 +1,361 @@
+// Variable-length partitioning on the GPU (§3.2.2): split, then merge.
+//
+// Split: the sequence is cut into chunks of kChunk values (chunk edges always start a partition);
+// inside a chunk one thread grows partitions left to right: v_j joins the open partition [i, j)
+// iff C = (j+1-i) D(v[i,j+1)) - (j-i) D(v[i,j)) <= tau * S_M and j - i < cap, where D is the
+// linear regressor's fast metric bitlen(max d - min d) over the inner differences d_k = w_k -
+// w_{k-1}. Starts go to a bitmap (the thread owns its chunk's words), then a popcount scan
+// compacts them.
+//
+// Merge, round-synchronous: each round computes for every adjacent pair the size of the merged
+// partition with the full regressor (S_M + len * b) and its gain over the two apart; every pair
+// with a positive gain whose priority (gain, SplitMix64 of its start) beats both neighbouring
+// pairs merges, all at once. Pair sizes are cached: only pairs touching a partition merged in the
+// previous round are refitted. Rounds repeat until none merges.
+#include "fit.cuh"
+#include "leco_internal.cuh"
+
+namespace leco {
+
+cudaError_t scan_u64(const uint64_t* in, uint64_t count, uint64_t* out, uint64_t* scratch,
+                     uint64_t* total, cudaStream_t st);
+
+namespace {
+
+constexpr uint64_t kChunk = 1ull << 16;
+constexpr uint64_t kNone = ~0ull;        // no merged size (pair longer than the cap)
+constexpr uint32_t kLongPair = 1u << 14; // pairs longer than this are fitted by a whole CTA
+
+__global__ void k_split(const void* __restrict__ values, int dtype, uint64_t n, uint32_t cap,
+                        double thresh, uint64_t* __restrict__ bitmap) {
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = c * kChunk;
+    const uint64_t e = min(a + kChunk, n);
+    uint64_t i = a;
+    uint64_t word = 1ull;  // position a opens a partition (a % 64 == 0)
+    uint64_t wi = a >> 6;
+    int64_t prev = (int64_t)load_value(values, dtype, a);
+    i128 dmax = 0, dmin = 0;
+    int cur = 0;
+    for (uint64_t j = a + 1; j < e; j++) {
+      if ((j & 63) == 0) {
+        bitmap[wi++] = word;
+        word = 0;
+      }
+      const int64_t w = (int64_t)load_value(values, dtype, j);
+      bool take = (j - i) < cap;
+      i128 nmax = dmax, nmin = dmin;
+      int next = 0;
+      if (take) {
+        const i128 d = (i128)w - (i128)prev;
+        if (j == i + 1) {
+          nmax = d;
+          nmin = d;
+        } else {
+          if (d > nmax) nmax = d;
+          if (d < nmin) nmin = d;
+        }
+        next = bitlen_u128((u128)(nmax - nmin));
+        const int64_t C = (int64_t)(j + 1 - i) * next - (int64_t)(j - i) * cur;
+        take = (double)C <= thresh;
+      }
+      if (take) {
+        cur = next;
+        dmax = nmax;
+        dmin = nmin;
+      } else {
+        word |= 1ull << (j & 63);
+        i = j;
+        cur = 0;
+        dmax = 0;
+        dmin = 0;
+      }
+      prev = w;
+    }
+    bitmap[wi] = word;
+  }
+}
+
+__global__ void k_popc(const uint64_t* __restrict__ bitmap, uint64_t nw, uint64_t* __restrict__ cnt) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nw;
+       w += (uint64_t)gridDim.x * blockDim.x)
+    cnt[w] = (uint64_t)__popcll(bitmap[w]);
+}
+
+__global__ void k_scatter_starts(const uint64_t* __restrict__ bitmap, uint64_t nw,
+                                 const uint64_t* __restrict__ pos, uint64_t n, uint64_t m,
+                                 uint64_t* __restrict__ starts) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nw;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t bits = bitmap[w];
+    uint64_t k = pos[w];
+    while (bits) {
+      const int t = __ffsll((long long)bits) - 1;
+      starts[k++] = w * 64 + (uint64_t)t;
+      bits &= bits - 1;
+    }
+    if (w == 0) starts[m] = n;
+  }
+}
+
+// sizes of single partitions (initial round): warp per partition
+__global__ void k_part_size(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
+                            uint64_t m, int model, uint64_t* __restrict__ sz) {
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t p = warp; p < m; p += nw) {
+    const uint64_t a = st[p], e = st[p + 1];
+    const FitResult R = fit_range<32>(values, dtype, a, (uint32_t)(e - a), model, threadIdx.x & 31u, nullptr);
+    if ((threadIdx.x & 31u) == 0) sz[p] = kSmBits + (e - a) * (uint64_t)R.b;
+  }
+}
+
+// merged sizes of dirty pairs up to kLongPair values: warp per pair
+__global__ void k_pair_size_warp(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
+                                 uint64_t m, int model, uint32_t cap, const uint8_t* __restrict__ dirty,
+                                 uint64_t* __restrict__ msz) {
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = warp; j + 1 < m; j += nw) {
+    if (!dirty[j]) continue;
+    const uint64_t a = st[j], e = st[j + 2];
+    const uint64_t len = e - a;
+    if (len > cap) {
+      if ((threadIdx.x & 31u) == 0) msz[j] = kNone;
+      continue;
+    }
+    if (len > kLongPair) continue;
+    const FitResult R = fit_range<32>(values, dtype, a, (uint32_t)len, model, threadIdx.x & 31u, nullptr);
+    if ((threadIdx.x & 31u) == 0) msz[j] = kSmBits + len * (uint64_t)R.b;
+  }
+}
+
+// merged sizes of dirty pairs longer than kLongPair: CTA per pair
+__global__ void __launch_bounds__(256)
+    k_pair_size_block(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
+                      uint64_t m, int model, uint32_t cap, const uint8_t* __restrict__ dirty,
+                      uint64_t* __restrict__ msz) {
+  __shared__ FitShared sm;
+  for (uint64_t j = blockIdx.x; j + 1 < m; j += gridDim.x) {
+    if (!dirty[j]) continue;
+    const uint64_t a = st[j], e = st[j + 2];
+    const uint64_t len = e - a;
+    if (len > cap || len <= kLongPair) continue;
+    const FitResult R = fit_range<256>(values, dtype, a, (uint32_t)len, model, threadIdx.x, &sm);
+    if (threadIdx.x == 0) msz[j] = kSmBits + len * (uint64_t)R.b;
+  }
+}
+
+__device__ __forceinline__ bool pair_gain(const uint64_t* sz, const uint64_t* msz, uint64_t j, int64_t* g) {
+  if (msz[j] == kNone) return false;
+  *g = (int64_t)(sz[j] + sz[j + 1]) - (int64_t)msz[j];
+  return true;
+}
+
+// priority order of two pairs: gain, then the hash of the start, then the smaller start
+__device__ __forceinline__ bool beats(int64_t g1, uint64_t s1, int64_t g2, uint64_t s2) {
+  if (g1 != g2) return g1 > g2;
+  const uint64_t h1 = splitmix64(s1), h2 = splitmix64(s2);
+  if (h1 != h2) return h1 > h2;
+  return s1 < s2;
+}
+
+__global__ void k_select(const uint64_t* __restrict__ st, const uint64_t* __restrict__ sz,
+                         const uint64_t* __restrict__ msz, uint64_t m, uint8_t* __restrict__ sel,
+                         unsigned long long* __restrict__ nsel) {
+  uint32_t local = 0;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j + 1 < m;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    int64_t g;
+    bool ok = pair_gain(sz, msz, j, &g) && g > 0;
+    if (ok && j > 0) {
+      int64_t gl;
+      if (pair_gain(sz, msz, j - 1, &gl) && !beats(g, st[j], gl, st[j - 1])) ok = false;
+    }
+    if (ok && j + 2 < m) {
+      int64_t gr;
+      if (pair_gain(sz, msz, j + 1, &gr) && !beats(g, st[j], gr, st[j + 1])) ok = false;
+    }
+    sel[j] = ok ? 1 : 0;
+    local += ok ? 1u : 0u;
+  }
+  local = (uint32_t)warp_sum_u64(local);
+  if ((threadIdx.x & 31u) == 0 && local) atomicAdd(nsel, (unsigned long long)local);
+}
+
+// partition p survives unless it was merged into its left neighbour
+__global__ void k_keep(const uint8_t* __restrict__ sel, uint64_t m, uint64_t* __restrict__ keep) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
+       p += (uint64_t)gridDim.x * blockDim.x)
+    keep[p] = (p == 0 || !sel[p - 1]) ? 1ull : 0ull;
+}
+
+__global__ void k_compact(const uint64_t* __restrict__ st, const uint64_t* __restrict__ sz,
+                          const uint64_t* __restrict__ msz, const uint8_t* __restrict__ sel,
+                          const uint64_t* __restrict__ newidx, uint64_t m, uint64_t n, uint64_t new_m,
+                          uint64_t* __restrict__ nst, uint64_t* __restrict__ nsz,
+                          uint64_t* __restrict__ nmsz, uint8_t* __restrict__ ndirty) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    if (p > 0 && sel[p - 1]) continue;  // absorbed by p-1
+    const uint64_t k = newidx[p];
+    const bool mp = p + 1 < m && sel[p];
+    nst[k] = st[p];
+    nsz[k] = mp ? msz[p] : sz[p];
+    const uint64_t q = mp ? p + 2 : p + 1;  // next surviving partition
+    if (q < m) {
+      const bool mq = q + 1 < m && sel[q];
+      const bool d = mp || mq;
+      ndirty[k] = d ? 1 : 0;
+      if (!d) nmsz[k] = msz[p];
+    }
+    if (k == 0) nst[new_m] = n;
+  }
+}
+
+__global__ void k_fill_u8(uint8_t* p, uint64_t count, uint8_t v) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
+  const uint64_t need = (items + per_block - 1) / per_block;
+  const uint64_t cap = (uint64_t)sm_count() * max_blocks_per_sm;
+  return (int)(need < cap ? (need ? need : 1) : cap);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, uint64_t elems, cudaStream_t st) {
+  return cudaMallocAsync((void**)p, (elems ? elems : 1) * sizeof(T), st);
+}
+
+}  // namespace
+
+// Runs split + merge; writes m+1 starts to starts_out (capacity n+1) and m to *m_out.
+cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
+                          int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
+  *m_out = 0;
+  if (n == 0) {
+    const uint64_t zero = 0;
+    cudaError_t e = cudaMemcpyAsync(starts_out, &zero, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  }
+  const double thresh = tau * (double)kSmBits;
+  const uint64_t nw = (n + 63) / 64;
+  uint64_t *bitmap = nullptr, *cnt = nullptr, *pos = nullptr, *scan_scratch = nullptr, *d_total = nullptr;
+  cudaError_t e = cudaSuccess;
+  const uint64_t scan_elems = nw / 2048 + 2;
+#define LECO_TRY(x)          \
+  do {                       \
+    e = (x);                 \
+    if (e != cudaSuccess) goto done; \
+  } while (0)
+  {
+    LECO_TRY(dalloc(&bitmap, nw, st));
+    LECO_TRY(dalloc(&cnt, nw, st));
+    LECO_TRY(dalloc(&pos, nw, st));
+    LECO_TRY(dalloc(&scan_scratch, scan_elems + 1, st));
+    LECO_TRY(dalloc(&d_total, 1, st));
+    const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+    k_split<<<grid_for(nchunks, 64, 32), 64, 0, st>>>(values, dtype, n, cap, thresh, bitmap);
+    LECO_TRY(cudaGetLastError());
+    k_popc<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, cnt);
+    LECO_TRY(cudaGetLastError());
+    LECO_TRY(scan_u64(cnt, nw, pos, scan_scratch, d_total, st));
+    uint64_t m = 0;
+    LECO_TRY(cudaMemcpyAsync(&m, d_total, 8, cudaMemcpyDeviceToHost, st));
+    LECO_TRY(cudaStreamSynchronize(st));
+    k_scatter_starts<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, pos, n, m, starts_out);
+    LECO_TRY(cudaGetLastError());
+    cudaFreeAsync(cnt, st);
+    cnt = nullptr;
+    cudaFreeAsync(pos, st);
+    pos = nullptr;
+    cudaFreeAsync(bitmap, st);
+    bitmap = nullptr;
+    cudaFreeAsync(scan_scratch, st);
+    scan_scratch = nullptr;
+
+    // merge state (ping-pong)
+    uint64_t *st_b = nullptr, *sz_a = nullptr, *sz_b = nullptr, *msz_a = nullptr, *msz_b = nullptr;
+    uint64_t *keep = nullptr, *newidx = nullptr, *scr = nullptr;
+    uint8_t *dirty_a = nullptr, *dirty_b = nullptr, *sel = nullptr;
+    unsigned long long* d_nsel = nullptr;
+    const uint64_t m0 = m;
+    const uint64_t scr_elems = m0 / 2048 + 2;
+    bool ok = true;
+    ok = ok && dalloc(&st_b, m0 + 1, st) == cudaSuccess;
+    ok = ok && dalloc(&sz_a, m0, st) == cudaSuccess && dalloc(&sz_b, m0, st) == cudaSuccess;
+    ok = ok && dalloc(&msz_a, m0, st) == cudaSuccess && dalloc(&msz_b, m0, st) == cudaSuccess;
+    ok = ok && dalloc(&keep, m0, st) == cudaSuccess && dalloc(&newidx, m0, st) == cudaSuccess;
+    ok = ok && dalloc(&scr, scr_elems + 1, st) == cudaSuccess;
+    ok = ok && dalloc(&dirty_a, m0, st) == cudaSuccess && dalloc(&dirty_b, m0, st) == cudaSuccess;
+    ok = ok && dalloc(&sel, m0, st) == cudaSuccess && dalloc(&d_nsel, 1, st) == cudaSuccess;
+    uint64_t* cur_st = starts_out;
+    uint64_t* nxt_st = st_b;
+    if (ok && m > 1) {
+      k_part_size<<<grid_for(m * 32, 256, 8), 256, 0, st>>>(values, dtype, cur_st, m, model, sz_a);
+      k_fill_u8<<<grid_for(m, 256, 8), 256, 0, st>>>(dirty_a, m, 1);
+      e = cudaGetLastError();
+      while (e == cudaSuccess && m > 1) {
+        k_pair_size_warp<<<grid_for(m * 32, 256, 8), 256, 0, st>>>(values, dtype, cur_st, m, model, cap,
+                                                                     dirty_a, msz_a);
+        k_pair_size_block<<<grid_for(m, 1, 4), 256, 0, st>>>(values, dtype, cur_st, m, model, cap,
+                                                             dirty_a, msz_a);
+        cudaMemsetAsync(d_nsel, 0, 8, st);
+        k_select<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, m, sel, d_nsel);
+        unsigned long long nsel = 0;
+        e = cudaMemcpyAsync(&nsel, d_nsel, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || nsel == 0) break;
+        k_keep<<<grid_for(m, 256, 8), 256, 0, st>>>(sel, m, keep);
+        e = scan_u64(keep, m, newidx, scr, d_total, st);
+        if (e != cudaSuccess) break;
+        const uint64_t new_m = m - nsel;
+        k_compact<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, sel, newidx, m, n, new_m,
+                                                       nxt_st, sz_b, msz_b, dirty_b);
+        e = cudaGetLastError();
+        uint64_t* t64;
+        uint8_t* t8;
+        t64 = cur_st; cur_st = nxt_st; nxt_st = t64;
+        t64 = sz_a; sz_a = sz_b; sz_b = t64;
+        t64 = msz_a; msz_a = msz_b; msz_b = t64;
+        t8 = dirty_a; dirty_a = dirty_b; dirty_b = t8;
+        m = new_m;
+      }
+      if (e == cudaSuccess && cur_st != starts_out)
+        e = cudaMemcpyAsync(starts_out, cur_st, (m + 1) * 8, cudaMemcpyDeviceToDevice, st);
+    } else if (!ok) {
+      e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // st_b may be cur_st's partner; both are scratch except starts_out
+    cudaFreeAsync(cur_st == starts_out ? nxt_st : cur_st, st);
+    cudaFreeAsync(sz_a, st);
+    cudaFreeAsync(sz_b, st);
+    cudaFreeAsync(msz_a, st);
+    cudaFreeAsync(msz_b, st);
+    cudaFreeAsync(keep, st);
+    cudaFreeAsync(newidx, st);
+    cudaFreeAsync(scr, st);
+    cudaFreeAsync(dirty_a, st);
+    cudaFreeAsync(dirty_b, st);
+    cudaFreeAsync(sel, st);
+    cudaFreeAsync(d_nsel, st);
+    if (e == cudaSuccess) *m_out = m;
+  }
+done:
+  if (bitmap) cudaFreeAsync(bitmap, st);
+  if (cnt) cudaFreeAsync(cnt, st);
+  if (pos) cudaFreeAsync(pos, st);
+  if (scan_scratch) cudaFreeAsync(scan_scratch, st);
+  if (d_total) cudaFreeAsync(d_total, st);
+#undef LECO_TRY
+  return e;
+}
+
+}  // namespace leco

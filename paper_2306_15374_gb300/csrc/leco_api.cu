@@ -1,0 +1,519 @@
+// C ABI of the GB300 LeCo library (declared in include/leco.h): argument checking, column
+// lifetime, the encode pipeline (partition -> fit -> offsets -> pack), the decode entry points
+// and the self-describing blob (header + records + starts + words, CRC-32).
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "leco_internal.cuh"
+
+using namespace leco;
+
+struct leco_column {
+  uint64_t n = 0;
+  uint64_t m = 0;
+  uint64_t nwords = 0;
+  uint64_t total_bits = 0;
+  int32_t dtype = LECO_U64;
+  int32_t kind = LECO_PART_FIXED;
+  int32_t model = LECO_MODEL_LINEAR;
+  uint32_t L = 0;
+  double tau = 0.0;
+  int device = 0;
+  Record* rec = nullptr;
+  Aux* aux = nullptr;
+  uint64_t* starts = nullptr;  // variable only
+  uint32_t* status = nullptr;
+  uint64_t* words = nullptr;
+  void* meta_block = nullptr;
+  uint64_t meta_bytes = 0;
+  uint64_t words_bytes = 0;
+  cudaStream_t home = nullptr;  // stream the column was created on
+};
+
+namespace {
+
+constexpr uint32_t kMagic = 0x4F43454Cu;  // "LECO"
+constexpr uint32_t kVersion = 1;
+constexpr uint64_t kHeaderBytes = 64;
+
+inline leco_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LECO_OK;
+  if (e == cudaErrorMemoryAllocation) return LECO_ERR_OOM;
+  return LECO_ERR_CUDA;
+}
+
+inline uint64_t value_bytes(int dtype) { return dtype == LECO_U32 ? 4 : 8; }
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+ColumnView view_of(const leco_column* c) {
+  ColumnView v;
+  v.n = c->n;
+  v.m = c->m;
+  v.dtype = c->dtype;
+  v.L = c->kind == LECO_PART_FIXED ? c->L : 0;
+  v.rec = c->rec;
+  v.aux = c->aux;
+  v.words = c->words;
+  v.starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
+  v.status = c->status;
+  return v;
+}
+
+// Allocate the metadata block (records, decode table, starts for variable columns, status).
+leco_status alloc_meta(leco_column* c, cudaStream_t st) {
+  const uint64_t rec_b = align256(32 * (c->m ? c->m : 1));
+  const uint64_t starts_b = c->kind == LECO_PART_VAR ? align256(8 * (c->m + 1)) : 0;
+  c->meta_bytes = 2 * rec_b + starts_b + 256;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, c->meta_bytes, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  char* b = (char*)p;
+  c->meta_block = p;
+  c->rec = (Record*)b;
+  c->aux = (Aux*)(b + rec_b);
+  c->starts = starts_b ? (uint64_t*)(b + 2 * rec_b) : nullptr;
+  c->status = (uint32_t*)(b + 2 * rec_b + starts_b);
+  return from_cuda(cudaMemsetAsync(c->status, 0, 256, st));
+}
+
+void release(leco_column* c, cudaStream_t st) {
+  if (!c) return;
+  if (c->words) cudaFreeAsync(c->words, st);
+  if (c->meta_block) cudaFreeAsync(c->meta_block, st);
+  delete c;
+}
+
+// fit + offsets + pack of an already partitioned column (c->m, c->starts or c->L set)
+leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t st) {
+  const uint64_t m = c->m;
+  const uint64_t scr_elems = m + offsets_scratch_elems(m) + 1;
+  uint64_t* scr = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&scr, scr_elems * 8, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  uint64_t* lenbits = scr;
+  uint64_t* off_scr = scr + m;
+  uint64_t* d_total = scr + scr_elems - 1;
+  const uint64_t* starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
+  uint64_t total = 0;
+  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, st);
+  if (e == cudaSuccess)
+    e = launch_offsets(c->rec, lenbits, m, off_scr, offsets_scratch_elems(m), d_total, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && total >= (1ull << 48)) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) {
+    c->total_bits = total;
+    c->nwords = stream_words(total);
+    c->words_bytes = c->nwords * 8;
+    e = cudaMallocAsync((void**)&c->words, c->words_bytes, st);
+  }
+  if (e == cudaSuccess) e = launch_build_aux(c->rec, m, c->n, c->aux, c->status, st);
+  if (e == cudaSuccess)
+    e = launch_pack(d_values, c->dtype, c->rec, c->aux, m, c->n, total, c->words, c->nwords, st);
+  cudaFreeAsync(scr, st);
+  if (e == cudaErrorInvalidValue) return LECO_ERR_INVALID_ARG;
+  return from_cuda(e);
+}
+
+bool valid_dtype(int d) { return d == LECO_U32 || d == LECO_U64; }
+bool valid_model(int m) { return m == LECO_MODEL_CONSTANT || m == LECO_MODEL_LINEAR; }
+
+// ---------------------------------------------------------------------------- CRC-32 (IEEE 802.3)
+
+uint32_t crc_table[256];
+std::once_flag crc_once;
+
+void crc_init() {
+  for (uint32_t i = 0; i < 256; i++) {
+    uint32_t c = i;
+    for (int k = 0; k < 8; k++) c = (c & 1) ? (0xEDB88320u ^ (c >> 1)) : (c >> 1);
+    crc_table[i] = c;
+  }
+}
+
+uint32_t crc32_update(uint32_t crc, const void* data, uint64_t len) {
+  std::call_once(crc_once, crc_init);
+  const uint8_t* p = (const uint8_t*)data;
+  uint32_t c = ~crc;
+  for (uint64_t i = 0; i < len; i++) c = crc_table[(c ^ p[i]) & 0xFF] ^ (c >> 8);
+  return ~c;
+}
+
+struct BlobHeader {
+  uint32_t magic;
+  uint32_t version;
+  uint64_t n;
+  uint64_t m;
+  uint64_t nwords;
+  uint8_t dtype, kind, model, reserved0;
+  uint32_t L;
+  double tau;
+  uint64_t total_bits;
+  uint32_t crc;
+  uint32_t reserved1;
+};
+static_assert(sizeof(BlobHeader) == kHeaderBytes, "blob header layout");
+
+uint64_t blob_bytes(const leco_column* c) {
+  return kHeaderBytes + 32 * c->m + (c->kind == LECO_PART_VAR ? 8 * (c->m + 1) : 0) + 8 * c->nwords;
+}
+
+// host-side consistency of records/starts/words (everything a kernel indexes with)
+bool validate_host(const BlobHeader& h, const Record* rec, const uint64_t* starts,
+                   const uint64_t* words) {
+  uint64_t off = 0;
+  for (uint64_t p = 0; p < h.m; p++) {
+    const Record& r = rec[p];
+    if (r.word3 >> 63) return false;
+    const uint32_t b = w3_b(r.word3);
+    if (b > 64) return false;
+    const uint64_t a = r.start;
+    uint64_t e;
+    if (h.kind == LECO_PART_FIXED) {
+      if (a != p * (uint64_t)h.L) return false;
+      e = a + h.L < h.n ? a + h.L : h.n;
+    } else {
+      if (starts[p] != a || starts[p + 1] <= a) return false;
+      e = starts[p + 1];
+    }
+    if (e <= a || e - a > kMaxPartLen) return false;
+    if (w3_off(r.word3) != off) return false;
+    off += (e - a) * b;
+    if (off >= (1ull << 48)) return false;
+  }
+  if (h.kind == LECO_PART_VAR && (starts[0] != 0 || starts[h.m] != h.n)) return false;
+  if (h.kind == LECO_PART_FIXED && h.m != (h.n + h.L - 1) / h.L) return false;
+  if (off != h.total_bits || h.nwords != stream_words(off)) return false;
+  for (uint64_t w = (off + 63) / 64; w < h.nwords; w++)
+    if (words[w]) return false;  // padding must be zero
+  if (off % 64 && (words[off / 64] >> (off % 64))) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* leco_status_string(leco_status s) {
+  switch (s) {
+    case LECO_OK: return "LECO_OK";
+    case LECO_ERR_INVALID_ARG: return "LECO_ERR_INVALID_ARG";
+    case LECO_ERR_OOM: return "LECO_ERR_OOM";
+    case LECO_ERR_INDEX_RANGE: return "LECO_ERR_INDEX_RANGE";
+    case LECO_ERR_CUDA: return "LECO_ERR_CUDA";
+    case LECO_ERR_CORRUPT: return "LECO_ERR_CORRUPT";
+    case LECO_ERR_TIMEOUT: return "LECO_ERR_TIMEOUT";
+    case LECO_ERR_BUDGET: return "LECO_ERR_BUDGET";
+  }
+  return "LECO_ERR_UNKNOWN";
+}
+
+uint32_t leco_version(void) { return 10000u; }
+
+leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtype,
+                               leco_partition_policy policy, leco_model model,
+                               uint64_t* d_starts_out, uint64_t* m_out, leco_stream_t stream) {
+  if (!d_starts_out || !m_out || (n && !d_values) || !valid_dtype(dtype) || !valid_model(model))
+    return LECO_ERR_INVALID_ARG;
+  if (policy.kind != LECO_PART_VAR || !(policy.tau >= 0.0 && policy.tau <= 1.0) ||
+      policy.part_size > kMaxPartLen)
+    return LECO_ERR_INVALID_ARG;
+  const uint32_t cap = policy.part_size ? policy.part_size : kMaxPartLen;
+  return from_cuda(var_partition(d_values, dtype, n, policy.tau, cap, model, d_starts_out, m_out,
+                                 (cudaStream_t)stream));
+}
+
+leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
+                        leco_partition_policy policy, leco_model model, leco_stream_t stream,
+                        leco_column** out) {
+  if (!out) return LECO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((n && !d_values) || !valid_dtype(dtype) || !valid_model(model)) return LECO_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  leco_column* c = new (std::nothrow) leco_column();
+  if (!c) return LECO_ERR_OOM;
+  c->n = n;
+  c->dtype = dtype;
+  c->model = model;
+  c->kind = policy.kind;
+  c->home = st;
+  cudaGetDevice(&c->device);
+  leco_status s = LECO_OK;
+  if (policy.kind == LECO_PART_FIXED) {
+    if (policy.part_size < 1 || policy.part_size > kMaxPartLen) {
+      delete c;
+      return LECO_ERR_INVALID_ARG;
+    }
+    c->L = policy.part_size;
+    c->m = (n + c->L - 1) / c->L;
+    s = alloc_meta(c, st);
+  } else if (policy.kind == LECO_PART_VAR) {
+    if (!(policy.tau >= 0.0 && policy.tau <= 1.0) || policy.part_size > kMaxPartLen) {
+      delete c;
+      return LECO_ERR_INVALID_ARG;
+    }
+    c->tau = policy.tau;
+    c->L = 0;
+    uint64_t* tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&tmp, 8 * (n + 1), st);
+    if (e != cudaSuccess) {
+      delete c;
+      return from_cuda(e);
+    }
+    uint64_t m = 0;
+    s = leco_var_partition(d_values, n, dtype, policy, model, tmp, &m, stream);
+    if (s == LECO_OK) {
+      c->m = m;
+      s = alloc_meta(c, st);
+    }
+    if (s == LECO_OK)
+      s = from_cuda(cudaMemcpyAsync(c->starts, tmp, 8 * (m + 1), cudaMemcpyDeviceToDevice, st));
+    cudaFreeAsync(tmp, st);
+  } else {
+    delete c;
+    return LECO_ERR_INVALID_ARG;
+  }
+  if (s == LECO_OK) s = encode_partitions(c, d_values, st);
+  if (s != LECO_OK) {
+    release(c, st);
+    return s;
+  }
+  *out = c;
+  return LECO_OK;
+}
+
+leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype dtype,
+                                    const uint64_t* d_starts, uint64_t m, leco_model model,
+                                    leco_stream_t stream, leco_column** out) {
+  if (!out) return LECO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((n && !d_values) || !d_starts || !valid_dtype(dtype) || !valid_model(model))
+    return LECO_ERR_INVALID_ARG;
+  if ((n == 0) != (m == 0) || m > n) return LECO_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint64_t> h(m + 1);
+  cudaError_t e = cudaMemcpyAsync(h.data(), d_starts, 8 * (m + 1), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (h[0] != 0 || h[m] != n) return LECO_ERR_INVALID_ARG;
+  for (uint64_t p = 0; p < m; p++)
+    if (h[p + 1] <= h[p] || h[p + 1] - h[p] > kMaxPartLen) return LECO_ERR_INVALID_ARG;
+  leco_column* c = new (std::nothrow) leco_column();
+  if (!c) return LECO_ERR_OOM;
+  c->n = n;
+  c->m = m;
+  c->dtype = dtype;
+  c->model = model;
+  c->kind = LECO_PART_VAR;
+  c->home = st;
+  cudaGetDevice(&c->device);
+  leco_status s = alloc_meta(c, st);
+  if (s == LECO_OK)
+    s = from_cuda(cudaMemcpyAsync(c->starts, d_starts, 8 * (m + 1), cudaMemcpyDeviceToDevice, st));
+  if (s == LECO_OK) s = encode_partitions(c, d_values, st);
+  if (s != LECO_OK) {
+    release(c, st);
+    return s;
+  }
+  *out = c;
+  return LECO_OK;
+}
+
+leco_status leco_decode_all(const leco_column* col, void* d_out, leco_stream_t stream) {
+  if (!col || (col->n && !d_out)) return LECO_ERR_INVALID_ARG;
+  return from_cuda(launch_decode(view_of(col), 0, col->n, d_out, (cudaStream_t)stream));
+}
+
+leco_status leco_decode_range(const leco_column* col, uint64_t begin, uint64_t count, void* d_out,
+                              leco_stream_t stream) {
+  if (!col || (count && !d_out) || begin > col->n || count > col->n - begin)
+    return LECO_ERR_INVALID_ARG;
+  return from_cuda(launch_decode(view_of(col), begin, count, d_out, (cudaStream_t)stream));
+}
+
+leco_status leco_random_access(const leco_column* col, const uint64_t* d_idx, uint64_t k,
+                               void* d_out, leco_stream_t stream) {
+  if (!col || (k && (!d_idx || !d_out))) return LECO_ERR_INVALID_ARG;
+  return from_cuda(launch_random_access(view_of(col), d_idx, k, d_out, (cudaStream_t)stream));
+}
+
+leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, uint32_t flags,
+                            leco_sum_result* d_out, leco_stream_t stream) {
+  if (!col || !d_out || (flags & ~LECO_FILTER_PRUNE)) return LECO_ERR_INVALID_ARG;
+  return from_cuda(launch_filter_sum(view_of(col), lo, hi, flags, d_out, (cudaStream_t)stream));
+}
+
+leco_status leco_sync(const leco_column* col, leco_stream_t stream) {
+  if (!col) return LECO_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return LECO_ERR_CUDA;
+  uint32_t flags = 0;
+  e = cudaMemcpy(&flags, col->status, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flags) e = cudaMemset(col->status, 0, 4);
+  if (e != cudaSuccess) return LECO_ERR_CUDA;
+  if (flags & kStatIndexRange) return LECO_ERR_INDEX_RANGE;
+  if (flags & kStatCorrupt) return LECO_ERR_CORRUPT;
+  if (flags & kStatTimeout) return LECO_ERR_TIMEOUT;
+  return LECO_OK;
+}
+
+leco_status leco_stats_get(const leco_column* col, leco_stats* out) {
+  if (!col || !out) return LECO_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->n = col->n;
+  out->partitions = col->m;
+  out->record_bytes = 32 * col->m;
+  out->residual_bytes = 8 * col->nwords;
+  out->total_bytes = out->record_bytes + out->residual_bytes +
+                     (col->kind == LECO_PART_VAR ? 8 * (col->m + 1) : 0);
+  out->ratio = col->n ? (double)out->total_bytes / (double)(col->n * value_bytes(col->dtype)) : 0.0;
+  out->dtype = col->dtype;
+  out->kind = col->kind;
+  out->model = col->model;
+  out->part_size = col->kind == LECO_PART_FIXED ? col->L : 0;
+  out->residual_bits = col->total_bits;
+  out->device_bytes = col->meta_bytes + col->words_bytes;
+  return LECO_OK;
+}
+
+leco_status leco_column_export(const leco_column* col, void* host_records, void* host_words,
+                               void* host_starts) {
+  if (!col) return LECO_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(col->home);
+  if (e == cudaSuccess && host_records && col->m)
+    e = cudaMemcpy(host_records, col->rec, 32 * col->m, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && host_words && col->nwords)
+    e = cudaMemcpy(host_words, col->words, 8 * col->nwords, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && host_starts && col->kind == LECO_PART_VAR)
+    e = cudaMemcpy(host_starts, col->starts, 8 * (col->m + 1), cudaMemcpyDeviceToHost);
+  return from_cuda(e);
+}
+
+leco_status leco_serialize(const leco_column* col, void* host_buf, uint64_t cap, uint64_t* bytes) {
+  if (!col || !bytes) return LECO_ERR_INVALID_ARG;
+  const uint64_t need = blob_bytes(col);
+  *bytes = need;
+  if (!host_buf) return LECO_OK;
+  if (cap < need) return LECO_ERR_INVALID_ARG;
+  char* b = (char*)host_buf;
+  char* body = b + kHeaderBytes;
+  char* p = body;
+  leco_status s = leco_column_export(col, p, nullptr, nullptr);
+  if (s != LECO_OK) return s;
+  p += 32 * col->m;
+  if (col->kind == LECO_PART_VAR) {
+    s = from_cuda(cudaMemcpy(p, col->starts, 8 * (col->m + 1), cudaMemcpyDeviceToHost));
+    if (s != LECO_OK) return s;
+    p += 8 * (col->m + 1);
+  }
+  s = leco_column_export(col, nullptr, p, nullptr);
+  if (s != LECO_OK) return s;
+  BlobHeader h;
+  memset(&h, 0, sizeof(h));
+  h.magic = kMagic;
+  h.version = kVersion;
+  h.n = col->n;
+  h.m = col->m;
+  h.nwords = col->nwords;
+  h.dtype = (uint8_t)col->dtype;
+  h.kind = (uint8_t)col->kind;
+  h.model = (uint8_t)col->model;
+  h.L = col->kind == LECO_PART_FIXED ? col->L : 0;
+  h.tau = col->tau;
+  h.total_bits = col->total_bits;
+  h.crc = crc32_update(0, body, need - kHeaderBytes);
+  memcpy(b, &h, sizeof(h));
+  return LECO_OK;
+}
+
+leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t stream,
+                             leco_column** out) {
+  if (!out || !host_buf) return LECO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (bytes < kHeaderBytes) return LECO_ERR_CORRUPT;
+  BlobHeader h;
+  memcpy(&h, host_buf, sizeof(h));
+  if (h.magic != kMagic || h.version != kVersion) return LECO_ERR_CORRUPT;
+  if (!valid_dtype(h.dtype) || !valid_model(h.model) ||
+      (h.kind != LECO_PART_FIXED && h.kind != LECO_PART_VAR))
+    return LECO_ERR_CORRUPT;
+  if (h.kind == LECO_PART_FIXED && (h.L < 1 || h.L > kMaxPartLen)) return LECO_ERR_CORRUPT;
+  if (h.m > h.n || (h.n > 0) != (h.m > 0) || h.nwords < 2 || h.nwords > (1ull << 42))
+    return LECO_ERR_CORRUPT;
+  const uint64_t need = kHeaderBytes + 32 * h.m + (h.kind == LECO_PART_VAR ? 8 * (h.m + 1) : 0) +
+                        8 * h.nwords;
+  if (bytes != need) return LECO_ERR_CORRUPT;
+  const char* body = (const char*)host_buf + kHeaderBytes;
+  if (crc32_update(0, body, need - kHeaderBytes) != h.crc) return LECO_ERR_CORRUPT;
+  // records/starts/words may be unaligned inside the caller's buffer: validate on copies
+  std::vector<Record> rec(h.m);
+  std::vector<uint64_t> starts(h.kind == LECO_PART_VAR ? h.m + 1 : 0);
+  std::vector<uint64_t> words(h.nwords);
+  const char* p = body;
+  if (h.m) memcpy(rec.data(), p, 32 * h.m);
+  p += 32 * h.m;
+  if (h.kind == LECO_PART_VAR) {
+    memcpy(starts.data(), p, 8 * (h.m + 1));
+    p += 8 * (h.m + 1);
+  }
+  memcpy(words.data(), p, 8 * h.nwords);
+  if (!validate_host(h, rec.data(), starts.data(), words.data())) return LECO_ERR_CORRUPT;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  leco_column* c = new (std::nothrow) leco_column();
+  if (!c) return LECO_ERR_OOM;
+  c->n = h.n;
+  c->m = h.m;
+  c->nwords = h.nwords;
+  c->total_bits = h.total_bits;
+  c->dtype = h.dtype;
+  c->kind = h.kind;
+  c->model = h.model;
+  c->L = h.kind == LECO_PART_FIXED ? h.L : 0;
+  c->tau = h.tau;
+  c->home = st;
+  cudaGetDevice(&c->device);
+  leco_status s = alloc_meta(c, st);
+  if (s == LECO_OK) {
+    c->words_bytes = 8 * c->nwords;
+    s = from_cuda(cudaMallocAsync((void**)&c->words, c->words_bytes, st));
+  }
+  if (s == LECO_OK && h.m)
+    s = from_cuda(cudaMemcpyAsync(c->rec, rec.data(), 32 * h.m, cudaMemcpyHostToDevice, st));
+  if (s == LECO_OK && h.kind == LECO_PART_VAR)
+    s = from_cuda(cudaMemcpyAsync(c->starts, starts.data(), 8 * (h.m + 1), cudaMemcpyHostToDevice, st));
+  if (s == LECO_OK)
+    s = from_cuda(cudaMemcpyAsync(c->words, words.data(), 8 * h.nwords, cudaMemcpyHostToDevice, st));
+  if (s == LECO_OK) s = from_cuda(launch_build_aux(c->rec, c->m, c->n, c->aux, c->status, st));
+  // the host vectors die at return: finish the copies first
+  if (s == LECO_OK) s = from_cuda(cudaStreamSynchronize(st));
+  if (s != LECO_OK) {
+    release(c, st);
+    return s;
+  }
+  *out = c;
+  return LECO_OK;
+}
+
+void leco_column_free(leco_column* col) {
+  if (!col) return;
+  int prev = 0;
+  const int dev = col->device;
+  cudaGetDevice(&prev);
+  if (prev != dev) cudaSetDevice(dev);
+  cudaDeviceSynchronize();
+  release(col, nullptr);
+  cudaStreamSynchronize(nullptr);
+  if (prev != dev) cudaSetDevice(prev);
+}
+
+void leco_column_free_async(leco_column* col, leco_stream_t stream) {
+  if (!col) return;
+  release(col, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Internal definitions of the GB300 LeCo library: device layouts, format accessors and the
+// device helpers shared by the kernels. Not part of the public ABI (see include/leco.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "leco.h"
+
+namespace leco {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+constexpr uint64_t kOffMask = (1ull << 48) - 1;
+constexpr uint32_t kMaxPartLen = 1u << 24;  // keeps every fit quantity inside int128
+constexpr uint64_t kSmBits = 256;           // model size S_M: one 32-byte record (§3.2.2)
+
+// Canonical 32-byte partition header (§3.3 storage format): theta as binary64.
+struct Record {
+  double theta0;
+  double theta1;
+  uint64_t start;
+  uint64_t word3;  // off:48 | b:7 | s:7 | exact:1 | 0:1
+};
+static_assert(sizeof(Record) == 32, "record layout");
+
+// Device decode table, derived from the records when a column is created: the same header with
+// theta replaced by the grid integers (A, B) when the exact flag was verified. word3 keeps the
+// canonical layout; its exact bit is cleared when verification failed (binary64 path then).
+struct Aux {
+  int64_t A;
+  int64_t B;
+  uint64_t start;
+  uint64_t word3;
+};
+static_assert(sizeof(Aux) == 32, "aux layout");
+
+// status word bits (device)
+enum : uint32_t { kStatIndexRange = 1u, kStatCorrupt = 2u, kStatTimeout = 4u };
+
+__host__ __device__ __forceinline__ uint64_t w3_off(uint64_t w3) { return w3 & kOffMask; }
+__host__ __device__ __forceinline__ uint32_t w3_b(uint64_t w3) { return (uint32_t)(w3 >> 48) & 0x7Fu; }
+__host__ __device__ __forceinline__ int32_t w3_s(uint64_t w3) {
+  int32_t s = (int32_t)((w3 >> 55) & 0x7F);
+  return s >= 64 ? s - 128 : s;
+}
+__host__ __device__ __forceinline__ uint32_t w3_exact(uint64_t w3) { return (uint32_t)(w3 >> 62) & 1u; }
+__host__ __device__ __forceinline__ uint64_t make_w3(uint64_t off, uint32_t b, int32_t s, uint32_t exact) {
+  return (off & kOffMask) | ((uint64_t)(b & 0x7F) << 48) | ((uint64_t)((uint32_t)s & 0x7F) << 55) |
+         ((uint64_t)(exact & 1) << 62);
+}
+
+// words a stream of total_bits needs: data words + 2 zero padding words, rounded up to 16 bytes
+__host__ __device__ __forceinline__ uint64_t stream_words(uint64_t total_bits) {
+  uint64_t w = (total_bits + 63) / 64 + 2;
+  return (w + 1) & ~1ull;
+}
+
+// ---------------------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ uint64_t zz_encode(int64_t r) {
+  return ((uint64_t)r << 1) ^ (uint64_t)(r >> 63);
+}
+__device__ __forceinline__ int64_t zz_decode(uint64_t z) {
+  return (int64_t)((z >> 1) ^ (0ull - (z & 1ull)));
+}
+__device__ __forceinline__ uint64_t low_mask(uint32_t b) {
+  return b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+}
+
+// b-bit field at absolute bit position pos of the LSB-first stream. The stream's padding words
+// make words[pos/64 + 1] readable for every pos <= total bits.
+__device__ __forceinline__ uint64_t read_field(const uint64_t* __restrict__ words, uint64_t pos,
+                                               uint32_t b) {
+  const uint64_t w = pos >> 6;
+  const uint32_t o = (uint32_t)pos & 63u;
+  const uint64_t lo = __ldg(words + w);
+  const uint64_t hi = __ldg(words + w + 1);
+  // (hi << 1) << (63 - o) is hi << (64 - o) without the undefined shift by 64 when o == 0
+  return ((lo >> o) | ((hi << 1) << (63 - o))) & low_mask(b);
+}
+
+// binary64 prediction of §3.3: floor(fl(fl(theta1 * x) + theta0)), NaN -> 0, saturating
+__device__ __forceinline__ int64_t predict_f64(double theta0, double theta1, uint64_t x) {
+  const double y = __dadd_rn(__dmul_rn(theta1, __ull2double_rn(x)), theta0);
+  if (y != y) return 0;
+  if (y >= 9223372036854775808.0) return INT64_MAX;
+  if (y < -9223372036854775808.0) return INT64_MIN;
+  return __double2ll_rd(y);
+}
+
+// prediction from the decode table (integer grid when exact, else binary64 from the record)
+__device__ __forceinline__ int64_t predict_aux(const Aux& a, const Record* __restrict__ rec,
+                                               uint64_t p, uint64_t x) {
+  if (w3_exact(a.word3)) {
+    const int32_t s = w3_s(a.word3);
+    const int64_t f = a.A + a.B * (int64_t)x;
+    return s > 0 ? (f >> s) : f;
+  }
+  return predict_f64(__ldg(&rec[p].theta0), __ldg(&rec[p].theta1), x);
+}
+
+__device__ __forceinline__ uint64_t load_value(const void* __restrict__ v, int dtype, uint64_t i) {
+  return dtype == LECO_U32 ? (uint64_t)__ldg((const uint32_t*)v + i) : __ldg((const uint64_t*)v + i);
+}
+
+__device__ __forceinline__ int bitlen_u64(uint64_t x) { return 64 - __clzll((long long)x); }
+__device__ __forceinline__ int bitlen_u128(u128 x) {
+  const uint64_t hi = (uint64_t)(x >> 64);
+  return hi ? 128 - __clzll((long long)hi) : bitlen_u64((uint64_t)x);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): first output of the generator seeded with x
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// warp reductions
+__device__ __forceinline__ i128 warp_sum_i128(i128 v) {
+  uint64_t lo = (uint64_t)v, hi = (uint64_t)((u128)v >> 64);
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const uint64_t h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const uint64_t nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return (i128)(((u128)hi << 64) | lo);
+}
+__device__ __forceinline__ int64_t warp_max_i64(int64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int64_t warp_min_i64(int64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------- host-side launchers
+// (defined in the .cu files; all return cudaError_t of the launch)
+
+struct ColumnView {
+  uint64_t n;
+  uint64_t m;
+  int dtype;
+  uint32_t L;                  // fixed partition length, 0 for variable
+  const Record* rec;
+  const Aux* aux;
+  const uint64_t* words;
+  const uint64_t* starts;      // variable: m+1 entries; fixed: nullptr
+  uint32_t* status;
+};
+
+// encode pipeline (k_encode.cu)
+cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
+                       uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
+                       cudaStream_t st);
+cudaError_t launch_offsets(Record* rec, const uint64_t* lenbits, uint64_t m, uint64_t* scratch,
+                           uint64_t scratch_elems, uint64_t* total_out, cudaStream_t st);
+uint64_t offsets_scratch_elems(uint64_t m);
+cudaError_t launch_build_aux(const Record* rec, uint64_t m, uint64_t n, Aux* aux, uint32_t* status,
+                             cudaStream_t st);
+cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux,
+                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
+                        uint64_t nwords, cudaStream_t st);
+
+// decode family (k_decode.cu)
+cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
+                          cudaStream_t st);
+cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
+                              leco_sum_result* out, cudaStream_t st);
+cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint64_t k, void* out,
+                                 cudaStream_t st);
+
+// variable partitioner (k_var.cu)
+cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
+                          int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st);
+
+int sm_count();
+
+}  // namespace leco

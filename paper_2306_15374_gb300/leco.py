@@ -1,0 +1,282 @@
+"""Python binding of libleco (include/leco.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls. Device buffers are torch CUDA tensors
+(their data pointers are passed through); streams are torch CUDA streams (default: the current
+one). Values are stored in 8- or 4-byte integer tensors holding the unsigned bit patterns
+(torch.int64/uint64 for 64-bit columns, torch.int32/uint32 for 32-bit ones). All compute runs in
+the CUDA library; there is no CPU fallback: if libleco.so is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import builder as _build
+
+LECO_OK = 0
+LECO_ERR_INVALID_ARG = 1
+LECO_ERR_OOM = 2
+LECO_ERR_INDEX_RANGE = 3
+LECO_ERR_CUDA = 4
+LECO_ERR_CORRUPT = 5
+LECO_ERR_TIMEOUT = 6
+LECO_ERR_BUDGET = 7
+
+LECO_U32 = 0
+LECO_U64 = 1
+LECO_MODEL_CONSTANT = 0
+LECO_MODEL_LINEAR = 1
+LECO_PART_FIXED = 0
+LECO_PART_VAR = 1
+LECO_FILTER_PRUNE = 1
+
+
+class LecoError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {leco_status_string(status)} ({status})" if what else
+                         f"{leco_status_string(status)} ({status})")
+
+
+class PartitionPolicy(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("part_size", ctypes.c_uint32), ("tau", ctypes.c_double)]
+
+
+class SumResult(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("sum_lo", ctypes.c_uint64), ("sum_hi", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64), ("partitions", ctypes.c_uint64), ("record_bytes", ctypes.c_uint64),
+        ("residual_bytes", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64), ("ratio", ctypes.c_double),
+        ("dtype", ctypes.c_int32), ("kind", ctypes.c_int32), ("model", ctypes.c_int32),
+        ("part_size", ctypes.c_uint32), ("residual_bits", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+    ]
+
+
+def fixed(L: int) -> PartitionPolicy:
+    return PartitionPolicy(LECO_PART_FIXED, int(L), 0.0)
+
+
+def variable(tau: float = 0.03, cap: int = 0) -> PartitionPolicy:
+    return PartitionPolicy(LECO_PART_VAR, int(cap), float(tau))
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libleco.so from the package's _build directory (build it first with build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.SO):
+        raise RuntimeError(f"libleco.so is not built ({_build.SO}); run paper_2306_15374_gb300.build()")
+    L = ctypes.CDLL(_build.SO)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    col_pp = ctypes.POINTER(ctypes.c_void_p)
+    sigs = {
+        "leco_status_string": (ctypes.c_char_p, [i32]),
+        "leco_version": (u32, []),
+        "leco_encode": (i32, [vp, u64, i32, PartitionPolicy, i32, vp, col_pp]),
+        "leco_var_partition": (i32, [vp, u64, i32, PartitionPolicy, i32, vp, ctypes.POINTER(u64), vp]),
+        "leco_encode_with_starts": (i32, [vp, u64, i32, vp, u64, i32, vp, col_pp]),
+        "leco_decode_all": (i32, [vp, vp, vp]),
+        "leco_decode_range": (i32, [vp, u64, u64, vp, vp]),
+        "leco_random_access": (i32, [vp, vp, u64, vp, vp]),
+        "leco_filter_sum": (i32, [vp, u64, u64, u32, vp, vp]),
+        "leco_sync": (i32, [vp, vp]),
+        "leco_stats_get": (i32, [vp, ctypes.POINTER(Stats)]),
+        "leco_column_export": (i32, [vp, vp, vp, vp]),
+        "leco_serialize": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
+        "leco_deserialize": (i32, [vp, u64, vp, col_pp]),
+        "leco_column_free": (None, [vp]),
+        "leco_column_free_async": (None, [vp, vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list[str]:
+    """Names of the leco_* entry points this binding resolves from the library."""
+    L = lib()
+    return [n for n in dir(L) if n.startswith("leco_")]
+
+
+# ------------------------------------------------------------------------------ helpers
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dtype_of(t) -> int:
+    import torch
+
+    if t.element_size() == 8:
+        return LECO_U64
+    if t.element_size() == 4:
+        return LECO_U32
+    raise ValueError(f"values must be 4- or 8-byte integers, got {t.dtype}")
+
+
+def _dev(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(status: int, what: str):
+    if status != LECO_OK:
+        raise LecoError(status, what)
+
+
+class Column:
+    """Owning handle of a leco_column (freed with leco_column_free when collected)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("column already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().leco_column_free(self._h)
+            self._h = None
+
+    def free_async(self, stream=None):
+        if self._h:
+            lib().leco_column_free_async(self._h, _stream(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().leco_stats_get(self.handle, ctypes.byref(s)), "leco_stats_get")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    @property
+    def n(self) -> int:
+        return self.stats()["n"]
+
+    @property
+    def dtype(self) -> int:
+        return self.stats()["dtype"]
+
+
+# ------------------------------------------------------------------------------ entry points
+
+def leco_status_string(status: int) -> str:
+    return lib().leco_status_string(int(status)).decode()
+
+
+def leco_version() -> int:
+    return int(lib().leco_version())
+
+
+def leco_encode(values, policy: PartitionPolicy, model: int = LECO_MODEL_LINEAR, stream=None,
+                dtype: int | None = None) -> Column:
+    h = ctypes.c_void_p()
+    dt = _dtype_of(values) if dtype is None else dtype
+    _check(lib().leco_encode(_dev(values), values.numel(), dt, policy, model, _stream(stream),
+                             ctypes.byref(h)), "leco_encode")
+    return Column(h)
+
+
+def leco_var_partition(values, starts_out, policy: PartitionPolicy, model: int = LECO_MODEL_LINEAR,
+                       stream=None) -> int:
+    """Split + merge on the device; starts_out (int64 CUDA tensor of n+1) gets m+1 starts; returns m."""
+    m = ctypes.c_uint64(0)
+    _check(lib().leco_var_partition(_dev(values), values.numel(), _dtype_of(values), policy, model,
+                                    _dev(starts_out), ctypes.byref(m), _stream(stream)),
+           "leco_var_partition")
+    return int(m.value)
+
+
+def leco_encode_with_starts(values, starts, m: int, model: int = LECO_MODEL_LINEAR,
+                            stream=None) -> Column:
+    h = ctypes.c_void_p()
+    _check(lib().leco_encode_with_starts(_dev(values), values.numel(), _dtype_of(values), _dev(starts),
+                                         int(m), model, _stream(stream), ctypes.byref(h)),
+           "leco_encode_with_starts")
+    return Column(h)
+
+
+def leco_decode_all(col: Column, out, stream=None) -> None:
+    _check(lib().leco_decode_all(col.handle, _dev(out), _stream(stream)), "leco_decode_all")
+
+
+def leco_decode_range(col: Column, begin: int, count: int, out, stream=None) -> None:
+    _check(lib().leco_decode_range(col.handle, int(begin), int(count), _dev(out), _stream(stream)),
+           "leco_decode_range")
+
+
+def leco_random_access(col: Column, idx, out, stream=None) -> None:
+    _check(lib().leco_random_access(col.handle, _dev(idx), idx.numel(), _dev(out), _stream(stream)),
+           "leco_random_access")
+
+
+def leco_filter_sum(col: Column, lo: int, hi: int, out, flags: int = 0, stream=None) -> None:
+    """out: CUDA tensor of >= 3 int64 (count, sum_lo, sum_hi)."""
+    _check(lib().leco_filter_sum(col.handle, int(lo), int(hi), int(flags), _dev(out), _stream(stream)),
+           "leco_filter_sum")
+
+
+def leco_sync(col: Column, stream=None) -> int:
+    """Returns the status code (LECO_OK or the first device-side error) without raising."""
+    return int(lib().leco_sync(col.handle, _stream(stream)))
+
+
+def leco_stats_get(col: Column) -> dict:
+    return col.stats()
+
+
+def leco_column_export(col: Column):
+    """(records bytes, words bytes, starts bytes or None) copied to host as Python bytes."""
+    st = col.stats()
+    m, nw = st["partitions"], st["residual_bytes"] // 8
+    rec = ctypes.create_string_buffer(max(32 * m, 1))
+    words = ctypes.create_string_buffer(max(8 * nw, 1))
+    starts = ctypes.create_string_buffer(8 * (m + 1)) if st["kind"] == LECO_PART_VAR else None
+    _check(lib().leco_column_export(col.handle, rec, words, starts), "leco_column_export")
+    return rec.raw[: 32 * m], words.raw[: 8 * nw], (starts.raw if starts is not None else None)
+
+
+def leco_serialize(col: Column) -> bytes:
+    need = ctypes.c_uint64(0)
+    _check(lib().leco_serialize(col.handle, None, 0, ctypes.byref(need)), "leco_serialize")
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().leco_serialize(col.handle, buf, need.value, ctypes.byref(need)), "leco_serialize")
+    return buf.raw[: need.value]
+
+
+def leco_deserialize(blob: bytes, stream=None) -> Column:
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().leco_deserialize(buf, len(blob), _stream(stream), ctypes.byref(h)), "leco_deserialize")
+    return Column(h)
+
+
+def leco_column_free(col: Column) -> None:
+    col.free()

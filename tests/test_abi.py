@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point its headers declare
+(no GPU needed: nothing here launches a kernel)."""
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(leco_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def built():
+    import paper_2306_15374_gb300 as pkg
+
+    return pkg.build()
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for required in ("leco_encode", "leco_decode_all", "leco_random_access", "leco_filter_sum",
+                     "leco_decode_range", "leco_serialize", "leco_deserialize", "leco_sync"):
+        assert required in names
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        assert "torch" not in text and "at::" not in text and "c10" not in text
+
+
+def test_library_exports_every_declared_symbol(built):
+    import ctypes
+
+    L = ctypes.CDLL(built)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_resolves_entry_points(built):
+    from paper_2306_15374_gb300 import leco
+
+    names = set(leco.exported_symbols())
+    assert {"leco_encode", "leco_decode_all", "leco_random_access", "leco_filter_sum"} <= names
+    assert leco.leco_status_string(leco.LECO_ERR_CORRUPT) == "LECO_ERR_CORRUPT"
+    assert leco.leco_version() >= 10000
+
+
+def test_host_side_argument_errors(built):
+    """Argument checks happen on the host, before any CUDA call."""
+    import ctypes
+
+    from paper_2306_15374_gb300 import leco
+
+    L = leco.lib()
+    h = ctypes.c_void_p()
+    assert L.leco_encode(None, 10, 1, leco.fixed(16), 1, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_encode(None, 0, 7, leco.fixed(16), 1, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_encode(None, 0, 1, leco.fixed(16), 1, None, None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_decode_all(None, None, None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_deserialize(b"LECO", 4, None, ctypes.byref(h)) == leco.LECO_ERR_CORRUPT
+    assert L.leco_deserialize(b"\0" * 64, 64, None, ctypes.byref(h)) == leco.LECO_ERR_CORRUPT
+    assert L.leco_filter_sum(None, 0, 1, 0, None, None) == leco.LECO_ERR_INVALID_ARG
