@@ -37,8 +37,8 @@ WORKLOAD = "LeCo-fix L=4096 linear, 3 x 200M uint64 (linear+noise, sorted normal
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["leco", "reference"], default="leco")
     ap.add_argument("--n", type=int, default=200_000_000)
     ap.add_argument("--lookups", type=int, default=10_000_000)
@@ -175,7 +175,15 @@ def run_reference(args):
 
     oracle.build()
     columns = {d: W.cfg2(d, args.n) for d in DISTS}
-    samples = prepare_cpu_samples(columns, args.sample_every, args.lookups, args.n)
+    every = args.sample_every
+    samples = prepare_cpu_samples(columns, every, args.lookups, args.n)
+    # keep the whole run within about 90 s of oracle time: thin the per-step sample if needed
+    _, t1 = cpu_oracle_run(samples, None)
+    budget = 90.0
+    if (args.steps + args.warmup) * t1 > budget:
+        every = int(every * (args.steps + args.warmup) * t1 / budget) + 1
+        samples = prepare_cpu_samples(columns, every, args.lookups, args.n)
+    args.sample_every = every
     del columns
     for _ in range(args.warmup):
         cpu_oracle_run(samples, None)
@@ -306,12 +314,35 @@ def run_leco(args):
     for o in ops:
         tms = sum(a.elapsed_time(b) for d in DISTS for a, b in ev[(d, o)]) / args.steps
         per[o] = tms
+    # filter variants outside the step: model-bound pruning (§5.1) and decode-every-value
+    variants = {}
+    for name, fl in (("prune", leco.LECO_FILTER_PRUNE), ("decode_all", leco.LECO_FILTER_DECODE_ALL)):
+        reps = max(3, min(args.steps, 50))
+        for d in DISTS:
+            leco.leco_filter_sum(cols[d], bounds[d][0], bounds[d][1], res, flags=fl)
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(reps):
+            for d in DISTS:
+                leco.leco_filter_sum(cols[d], bounds[d][0], bounds[d][1], res, flags=fl)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        variants[name] = v0.elapsed_time(v1) / reps
     peak, peak_kind = measured_peaks()
     dec_gbs = dec_b / (per["decode"] * 1e-3) / 1e9
     ops_out = {
         "decode": {"gbs": dec_gbs, "ms": per["decode"], "frac_hbm": dec_gbs / peak},
         "filter_sum": {"gbs": filt_b / (per["filter"] * 1e-3) / 1e9, "ms": per["filter"],
-                       "frac_hbm": filt_b / (per["filter"] * 1e-3) / 1e9 / peak},
+                       "frac_hbm": filt_b / (per["filter"] * 1e-3) / 1e9 / peak,
+                       "mode": "scan all residual words, decode groups whose model bounds meet [lo, hi]"},
+        "filter_sum_prune": {"ms": variants["prune"],
+                             "scan_equivalent_gbs": filt_b / (variants["prune"] * 1e-3) / 1e9,
+                             "mode": "LECO_FILTER_PRUNE: tiles whose model bounds miss [lo, hi] are not read"},
+        "filter_sum_decode_all": {"gbs": filt_b / (variants["decode_all"] * 1e-3) / 1e9,
+                                  "ms": variants["decode_all"],
+                                  "frac_hbm": filt_b / (variants["decode_all"] * 1e-3) / 1e9 / peak,
+                                  "mode": "LECO_FILTER_DECODE_ALL: every value decoded and compared"},
         "random_access": {"mlookups_s": 3 * k / (per["lookup"] * 1e-3) / 1e6, "ms": per["lookup"],
                           "gbs": look_b / (per["lookup"] * 1e-3) / 1e9},
         "encode": {"gbs": sum(8 * n + comp[d] for d in DISTS) / (sum(enc_ms) * 1e-3) / 1e9,

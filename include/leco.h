@@ -100,9 +100,15 @@ typedef struct {
   uint64_t device_bytes;   /* bytes the column holds on the device */
 } leco_stats;
 
-/* Filter flags. LECO_FILTER_PRUNE skips partitions whose value bounds (from the model and the
- * residual width, §5.1 pruning) lie outside [lo, hi]; the result is identical. */
+/* Filter flags; every mode returns the identical result.
+ * 0: scan every residual word of the column; each 32-value group is first bounded by its model
+ *    (prediction at both ends +- the residual range of width b) and decoded only if it can meet
+ *    [lo, hi] (groups certainly inside are summed without the compare).
+ * LECO_FILTER_PRUNE: additionally skip reading the residuals of 2048-position tiles whose
+ *    partitions' model bounds all miss [lo, hi] (the model-bound pruning of §5.1).
+ * LECO_FILTER_DECODE_ALL: decode and compare every value (no group bounds); a diagnostic mode. */
 #define LECO_FILTER_PRUNE 1u
+#define LECO_FILTER_DECODE_ALL 2u
 
 /* ------------------------------------------------------------------------------------------ */
 /* Library */

@@ -19,7 +19,8 @@ __device__ __forceinline__ uint64_t part_begin(const uint64_t* starts, uint32_t 
 // one CTA per partition (grid-stride)
 __global__ void __launch_bounds__(kFitBlock)
     k_fit(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
-          uint32_t L, uint64_t m, int model, Record* __restrict__ rec, uint64_t* __restrict__ lenbits) {
+          uint32_t L, uint64_t m, int model, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
+          uint32_t* __restrict__ max_b) {
   __shared__ FitShared sm;
   for (uint64_t p = blockIdx.x; p < m; p += gridDim.x) {
     const uint64_t a = part_begin(starts, L, n, p);
@@ -34,15 +35,16 @@ __global__ void __launch_bounds__(kFitBlock)
       r.word3 = make_w3(0, R.b, R.s, 1);
       rec[p] = r;
       lenbits[p] = (uint64_t)N * R.b;
+      if (R.b) atomicMax(max_b, R.b);
     }
   }
 }
 
 // ------------------------------------------------------------------------------ exclusive scan
 
-constexpr int kScanBlock = 256;
-constexpr int kScanItems = 8;
-constexpr uint64_t kScanTile = kScanBlock * kScanItems;
+constexpr int kPrefixBlock = 256;
+constexpr int kPrefixItems = 8;
+constexpr uint64_t kPrefixTile = kPrefixBlock * kPrefixItems;
 
 __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* warp_tot,
                                                          uint64_t* total) {
@@ -55,14 +57,14 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* w
   if (lane == 31) warp_tot[wid] = inc;
   __syncthreads();
   if (wid == 0) {
-    uint64_t t = lane < (kScanBlock / 32) ? warp_tot[lane] : 0;
+    uint64_t t = lane < (kPrefixBlock / 32) ? warp_tot[lane] : 0;
     uint64_t ti = t;
     for (int o = 1; o < 32; o <<= 1) {
       const uint64_t u = __shfl_up_sync(0xffffffffu, ti, o);
       if (lane >= o) ti += u;
     }
-    if (lane < (kScanBlock / 32)) warp_tot[lane] = ti - t;
-    if (lane == (kScanBlock / 32) - 1) *total = ti;
+    if (lane < (kPrefixBlock / 32)) warp_tot[lane] = ti - t;
+    if (lane == (kPrefixBlock / 32) - 1) *total = ti;
   }
   __syncthreads();
   const uint64_t r = warp_tot[wid] + inc - v;
@@ -70,31 +72,31 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* w
   return r;
 }
 
-__global__ void __launch_bounds__(kScanBlock)
-    k_scan_tiles(const uint64_t* __restrict__ in, uint64_t count, uint64_t* __restrict__ tile_sums) {
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+__global__ void __launch_bounds__(kPrefixBlock)
+    k_prefix_tiles(const uint64_t* __restrict__ in, uint64_t count, uint64_t* __restrict__ tile_sums) {
+  const uint64_t base = (uint64_t)blockIdx.x * kPrefixTile;
   uint64_t s = 0;
-  for (int k = 0; k < kScanItems; k++) {
-    const uint64_t i = base + (uint64_t)k * kScanBlock + threadIdx.x;
+  for (int k = 0; k < kPrefixItems; k++) {
+    const uint64_t i = base + (uint64_t)k * kPrefixBlock + threadIdx.x;
     if (i < count) s += in[i];
   }
   s = warp_sum_u64(s);
-  __shared__ uint64_t ws[kScanBlock / 32];
+  __shared__ uint64_t ws[kPrefixBlock / 32];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     uint64_t t = 0;
-    for (int k = 0; k < kScanBlock / 32; k++) t += ws[k];
+    for (int k = 0; k < kPrefixBlock / 32; k++) t += ws[k];
     tile_sums[blockIdx.x] = t;
   }
 }
 
-__global__ void __launch_bounds__(kScanBlock)
-    k_scan_top(uint64_t* __restrict__ tile_sums, uint64_t ntiles, uint64_t* __restrict__ total) {
-  __shared__ uint64_t wt[kScanBlock / 32];
+__global__ void __launch_bounds__(kPrefixBlock)
+    k_prefix_top(uint64_t* __restrict__ tile_sums, uint64_t ntiles, uint64_t* __restrict__ total) {
+  __shared__ uint64_t wt[kPrefixBlock / 32];
   __shared__ uint64_t tot;
   uint64_t carry = 0;
-  for (uint64_t base = 0; base < ntiles; base += kScanBlock) {
+  for (uint64_t base = 0; base < ntiles; base += kPrefixBlock) {
     const uint64_t i = base + threadIdx.x;
     const uint64_t v = i < ntiles ? tile_sums[i] : 0;
     const uint64_t ex = block_exclusive_scan(v, wt, &tot);
@@ -106,21 +108,21 @@ __global__ void __launch_bounds__(kScanBlock)
   if (threadIdx.x == 0) *total = carry;
 }
 
-__global__ void __launch_bounds__(kScanBlock)
-    k_scan_apply(const uint64_t* __restrict__ in, uint64_t count,
+__global__ void __launch_bounds__(kPrefixBlock)
+    k_prefix_apply(const uint64_t* __restrict__ in, uint64_t count,
                  const uint64_t* __restrict__ tile_prefix, uint64_t* __restrict__ out) {
-  __shared__ uint64_t wt[kScanBlock / 32];
+  __shared__ uint64_t wt[kPrefixBlock / 32];
   __shared__ uint64_t tot;
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
-  uint64_t v[kScanItems];
+  const uint64_t base = (uint64_t)blockIdx.x * kPrefixTile + (uint64_t)threadIdx.x * kPrefixItems;
+  uint64_t v[kPrefixItems];
   uint64_t s = 0;
-  for (int k = 0; k < kScanItems; k++) {
+  for (int k = 0; k < kPrefixItems; k++) {
     const uint64_t i = base + k;
     v[k] = i < count ? in[i] : 0;
     s += v[k];
   }
   uint64_t run = block_exclusive_scan(s, wt, &tot) + tile_prefix[blockIdx.x];
-  for (int k = 0; k < kScanItems; k++) {
+  for (int k = 0; k < kPrefixItems; k++) {
     const uint64_t i = base + k;
     if (i < count) out[i] = run;
     run += v[k];
@@ -254,16 +256,17 @@ int sm_count() {
 
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
                        uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
-                       cudaStream_t st) {
-  if (m == 0) return cudaSuccess;
+                       uint32_t* max_b, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess || m == 0) return e;
   const uint64_t cap = (uint64_t)sm_count() * 16;
   const int grid = (int)(m < cap ? m : cap);
-  k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits);
+  k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
   return cudaGetLastError();
 }
 
 uint64_t offsets_scratch_elems(uint64_t m) {
-  const uint64_t ntiles = (m + kScanTile - 1) / kScanTile;
+  const uint64_t ntiles = (m + kPrefixTile - 1) / kPrefixTile;
   return m + ntiles + 1;  // exclusive offsets + tile prefixes + total
 }
 
@@ -271,10 +274,10 @@ uint64_t offsets_scratch_elems(uint64_t m) {
 cudaError_t scan_u64(const uint64_t* in, uint64_t count, uint64_t* out, uint64_t* scratch,
                      uint64_t* total, cudaStream_t st) {
   if (count == 0) return cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
-  const uint64_t ntiles = (count + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, count, scratch);
-  k_scan_top<<<1, kScanBlock, 0, st>>>(scratch, ntiles, total);
-  k_scan_apply<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, count, scratch, out);
+  const uint64_t ntiles = (count + kPrefixTile - 1) / kPrefixTile;
+  k_prefix_tiles<<<(unsigned)ntiles, kPrefixBlock, 0, st>>>(in, count, scratch);
+  k_prefix_top<<<1, kPrefixBlock, 0, st>>>(scratch, ntiles, total);
+  k_prefix_apply<<<(unsigned)ntiles, kPrefixBlock, 0, st>>>(in, count, scratch, out);
   return cudaGetLastError();
 }
 

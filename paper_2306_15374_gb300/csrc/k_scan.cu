@@ -1,0 +1,539 @@
+// Tiled column scans (§3.3 range decompression; the filter + sum of §5.1 without materialising
+// values): full/range decode and the fused filter-sum.
+//
+// Tile t covers positions [t kScanTile, (t+1) kScanTile); its residuals are one contiguous bit
+// range. A persistent CTA has one producer warp and eight consumer warps. The producer walks the
+// CTA's tiles in order: it waits until a shared-memory stage is empty, then issues one 1-D bulk
+// copy (TMA) of the tile's 16-byte-aligned word range and one of its decode-table entries (when at
+// most kMaxP partitions touch it), completing on the stage's "full" mbarrier. Each consumer warp
+// decodes 512 positions of the tile lane-strided (lane j takes positions g + j), so global stores
+// are coalesced and neighbouring fields are read from shared memory without bank conflicts. Inside
+// a partition a lane carries its fixed-point prediction F = A + B x and its bit position, stepping
+// by 32 B and 32 b per group. The filter bounds each 32-value group with its model (prediction at
+// both ends +- the residual range of width b) and decodes only groups that can meet [lo, hi].
+// Tile descriptors (word range, partitions, value bounds) are built once per column.
+#include "leco_internal.cuh"
+#include "tma.cuh"
+
+namespace leco {
+
+namespace {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;
+constexpr int kPerWarp = (int)kScanTile / kConsumerWarps;
+constexpr int kStages = 4;
+constexpr int kMaxP = 64;
+constexpr uint32_t kAuxBytes = kMaxP * 32;
+
+enum Mode { kDecode64 = 0, kDecode32 = 1, kFilter = 2 };
+
+struct TileMeta {
+  uint64_t p0;
+  uint64_t bit_base;  // absolute bit position of the first staged word
+  uint32_t np;
+  uint32_t staged;    // decode-table entries p0 .. p0+np-1 are in shared memory
+  uint32_t skip;      // pruned: nothing was copied
+  uint32_t pad;
+};
+
+struct Ctrl {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  TileMeta meta[kStages];
+  uint64_t red[3][kConsumerWarps];
+  uint64_t issued;
+  uint64_t consumed[kConsumerWarps];
+  int abort;
+};
+
+constexpr uint32_t kCtrlBytes = (sizeof(Ctrl) + 127) & ~127u;
+
+struct ScanArgs {
+  ColumnView c;
+  uint64_t begin, end;       // requested positions
+  uint64_t t_first, t_last;  // tiles touching [begin, end)
+  void* out;                 // decode output (position i -> out[i - begin])
+  uint64_t lo, hi;           // filter range
+  uint32_t flags;
+  leco_sum_result* res;
+};
+
+__device__ __forceinline__ uint64_t pstart(const ColumnView& c, uint64_t p) {
+  if (c.starts) return __ldg(c.starts + p);
+  const uint64_t s = p * (uint64_t)c.L;
+  return s < c.n ? s : c.n;
+}
+
+// partition holding position i, searched inside [lo, hi) (hi exclusive, i >= start(lo))
+__device__ __forceinline__ uint64_t part_of(const ColumnView& c, uint64_t i, uint64_t lo, uint64_t hi) {
+  if (!c.starts) return c.n <= 0xFFFFFFFFull ? (uint64_t)((uint32_t)i / c.L) : i / c.L;
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(c.starts + mid) <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ Aux ldg_aux(const Aux* a) {
+  const ulonglong2* q = reinterpret_cast<const ulonglong2*>(a);
+  const ulonglong2 v0 = __ldg(q), v1 = __ldg(q + 1);
+  Aux r;
+  r.A = (int64_t)v0.x;
+  r.B = (int64_t)v0.y;
+  r.start = v1.x;
+  r.word3 = v1.y;
+  return r;
+}
+
+// Model bounds of positions [x0, x1] of a partition: prediction at both ends (monotone in x) +- the
+// residual range of width b. False for a binary64 partition or bounds that wrap the value domain.
+__device__ __forceinline__ bool part_bounds(int dtype, const Aux& a, uint64_t x0, uint64_t x1,
+                                            uint64_t* vlo_out, uint64_t* vhi_out) {
+  if (!w3_exact(a.word3)) return false;
+  int32_t sh = w3_s(a.word3);
+  sh = sh > 0 ? sh : 0;
+  int64_t p0v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x0) >> sh;
+  int64_t p1v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x1) >> sh;
+  if (p0v > p1v) {
+    const int64_t t = p0v;
+    p0v = p1v;
+    p1v = t;
+  }
+  const uint32_t b = w3_b(a.word3);
+  const i128 rneg = b == 0 ? 0 : -((i128)1 << (b - 1));
+  const i128 rpos = b == 0 ? 0 : (((i128)1 << (b - 1)) - 1);
+  const i128 vlo = (i128)p0v + rneg, vhi = (i128)p1v + rpos;
+  const i128 top = dtype == LECO_U32 ? ((i128)1 << 32) : ((i128)1 << 64);
+  if (vlo < 0 || vhi >= top) return false;
+  *vlo_out = (uint64_t)vlo;
+  *vhi_out = (uint64_t)vhi;
+  return true;
+}
+
+// 0 = may meet [lo, hi], 1 = certainly misses, 2 = certainly inside
+__device__ __forceinline__ int classify(bool ok, uint64_t vlo, uint64_t vhi, uint64_t lo, uint64_t hi) {
+  if (!ok) return 0;
+  if (vhi < lo || vlo > hi) return 1;
+  if (vlo >= lo && vhi <= hi) return 2;
+  return 0;
+}
+
+// b-bit field (b <= 32) at bit position bit of a staged word buffer
+__device__ __forceinline__ uint32_t field32(const uint32_t* w, uint32_t bit, uint32_t mask) {
+  const uint32_t k = bit >> 5;
+  return __funnelshift_r(w[k], w[k + 1], bit) & mask;
+}
+
+// b-bit field (32 < b <= 64)
+__device__ __forceinline__ uint64_t field64(const uint32_t* w, uint32_t bit, uint64_t mask) {
+  const uint32_t k = bit >> 5;
+  const uint32_t w0 = w[k], w1 = w[k + 1], w2 = w[k + 2];
+  const uint32_t lo = __funnelshift_r(w0, w1, bit);
+  const uint32_t hi = __funnelshift_r(w1, w2, bit);
+  return (((uint64_t)hi << 32) | lo) & mask;
+}
+
+__device__ __forceinline__ int64_t unzigzag32(uint32_t z) {
+  return (int64_t)(int32_t)((z >> 1) ^ (0u - (z & 1u)));
+}
+
+struct Acc {
+  uint64_t cnt = 0, lo = 0, hi = 0;
+  __device__ __forceinline__ void add(uint64_t v) {
+    cnt++;
+    const uint64_t t = lo + v;
+    hi += t < lo ? 1ull : 0ull;
+    lo = t;
+  }
+};
+
+template <int MODE>
+__device__ __forceinline__ void emit(const ScanArgs& g, Acc& acc, uint64_t i, uint64_t v, uint64_t vmask) {
+  if (MODE == kDecode64) {
+    reinterpret_cast<uint64_t*>(g.out)[i - g.begin] = v;
+  } else if (MODE == kDecode32) {
+    reinterpret_cast<uint32_t*>(g.out)[i - g.begin] = (uint32_t)v;
+  } else {
+    v &= vmask;
+    if (v >= g.lo && v <= g.hi) acc.add(v);
+  }
+}
+
+// one position decoded from scratch (partition search, multiply): boundary groups only
+__device__ __forceinline__ uint64_t value_at(const ScanArgs& g, const uint32_t* words, const Aux* saux,
+                                             const TileMeta& mt, uint64_t i, uint64_t q) {
+  const ColumnView& c = g.c;
+  Aux a;
+  if (mt.staged) {
+    const uint64_t last = mt.p0 + mt.np - 1;
+    while (q < last && saux[q + 1 - mt.p0].start <= i) q++;
+    a = saux[q - mt.p0];
+  } else {
+    q = part_of(c, i, q, mt.p0 + mt.np);
+    a = ldg_aux(c.aux + q);
+  }
+  const uint64_t x = i - a.start;
+  const uint32_t b = w3_b(a.word3);
+  const uint32_t bit = (uint32_t)(w3_off(a.word3) + (uint64_t)b * x - mt.bit_base);
+  const uint64_t z = b <= 32 ? (uint64_t)field32(words, bit, (uint32_t)low_mask(b)) : field64(words, bit, low_mask(b));
+  return (uint64_t)predict_aux(a, c.rec, q, x) + (uint64_t)zz_decode(z);
+}
+
+// Tight loop over ng whole 32-value groups of one exact partition (the common case). Lane j
+// handles positions i0 + j + 32 k; its fixed-point prediction F and bit position step by 32 B and
+// 32 b. Filter runs are classified once by their model bounds: missed runs cost nothing, runs
+// certainly inside are summed without the compare.
+template <int MODE, bool WIDE>
+__device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const uint32_t* words,
+                                           const Aux& a, uint64_t i0, uint32_t ng, uint64_t bit_base,
+                                           uint32_t lane, int cls) {
+  const uint32_t b = w3_b(a.word3);
+  int32_t sh = w3_s(a.word3);
+  sh = (sh > 0 ? sh : 0) & 63;
+  const uint64_t x = i0 + lane - a.start;
+  uint64_t F = (uint64_t)a.A + (uint64_t)a.B * x;
+  const uint64_t B32 = (uint64_t)a.B * 32u;
+  uint32_t bit = (uint32_t)(w3_off(a.word3) + (uint64_t)b * x - bit_base);
+  const uint32_t b32 = 32u * b;
+  const uint64_t mask64 = low_mask(b);
+  const uint32_t mask32 = (uint32_t)mask64;
+  if (MODE == kDecode64) {
+    uint64_t* o = reinterpret_cast<uint64_t*>(g.out) + (i0 + lane - g.begin);
+#pragma unroll 4
+    for (uint32_t k = 0; k < ng; k++) {
+      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+      *o = (uint64_t)(((int64_t)F >> sh) + r);
+      o += 32;
+      F += B32;
+      bit += b32;
+    }
+  } else if (MODE == kDecode32) {
+    uint32_t* o = reinterpret_cast<uint32_t*>(g.out) + (i0 + lane - g.begin);
+#pragma unroll 4
+    for (uint32_t k = 0; k < ng; k++) {
+      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+      *o = (uint32_t)(uint64_t)(F >> sh) + (uint32_t)r;
+      o += 32;
+      F += B32;
+      bit += b32;
+    }
+  } else {
+    const uint64_t vmask = g.c.dtype == LECO_U32 ? 0xFFFFFFFFull : ~0ull;
+    if (cls == 1) return;
+    if (cls == 2) {
+      for (uint32_t k = 0; k < ng; k++) {
+        const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+        acc.add((uint64_t)(((int64_t)F >> sh) + r) & vmask);
+        F += B32;
+        bit += b32;
+      }
+      return;
+    }
+    for (uint32_t k = 0; k < ng; k++) {
+      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+      const uint64_t v = (uint64_t)(((int64_t)F >> sh) + r) & vmask;
+      if (v >= g.lo && v <= g.hi) acc.add(v);
+      F += B32;
+      bit += b32;
+    }
+  }
+}
+
+template <int MODE>
+__device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, const uint32_t* words,
+                             const Aux* saux, Acc& acc) {
+  const ColumnView& c = g.c;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint64_t tile_base = t * kScanTile;
+  const uint64_t wbeg = max(g.begin, tile_base + (uint64_t)warp * kPerWarp);
+  const uint64_t wend = min(min(g.end, c.n), tile_base + (uint64_t)(warp + 1) * kPerWarp);
+  const uint64_t vmask = c.dtype == LECO_U32 ? 0xFFFFFFFFull : ~0ull;
+  const uint64_t last = mt.p0 + mt.np - 1;
+  uint64_t q = mt.p0;
+  uint64_t gp = wbeg;
+  while (gp < wend) {
+    // partition holding gp (warp-uniform)
+    Aux a;
+    if (mt.staged) {
+      while (q < last && saux[q + 1 - mt.p0].start <= gp) q++;
+      a = saux[q - mt.p0];
+    } else {
+      q = part_of(c, gp, q, mt.p0 + mt.np);
+      a = ldg_aux(c.aux + q);
+    }
+    const uint64_t qend = (q < last && mt.staged) ? saux[q + 1 - mt.p0].start : pstart(c, q + 1);
+    const uint64_t run_end = min(qend, wend);
+    const uint32_t ng = (uint32_t)((run_end - gp) >> 5);
+    if (ng && w3_exact(a.word3)) {
+      int cls = 0;
+      if (MODE == kFilter && !(g.flags & LECO_FILTER_DECODE_ALL)) {
+        uint64_t vlo = 0, vhi = 0;
+        const bool ok = part_bounds(c.dtype, a, gp - a.start, gp + 32ull * ng - 1 - a.start, &vlo, &vhi);
+        cls = classify(ok, vlo, vhi, g.lo, g.hi);
+      }
+      if (w3_b(a.word3) > 32)
+        run_groups<MODE, true>(g, acc, words, a, gp, ng, mt.bit_base, lane, cls);
+      else
+        run_groups<MODE, false>(g, acc, words, a, gp, ng, mt.bit_base, lane, cls);
+      gp += 32ull * ng;
+    } else {
+      // a group that crosses a partition end, a partial last group, or a binary64 partition:
+      // each lane decodes its position from scratch
+      const uint64_t i = gp + lane;
+      if (i < wend) emit<MODE>(g, acc, i, value_at(g, words, saux, mt, i, q), vmask);
+      gp += 32;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_tilescan(const ScanArgs g) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Ctrl& ctl = *reinterpret_cast<Ctrl*>(smem_raw);
+  const uint32_t stride = g.c.stage_bytes + kAuxBytes;
+  unsigned char* stages = smem_raw + kCtrlBytes;
+  const uint64_t ntile = g.t_last - g.t_first + 1;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&ctl.full[s], 1);
+      mbar_init(&ctl.empty[s], kConsumerWarps);
+    }
+    ctl.abort = 0;
+    ctl.issued = 0;
+    mbar_fence_init();
+  }
+  if (threadIdx.x < kConsumerWarps) ctl.consumed[threadIdx.x] = 0;
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {
+    // producer: lanes fetch 32 descriptors at a time, lane 0 issues the copies in order
+    uint64_t it = 0;
+    bool stop = false;
+    for (uint64_t k0 = blockIdx.x; k0 < ntile && !stop; k0 += 32ull * gridDim.x) {
+      const uint64_t kk = k0 + (uint64_t)lane * gridDim.x;
+      TileDesc d = {};
+      if (kk < ntile) d = g.c.tiles[g.t_first + kk];
+      for (int j = 0; j < 32; j++) {
+        const uint64_t k = k0 + (uint64_t)j * gridDim.x;
+        if (k >= ntile) break;
+        const uint64_t p0 = __shfl_sync(0xffffffffu, d.p0, j);
+        const uint64_t g0 = __shfl_sync(0xffffffffu, d.g0, j);
+        const uint64_t vmin = __shfl_sync(0xffffffffu, d.vmin, j);
+        const uint64_t vmax = __shfl_sync(0xffffffffu, d.vmax, j);
+        const uint32_t np = __shfl_sync(0xffffffffu, d.np, j);
+        const uint32_t wbytes = __shfl_sync(0xffffffffu, d.wbytes, j);
+        const uint32_t bounds = __shfl_sync(0xffffffffu, d.bounds, j);
+        int ok = 1;
+        if (lane == 0) {
+          const int s = (int)(it % kStages);
+          if (it >= (uint64_t)kStages)
+            ok = mbar_wait_bounded(&ctl.empty[s], (uint32_t)(((it / kStages) - 1) & 1)) ? 1 : 0;
+          if (ok && *(volatile int*)&ctl.abort) ok = 0;
+          if (ok) {
+            TileMeta mt;
+            mt.p0 = p0;
+            mt.np = np;
+            mt.staged = np <= (uint32_t)kMaxP;
+            mt.bit_base = g0 * 8;
+            mt.skip = (MODE == kFilter && (g.flags & LECO_FILTER_PRUNE) && bounds &&
+                       (vmax < g.lo || vmin > g.hi)) ? 1u : 0u;
+            mt.pad = 0;
+            ctl.meta[s] = mt;
+            unsigned char* dst = stages + (size_t)s * stride;
+            const uint32_t abytes = (mt.staged && !mt.skip) ? np * 32u : 0u;
+            const uint32_t wb = mt.skip ? 0u : wbytes;
+            mbar_arrive_expect_tx(&ctl.full[s], wb + abytes);
+            if (wb) bulk_g2s(dst, reinterpret_cast<const char*>(g.c.words) + g0, wb, &ctl.full[s]);
+            if (abytes) bulk_g2s(dst + g.c.stage_bytes, g.c.aux + p0, abytes, &ctl.full[s]);
+            ctl.issued = it + 1;
+          } else {
+            atomicOr(g.c.status, kStatTimeout);
+            *(volatile int*)&ctl.abort = 1;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          stop = true;
+          break;
+        }
+        it++;
+      }
+    }
+  } else {
+    Acc acc;
+    uint64_t it = 0;
+    for (uint64_t k = blockIdx.x; k < ntile; k += gridDim.x, it++) {
+      const int s = (int)(it % kStages);
+      const bool ok = mbar_wait_bounded(&ctl.full[s], (uint32_t)((it / kStages) & 1));
+      if (!ok || *(volatile int*)&ctl.abort) {
+        if (lane == 0) {
+          atomicOr(g.c.status, kStatTimeout);
+          *(volatile int*)&ctl.abort = 1;
+        }
+        break;
+      }
+      const TileMeta mt = ctl.meta[s];
+      if (!mt.skip) {
+        const unsigned char* base = stages + (size_t)s * stride;
+        process_tile<MODE>(g, g.t_first + k, mt, reinterpret_cast<const uint32_t*>(base),
+                           reinterpret_cast<const Aux*>(base + g.c.stage_bytes), acc);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&ctl.empty[s]);
+        ctl.consumed[warp] = it + 1;
+      }
+    }
+    if (MODE == kFilter) {
+      uint64_t cnt = warp_sum_u64(acc.cnt);
+      uint64_t lo = acc.lo, hi = acc.hi;
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const uint64_t h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const uint64_t nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+      }
+      if (lane == 0) {
+        ctl.red[0][warp] = cnt;
+        ctl.red[1][warp] = lo;
+        ctl.red[2][warp] = hi;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (ctl.abort) {
+      // a wait gave up: drain (bounded) the copies this CTA issued but nobody consumed
+      uint64_t done = ctl.issued;
+      for (int w = 0; w < kConsumerWarps; w++) done = min(done, ctl.consumed[w]);
+      for (uint64_t u = done; u < ctl.issued; u++)
+        mbar_wait_bounded(&ctl.full[u % kStages], (uint32_t)((u / kStages) & 1), 100000000ull);
+    } else if (MODE == kFilter) {
+      uint64_t tc = 0, tl = 0, th = 0;
+      for (int w = 0; w < kConsumerWarps; w++) {
+        tc += ctl.red[0][w];
+        const uint64_t nl = tl + ctl.red[1][w];
+        th += ctl.red[2][w] + (nl < tl ? 1ull : 0ull);
+        tl = nl;
+      }
+      if (tc) {
+        atomicAdd((unsigned long long*)&g.res->count, (unsigned long long)tc);
+        const unsigned long long old = atomicAdd((unsigned long long*)&g.res->sum_lo, (unsigned long long)tl);
+        const uint64_t carry = (old + tl < old) ? 1ull : 0ull;
+        if (th + carry) atomicAdd((unsigned long long*)&g.res->sum_hi, (unsigned long long)(th + carry));
+      }
+    }
+  }
+}
+
+// one descriptor per tile: partitions, 16-byte-aligned word range, model value bounds
+__global__ void k_tile_desc(const ColumnView c, TileDesc* __restrict__ tiles) {
+  const uint64_t nt = scan_tiles(c.n);
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = t * kScanTile, i1 = min(i0 + kScanTile, c.n);
+    const uint64_t p0 = part_of(c, i0, 0, c.m);
+    const uint64_t p1 = part_of(c, i1 - 1, p0, c.m);
+    const Aux a0 = ldg_aux(c.aux + p0);
+    const Aux a1 = ldg_aux(c.aux + p1);
+    const uint64_t bstart = w3_off(a0.word3) + (uint64_t)w3_b(a0.word3) * (i0 - a0.start);
+    const uint64_t bend = w3_off(a1.word3) + (uint64_t)w3_b(a1.word3) * (i1 - a1.start);
+    const uint64_t g0 = (bstart >> 7) << 4;
+    const uint64_t g1 = ((bend + 64 + 127) >> 7) << 4;  // one extra 64-bit word for funnel reads
+    TileDesc d;
+    d.p0 = p0;
+    d.np = (uint32_t)(p1 - p0 + 1);
+    d.g0 = g0;
+    d.wbytes = (uint32_t)(g1 - g0);
+    d.pad = 0;
+    uint64_t vmin = ~0ull, vmax = 0;
+    bool ok = true;
+    for (uint64_t p = p0; p <= p1 && ok; p++) {
+      const Aux a = p == p0 ? a0 : (p == p1 ? a1 : ldg_aux(c.aux + p));
+      const uint64_t ps = max(i0, a.start);
+      const uint64_t pe = min(i1, pstart(c, p + 1));
+      uint64_t lo = 0, hi = 0;
+      ok = part_bounds(c.dtype, a, ps - a.start, pe - 1 - a.start, &lo, &hi);
+      vmin = min(vmin, lo);
+      vmax = max(vmax, hi);
+    }
+    d.bounds = ok ? 1u : 0u;
+    d.vmin = ok ? vmin : 0;
+    d.vmax = ok ? vmax : ~0ull;
+    tiles[t] = d;
+  }
+}
+
+template <int MODE>
+int blocks_per_sm(uint32_t smem) {
+  cudaFuncSetAttribute(k_tilescan<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tilescan<MODE>, kThreads, smem);
+  return nb > 0 ? nb : 1;
+}
+
+template <int MODE>
+cudaError_t launch_scan(const ScanArgs& g, cudaStream_t st) {
+  const uint64_t ntile = g.t_last - g.t_first + 1;
+  const uint32_t smem = kCtrlBytes + kStages * (g.c.stage_bytes + kAuxBytes);
+  const uint64_t cap = (uint64_t)sm_count() * blocks_per_sm<MODE>(smem);
+  const unsigned grid = (unsigned)(ntile < cap ? ntile : cap);
+  k_tilescan<MODE><<<grid, kThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st) {
+  const uint64_t nt = scan_tiles(c.n);
+  if (nt == 0) return cudaSuccess;
+  const uint64_t want = (nt + 127) / 128, cap = (uint64_t)sm_count() * 8;
+  k_tile_desc<<<(int)(want < cap ? want : cap), 128, 0, st>>>(c, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
+                          cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  ScanArgs g;
+  g.c = c;
+  g.begin = begin;
+  g.end = begin + count;
+  g.t_first = begin / kScanTile;
+  g.t_last = (begin + count - 1) / kScanTile;
+  g.out = out;
+  g.lo = g.hi = 0;
+  g.flags = 0;
+  g.res = nullptr;
+  return c.dtype == LECO_U32 ? launch_scan<kDecode32>(g, st) : launch_scan<kDecode64>(g, st);
+}
+
+cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
+                              leco_sum_result* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(leco_sum_result), st);
+  if (e != cudaSuccess || c.n == 0 || lo > hi) return e;
+  ScanArgs g;
+  g.c = c;
+  g.begin = 0;
+  g.end = c.n;
+  g.t_first = 0;
+  g.t_last = (c.n - 1) / kScanTile;
+  g.out = nullptr;
+  g.lo = lo;
+  g.hi = hi;
+  g.flags = flags;
+  g.res = out;
+  return launch_scan<kFilter>(g, st);
+}
+
+}  // namespace leco

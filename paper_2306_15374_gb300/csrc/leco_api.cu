@@ -25,7 +25,10 @@ struct leco_column {
   Record* rec = nullptr;
   Aux* aux = nullptr;
   uint64_t* starts = nullptr;  // variable only
+  TileDesc* tiles = nullptr;   // scan tile descriptors
   uint32_t* status = nullptr;
+  uint32_t max_b = 0;          // widest partition
+  uint32_t stage_bytes = 0;    // shared-memory bytes per staged scan tile
   uint64_t* words = nullptr;
   void* meta_block = nullptr;
   uint64_t meta_bytes = 0;
@@ -59,6 +62,8 @@ ColumnView view_of(const leco_column* c) {
   v.aux = c->aux;
   v.words = c->words;
   v.starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
+  v.tiles = c->tiles;
+  v.stage_bytes = c->stage_bytes;
   v.status = c->status;
   return v;
 }
@@ -67,7 +72,8 @@ ColumnView view_of(const leco_column* c) {
 leco_status alloc_meta(leco_column* c, cudaStream_t st) {
   const uint64_t rec_b = align256(32 * (c->m ? c->m : 1));
   const uint64_t starts_b = c->kind == LECO_PART_VAR ? align256(8 * (c->m + 1)) : 0;
-  c->meta_bytes = 2 * rec_b + starts_b + 256;
+  const uint64_t tiles_b = align256(sizeof(TileDesc) * (scan_tiles(c->n) + 1));
+  c->meta_bytes = 2 * rec_b + starts_b + tiles_b + 256;
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, c->meta_bytes, st);
   if (e != cudaSuccess) return from_cuda(e);
@@ -76,7 +82,8 @@ leco_status alloc_meta(leco_column* c, cudaStream_t st) {
   c->rec = (Record*)b;
   c->aux = (Aux*)(b + rec_b);
   c->starts = starts_b ? (uint64_t*)(b + 2 * rec_b) : nullptr;
-  c->status = (uint32_t*)(b + 2 * rec_b + starts_b);
+  c->tiles = (TileDesc*)(b + 2 * rec_b + starts_b);
+  c->status = (uint32_t*)(b + 2 * rec_b + starts_b + tiles_b);
   return from_cuda(cudaMemsetAsync(c->status, 0, 256, st));
 }
 
@@ -90,28 +97,33 @@ void release(leco_column* c, cudaStream_t st) {
 // fit + offsets + pack of an already partitioned column (c->m, c->starts or c->L set)
 leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t st) {
   const uint64_t m = c->m;
-  const uint64_t scr_elems = m + offsets_scratch_elems(m) + 1;
+  const uint64_t scr_elems = m + offsets_scratch_elems(m) + 2;
   uint64_t* scr = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&scr, scr_elems * 8, st);
   if (e != cudaSuccess) return from_cuda(e);
   uint64_t* lenbits = scr;
   uint64_t* off_scr = scr + m;
-  uint64_t* d_total = scr + scr_elems - 1;
+  uint64_t* d_total = scr + scr_elems - 2;  // [total bits, max width]
+  uint32_t* d_maxb = reinterpret_cast<uint32_t*>(scr + scr_elems - 1);
   const uint64_t* starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
-  uint64_t total = 0;
-  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, st);
+  uint64_t hres[2] = {0, 0};
+  uint64_t& total = hres[0];
+  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, d_maxb, st);
   if (e == cudaSuccess)
     e = launch_offsets(c->rec, lenbits, m, off_scr, offsets_scratch_elems(m), d_total, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hres, d_total, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && total >= (1ull << 48)) e = cudaErrorInvalidValue;
   if (e == cudaSuccess) {
     c->total_bits = total;
+    c->max_b = (uint32_t)hres[1];
+    c->stage_bytes = stage_word_bytes(c->max_b);
     c->nwords = stream_words(total);
     c->words_bytes = c->nwords * 8;
     e = cudaMallocAsync((void**)&c->words, c->words_bytes, st);
   }
   if (e == cudaSuccess) e = launch_build_aux(c->rec, m, c->n, c->aux, c->status, st);
+  if (e == cudaSuccess) e = launch_tile_desc(view_of(c), c->tiles, st);
   if (e == cudaSuccess)
     e = launch_pack(d_values, c->dtype, c->rec, c->aux, m, c->n, total, c->words, c->nwords, st);
   cudaFreeAsync(scr, st);
@@ -343,7 +355,7 @@ leco_status leco_random_access(const leco_column* col, const uint64_t* d_idx, ui
 
 leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, uint32_t flags,
                             leco_sum_result* d_out, leco_stream_t stream) {
-  if (!col || !d_out || (flags & ~LECO_FILTER_PRUNE)) return LECO_ERR_INVALID_ARG;
+  if (!col || !d_out || (flags & ~(LECO_FILTER_PRUNE | LECO_FILTER_DECODE_ALL))) return LECO_ERR_INVALID_ARG;
   return from_cuda(launch_filter_sum(view_of(col), lo, hi, flags, d_out, (cudaStream_t)stream));
 }
 
@@ -476,6 +488,8 @@ leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t
   c->L = h.kind == LECO_PART_FIXED ? h.L : 0;
   c->tau = h.tau;
   c->home = st;
+  for (uint64_t p = 0; p < h.m; p++) c->max_b = c->max_b > w3_b(rec[p].word3) ? c->max_b : w3_b(rec[p].word3);
+  c->stage_bytes = stage_word_bytes(c->max_b);
   cudaGetDevice(&c->device);
   leco_status s = alloc_meta(c, st);
   if (s == LECO_OK) {
@@ -489,6 +503,7 @@ leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t
   if (s == LECO_OK)
     s = from_cuda(cudaMemcpyAsync(c->words, words.data(), 8 * h.nwords, cudaMemcpyHostToDevice, st));
   if (s == LECO_OK) s = from_cuda(launch_build_aux(c->rec, c->m, c->n, c->aux, c->status, st));
+  if (s == LECO_OK) s = from_cuda(launch_tile_desc(view_of(c), c->tiles, st));
   // the host vectors die at return: finish the copies first
   if (s == LECO_OK) s = from_cuda(cudaStreamSynchronize(st));
   if (s != LECO_OK) {

@@ -36,6 +36,32 @@ struct Aux {
 };
 static_assert(sizeof(Aux) == 32, "aux layout");
 
+// Scan tiles: tile t covers positions [t kScanTile, (t+1) kScanTile). Positions are encoded in order
+// with dense bit offsets, so a tile's residuals are one contiguous bit range; its descriptor is
+// built once per column and names the 16-byte-aligned word range to stage and the tile's value
+// bounds under the models (used to skip groups and, with pruning, whole tiles).
+constexpr uint64_t kScanTile = 4096;
+
+struct TileDesc {
+  uint64_t p0;      // first partition touching the tile
+  uint64_t g0;      // byte offset of the staged word range in the residual stream (16-aligned)
+  uint64_t vmin;    // every value of the tile lies in [vmin, vmax] (unsigned) when bounds == 1
+  uint64_t vmax;
+  uint32_t np;      // partitions touching the tile
+  uint32_t wbytes;  // bytes of the staged word range (multiple of 16)
+  uint32_t bounds;  // 1: [vmin, vmax] is valid
+  uint32_t pad;
+};
+static_assert(sizeof(TileDesc) == 48, "tile descriptor layout");
+
+__host__ __device__ __forceinline__ uint64_t scan_tiles(uint64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+// shared-memory bytes of one staged word range when no partition is wider than max_b bits
+__host__ __device__ __forceinline__ uint32_t stage_word_bytes(uint32_t max_b) {
+  const uint64_t bytes = kScanTile * (uint64_t)max_b / 8 + 64;
+  return (uint32_t)((bytes + 15) & ~15ull);
+}
+
 // status word bits (device)
 enum : uint32_t { kStatIndexRange = 1u, kStatCorrupt = 2u, kStatTimeout = 4u };
 
@@ -160,13 +186,15 @@ struct ColumnView {
   const Aux* aux;
   const uint64_t* words;
   const uint64_t* starts;      // variable: m+1 entries; fixed: nullptr
+  const TileDesc* tiles;       // scan_tiles(n) descriptors
+  uint32_t stage_bytes;        // stage_word_bytes(max width of the column)
   uint32_t* status;
 };
 
 // encode pipeline (k_encode.cu)
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
                        uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
-                       cudaStream_t st);
+                       uint32_t* max_b, cudaStream_t st);
 cudaError_t launch_offsets(Record* rec, const uint64_t* lenbits, uint64_t m, uint64_t* scratch,
                            uint64_t scratch_elems, uint64_t* total_out, cudaStream_t st);
 uint64_t offsets_scratch_elems(uint64_t m);
@@ -176,7 +204,8 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
                         uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
                         uint64_t nwords, cudaStream_t st);
 
-// decode family (k_decode.cu)
+// scans (k_scan.cu) and lookups (k_decode.cu)
+cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st);
 cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
                           cudaStream_t st);
 cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,

@@ -29,6 +29,7 @@ LECO_MODEL_LINEAR = 1
 LECO_PART_FIXED = 0
 LECO_PART_VAR = 1
 LECO_FILTER_PRUNE = 1
+LECO_FILTER_DECODE_ALL = 2
 
 
 class LecoError(RuntimeError):

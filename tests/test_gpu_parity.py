@@ -105,10 +105,12 @@ def test_decode_range_lookup_filter(lc, case):
     res = torch.zeros(3, dtype=torch.int64, device="cuda")
     bounds = [W.filter_bounds(v), (0, (1 << 64) - 1), (5, 4), (int(v[n // 2]), int(v[n // 2]))]
     for lo, hi in bounds:
-        lc.leco_filter_sum(col, lo, hi, res)
-        r = from_dev(res)
-        got = (int(r[0]), int(r[1]) | (int(r[2]) << 64))
-        assert got == oracle.filter_sum(rec, words, n, lo, hi, bits) == exact_sum(v, lo, hi)
+        want = oracle.filter_sum(rec, words, n, lo, hi, bits)
+        assert want == exact_sum(v, lo, hi)
+        for flags in (0, lc.LECO_FILTER_PRUNE, lc.LECO_FILTER_DECODE_ALL, 3):
+            lc.leco_filter_sum(col, lo, hi, res, flags=flags)
+            r = from_dev(res)
+            assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == want, flags
 
 
 def test_out_of_range_lookup_sets_status(lc):
@@ -241,9 +243,17 @@ def test_var_column_parity(lc, case):
     assert (from_dev(o2) == v[idx]).all()
     res = torch.zeros(3, dtype=torch.int64, device="cuda")
     lo, hi = W.filter_bounds(v)
-    lc.leco_filter_sum(col, lo, hi, res)
-    r = from_dev(res)
-    assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == exact_sum(v, lo, hi)
+    for flags in (0, lc.LECO_FILTER_PRUNE, lc.LECO_FILTER_DECODE_ALL):
+        lc.leco_filter_sum(col, lo, hi, res, flags=flags)
+        r = from_dev(res)
+        assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == exact_sum(v, lo, hi)
+    # ranges crossing partition and tile boundaries
+    g = W.rng(5)
+    for _ in range(10):
+        a, b = sorted(int(x) for x in g.integers(0, n + 1, size=2))
+        o3 = torch.empty(max(b - a, 1), dtype=tdt, device="cuda")
+        lc.leco_decode_range(col, a, b - a, o3)
+        assert (from_dev(o3)[: b - a] == v[a:b]).all()
     # the blob of a variable column round-trips as well
     col2 = lc.leco_deserialize(lc.leco_serialize(col))
     lc.leco_decode_all(col2, out)
@@ -289,7 +299,9 @@ def test_full_size_cfg2(lc, dist):
     assert (from_dev(o2) == v[idx]).all()
     res = torch.zeros(3, dtype=torch.int64, device="cuda")
     lo, hi = W.filter_bounds(v)
-    lc.leco_filter_sum(col, lo, hi, res)
-    r = from_dev(res)
-    assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == exact_sum(v, lo, hi)
+    want = exact_sum(v, lo, hi)
+    for flags in (0, lc.LECO_FILTER_PRUNE, lc.LECO_FILTER_DECODE_ALL):
+        lc.leco_filter_sum(col, lo, hi, res, flags=flags)
+        r = from_dev(res)
+        assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == want
     assert lc.leco_sync(col) == lc.LECO_OK
