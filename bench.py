@@ -45,6 +45,10 @@ def parse_args():
     ap.add_argument("--sample-every", type=int, default=100, help="CPU sample: every k-th partition")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["fix", "var"], default="fix",
+                    help="fix: the 3 x 200M fixed-partition columns (default); var: the variable-partition "
+                         "columns (200M piecewise-linear uint64, 500M uint32 timestamps)")
+    ap.add_argument("--tau", type=float, default=0.03)
     return ap.parse_args()
 
 
@@ -431,8 +435,90 @@ def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
             "h2d_bytes_per_step": 3 * 8 * k, "d2h_bytes_per_step": 3 * (8 * n + 8 * k + 24)}
 
 
+def run_var(args):
+    """Variable partitions: GPU split/merge + encode (timed once per column), then decode, filter-sum
+    and 10M lookups per column, reported per op (not the default workload)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2306_15374_gb300 as pkg
+
+    pkg.build()
+    from paper_2306_15374_gb300 import leco
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    n_a = args.n
+    n_b = int(args.n * 2.5)
+    specs = [("piecewise_u64", lambda: W.cfg3("a", n_a), 64), ("timestamps_u32", lambda: W.cfg3("b", n_b), 32)]
+    k = args.lookups
+    out = {}
+    for name, gen, bits in specs:
+        v = gen()
+        n = len(v)
+        if bits == 32:
+            dv = torch.from_numpy(v.astype(np.uint32).view(np.int32)).to(dev)
+        else:
+            dv = torch.from_numpy(v.view(np.int64)).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        col = leco.leco_encode(dv, leco.variable(args.tau), leco.LECO_MODEL_LINEAR)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        enc_ms = e0.elapsed_time(e1)
+        fix = leco.leco_encode(dv, leco.fixed(4096), leco.LECO_MODEL_LINEAR)
+        st, stf = col.stats(), fix.stats()
+        comp = st["record_bytes"] + st["residual_bytes"] + 8 * (st["partitions"] + 1)
+        tdt = torch.int32 if bits == 32 else torch.int64
+        o = torch.empty(n, dtype=tdt, device=dev)
+        idx = torch.from_numpy(W.uniform_indices(k, n, seed=11).view(np.int64)).to(dev)
+        ok_ = torch.empty(k, dtype=tdt, device=dev)
+        res = torch.zeros(3, dtype=torch.int64, device=dev)
+        lo, hi = W.filter_bounds(v)
+        reps = max(3, min(args.steps, 50))
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        t_dec = timed(lambda: leco.leco_decode_all(col, o))
+        ok = bool(torch.equal(o, dv))
+        t_fil = timed(lambda: leco.leco_filter_sum(col, lo, hi, res))
+        t_pru = timed(lambda: leco.leco_filter_sum(col, lo, hi, res, flags=leco.LECO_FILTER_PRUNE))
+        t_ra = timed(lambda: leco.leco_random_access(col, idx, ok_))
+        peak, _ = measured_peaks()
+        vb = bits // 8
+        out[name] = {
+            "n": n, "partitions": st["partitions"], "ratio": comp / (n * vb), "ratio_fixed_4096": stf["ratio"],
+            "partition_encode_ms": enc_ms, "partition_encode_gbs": (n * vb + comp) / (enc_ms * 1e-3) / 1e9,
+            "decode_ms": t_dec, "decode_gbs": (comp + n * vb) / (t_dec * 1e-3) / 1e9,
+            "decode_frac_hbm": (comp + n * vb) / (t_dec * 1e-3) / 1e9 / peak, "decode_equals_input": ok,
+            "filter_ms": t_fil, "filter_gbs": (comp + 24) / (t_fil * 1e-3) / 1e9,
+            "filter_prune_ms": t_pru, "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6,
+        }
+        for c in (col, fix):
+            c.free()
+        del dv, o
+    print(json.dumps({"workload": "LeCo-var tau=%g: 200M piecewise-linear uint64, 500M uint32 timestamps" % args.tau,
+                      "results": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "var" and args.impl != "reference":
+        return run_var(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_leco(args)

@@ -34,7 +34,7 @@ struct TileMeta {
   uint32_t np;
   uint32_t staged;    // decode-table entries p0 .. p0+np-1 are in shared memory
   uint32_t skip;      // pruned: nothing was copied
-  uint32_t pad;
+  uint32_t cls;       // filter: 1 = the tile misses [lo, hi], 2 = lies inside it, 0 = undecided
 };
 
 struct Ctrl {
@@ -90,27 +90,23 @@ __device__ __forceinline__ Aux ldg_aux(const Aux* a) {
 }
 
 // Model bounds of positions [x0, x1] of a partition: prediction at both ends (monotone in x) +- the
-// residual range of width b. False for a binary64 partition or bounds that wrap the value domain.
+// residual range [-2^(b-1), 2^(b-1) - 1] of width b. False for a binary64 partition, b > 62, or
+// bounds that would leave the value domain (wrap-around).
 __device__ __forceinline__ bool part_bounds(int dtype, const Aux& a, uint64_t x0, uint64_t x1,
                                             uint64_t* vlo_out, uint64_t* vhi_out) {
-  if (!w3_exact(a.word3)) return false;
+  const uint32_t b = w3_b(a.word3);
+  if (!w3_exact(a.word3) || b > 62) return false;
   int32_t sh = w3_s(a.word3);
-  sh = sh > 0 ? sh : 0;
+  sh = (sh > 0 ? sh : 0) & 63;
   int64_t p0v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x0) >> sh;
   int64_t p1v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x1) >> sh;
-  if (p0v > p1v) {
-    const int64_t t = p0v;
-    p0v = p1v;
-    p1v = t;
-  }
-  const uint32_t b = w3_b(a.word3);
-  const i128 rneg = b == 0 ? 0 : -((i128)1 << (b - 1));
-  const i128 rpos = b == 0 ? 0 : (((i128)1 << (b - 1)) - 1);
-  const i128 vlo = (i128)p0v + rneg, vhi = (i128)p1v + rpos;
-  const i128 top = dtype == LECO_U32 ? ((i128)1 << 32) : ((i128)1 << 64);
-  if (vlo < 0 || vhi >= top) return false;
-  *vlo_out = (uint64_t)vlo;
-  *vhi_out = (uint64_t)vhi;
+  const int64_t pmin = p0v < p1v ? p0v : p1v, pmax = p0v < p1v ? p1v : p0v;
+  const int64_t half = b ? (int64_t)1 << (b - 1) : 0;
+  if (pmin < half) return false;  // the lower bound would drop below zero
+  const uint64_t vhi = (uint64_t)pmax + (uint64_t)(half ? half - 1 : 0);
+  if (dtype == LECO_U32 && vhi > 0xFFFFFFFFull) return false;
+  *vlo_out = (uint64_t)(pmin - half);
+  *vhi_out = vhi;
   return true;
 }
 
@@ -269,8 +265,8 @@ __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, 
     const uint64_t run_end = min(qend, wend);
     const uint32_t ng = (uint32_t)((run_end - gp) >> 5);
     if (ng && w3_exact(a.word3)) {
-      int cls = 0;
-      if (MODE == kFilter && !(g.flags & LECO_FILTER_DECODE_ALL)) {
+      int cls = (int)mt.cls;
+      if (MODE == kFilter && cls == 0 && !(g.flags & LECO_FILTER_DECODE_ALL)) {
         uint64_t vlo = 0, vhi = 0;
         const bool ok = part_bounds(c.dtype, a, gp - a.start, gp + 32ull * ng - 1 - a.start, &vlo, &vhi);
         cls = classify(ok, vlo, vhi, g.lo, g.hi);
@@ -344,9 +340,10 @@ __global__ void __launch_bounds__(kThreads) k_tilescan(const ScanArgs g) {
             mt.np = np;
             mt.staged = np <= (uint32_t)kMaxP;
             mt.bit_base = g0 * 8;
-            mt.skip = (MODE == kFilter && (g.flags & LECO_FILTER_PRUNE) && bounds &&
-                       (vmax < g.lo || vmin > g.hi)) ? 1u : 0u;
-            mt.pad = 0;
+            mt.cls = 0;
+            if (MODE == kFilter && !(g.flags & LECO_FILTER_DECODE_ALL))
+              mt.cls = (uint32_t)classify(bounds != 0, vmin, vmax, g.lo, g.hi);
+            mt.skip = ((g.flags & LECO_FILTER_PRUNE) && mt.cls == 1) ? 1u : 0u;
             ctl.meta[s] = mt;
             unsigned char* dst = stages + (size_t)s * stride;
             const uint32_t abytes = (mt.staged && !mt.skip) ? np * 32u : 0u;
@@ -382,7 +379,7 @@ __global__ void __launch_bounds__(kThreads) k_tilescan(const ScanArgs g) {
         break;
       }
       const TileMeta mt = ctl.meta[s];
-      if (!mt.skip) {
+      if (!mt.skip && !(MODE == kFilter && mt.cls == 1)) {
         const unsigned char* base = stages + (size_t)s * stride;
         process_tile<MODE>(g, g.t_first + k, mt, reinterpret_cast<const uint32_t*>(base),
                            reinterpret_cast<const Aux*>(base + g.c.stage_bytes), acc);
