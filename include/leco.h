@@ -146,6 +146,26 @@ leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype
                                     const uint64_t* d_starts, uint64_t m, leco_model model,
                                     leco_stream_t stream, leco_column** out);
 
+/* Fixed-partition encode that allocates no device memory (the paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc, e.g. an engine whose device memory is all reserved by
+ * its own pool, or a path that cannot afford an allocation's implicit synchronization).
+ * Same records and residual words as leco_encode with policy fixed(L), written to caller buffers:
+ *   d_values   n values of dtype on the device (read only);
+ *   d_records  ceil(n / L) * 32 bytes on the device (the 32-byte records described above);
+ *   d_words    words_cap * 8 bytes on the device (the residual stream, padding included);
+ *   nwords_out host; receives the stream's word count, also when words_cap is too small.
+ * Scratch lives in a fixed 12.6 MB __device__ array that every GPU loading the library holds
+ * until exit; ceil(n / L) must not exceed 2^18 (INVALID_ARG otherwise). The first call on a
+ * device looks up that array's device address (make it before any stream capture). All calls on
+ * a device share the array, so calls whose GPU work overlaps (e.g. on different streams) race;
+ * nothing of it needs clearing between calls. The call synchronizes `stream` once to size the
+ * stream; INVALID_ARG when words_cap < *nwords_out (nothing packed then), CUDA on a runtime
+ * failure. No cudaMalloc, cudaFree or allocating library routine is called. */
+leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t n, leco_dtype dtype, uint32_t L,
+                                      leco_model model, void* d_records, void* d_words,
+                                      uint64_t words_cap, uint64_t* nwords_out,
+                                      leco_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------ */
 /* Decode (§3.3 Decoder)
  *

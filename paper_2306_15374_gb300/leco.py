@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "leco_deserialize": (i32, [vp, u64, vp, col_pp]),
         "leco_column_free": (None, [vp]),
         "leco_column_free_async": (None, [vp, vp]),
+        "leco_encode_fixed_noalloc": (i32, [vp, u64, i32, u32, i32, vp, vp, u64, ctypes.POINTER(u64), vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -281,3 +282,21 @@ def leco_deserialize(blob: bytes, stream=None) -> Column:
 
 def leco_column_free(col: Column) -> None:
     col.free()
+
+
+def leco_encode_fixed_noalloc(values, L: int, records_out, words_out, model: int = LECO_MODEL_LINEAR,
+                              stream=None) -> int:
+    """Fixed-partition encode into caller buffers with no device allocation (see include/leco.h).
+    records_out: CUDA tensor of >= 32 * ceil(n / L) bytes; words_out: CUDA tensor whose byte size
+    / 8 is the word capacity. Returns the stream's word count; raises LecoError (INVALID_ARG) when
+    the capacity is too small, with the needed count in the exception's .nwords."""
+    nw = ctypes.c_uint64(0)
+    cap = words_out.numel() * words_out.element_size() // 8
+    st = lib().leco_encode_fixed_noalloc(_dev(values), values.numel(), _dtype_of(values), int(L), model,
+                                         _dev(records_out), _dev(words_out), cap, ctypes.byref(nw),
+                                         _stream(stream))
+    if st != LECO_OK:
+        err = LecoError(st, "leco_encode_fixed_noalloc")
+        err.nwords = int(nw.value)
+        raise err
+    return int(nw.value)
