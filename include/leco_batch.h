@@ -1,0 +1,80 @@
+/*
+ * leco_batch.h — batched and tuned forms of the GB300 LeCo library (libleco.so).
+ *
+ * The paper decodes one column at a time on one CPU thread (§4.2); these calls are this library's
+ * systems layer around the same per-value decode of §3.3: many columns of uneven lengths decoded
+ * by one persistent kernel launch (optionally a CUDA graph), and an autotuner that picks the scan
+ * pipeline's shape. Conventions (device pointers, streams, ownership, errors) are those of leco.h.
+ */
+#ifndef LECO_BATCH_H
+#define LECO_BATCH_H
+
+#include "leco.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Shape of the scan pipeline: shared-memory stages in flight per CTA (2..8) and consumer warps
+ * (4 or 8); ms is the measured time of the chosen configuration (leco_tune_scan only). */
+typedef struct {
+  uint32_t stages;
+  uint32_t consumer_warps;
+  double ms;
+} leco_scan_config;
+
+/* Time every candidate configuration of the scan on this column (op 0: leco_decode_all; op 1:
+ * leco_filter_sum over [lo, hi] with flags 0), keep the fastest in the process-wide tuning table
+ * (keyed by op, value width and the column's widest partition), and return it in *best. Later
+ * decodes and filter-sums of columns in the same key use it. Synchronizes `stream`; allocates a
+ * temporary decode output. Errors: INVALID_ARG, OOM, CUDA. */
+leco_status leco_tune_scan(const leco_column* col, uint32_t op, uint64_t lo, uint64_t hi,
+                           leco_stream_t stream, leco_scan_config* best);
+
+/* Write / read the tuning table as JSON (host file path). */
+leco_status leco_tune_save(const char* path);
+leco_status leco_tune_load(const char* path);
+
+/* A prepared multi-column decode: every scan tile of every column becomes one job of a work
+ * table on the device, so all columns decode in one persistent kernel launch. d_outs[c] receives
+ * all values of cols[c] (n * value bytes, caller-owned, device). Columns may mix 32- and 64-bit
+ * values and partition kinds; all must live on the current device. The plan owns its tables and
+ * must be freed with leco_batch_plan_free; the columns must outlive it. */
+typedef struct leco_batch_plan leco_batch_plan;
+
+leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* d_outs, uint32_t ncols,
+                                   leco_batch_plan** out);
+
+/* One kernel launch on `stream` decoding every column of the plan. */
+leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream);
+
+/* The same launch as a CUDA graph: the first call captures it (on a private stream) and
+ * instantiates the graph; every call launches the graph on `stream`. */
+leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream);
+
+/* Number of jobs (scan tiles) in the plan. */
+uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan);
+
+/* Waits for the device, then releases the plan's tables and graph. NULL is ignored. */
+void leco_batch_plan_free(leco_batch_plan* plan);
+
+/* create + run + free in one call (synchronizes `stream` before freeing). */
+leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_outs, uint32_t ncols,
+                              leco_stream_t stream);
+
+/* Fixed-partition encode of ncols columns at once (§3.2.1 partitions, §3.1 fit, §3.3 packing):
+ * column c has n[c] values of `dtype` at d_vals[c] (device), model models[c] and partition size
+ * L[c] (1 .. 2^24). Every stage runs over all columns in one launch (fit, offset scan, decode
+ * table, tile descriptors, pack); one stream synchronization sizes the residual streams. out[c]
+ * receives a column identical to leco_encode(d_vals[c], n[c], dtype, fixed(L[c]), models[c]);
+ * the columns share their device blocks, which are released when the last of them is freed.
+ * Errors: INVALID_ARG, OOM, CUDA (then no column is returned). */
+leco_status leco_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                              const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
+                              leco_column** out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LECO_BATCH_H */

@@ -140,12 +140,8 @@ __global__ void k_set_offsets(Record* __restrict__ rec, const uint64_t* __restri
 // Verify the exact flag of each record and derive the grid integers; a record that does not pass
 // keeps the binary64 path (the definition), so a foreign or damaged header can never decode
 // differently from the prediction it states.
-__global__ void k_build_aux(const Record* __restrict__ rec, uint64_t m, uint64_t n, Aux* __restrict__ aux) {
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
-       p += (uint64_t)gridDim.x * blockDim.x) {
-    const Record r = rec[p];
-    const uint64_t e = p + 1 < m ? rec[p + 1].start : n;
-    const uint64_t N = e > r.start ? e - r.start : 0;
+__device__ Aux aux_of(const Record& r, uint64_t N) {
+  {
     Aux a;
     a.start = r.start;
     a.A = 0;
@@ -178,7 +174,16 @@ __global__ void k_build_aux(const Record* __restrict__ rec, uint64_t m, uint64_t
       }
     }
     a.word3 = ok ? r.word3 : (r.word3 & ~(1ull << 62));
-    aux[p] = a;
+    return a;
+  }
+}
+
+__global__ void k_build_aux(const Record* __restrict__ rec, uint64_t m, uint64_t n, Aux* __restrict__ aux) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const Record r = rec[p];
+    const uint64_t e = p + 1 < m ? rec[p + 1].start : n;
+    aux[p] = aux_of(r, e > r.start ? e - r.start : 0);
   }
 }
 
@@ -187,17 +192,12 @@ __global__ void k_build_aux(const Record* __restrict__ rec, uint64_t m, uint64_t
 // Gather packing: thread per output word. The word's bits [64w, 64w+64) are filled from the
 // fields that overlap it (first partition by a search over the offsets), each field recomputed
 // from the input value and the partition's prediction. No atomics, no pre-zeroing.
-__global__ void __launch_bounds__(256)
-    k_pack(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
-           const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t total_bits,
-           uint64_t* __restrict__ words, uint64_t nwords) {
-  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
-       w += (uint64_t)gridDim.x * blockDim.x) {
+__device__ uint64_t pack_word(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
+                              const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t total_bits,
+                              uint64_t w) {
+  {
     const uint64_t bit0 = w * 64;
-    if (bit0 >= total_bits) {
-      words[w] = 0;
-      continue;
-    }
+    if (bit0 >= total_bits) return 0;
     uint64_t lo = 0, hi = m;  // largest p with off(p) <= bit0
     while (hi - lo > 1) {
       const uint64_t mid = (lo + hi) >> 1;
@@ -229,7 +229,83 @@ __global__ void __launch_bounds__(256)
       }
       if (x < N) break;
     }
-    words[w] = acc;
+    return acc;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_pack(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
+           const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t total_bits,
+           uint64_t* __restrict__ words, uint64_t nwords) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
+       w += (uint64_t)gridDim.x * blockDim.x)
+    words[w] = pack_word(values, dtype, rec, aux, m, n, total_bits, w);
+}
+
+// ------------------------------------------------------------------------------ batched encode
+
+// CTA per partition of every column: the partition's column by a search over part_base
+__global__ void __launch_bounds__(kFitBlock)
+    k_fit_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base, uint32_t ncols,
+                uint64_t P, int dtype, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
+                uint32_t* __restrict__ max_b) {
+  __shared__ FitShared sm;
+  for (uint64_t p = blockIdx.x; p < P; p += gridDim.x) {
+    const uint32_t c = find_col(part_base, ncols, p);
+    const EncCol col = cols[c];
+    const uint64_t a = (p - part_base[c]) * (uint64_t)col.L;
+    const uint64_t e = a + col.L < col.n ? a + col.L : col.n;
+    const uint32_t N = (uint32_t)(e - a);
+    const FitResult R = fit_range<kFitBlock>(col.values, dtype, a, N, col.model, threadIdx.x, &sm);
+    if (threadIdx.x == 0) {
+      Record r;
+      r.theta0 = R.theta0;
+      r.theta1 = R.theta1;
+      r.start = a;
+      r.word3 = make_w3(0, R.b, R.s, 1);
+      rec[p] = r;
+      lenbits[p] = (uint64_t)N * R.b;
+      if (R.b) atomicMax(max_b + c, R.b);
+    }
+  }
+}
+
+// column-relative offsets from the global exclusive scan, and each column's total bits
+__global__ void k_set_offsets_multi(Record* __restrict__ rec, const uint64_t* __restrict__ off,
+                                    const uint64_t* __restrict__ lenbits, const uint64_t* __restrict__ part_base,
+                                    uint32_t ncols, uint64_t P, uint64_t* __restrict__ col_bits) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = find_col(part_base, ncols, p);
+    const uint64_t base = off[part_base[c]];
+    rec[p].word3 = (rec[p].word3 & ~kOffMask) | ((off[p] - base) & kOffMask);
+    if (p + 1 == part_base[c + 1]) col_bits[c] = off[p] + lenbits[p] - base;
+  }
+}
+
+__global__ void k_aux_multi(const Record* __restrict__ rec, const EncCol* __restrict__ cols,
+                            const uint64_t* __restrict__ part_base, uint32_t ncols, uint64_t P,
+                            Aux* __restrict__ aux) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = find_col(part_base, ncols, p);
+    const Record r = rec[p];
+    const uint64_t e = p + 1 < part_base[c + 1] ? rec[p + 1].start : cols[c].n;
+    aux[p] = aux_of(r, e > r.start ? e - r.start : 0);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_pack_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
+                 const uint64_t* __restrict__ word_base, const uint64_t* __restrict__ col_bits, uint32_t ncols,
+                 uint64_t W, int dtype, const Record* __restrict__ rec, const Aux* __restrict__ aux,
+                 uint64_t* __restrict__ words) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < W;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = find_col(word_base, ncols, w);
+    const uint64_t p0 = part_base[c];
+    words[w] = pack_word(cols[c].values, dtype, rec + p0, aux + p0, part_base[c + 1] - p0, cols[c].n, col_bits[c],
+                         w - word_base[c]);
   }
 }
 
@@ -307,6 +383,46 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
   if (nwords == 0) return cudaSuccess;
   k_pack<<<grid_for(nwords, 256, 8), 256, 0, st>>>(values, dtype, rec, aux, m, n, total_bits, words,
                                                    nwords);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
+                             Record* rec, uint64_t* lenbits, uint32_t* max_b, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t) * (ncols ? ncols : 1), st);
+  if (e != cudaSuccess || P == 0) return e;
+  const uint64_t cap = (uint64_t)sm_count() * 16;
+  k_fit_multi<<<(int)(P < cap ? P : cap), kFitBlock, 0, st>>>(cols, part_base, ncols, P, dtype, rec, lenbits, max_b);
+  return cudaGetLastError();
+}
+
+uint64_t offsets_multi_scratch_elems(uint64_t P) { return P + (P + kPrefixTile - 1) / kPrefixTile + 2; }
+
+cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base, uint32_t ncols,
+                                 uint64_t P, uint64_t* scratch, uint64_t* col_bits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(col_bits, 0, sizeof(uint64_t) * (ncols ? ncols : 1), st);
+  if (e != cudaSuccess || P == 0) return e;
+  uint64_t* off = scratch;
+  uint64_t* tiles = scratch + P;
+  uint64_t* total = scratch + offsets_multi_scratch_elems(P) - 1;
+  e = scan_u64(lenbits, P, off, tiles, total, st);
+  if (e != cudaSuccess) return e;
+  k_set_offsets_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, off, lenbits, part_base, ncols, P, col_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aux_multi(const Record* rec, const EncCol* cols, const uint64_t* part_base, uint32_t ncols,
+                             uint64_t P, Aux* aux, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  k_aux_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, cols, part_base, ncols, P, aux);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
+                              const uint64_t* col_bits, uint32_t ncols, uint64_t W, int dtype, const Record* rec,
+                              const Aux* aux, uint64_t* words, cudaStream_t st) {
+  if (W == 0) return cudaSuccess;
+  k_pack_multi<<<grid_for(W, 256, 8), 256, 0, st>>>(cols, part_base, word_base, col_bits, ncols, W, dtype, rec, aux,
+                                                    words);
   return cudaGetLastError();
 }
 

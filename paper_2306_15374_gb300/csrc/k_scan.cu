@@ -12,6 +12,8 @@
 // by 32 B and 32 b per group. The filter bounds each 32-value group with its model (prediction at
 // both ends +- the residual range of width b) and decodes only groups that can meet [lo, hi].
 // Tile descriptors (word range, partitions, value bounds) are built once per column.
+#include <string.h>
+
 #include "leco_internal.cuh"
 #include "tma.cuh"
 
@@ -19,14 +21,12 @@ namespace leco {
 
 namespace {
 
-constexpr int kConsumerWarps = 8;
-constexpr int kThreads = (kConsumerWarps + 1) * 32;
-constexpr int kPerWarp = (int)kScanTile / kConsumerWarps;
-constexpr int kStages = 4;
+constexpr int kMaxStages = 8;
+constexpr int kMaxConsumerWarps = 8;
 constexpr int kMaxP = 64;
 constexpr uint32_t kAuxBytes = kMaxP * 32;
 
-enum Mode { kDecode64 = 0, kDecode32 = 1, kFilter = 2 };
+enum Mode { kDecode64 = 0, kDecode32 = 1, kFilter = 2, kDecodeAny = 3 };
 
 struct TileMeta {
   uint64_t p0;
@@ -37,27 +37,34 @@ struct TileMeta {
   uint32_t cls;       // filter: 1 = the tile misses [lo, hi], 2 = lies inside it, 0 = undecided
 };
 
-struct Ctrl {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  TileMeta meta[kStages];
-  uint64_t red[3][kConsumerWarps];
-  uint64_t issued;
-  uint64_t consumed[kConsumerWarps];
-  int abort;
-};
-
-constexpr uint32_t kCtrlBytes = (sizeof(Ctrl) + 127) & ~127u;
-
 struct ScanArgs {
   ColumnView c;
-  uint64_t begin, end;       // requested positions
+  uint64_t begin, end;       // positions to emit
   uint64_t t_first, t_last;  // tiles touching [begin, end)
-  void* out;                 // decode output (position i -> out[i - begin])
+  void* out;                 // decode output: position i -> out[i - begin]
   uint64_t lo, hi;           // filter range
   uint32_t flags;
   leco_sum_result* res;
 };
+
+// what a consumer needs for one staged tile (written by the producer into the stage's slot)
+struct Job {
+  TileMeta mt;
+  ScanArgs g;
+  uint64_t tile;
+};
+
+struct Ctrl {
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t red[3][kMaxConsumerWarps];
+  uint64_t issued;
+  uint64_t consumed[kMaxConsumerWarps];
+  int abort;
+  Job job[kMaxStages];
+};
+
+constexpr uint32_t kCtrlBytes = (sizeof(Ctrl) + 127) & ~127u;
 
 __device__ __forceinline__ uint64_t pstart(const ColumnView& c, uint64_t p) {
   if (c.starts) return __ldg(c.starts + p);
@@ -241,12 +248,12 @@ __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const ui
 
 template <int MODE>
 __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, const uint32_t* words,
-                             const Aux* saux, Acc& acc) {
+                             const Aux* saux, Acc& acc, uint32_t per_warp) {
   const ColumnView& c = g.c;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint64_t tile_base = t * kScanTile;
-  const uint64_t wbeg = max(g.begin, tile_base + (uint64_t)warp * kPerWarp);
-  const uint64_t wend = min(min(g.end, c.n), tile_base + (uint64_t)(warp + 1) * kPerWarp);
+  const uint64_t wbeg = max(g.begin, tile_base + (uint64_t)warp * per_warp);
+  const uint64_t wend = min(min(g.end, c.n), tile_base + (uint64_t)(warp + 1) * per_warp);
   const uint64_t vmask = c.dtype == LECO_U32 ? 0xFFFFFFFFull : ~0ull;
   const uint64_t last = mt.p0 + mt.np - 1;
   uint64_t q = mt.p0;
@@ -290,70 +297,78 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_tilescan(const ScanArgs g) {
+// Producer side for one job: the staged tile's metadata from its descriptor, plus the filter
+// classification (and pruning) for this range.
+__device__ __forceinline__ TileMeta meta_from(const TileDesc& d, int mode, const ScanArgs& g) {
+  TileMeta mt;
+  mt.p0 = d.p0;
+  mt.np = d.np;
+  mt.staged = d.np <= (uint32_t)kMaxP;
+  mt.bit_base = d.g0 * 8;
+  mt.cls = 0;
+  if (mode == kFilter && !(g.flags & LECO_FILTER_DECODE_ALL))
+    mt.cls = (uint32_t)classify(d.bounds != 0, d.vmin, d.vmax, g.lo, g.hi);
+  mt.skip = ((g.flags & LECO_FILTER_PRUNE) && mt.cls == 1) ? 1u : 0u;
+  return mt;
+}
+
+// Persistent scan. One producer warp (the last) and CW consumer warps; nst stages of stage_bytes
+// word bytes + the decode-table slot. MULTI: jobs come from a work table (column, tile, range,
+// output) over several columns; otherwise every tile of [g.begin, g.end) of the one column g.c.
+template <int MODE, int CW, bool MULTI>
+__global__ void __launch_bounds__((CW + 1) * 32)
+    k_tilescan(const ScanArgs g0, const ColumnView* __restrict__ cols, const BatchItem* __restrict__ items,
+               uint64_t nitems, uint32_t nst, uint32_t stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ctrl& ctl = *reinterpret_cast<Ctrl*>(smem_raw);
-  const uint32_t stride = g.c.stage_bytes + kAuxBytes;
+  const uint32_t stride = stage_bytes + kAuxBytes;
   unsigned char* stages = smem_raw + kCtrlBytes;
-  const uint64_t ntile = g.t_last - g.t_first + 1;
+  const uint64_t njobs = MULTI ? nitems : g0.t_last - g0.t_first + 1;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; s++) {
+    for (uint32_t s = 0; s < nst; s++) {
       mbar_init(&ctl.full[s], 1);
-      mbar_init(&ctl.empty[s], kConsumerWarps);
+      mbar_init(&ctl.empty[s], CW);
     }
     ctl.abort = 0;
     ctl.issued = 0;
     mbar_fence_init();
   }
-  if (threadIdx.x < kConsumerWarps) ctl.consumed[threadIdx.x] = 0;
+  if (threadIdx.x < CW) ctl.consumed[threadIdx.x] = 0;
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
-    // producer: lanes fetch 32 descriptors at a time, lane 0 issues the copies in order
+  if (warp == CW) {
+    // producer: the warp's lanes fetch 32 jobs' inputs at a time, lane 0 issues the copies in order
     uint64_t it = 0;
     bool stop = false;
-    for (uint64_t k0 = blockIdx.x; k0 < ntile && !stop; k0 += 32ull * gridDim.x) {
+    for (uint64_t k0 = blockIdx.x; k0 < njobs && !stop; k0 += 32ull * gridDim.x) {
       const uint64_t kk = k0 + (uint64_t)lane * gridDim.x;
+      ScanArgs mine = g0;
+      uint64_t tile = 0;
       TileDesc d = {};
-      if (kk < ntile) d = g.c.tiles[g.t_first + kk];
+      if (kk < njobs) {
+        if (MULTI) {
+          const BatchItem bi = items[kk];
+          mine.c = cols[bi.col];
+          mine.begin = bi.begin;
+          mine.end = bi.end;
+          mine.out = bi.out;
+          tile = bi.tile;
+        } else {
+          tile = g0.t_first + kk;
+        }
+        d = mine.c.tiles[tile];
+      }
       for (int j = 0; j < 32; j++) {
         const uint64_t k = k0 + (uint64_t)j * gridDim.x;
-        if (k >= ntile) break;
-        const uint64_t p0 = __shfl_sync(0xffffffffu, d.p0, j);
-        const uint64_t g0 = __shfl_sync(0xffffffffu, d.g0, j);
-        const uint64_t vmin = __shfl_sync(0xffffffffu, d.vmin, j);
-        const uint64_t vmax = __shfl_sync(0xffffffffu, d.vmax, j);
-        const uint32_t np = __shfl_sync(0xffffffffu, d.np, j);
-        const uint32_t wbytes = __shfl_sync(0xffffffffu, d.wbytes, j);
-        const uint32_t bounds = __shfl_sync(0xffffffffu, d.bounds, j);
+        if (k >= njobs) break;
+        const uint32_t s = (uint32_t)(it % nst);
         int ok = 1;
         if (lane == 0) {
-          const int s = (int)(it % kStages);
-          if (it >= (uint64_t)kStages)
-            ok = mbar_wait_bounded(&ctl.empty[s], (uint32_t)(((it / kStages) - 1) & 1)) ? 1 : 0;
+          if (it >= (uint64_t)nst) ok = mbar_wait_bounded(&ctl.empty[s], (uint32_t)(((it / nst) - 1) & 1)) ? 1 : 0;
           if (ok && *(volatile int*)&ctl.abort) ok = 0;
-          if (ok) {
-            TileMeta mt;
-            mt.p0 = p0;
-            mt.np = np;
-            mt.staged = np <= (uint32_t)kMaxP;
-            mt.bit_base = g0 * 8;
-            mt.cls = 0;
-            if (MODE == kFilter && !(g.flags & LECO_FILTER_DECODE_ALL))
-              mt.cls = (uint32_t)classify(bounds != 0, vmin, vmax, g.lo, g.hi);
-            mt.skip = ((g.flags & LECO_FILTER_PRUNE) && mt.cls == 1) ? 1u : 0u;
-            ctl.meta[s] = mt;
-            unsigned char* dst = stages + (size_t)s * stride;
-            const uint32_t abytes = (mt.staged && !mt.skip) ? np * 32u : 0u;
-            const uint32_t wb = mt.skip ? 0u : wbytes;
-            mbar_arrive_expect_tx(&ctl.full[s], wb + abytes);
-            if (wb) bulk_g2s(dst, reinterpret_cast<const char*>(g.c.words) + g0, wb, &ctl.full[s]);
-            if (abytes) bulk_g2s(dst + g.c.stage_bytes, g.c.aux + p0, abytes, &ctl.full[s]);
-            ctl.issued = it + 1;
-          } else {
-            atomicOr(g.c.status, kStatTimeout);
+          if (!ok) {
+            atomicOr(g0.c.status, kStatTimeout);
             *(volatile int*)&ctl.abort = 1;
           }
         }
@@ -362,27 +377,58 @@ __global__ void __launch_bounds__(kThreads) k_tilescan(const ScanArgs g) {
           stop = true;
           break;
         }
+        // lane j publishes its job into the free stage slot
+        if (lane == (uint32_t)j) {
+          Job& jb = ctl.job[s];
+          jb.g = mine;
+          jb.tile = tile;
+          jb.mt = meta_from(d, MODE, mine);
+        }
+        __syncwarp();
+        if (lane == 0) {
+          const Job& jb = ctl.job[s];
+          unsigned char* dst = stages + (size_t)s * stride;
+          const TileDesc dd = jb.g.c.tiles[jb.tile];
+          const uint32_t abytes = (jb.mt.staged && !jb.mt.skip) ? jb.mt.np * 32u : 0u;
+          const uint32_t wb = jb.mt.skip ? 0u : dd.wbytes;
+          mbar_arrive_expect_tx(&ctl.full[s], wb + abytes);
+          if (wb) bulk_g2s(dst, reinterpret_cast<const char*>(jb.g.c.words) + dd.g0, wb, &ctl.full[s]);
+          if (abytes) bulk_g2s(dst + stage_bytes, jb.g.c.aux + jb.mt.p0, abytes, &ctl.full[s]);
+          ctl.issued = it + 1;
+        }
+        __syncwarp();
         it++;
       }
     }
   } else {
     Acc acc;
     uint64_t it = 0;
-    for (uint64_t k = blockIdx.x; k < ntile; k += gridDim.x, it++) {
-      const int s = (int)(it % kStages);
-      const bool ok = mbar_wait_bounded(&ctl.full[s], (uint32_t)((it / kStages) & 1));
+    const uint32_t per_warp = (uint32_t)(kScanTile / CW);
+    for (uint64_t k = blockIdx.x; k < njobs; k += gridDim.x, it++) {
+      const uint32_t s = (uint32_t)(it % nst);
+      const bool ok = mbar_wait_bounded(&ctl.full[s], (uint32_t)((it / nst) & 1));
       if (!ok || *(volatile int*)&ctl.abort) {
         if (lane == 0) {
-          atomicOr(g.c.status, kStatTimeout);
+          atomicOr(g0.c.status, kStatTimeout);
           *(volatile int*)&ctl.abort = 1;
         }
         break;
       }
-      const TileMeta mt = ctl.meta[s];
+      const TileMeta mt = ctl.job[s].mt;
       if (!mt.skip && !(MODE == kFilter && mt.cls == 1)) {
+        const ScanArgs g = ctl.job[s].g;
+        const uint64_t tile = ctl.job[s].tile;
         const unsigned char* base = stages + (size_t)s * stride;
-        process_tile<MODE>(g, g.t_first + k, mt, reinterpret_cast<const uint32_t*>(base),
-                           reinterpret_cast<const Aux*>(base + g.c.stage_bytes), acc);
+        const uint32_t* words = reinterpret_cast<const uint32_t*>(base);
+        const Aux* saux = reinterpret_cast<const Aux*>(base + stage_bytes);
+        if (MODE == kDecodeAny) {
+          if (g.c.dtype == LECO_U32)
+            process_tile<kDecode32>(g, tile, mt, words, saux, acc, per_warp);
+          else
+            process_tile<kDecode64>(g, tile, mt, words, saux, acc, per_warp);
+        } else {
+          process_tile<MODE>(g, tile, mt, words, saux, acc, per_warp);
+        }
       }
       __syncwarp();
       if (lane == 0) {
@@ -412,32 +458,30 @@ __global__ void __launch_bounds__(kThreads) k_tilescan(const ScanArgs g) {
     if (ctl.abort) {
       // a wait gave up: drain (bounded) the copies this CTA issued but nobody consumed
       uint64_t done = ctl.issued;
-      for (int w = 0; w < kConsumerWarps; w++) done = min(done, ctl.consumed[w]);
+      for (int w = 0; w < CW; w++) done = min(done, ctl.consumed[w]);
       for (uint64_t u = done; u < ctl.issued; u++)
-        mbar_wait_bounded(&ctl.full[u % kStages], (uint32_t)((u / kStages) & 1), 100000000ull);
+        mbar_wait_bounded(&ctl.full[u % nst], (uint32_t)((u / nst) & 1), 100000000ull);
     } else if (MODE == kFilter) {
       uint64_t tc = 0, tl = 0, th = 0;
-      for (int w = 0; w < kConsumerWarps; w++) {
+      for (int w = 0; w < CW; w++) {
         tc += ctl.red[0][w];
         const uint64_t nl = tl + ctl.red[1][w];
         th += ctl.red[2][w] + (nl < tl ? 1ull : 0ull);
         tl = nl;
       }
       if (tc) {
-        atomicAdd((unsigned long long*)&g.res->count, (unsigned long long)tc);
-        const unsigned long long old = atomicAdd((unsigned long long*)&g.res->sum_lo, (unsigned long long)tl);
+        atomicAdd((unsigned long long*)&g0.res->count, (unsigned long long)tc);
+        const unsigned long long old = atomicAdd((unsigned long long*)&g0.res->sum_lo, (unsigned long long)tl);
         const uint64_t carry = (old + tl < old) ? 1ull : 0ull;
-        if (th + carry) atomicAdd((unsigned long long*)&g.res->sum_hi, (unsigned long long)(th + carry));
+        if (th + carry) atomicAdd((unsigned long long*)&g0.res->sum_hi, (unsigned long long)(th + carry));
       }
     }
   }
 }
 
 // one descriptor per tile: partitions, 16-byte-aligned word range, model value bounds
-__global__ void k_tile_desc(const ColumnView c, TileDesc* __restrict__ tiles) {
-  const uint64_t nt = scan_tiles(c.n);
-  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt;
-       t += (uint64_t)gridDim.x * blockDim.x) {
+__device__ TileDesc tile_desc_one(const ColumnView& c, uint64_t t) {
+  {
     const uint64_t i0 = t * kScanTile, i1 = min(i0 + kScanTile, c.n);
     const uint64_t p0 = part_of(c, i0, 0, c.m);
     const uint64_t p1 = part_of(c, i1 - 1, p0, c.m);
@@ -467,26 +511,51 @@ __global__ void k_tile_desc(const ColumnView c, TileDesc* __restrict__ tiles) {
     d.bounds = ok ? 1u : 0u;
     d.vmin = ok ? vmin : 0;
     d.vmax = ok ? vmax : ~0ull;
-    tiles[t] = d;
+    return d;
   }
 }
 
-template <int MODE>
-int blocks_per_sm(uint32_t smem) {
-  cudaFuncSetAttribute(k_tilescan<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tilescan<MODE>, kThreads, smem);
-  return nb > 0 ? nb : 1;
+__global__ void k_tile_desc(const ColumnView c, TileDesc* __restrict__ tiles) {
+  const uint64_t nt = scan_tiles(c.n);
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    tiles[t] = tile_desc_one(c, t);
 }
 
-template <int MODE>
-cudaError_t launch_scan(const ScanArgs& g, cudaStream_t st) {
-  const uint64_t ntile = g.t_last - g.t_first + 1;
-  const uint32_t smem = kCtrlBytes + kStages * (g.c.stage_bytes + kAuxBytes);
-  const uint64_t cap = (uint64_t)sm_count() * blocks_per_sm<MODE>(smem);
-  const unsigned grid = (unsigned)(ntile < cap ? ntile : cap);
-  k_tilescan<MODE><<<grid, kThreads, smem, st>>>(g);
+__global__ void k_tile_desc_multi(const ColumnView* __restrict__ views, const uint64_t* __restrict__ tile_base,
+                                  uint32_t ncols, uint64_t T, TileDesc* __restrict__ tiles) {
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < T;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = find_col(tile_base, ncols, g);
+    tiles[g] = tile_desc_one(views[c], g - tile_base[c]);
+  }
+}
+
+template <int MODE, int CW, bool MULTI>
+cudaError_t launch_scan_cfg(const ScanArgs& g, const ColumnView* cols, const BatchItem* items,
+                            uint64_t nitems, uint32_t stage_bytes, ScanConfig cfg, cudaStream_t st) {
+  const uint32_t nst = cfg.stages < 2 ? 2u : (cfg.stages > (uint32_t)kMaxStages ? (uint32_t)kMaxStages : cfg.stages);
+  const uint32_t smem = kCtrlBytes + nst * (stage_bytes + kAuxBytes);
+  auto kern = k_tilescan<MODE, CW, MULTI>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, (CW + 1) * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (nb < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t njobs = MULTI ? nitems : g.t_last - g.t_first + 1;
+  const uint64_t cap = (uint64_t)sm_count() * nb;
+  const unsigned grid = (unsigned)(njobs < cap ? njobs : cap);
+  kern<<<grid, (CW + 1) * 32, smem, st>>>(g, cols, items, nitems, nst, stage_bytes);
   return cudaGetLastError();
+}
+
+template <int MODE, bool MULTI>
+cudaError_t launch_scan(const ScanArgs& g, const ColumnView* cols, const BatchItem* items, uint64_t nitems,
+                        uint32_t stage_bytes, ScanConfig cfg, cudaStream_t st) {
+  if (cfg.consumer_warps == 4)
+    return launch_scan_cfg<MODE, 4, MULTI>(g, cols, items, nitems, stage_bytes, cfg, st);
+  return launch_scan_cfg<MODE, 8, MULTI>(g, cols, items, nitems, stage_bytes, cfg, st);
 }
 
 }  // namespace
@@ -499,8 +568,21 @@ cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t 
   return cudaGetLastError();
 }
 
+cudaError_t launch_tile_desc_multi(const ColumnView* views, const uint64_t* tile_base, uint32_t ncols, uint64_t T,
+                                   TileDesc* tiles, cudaStream_t st) {
+  if (T == 0) return cudaSuccess;
+  const uint64_t want = (T + 127) / 128, cap = (uint64_t)sm_count() * 8;
+  k_tile_desc_multi<<<(int)(want < cap ? want : cap), 128, 0, st>>>(views, tile_base, ncols, T, tiles);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
                           cudaStream_t st) {
+  return launch_decode_cfg(c, begin, count, out, scan_config_for(c, 0), st);
+}
+
+cudaError_t launch_decode_cfg(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
+                              ScanConfig cfg, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   ScanArgs g;
   g.c = c;
@@ -512,11 +594,17 @@ cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, v
   g.lo = g.hi = 0;
   g.flags = 0;
   g.res = nullptr;
-  return c.dtype == LECO_U32 ? launch_scan<kDecode32>(g, st) : launch_scan<kDecode64>(g, st);
+  return c.dtype == LECO_U32 ? launch_scan<kDecode32, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, st)
+                             : launch_scan<kDecode64, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, st);
 }
 
 cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
                               leco_sum_result* out, cudaStream_t st) {
+  return launch_filter_sum_cfg(c, lo, hi, flags, out, scan_config_for(c, 1), st);
+}
+
+cudaError_t launch_filter_sum_cfg(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
+                                  leco_sum_result* out, ScanConfig cfg, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(leco_sum_result), st);
   if (e != cudaSuccess || c.n == 0 || lo > hi) return e;
   ScanArgs g;
@@ -530,7 +618,16 @@ cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uin
   g.hi = hi;
   g.flags = flags;
   g.res = out;
-  return launch_scan<kFilter>(g, st);
+  return launch_scan<kFilter, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, st);
+}
+
+cudaError_t launch_batch_decode(const ColumnView* d_cols, const BatchItem* d_items, uint64_t nitems,
+                                uint32_t stage_bytes, ScanConfig cfg, uint32_t* status, cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  ScanArgs g;
+  memset(&g, 0, sizeof(g));
+  g.c.status = status;
+  return launch_scan<kDecodeAny, true>(g, d_cols, d_items, nitems, stage_bytes, cfg, st);
 }
 
 }  // namespace leco

@@ -7,34 +7,9 @@
 #include <mutex>
 #include <vector>
 
-#include "leco_internal.cuh"
+#include "column.cuh"
 
 using namespace leco;
-
-struct leco_column {
-  uint64_t n = 0;
-  uint64_t m = 0;
-  uint64_t nwords = 0;
-  uint64_t total_bits = 0;
-  int32_t dtype = LECO_U64;
-  int32_t kind = LECO_PART_FIXED;
-  int32_t model = LECO_MODEL_LINEAR;
-  uint32_t L = 0;
-  double tau = 0.0;
-  int device = 0;
-  Record* rec = nullptr;
-  Aux* aux = nullptr;
-  uint64_t* starts = nullptr;  // variable only
-  TileDesc* tiles = nullptr;   // scan tile descriptors
-  uint32_t* status = nullptr;
-  uint32_t max_b = 0;          // widest partition
-  uint32_t stage_bytes = 0;    // shared-memory bytes per staged scan tile
-  uint64_t* words = nullptr;
-  void* meta_block = nullptr;
-  uint64_t meta_bytes = 0;
-  uint64_t words_bytes = 0;
-  cudaStream_t home = nullptr;  // stream the column was created on
-};
 
 namespace {
 
@@ -42,31 +17,9 @@ constexpr uint32_t kMagic = 0x4F43454Cu;  // "LECO"
 constexpr uint32_t kVersion = 1;
 constexpr uint64_t kHeaderBytes = 64;
 
-inline leco_status from_cuda(cudaError_t e) {
-  if (e == cudaSuccess) return LECO_OK;
-  if (e == cudaErrorMemoryAllocation) return LECO_ERR_OOM;
-  return LECO_ERR_CUDA;
-}
-
 inline uint64_t value_bytes(int dtype) { return dtype == LECO_U32 ? 4 : 8; }
 
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
-
-ColumnView view_of(const leco_column* c) {
-  ColumnView v;
-  v.n = c->n;
-  v.m = c->m;
-  v.dtype = c->dtype;
-  v.L = c->kind == LECO_PART_FIXED ? c->L : 0;
-  v.rec = c->rec;
-  v.aux = c->aux;
-  v.words = c->words;
-  v.starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
-  v.tiles = c->tiles;
-  v.stage_bytes = c->stage_bytes;
-  v.status = c->status;
-  return v;
-}
 
 // Allocate the metadata block (records, decode table, starts for variable columns, status).
 leco_status alloc_meta(leco_column* c, cudaStream_t st) {
@@ -89,6 +42,15 @@ leco_status alloc_meta(leco_column* c, cudaStream_t st) {
 
 void release(leco_column* c, cudaStream_t st) {
   if (!c) return;
+  if (c->shared) {
+    if (c->shared->refs.fetch_sub(1) == 1) {
+      for (void* b : c->shared->blocks)
+        if (b) cudaFreeAsync(b, st);
+      delete c->shared;
+    }
+    delete c;
+    return;
+  }
   if (c->words) cudaFreeAsync(c->words, st);
   if (c->meta_block) cudaFreeAsync(c->meta_block, st);
   delete c;

@@ -1,0 +1,358 @@
+// Batched decode plans and the scan autotuner (declared in include/leco_batch.h).
+#include <string.h>
+
+#include <vector>
+
+#include "column.cuh"
+#include "leco_batch.h"
+
+using namespace leco;
+
+namespace leco {
+int tune_table_save(const char* path);
+int tune_table_load(const char* path);
+}  // namespace leco
+
+struct leco_batch_plan {
+  ColumnView* d_cols = nullptr;
+  BatchItem* d_items = nullptr;
+  uint32_t* d_status = nullptr;
+  uint64_t nitems = 0;
+  uint32_t stage_bytes = 64;
+  ScanConfig cfg{4, 8};
+  int device = 0;
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void plan_release(leco_batch_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->capture) cudaStreamDestroy(p->capture);
+  if (p->d_cols) cudaFree(p->d_cols);
+  if (p->d_items) cudaFree(p->d_items);
+  if (p->d_status) cudaFree(p->d_status);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+leco_status leco_tune_scan(const leco_column* col, uint32_t op, uint64_t lo, uint64_t hi,
+                           leco_stream_t stream, leco_scan_config* best) {
+  if (!col || !best || op > 1) return LECO_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const ColumnView v = view_of(col);
+  const uint64_t vb = col->dtype == LECO_U32 ? 4 : 8;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, op == 0 ? (col->n ? col->n * vb : 8) : sizeof(leco_sum_result), st);
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const uint32_t stages[] = {2, 3, 4, 6, 8};
+  const uint32_t warps[] = {4, 8};
+  ScanConfig chosen{4, 8};
+  float best_ms = -1.0f;
+  for (uint32_t cw : warps) {
+    for (uint32_t ns : stages) {
+      const ScanConfig cfg{ns, cw};
+      auto run = [&]() {
+        return op == 0 ? launch_decode_cfg(v, 0, col->n, buf, cfg, st)
+                       : launch_filter_sum_cfg(v, lo, hi, 0, (leco_sum_result*)buf, cfg, st);
+      };
+      if (run() != cudaSuccess) {  // e.g. too much shared memory for this column: skip
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(a, st);
+      bool ok = true;
+      for (int r = 0; r < 3 && ok; r++) ok = run() == cudaSuccess;
+      cudaEventRecord(b, st);
+      if (!ok || cudaEventSynchronize(b) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      ms /= 3.0f;
+      if (best_ms < 0 || ms < best_ms) {
+        best_ms = ms;
+        chosen = cfg;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFreeAsync(buf, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return LECO_ERR_CUDA;
+  if (best_ms < 0) return LECO_ERR_CUDA;
+  scan_config_store((int)op, col->dtype, col->stage_bytes, chosen);
+  best->stages = chosen.stages;
+  best->consumer_warps = chosen.consumer_warps;
+  best->ms = best_ms;
+  return LECO_OK;
+}
+
+leco_status leco_tune_save(const char* path) {
+  if (!path) return LECO_ERR_INVALID_ARG;
+  return tune_table_save(path) == 0 ? LECO_OK : LECO_ERR_INVALID_ARG;
+}
+
+leco_status leco_tune_load(const char* path) {
+  if (!path) return LECO_ERR_INVALID_ARG;
+  return tune_table_load(path) >= 0 ? LECO_OK : LECO_ERR_INVALID_ARG;
+}
+
+leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* d_outs, uint32_t ncols,
+                                   leco_batch_plan** out) {
+  if (!out || (ncols && (!cols || !d_outs))) return LECO_ERR_INVALID_ARG;
+  *out = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LECO_ERR_CUDA;
+  std::vector<ColumnView> views(ncols);
+  std::vector<BatchItem> items;
+  uint32_t stage_bytes = 64;
+  int dtype = LECO_U32;
+  for (uint32_t c = 0; c < ncols; c++) {
+    const leco_column* col = cols[c];
+    if (!col || col->device != dev || (col->n && !d_outs[c])) return LECO_ERR_INVALID_ARG;
+    views[c] = view_of(col);
+    stage_bytes = col->stage_bytes > stage_bytes ? col->stage_bytes : stage_bytes;
+    if (col->dtype == LECO_U64) dtype = LECO_U64;
+    const uint64_t vb = col->dtype == LECO_U32 ? 4 : 8;
+    const uint64_t nt = scan_tiles(col->n);
+    for (uint64_t t = 0; t < nt; t++) {
+      BatchItem it;
+      it.col = c;
+      it.pad = 0;
+      it.tile = t;
+      it.begin = t * kScanTile;
+      it.end = it.begin + kScanTile < col->n ? it.begin + kScanTile : col->n;
+      it.out = static_cast<char*>(d_outs[c]) + it.begin * vb;
+      items.push_back(it);
+    }
+  }
+  leco_batch_plan* p = new (std::nothrow) leco_batch_plan();
+  if (!p) return LECO_ERR_OOM;
+  p->device = dev;
+  p->nitems = items.size();
+  p->stage_bytes = stage_bytes;
+  p->cfg = scan_config_lookup(0, dtype, stage_bytes);
+  cudaError_t e = cudaMalloc((void**)&p->d_cols, sizeof(ColumnView) * (ncols ? ncols : 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_items, sizeof(BatchItem) * (items.empty() ? 1 : items.size()));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_status, 256);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, 256);
+  if (e == cudaSuccess && ncols)
+    e = cudaMemcpy(p->d_cols, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    plan_release(p);
+    return from_cuda(e);
+  }
+  *out = p;
+  return LECO_OK;
+}
+
+leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream) {
+  if (!plan) return LECO_ERR_INVALID_ARG;
+  return from_cuda(launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes, plan->cfg,
+                                       plan->d_status, (cudaStream_t)stream));
+}
+
+leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream) {
+  if (!plan) return LECO_ERR_INVALID_ARG;
+  if (!plan->exec) {
+    cudaError_t e = cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(plan->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t le = launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes,
+                                                 plan->cfg, plan->d_status, plan->capture);
+      e = cudaStreamEndCapture(plan->capture, &plan->graph);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return from_cuda(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+}
+
+uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan) { return plan ? plan->nitems : 0; }
+
+void leco_batch_plan_free(leco_batch_plan* plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  plan_release(plan);
+}
+
+leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_outs, uint32_t ncols,
+                              leco_stream_t stream) {
+  leco_batch_plan* p = nullptr;
+  leco_status s = leco_batch_plan_create(cols, d_outs, ncols, &p);
+  if (s != LECO_OK) return s;
+  s = leco_batch_plan_run(p, stream);
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  plan_release(p);
+  if (s == LECO_OK && e != cudaSuccess) s = LECO_ERR_CUDA;
+  return s;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------ batched encode
+
+extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                                         const uint32_t* L, uint32_t ncols, leco_dtype dtype,
+                                         leco_stream_t stream, leco_column** out) {
+  if (!out || (ncols && (!d_vals || !n || !models || !L)) || (dtype != LECO_U32 && dtype != LECO_U64))
+    return LECO_ERR_INVALID_ARG;
+  for (uint32_t c = 0; c < ncols; c++) {
+    out[c] = nullptr;
+    if ((n[c] && !d_vals[c]) || L[c] < 1 || L[c] > kMaxPartLen ||
+        (models[c] != LECO_MODEL_CONSTANT && models[c] != LECO_MODEL_LINEAR))
+      return LECO_ERR_INVALID_ARG;
+  }
+  if (ncols == 0) return LECO_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  // host tables: columns, first partition / scan tile of each column
+  std::vector<EncCol> ec(ncols);
+  std::vector<uint64_t> part_base(ncols + 1), tile_base(ncols + 1), word_base(ncols + 1);
+  part_base[0] = tile_base[0] = 0;
+  for (uint32_t c = 0; c < ncols; c++) {
+    ec[c] = EncCol{d_vals[c], n[c], L[c], (int32_t)models[c]};
+    part_base[c + 1] = part_base[c] + (n[c] + L[c] - 1) / L[c];
+    tile_base[c + 1] = tile_base[c] + scan_tiles(n[c]);
+  }
+  const uint64_t P = part_base[ncols], T = tile_base[ncols];
+  auto a256 = [](uint64_t x) { return (x + 255) & ~255ull; };
+  // shared block 0: records | decode table | tile descriptors | status words
+  const uint64_t rec_b = a256(32 * (P ? P : 1)), tiles_b = a256(sizeof(TileDesc) * (T ? T : 1));
+  const uint64_t stat_b = a256(4ull * ncols);
+  char* meta = nullptr;
+  // scratch: lenbits | scan scratch | col_bits | max_b | tables
+  const uint64_t scr_words = P + offsets_multi_scratch_elems(P) + 2 * (uint64_t)ncols + 8;
+  uint64_t* scr = nullptr;
+  EncCol* d_ec = nullptr;
+  uint64_t* d_bases = nullptr;  // part_base | tile_base | word_base
+  ColumnView* d_views = nullptr;
+  uint64_t* words = nullptr;
+  leco_shared_blocks* sh = nullptr;
+  std::vector<uint64_t> col_bits(ncols);
+  std::vector<uint32_t> max_b(ncols);
+  std::vector<ColumnView> views(ncols);
+  uint64_t W = 0;
+  cudaError_t e = cudaMallocAsync((void**)&meta, 2 * rec_b + tiles_b + stat_b, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&scr, 8 * scr_words, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_ec, sizeof(EncCol) * ncols, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_bases, 8 * 3 * (uint64_t)(ncols + 1), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_views, sizeof(ColumnView) * ncols, st);
+  Record* rec = reinterpret_cast<Record*>(meta);
+  Aux* aux = reinterpret_cast<Aux*>(meta + rec_b);
+  TileDesc* tiles = reinterpret_cast<TileDesc*>(meta + 2 * rec_b);
+  uint32_t* status = reinterpret_cast<uint32_t*>(meta + 2 * rec_b + tiles_b);
+  uint64_t* lenbits = scr;
+  uint64_t* offs = scr + P;
+  uint64_t* d_colbits = offs + offsets_multi_scratch_elems(P);
+  uint32_t* d_maxb = reinterpret_cast<uint32_t*>(d_colbits + ncols);
+  uint64_t* d_part = d_bases;
+  uint64_t* d_tile = d_bases + (ncols + 1);
+  uint64_t* d_word = d_bases + 2 * (ncols + 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, stat_b, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ec, ec.data(), sizeof(EncCol) * ncols, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_part, part_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tile, tile_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
+  // fit every partition of every column, then column-relative offsets and per-column totals
+  if (e == cudaSuccess) e = launch_fit_multi(d_ec, d_part, ncols, P, dtype, rec, lenbits, d_maxb, st);
+  if (e == cudaSuccess) e = launch_offsets_multi(rec, lenbits, d_part, ncols, P, offs, d_colbits, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(col_bits.data(), d_colbits, 8 * ncols, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(max_b.data(), d_maxb, 4 * ncols, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    word_base[0] = 0;
+    for (uint32_t c = 0; c < ncols; c++) {
+      if (col_bits[c] >= (1ull << 48)) e = cudaErrorInvalidValue;
+      word_base[c + 1] = word_base[c] + stream_words(col_bits[c]);
+    }
+    W = word_base[ncols];
+  }
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&words, 8 * W, st);
+  if (e == cudaSuccess) {
+    for (uint32_t c = 0; c < ncols; c++) {
+      ColumnView& v = views[c];
+      v.n = n[c];
+      v.m = part_base[c + 1] - part_base[c];
+      v.dtype = dtype;
+      v.L = L[c];
+      v.rec = rec + part_base[c];
+      v.aux = aux + part_base[c];
+      v.words = words + word_base[c];
+      v.starts = nullptr;
+      v.tiles = tiles + tile_base[c];
+      v.stage_bytes = stage_word_bytes(max_b[c]);
+      v.status = status + c;
+    }
+    e = cudaMemcpyAsync(d_word, word_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_views, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_aux_multi(rec, d_ec, d_part, ncols, P, aux, st);
+  if (e == cudaSuccess) e = launch_tile_desc_multi(d_views, d_tile, ncols, T, tiles, st);
+  if (e == cudaSuccess) e = launch_pack_multi(d_ec, d_part, d_word, d_colbits, ncols, W, dtype, rec, aux, words, st);
+  if (e == cudaSuccess) {
+    sh = new (std::nothrow) leco_shared_blocks();
+    if (!sh) e = cudaErrorMemoryAllocation;
+  }
+  if (e == cudaSuccess) {
+    sh->blocks[0] = meta;
+    sh->blocks[1] = words;
+    sh->refs.store((int)ncols);
+    for (uint32_t c = 0; c < ncols; c++) {
+      leco_column* col = new leco_column();
+      const ColumnView& v = views[c];
+      col->n = v.n;
+      col->m = v.m;
+      col->total_bits = col_bits[c];
+      col->nwords = word_base[c + 1] - word_base[c];
+      col->dtype = dtype;
+      col->kind = LECO_PART_FIXED;
+      col->model = models[c];
+      col->L = L[c];
+      col->device = dev;
+      col->rec = rec + part_base[c];
+      col->aux = aux + part_base[c];
+      col->tiles = tiles + tile_base[c];
+      col->status = status + c;
+      col->max_b = max_b[c];
+      col->stage_bytes = v.stage_bytes;
+      col->words = words + word_base[c];
+      col->meta_bytes = 64 * col->m + sizeof(TileDesc) * scan_tiles(col->n);
+      col->words_bytes = 8 * col->nwords;
+      col->home = st;
+      col->shared = sh;
+      out[c] = col;
+    }
+  }
+  cudaFreeAsync(scr, st);
+  cudaFreeAsync(d_ec, st);
+  cudaFreeAsync(d_bases, st);
+  cudaFreeAsync(d_views, st);
+  if (e != cudaSuccess) {
+    for (uint32_t c = 0; c < ncols; c++) {
+      delete out[c];
+      out[c] = nullptr;
+    }
+    delete sh;
+    if (meta) cudaFreeAsync(meta, st);
+    if (words) cudaFreeAsync(words, st);
+    return e == cudaErrorInvalidValue ? LECO_ERR_INVALID_ARG : from_cuda(e);
+  }
+  return LECO_OK;
+}

@@ -191,6 +191,65 @@ struct ColumnView {
   uint32_t* status;
 };
 
+// Tunable shape of the scan pipeline: shared-memory stages in flight per CTA and consumer warps.
+struct ScanConfig {
+  uint32_t stages;
+  uint32_t consumer_warps;
+};
+
+// One job of a multi-column scan: positions [begin, end) of scan tile `tile` of column `col`,
+// decoded to out (position i -> out[i - begin]).
+struct BatchItem {
+  uint32_t col;
+  uint32_t pad;
+  uint64_t tile;
+  uint64_t begin;
+  uint64_t end;
+  void* out;
+};
+static_assert(sizeof(BatchItem) == 40, "batch item layout");
+
+// One column of a batched encode (fixed partitions of length L).
+struct EncCol {
+  const void* values;
+  uint64_t n;
+  uint32_t L;
+  int32_t model;
+};
+
+// batched encode (k_encode.cu, k_scan.cu): arrays of all columns back to back; part_base /
+// word_base / tile_base hold each column's first partition / word / scan tile (ncols + 1 entries)
+cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
+                             Record* rec, uint64_t* lenbits, uint32_t* max_b, cudaStream_t st);
+uint64_t offsets_multi_scratch_elems(uint64_t P);
+cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base, uint32_t ncols,
+                                 uint64_t P, uint64_t* scratch, uint64_t* col_bits, cudaStream_t st);
+cudaError_t launch_aux_multi(const Record* rec, const EncCol* cols, const uint64_t* part_base, uint32_t ncols,
+                             uint64_t P, Aux* aux, cudaStream_t st);
+cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
+                              const uint64_t* col_bits, uint32_t ncols, uint64_t W, int dtype, const Record* rec,
+                              const Aux* aux, uint64_t* words, cudaStream_t st);
+cudaError_t launch_tile_desc_multi(const ColumnView* views, const uint64_t* tile_base, uint32_t ncols, uint64_t T,
+                                   TileDesc* tiles, cudaStream_t st);
+
+// largest c < ncols with base[c] <= x (base nondecreasing, base[ncols] > x)
+__device__ __forceinline__ uint32_t find_col(const uint64_t* __restrict__ base, uint32_t ncols, uint64_t x) {
+  uint32_t lo = 0, hi = ncols;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(base + mid) <= x)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// tuning table (tune.cu): op 0 = decode, 1 = filter-sum; keyed by value width and widest partition
+ScanConfig scan_config_for(const ColumnView& c, int op);
+ScanConfig scan_config_lookup(int op, int dtype, uint32_t stage_bytes);
+void scan_config_store(int op, int dtype, uint32_t stage_bytes, ScanConfig cfg);
+
 // encode pipeline (k_encode.cu)
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
                        uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
@@ -210,6 +269,12 @@ cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, v
                           cudaStream_t st);
 cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
                               leco_sum_result* out, cudaStream_t st);
+cudaError_t launch_filter_sum_cfg(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
+                                  leco_sum_result* out, ScanConfig cfg, cudaStream_t st);
+cudaError_t launch_decode_cfg(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
+                              ScanConfig cfg, cudaStream_t st);
+cudaError_t launch_batch_decode(const ColumnView* d_cols, const BatchItem* d_items, uint64_t nitems,
+                                uint32_t stage_bytes, ScanConfig cfg, uint32_t* status, cudaStream_t st);
 cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint64_t k, void* out,
                                  cudaStream_t st);
 

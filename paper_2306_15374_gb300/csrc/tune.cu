@@ -1,0 +1,82 @@
+// Scan-pipeline tuning table: the configuration (stages in flight, consumer warps) each scan uses,
+// keyed by operation, value width and the column's widest partition (which sets the stage size).
+// Entries come from leco_tune_scan (timed candidates on a real column) or from a JSON file.
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "leco_internal.cuh"
+
+namespace leco {
+
+namespace {
+
+std::mutex g_mu;
+std::map<std::tuple<int, int, int>, ScanConfig> g_table;
+
+// 0: widest partition <= 8 bits, 1: <= 16, 2: <= 32, 3: wider
+int width_bucket(uint32_t stage_bytes) {
+  const uint64_t max_b = (uint64_t)(stage_bytes > 64 ? stage_bytes - 64 : 0) * 8 / kScanTile;
+  return max_b <= 8 ? 0 : max_b <= 16 ? 1 : max_b <= 32 ? 2 : 3;
+}
+
+}  // namespace
+
+ScanConfig scan_config_lookup(int op, int dtype, uint32_t stage_bytes) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_table.find(std::make_tuple(op, dtype, width_bucket(stage_bytes)));
+  if (it != g_table.end()) return it->second;
+  return ScanConfig{4, 8};
+}
+
+ScanConfig scan_config_for(const ColumnView& c, int op) { return scan_config_lookup(op, c.dtype, c.stage_bytes); }
+
+void scan_config_store(int op, int dtype, uint32_t stage_bytes, ScanConfig cfg) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_table[std::make_tuple(op, dtype, width_bucket(stage_bytes))] = cfg;
+}
+
+int tune_table_save(const char* path) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  FILE* f = fopen(path, "w");
+  if (!f) return -1;
+  fprintf(f, "{\"scan_configs\": [");
+  bool first = true;
+  for (const auto& kv : g_table) {
+    fprintf(f, "%s\n  {\"op\": %d, \"dtype\": %d, \"width_bucket\": %d, \"stages\": %u, \"consumer_warps\": %u}",
+            first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+            kv.second.stages, kv.second.consumer_warps);
+    first = false;
+  }
+  fprintf(f, "\n]}\n");
+  fclose(f);
+  return 0;
+}
+
+// reads back what tune_table_save writes (one entry per line)
+int tune_table_load(const char* path) {
+  FILE* f = fopen(path, "r");
+  if (!f) return -1;
+  char line[512];
+  int n = 0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  while (fgets(line, sizeof(line), f)) {
+    int op, dtype, wb;
+    unsigned st, cw;
+    const char* p = strstr(line, "{\"op\"");
+    if (!p) continue;
+    if (sscanf(p, "{\"op\": %d, \"dtype\": %d, \"width_bucket\": %d, \"stages\": %u, \"consumer_warps\": %u}", &op,
+               &dtype, &wb, &st, &cw) == 5 &&
+        st >= 2 && st <= 8 && (cw == 4 || cw == 8)) {
+      g_table[std::make_tuple(op, dtype, wb)] = ScanConfig{st, cw};
+      n++;
+    }
+  }
+  fclose(f);
+  return n;
+}
+
+}  // namespace leco

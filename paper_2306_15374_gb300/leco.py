@@ -56,6 +56,10 @@ class Stats(ctypes.Structure):
     ]
 
 
+class ScanConfig(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+
 def fixed(L: int) -> PartitionPolicy:
     return PartitionPolicy(LECO_PART_FIXED, int(L), 0.0)
 
@@ -95,6 +99,17 @@ def lib() -> ctypes.CDLL:
         "leco_column_free": (None, [vp]),
         "leco_column_free_async": (None, [vp, vp]),
         "leco_encode_fixed_noalloc": (i32, [vp, u64, i32, u32, i32, vp, vp, u64, ctypes.POINTER(u64), vp]),
+        "leco_tune_scan": (i32, [vp, u32, u64, u64, vp, ctypes.POINTER(ScanConfig)]),
+        "leco_tune_save": (i32, [ctypes.c_char_p]),
+        "leco_tune_load": (i32, [ctypes.c_char_p]),
+        "leco_batch_plan_create": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, col_pp]),
+        "leco_batch_plan_run": (i32, [vp, vp]),
+        "leco_batch_plan_run_graph": (i32, [vp, vp]),
+        "leco_batch_plan_jobs": (u64, [vp]),
+        "leco_batch_plan_free": (None, [vp]),
+        "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
+        "leco_batch_encode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
+                                    ctypes.POINTER(u32), u32, i32, vp, ctypes.POINTER(vp)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -300,3 +315,95 @@ def leco_encode_fixed_noalloc(values, L: int, records_out, words_out, model: int
         err.nwords = int(nw.value)
         raise err
     return int(nw.value)
+
+
+# ------------------------------------------------------------------------------ batch / tuning (leco_batch.h)
+
+def leco_tune_scan(col: Column, op: int = 0, lo: int = 0, hi: int = (1 << 64) - 1, stream=None) -> dict:
+    """Time the scan configurations on this column (op 0 decode, 1 filter-sum) and keep the best."""
+    cfg = ScanConfig()
+    _check(lib().leco_tune_scan(col.handle, int(op), int(lo), int(hi), _stream(stream), ctypes.byref(cfg)),
+           "leco_tune_scan")
+    return {"stages": cfg.stages, "consumer_warps": cfg.consumer_warps, "ms": cfg.ms}
+
+
+def leco_tune_save(path: str) -> None:
+    _check(lib().leco_tune_save(path.encode()), "leco_tune_save")
+
+
+def leco_tune_load(path: str) -> None:
+    _check(lib().leco_tune_load(path.encode()), "leco_tune_load")
+
+
+def _handles(cols):
+    return (ctypes.c_void_p * max(len(cols), 1))(*[c.handle for c in cols])
+
+
+def _ptrs(outs):
+    return (ctypes.c_void_p * max(len(outs), 1))(*[o.data_ptr() for o in outs])
+
+
+class BatchPlan:
+    """Owning handle of a leco_batch_plan; keeps its columns and outputs alive."""
+
+    def __init__(self, handle, cols, outs):
+        self._h, self._cols, self._outs = handle, list(cols), list(outs)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("plan already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().leco_batch_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def leco_batch_plan_create(cols, outs) -> BatchPlan:
+    h = ctypes.c_void_p()
+    _check(lib().leco_batch_plan_create(_handles(cols), _ptrs(outs), len(cols), ctypes.byref(h)),
+           "leco_batch_plan_create")
+    return BatchPlan(h, cols, outs)
+
+
+def leco_batch_plan_run(plan: BatchPlan, stream=None) -> None:
+    _check(lib().leco_batch_plan_run(plan.handle, _stream(stream)), "leco_batch_plan_run")
+
+
+def leco_batch_plan_run_graph(plan: BatchPlan, stream=None) -> None:
+    _check(lib().leco_batch_plan_run_graph(plan.handle, _stream(stream)), "leco_batch_plan_run_graph")
+
+
+def leco_batch_plan_jobs(plan: BatchPlan) -> int:
+    return int(lib().leco_batch_plan_jobs(plan.handle))
+
+
+def leco_batch_plan_free(plan: BatchPlan) -> None:
+    plan.free()
+
+
+def leco_batch_decode(cols, outs, stream=None) -> None:
+    _check(lib().leco_batch_decode(_handles(cols), _ptrs(outs), len(cols), _stream(stream)), "leco_batch_decode")
+
+
+def leco_batch_encode(values, models, Ls, stream=None) -> list:
+    """Fixed-partition encode of several columns (CUDA tensors of one width) in one pass."""
+    k = len(values)
+    dt = _dtype_of(values[0]) if k else LECO_U64
+    if any(_dtype_of(v) != dt for v in values):
+        raise ValueError("all columns of a batched encode must have the same value width")
+    vals = (ctypes.c_void_p * max(k, 1))(*[v.data_ptr() for v in values])
+    ns = (ctypes.c_uint64 * max(k, 1))(*[v.numel() for v in values])
+    ms = (ctypes.c_int * max(k, 1))(*[int(m) for m in models])
+    ls = (ctypes.c_uint32 * max(k, 1))(*[int(x) for x in Ls])
+    out = (ctypes.c_void_p * max(k, 1))()
+    _check(lib().leco_batch_encode(vals, ns, ms, ls, k, dt, _stream(stream), out), "leco_batch_encode")
+    return [Column(ctypes.c_void_p(out[i])) for i in range(k)]
