@@ -45,7 +45,12 @@ def parse_args():
     ap.add_argument("--sample-every", type=int, default=100, help="CPU sample: every k-th partition")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["fix", "var"], default="fix",
+    ap.add_argument("--batch-columns", type=int, default=10_000)
+    ap.add_argument("--batch-total", type=float, default=3e9)
+    ap.add_argument("--serve-columns", type=int, default=2000)
+    ap.add_argument("--serve-total", type=float, default=2.5e9)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--workload", choices=["fix", "var", "batch", "serve"], default="fix",
                     help="fix: the 3 x 200M fixed-partition columns (default); var: the variable-partition "
                          "columns (200M piecewise-linear uint64, 500M uint32 timestamps)")
     ap.add_argument("--tau", type=float, default=0.03)
@@ -515,10 +520,202 @@ def run_var(args):
     return 0
 
 
+def run_batch(args):
+    """Batched form: 10,000 uint64 columns, lengths log-uniform in [1K, 10M] rescaled to 3B values,
+    each linear + bounded noise with its own seed, constant or linear model (50/50), partition size
+    256/1024/4096. Encode and decode all columns in one pass (decode: one persistent launch, also as
+    a CUDA graph, with the autotuned scan shape) against one launch per column."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2306_15374_gb300 as pkg
+
+    pkg.build()
+    from paper_2306_15374_gb300 import leco
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    g = W.rng(41)
+    ncols = args.batch_columns
+    lens = np.exp(g.uniform(np.log(1e3), np.log(1e7), size=ncols))
+    lens = np.maximum(1000, np.rint(lens * (args.batch_total / lens.sum()))).astype(np.int64)
+    models = g.integers(0, 2, size=ncols).tolist()
+    Ls = g.choice([256, 1024, 4096], size=ncols).tolist()
+    slopes = g.integers(1, 100, size=ncols)
+    noises = g.integers(1, 2000, size=ncols)
+    gen = torch.Generator(device=dev)
+    vals = []
+    for c in range(ncols):
+        gen.manual_seed(1000 + c)
+        n = int(lens[c])
+        v = torch.arange(n, dtype=torch.int64, device=dev) * int(slopes[c]) + (1 << 30)
+        v += torch.randint(-int(noises[c]), int(noises[c]) + 1, (n,), generator=gen, dtype=torch.int64, device=dev)
+        vals.append(v)
+    total = int(lens.sum())
+
+    def ev_time(fn, reps=1):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, r
+
+    # encode: batched vs one call per column (each call syncs once to size its stream)
+    cols = leco.leco_batch_encode(vals, models, Ls)
+    for c in cols:
+        c.free()
+    t_benc, cols = ev_time(lambda: leco.leco_batch_encode(vals, models, Ls))
+
+    def per_col_encode():
+        return [leco.leco_encode(v, leco.fixed(L), m) for v, L, m in zip(vals, Ls, models)]
+
+    t_penc, single = ev_time(per_col_encode)
+    same = all(leco.leco_column_export(a) == leco.leco_column_export(b)
+               for a, b in zip(cols[:: max(1, ncols // 50)], single[:: max(1, ncols // 50)]))
+    comp = sum(c.stats()["record_bytes"] + c.stats()["residual_bytes"] for c in cols)
+    for c in single:
+        c.free()
+    # autotune the scan on a representative column, then decode
+    mid = int(np.argsort(lens)[ncols // 2])
+    tuned = leco.leco_tune_scan(cols[mid], 0)
+    outs = [torch.empty(int(n), dtype=torch.int64, device=dev) for n in lens]
+    plan = leco.leco_batch_plan_create(cols, outs)
+    reps = max(3, min(args.steps, 20))
+    leco.leco_batch_plan_run(plan)
+    t_plan, _ = ev_time(lambda: leco.leco_batch_plan_run(plan), reps)
+    leco.leco_batch_plan_run_graph(plan)
+    t_graph, _ = ev_time(lambda: leco.leco_batch_plan_run_graph(plan), reps)
+    ok = all(torch.equal(o, v) for o, v in zip(outs, vals))
+    for o in outs:
+        o.zero_()
+
+    def per_col_decode():
+        for c, o in zip(cols, outs):
+            leco.leco_decode_all(c, o)
+
+    per_col_decode()
+    t_pdec, _ = ev_time(per_col_decode, max(1, reps // 4))
+    ok = ok and all(torch.equal(o, v) for o, v in zip(outs, vals))
+    peak, _ = measured_peaks()
+    dec_bytes = comp + 8 * total
+    enc_bytes = 8 * total + comp
+    print(json.dumps({
+        "workload": f"batched: {ncols} uint64 columns, {total} values (log-uniform 1K-10M rescaled), L in {{256,1024,4096}}, "
+                    "constant/linear 50/50",
+        "results": {
+            "encode_batched_ms": t_benc, "encode_batched_gbs": enc_bytes / (t_benc * 1e-3) / 1e9,
+            "encode_per_column_ms": t_penc, "encode_speedup": t_penc / t_benc, "encode_identical": same,
+            "decode_plan_ms": t_plan, "decode_plan_gbs": dec_bytes / (t_plan * 1e-3) / 1e9,
+            "decode_plan_frac_hbm": dec_bytes / (t_plan * 1e-3) / 1e9 / peak,
+            "decode_graph_ms": t_graph, "decode_per_column_ms": t_pdec,
+            "decode_speedup_vs_per_column": t_pdec / t_graph, "decode_equals_input": ok,
+            "jobs": leco.leco_batch_plan_jobs(plan), "tuned_scan": tuned, "compressed_bytes": comp,
+            "kernel_launches": {"decode_plan": 1, "decode_per_column": ncols},
+        }}), flush=True)
+    plan.free()
+    return 0
+
+
+def run_serve(args):
+    """Serving form: 2,000 resident uint64 columns (lengths log-uniform 100K-50M rescaled to 2.5B
+    values, half fixed L=4096, half variable), admitted against a 40 GB budget; a Poisson stream of
+    requests (50% lookups of log-uniform 1-4096 indices, 50% range decodes of log-uniform 1K-1M
+    values) at several offered loads, continuous batching vs one launch per request. Also an
+    admission-stress run with the budget at half the resident size."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2306_15374_gb300 as pkg
+
+    pkg.build()
+    from paper_2306_15374_gb300 import leco
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    g = W.rng(53)
+    ncols = args.serve_columns
+    lens = np.exp(g.uniform(np.log(1e5), np.log(5e7), size=ncols))
+    lens = np.maximum(100_000, np.rint(lens * (args.serve_total / lens.sum()))).astype(np.int64)
+    slopes = g.integers(1, 100, size=ncols)
+    noises = g.integers(1, 4000, size=ncols)
+    gen = torch.Generator(device=dev)
+
+    def build_columns():
+        out = []
+        for c in range(ncols):
+            gen.manual_seed(7000 + c)
+            n = int(lens[c])
+            v = torch.arange(n, dtype=torch.int64, device=dev) * int(slopes[c]) + (1 << 32)
+            v += torch.randint(-int(noises[c]), int(noises[c]) + 1, (n,), generator=gen, dtype=torch.int64, device=dev)
+            pol = leco.fixed(4096) if c % 2 == 0 else leco.variable(args.tau)
+            out.append(leco.leco_encode(v, pol, leco.LECO_MODEL_LINEAR))
+            del v
+        return out
+
+    results = {}
+    build_s = resident = None
+    for mode, mb in (("continuous", 0), ("per_request", 1)):
+        t0 = time.time()
+        cols = build_columns()
+        build_s = build_s or time.time() - t0
+        resident = resident or sum(c.stats()["device_bytes"] for c in cols)
+        s = leco.leco_server_create(int(40e9), max_batch_requests=mb, max_batch_values=1 << 24,
+                                    max_batch_lookups=1 << 17)
+        ids = [leco.leco_server_admit(s, c) for c in cols]  # the server owns the columns now
+        leco.leco_server_reset_stats(s)
+        leco.leco_server_drive_poisson(s, ids, rate=2e6, seconds=1.0, seed=1)  # saturation burst
+        st = leco.leco_server_stats_get(s)
+        sat = st["completed"] / st["elapsed_s"]
+        runs = []
+        for f in (0.25, 0.5, 0.75, 0.9, 1.1):
+            leco.leco_server_reset_stats(s)
+            sent = leco.leco_server_drive_poisson(s, ids, rate=f * sat, seconds=args.serve_seconds, seed=int(f * 100))
+            st = leco.leco_server_stats_get(s)
+            runs.append({"offered_frac": f, "offered_rps": f * sat, "sent": sent,
+                         "throughput_rps": st["completed"] / st["elapsed_s"],
+                         "lookups_per_s": st["lookups"] / st["elapsed_s"],
+                         "decoded_gbs": 8 * st["range_values"] / st["elapsed_s"] / 1e9,
+                         "p50_us": st["p50_us"], "p99_us": st["p99_us"], "batches": st["batches"],
+                         "launches": st["launches"], "max_batch": st["max_batch_size"]})
+        results[mode] = {"saturation_rps": sat, "loads": runs}
+        s.destroy()
+    # admission stress: a budget of half the resident size refuses the columns that do not fit
+    cols = build_columns()
+    s = leco.leco_server_create(int(resident // 2), max_batch_values=1 << 22, max_batch_lookups=1 << 14)
+    admitted = refused = 0
+    for c in cols:
+        try:
+            leco.leco_server_admit(s, c)
+            admitted += 1
+        except leco.LecoError as e:
+            assert e.status == leco.LECO_ERR_BUDGET
+            refused += 1
+            c.free()
+    st = leco.leco_server_stats_get(s)
+    stress = {"budget_bytes": int(resident // 2), "admitted": admitted, "refused": refused,
+              "resident_bytes": st["resident_bytes"], "reserved_bytes": st["reserved_bytes"]}
+    s.destroy()
+    print(json.dumps({
+        "workload": f"serving: {ncols} resident uint64 columns, {int(lens.sum())} values, half fixed / half variable, "
+                    "budget 40 GB; Poisson requests, 50% lookups (1-4096), 50% ranges (1K-1M)",
+        "build_s": build_s, "resident_bytes": resident, "results": results, "admission_stress": stress}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.workload == "var" and args.impl != "reference":
         return run_var(args)
+    if args.workload == "serve" and args.impl != "reference":
+        return run_serve(args)
+    if args.workload == "batch" and args.impl != "reference":
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_leco(args)

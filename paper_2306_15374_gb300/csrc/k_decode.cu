@@ -84,6 +84,29 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// Lookups of several columns in one launch (a serving batch): index q reads column col[q]; results
+// are widened to 64 bits (a 32-bit column's value is zero-extended).
+__global__ void __launch_bounds__(kBlock)
+    k_lookup_multi(const ColumnView* __restrict__ views, const uint32_t* __restrict__ col,
+                   const uint64_t* __restrict__ idx, uint64_t k, uint64_t* __restrict__ out) {
+  for (uint64_t q = (uint64_t)blockIdx.x * kBlock + threadIdx.x; q < k; q += (uint64_t)gridDim.x * kBlock) {
+    const ColumnView c = views[col[q]];
+    const uint64_t i = __ldg(idx + q);
+    if (i >= c.n) {
+      out[q] = 0;
+      atomicOr(c.status, kStatIndexRange);
+      continue;
+    }
+    const uint64_t p = find_part(c, i);
+    const Aux a = load_aux(c.aux, p);
+    const uint64_t x = i - a.start;
+    const uint32_t b = w3_b(a.word3);
+    const uint64_t z = read_field(c.words, w3_off(a.word3) + x * b, b);
+    const uint64_t v = (uint64_t)predict_aux(a, c.rec, p, x) + (uint64_t)zz_decode(z);
+    out[q] = c.dtype == LECO_U32 ? (v & 0xFFFFFFFFull) : v;
+  }
+}
+
 int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
   const uint64_t need = (items + per_block - 1) / per_block;
   const uint64_t cap = (uint64_t)sm_count() * max_blocks_per_sm;
@@ -100,6 +123,13 @@ cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint6
     k_random_access<uint32_t><<<grid, kBlock, 0, st>>>(c, idx, k, (uint32_t*)out);
   else
     k_random_access<uint64_t><<<grid, kBlock, 0, st>>>(c, idx, k, (uint64_t*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_multi(const ColumnView* views, const uint32_t* col, const uint64_t* idx, uint64_t k,
+                                uint64_t* out, cudaStream_t st) {
+  if (k == 0) return cudaSuccess;
+  k_lookup_multi<<<grid_for(k, kBlock, 8), kBlock, 0, st>>>(views, col, idx, k, out);
   return cudaGetLastError();
 }
 

@@ -273,6 +273,8 @@ cudaError_t launch_filter_sum_cfg(const ColumnView& c, uint64_t lo, uint64_t hi,
                                   leco_sum_result* out, ScanConfig cfg, cudaStream_t st);
 cudaError_t launch_decode_cfg(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
                               ScanConfig cfg, cudaStream_t st);
+cudaError_t launch_lookup_multi(const ColumnView* views, const uint32_t* col, const uint64_t* idx, uint64_t k,
+                                uint64_t* out, cudaStream_t st);
 cudaError_t launch_batch_decode(const ColumnView* d_cols, const BatchItem* d_items, uint64_t nitems,
                                 uint32_t stage_bytes, ScanConfig cfg, uint32_t* status, cudaStream_t st);
 cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint64_t k, void* out,

@@ -60,6 +60,25 @@ class ScanConfig(ctypes.Structure):
     _fields_ = [("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("max_batch_requests", ctypes.c_uint32),
+        ("max_batch_lookups", ctypes.c_uint64), ("max_batch_values", ctypes.c_uint64), ("max_columns", ctypes.c_uint32),
+        ("mock", ctypes.c_uint32), ("mock_batch_us", ctypes.c_uint32),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+        ("lookups", ctypes.c_uint64), ("range_values", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+        ("launches", ctypes.c_uint64), ("max_batch_size", ctypes.c_uint64), ("p50_us", ctypes.c_double),
+        ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
+        ("elapsed_s", ctypes.c_double), ("resident_bytes", ctypes.c_uint64), ("reserved_bytes", ctypes.c_uint64),
+        ("columns", ctypes.c_uint32),
+    ]
+
+
 def fixed(L: int) -> PartitionPolicy:
     return PartitionPolicy(LECO_PART_FIXED, int(L), 0.0)
 
@@ -110,6 +129,18 @@ def lib() -> ctypes.CDLL:
         "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
         "leco_batch_encode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
                                     ctypes.POINTER(u32), u32, i32, vp, ctypes.POINTER(vp)]),
+        "leco_server_create": (i32, [ctypes.POINTER(ServerConfig), col_pp]),
+        "leco_server_admit": (i32, [vp, vp, ctypes.POINTER(u32)]),
+        "leco_server_admit_mock": (i32, [vp, u64, i32, u64, ctypes.POINTER(u32)]),
+        "leco_server_evict": (i32, [vp, u32]),
+        "leco_server_submit_lookup": (i32, [vp, u32, vp, u64, vp, ctypes.POINTER(u64)]),
+        "leco_server_submit_range": (i32, [vp, u32, u64, u64, vp, ctypes.POINTER(u64)]),
+        "leco_server_wait": (i32, [vp, u64, u32, ctypes.POINTER(i32)]),
+        "leco_server_drive_poisson": (i32, [vp, ctypes.POINTER(u32), u32, ctypes.c_double, ctypes.c_double, u64,
+                                            ctypes.c_double, u64, u64, u64, ctypes.POINTER(u64)]),
+        "leco_server_stats_get": (i32, [vp, ctypes.POINTER(ServerStats)]),
+        "leco_server_reset_stats": (i32, [vp]),
+        "leco_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -392,6 +423,116 @@ def leco_batch_plan_free(plan: BatchPlan) -> None:
 
 def leco_batch_decode(cols, outs, stream=None) -> None:
     _check(lib().leco_batch_decode(_handles(cols), _ptrs(outs), len(cols), _stream(stream)), "leco_batch_decode")
+
+
+class Server:
+    """Owning handle of a leco_server. Keeps each pending request's output buffer alive."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self._pending = {}
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("server already destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h:
+            lib().leco_server_destroy(self._h)
+            self._h = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def leco_server_create(budget_bytes: int, max_inflight: int = 0, max_batch_requests: int = 0,
+                       max_batch_lookups: int = 0, max_batch_values: int = 0, max_columns: int = 0,
+                       mock: bool = False, mock_batch_us: int = 0) -> Server:
+    cfg = ServerConfig(int(budget_bytes), int(max_inflight), int(max_batch_requests), int(max_batch_lookups),
+                       int(max_batch_values), int(max_columns), 1 if mock else 0, int(mock_batch_us))
+    h = ctypes.c_void_p()
+    _check(lib().leco_server_create(ctypes.byref(cfg), ctypes.byref(h)), "leco_server_create")
+    return Server(h)
+
+
+def leco_server_admit(server: Server, col: Column) -> int:
+    """The server takes ownership of the column (the Column handle is emptied)."""
+    cid = ctypes.c_uint32(0)
+    _check(lib().leco_server_admit(server.handle, col.handle, ctypes.byref(cid)), "leco_server_admit")
+    col._h = None
+    return int(cid.value)
+
+
+def leco_server_admit_mock(server: Server, n: int, dtype: int, nbytes: int) -> int:
+    cid = ctypes.c_uint32(0)
+    _check(lib().leco_server_admit_mock(server.handle, int(n), int(dtype), int(nbytes), ctypes.byref(cid)),
+           "leco_server_admit_mock")
+    return int(cid.value)
+
+
+def leco_server_evict(server: Server, col_id: int) -> None:
+    _check(lib().leco_server_evict(server.handle, int(col_id)), "leco_server_evict")
+
+
+def leco_server_submit_lookup(server: Server, col_id: int, idx, out) -> int:
+    """idx: numpy uint64 array (copied); out: numpy array of the column's width (filled on completion)."""
+    import numpy as np
+
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    rid = ctypes.c_uint64(0)
+    _check(lib().leco_server_submit_lookup(server.handle, int(col_id), idx.ctypes.data_as(ctypes.c_void_p), idx.size,
+                                           out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid)),
+           "leco_server_submit_lookup")
+    server._pending[rid.value] = out
+    return int(rid.value)
+
+
+def leco_server_submit_range(server: Server, col_id: int, begin: int, count: int, out) -> int:
+    rid = ctypes.c_uint64(0)
+    _check(lib().leco_server_submit_range(server.handle, int(col_id), int(begin), int(count),
+                                          out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid)),
+           "leco_server_submit_range")
+    server._pending[rid.value] = out
+    return int(rid.value)
+
+
+def leco_server_wait(server: Server, req_id: int, timeout_ms: int = 60_000) -> int:
+    """Returns the request's status; raises LecoError(TIMEOUT) if it is still pending."""
+    res = ctypes.c_int(0)
+    _check(lib().leco_server_wait(server.handle, int(req_id), int(timeout_ms), ctypes.byref(res)), "leco_server_wait")
+    server._pending.pop(req_id, None)
+    return int(res.value)
+
+
+def leco_server_drive_poisson(server: Server, col_ids, rate: float, seconds: float, seed: int = 0,
+                              lookup_frac: float = 0.5, max_lookup: int = 4096, min_range: int = 1000,
+                              max_range: int = 1_000_000) -> int:
+    ids = (ctypes.c_uint32 * len(col_ids))(*[int(c) for c in col_ids])
+    sent = ctypes.c_uint64(0)
+    _check(lib().leco_server_drive_poisson(server.handle, ids, len(col_ids), float(rate), float(seconds), int(seed),
+                                           float(lookup_frac), int(max_lookup), int(min_range), int(max_range),
+                                           ctypes.byref(sent)), "leco_server_drive_poisson")
+    return int(sent.value)
+
+
+def leco_server_stats_get(server: Server) -> dict:
+    st = ServerStats()
+    _check(lib().leco_server_stats_get(server.handle, ctypes.byref(st)), "leco_server_stats_get")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def leco_server_reset_stats(server: Server) -> None:
+    _check(lib().leco_server_reset_stats(server.handle), "leco_server_reset_stats")
+
+
+def leco_server_destroy(server: Server) -> None:
+    server.destroy()
 
 
 def leco_batch_encode(values, models, Ls, stream=None) -> list:
