@@ -229,6 +229,24 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's step time: every rank processes the same units, so the job's time is the
+    max over ranks (all-reduce MAX; the identity at world 1)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_gbs(bytes_per_rank_step, world, ms):
+    """Whole-job throughput: the bytes all ranks processed in one step over the (max) step time."""
+    return world * bytes_per_rank_step / (ms * 1e-3) / 1e9
+
+
 def run_leco(args):
     import numpy as np
     import torch
@@ -321,11 +339,7 @@ def run_leco(args):
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, world, dev)
 
     per = {}
     dec_b = filt_b = look_b = 0
@@ -394,7 +408,7 @@ def run_leco(args):
                "sample": f"{sum(len(s['v']) for s in samples)} values: every {args.sample_every}th "
                          f"4096-value partition of each column; decode + filter-sum + proportional lookups"}
 
-    value = world * step_b / (ms * 1e-3) / 1e9
+    value = whole_job_gbs(step_b, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
