@@ -2,11 +2,12 @@
 // values): full/range decode and the fused filter-sum.
 //
 // Tile t covers positions [t kScanTile, (t+1) kScanTile); its residuals are one contiguous bit
-// range. A persistent CTA has one producer warp and eight consumer warps. The producer walks the
-// CTA's tiles in order: it waits until a shared-memory stage is empty, then issues one 1-D bulk
-// copy (TMA) of the tile's 16-byte-aligned word range and one of its decode-table entries (when at
-// most kMaxP partitions touch it), completing on the stage's "full" mbarrier. Each consumer warp
-// decodes 512 positions of the tile lane-strided (lane j takes positions g + j), so global stores
+// range. A persistent CTA has one producer warp and four or eight consumer warps. The producer
+// walks the CTA's tiles in order: it waits until a shared-memory stage is empty, then issues one
+// 1-D bulk copy (TMA) of the tile's 16-byte-aligned word range and one of its decode-table entries
+// (when at most kMaxP partitions touch it), completing on the stage's "full" mbarrier; tiles that
+// pruning removes never enter the ring. Each consumer warp decodes 4096 / (consumer warps)
+// positions of the tile lane-strided (lane j takes positions g + j), so global stores
 // are coalesced and neighbouring fields are read from shared memory without bank conflicts. Inside
 // a partition a lane carries its fixed-point prediction F = A + B x and its bit position, stepping
 // by 32 B and 32 b per group. The filter bounds each 32-value group with its model (prediction at
@@ -33,8 +34,9 @@ struct TileMeta {
   uint64_t bit_base;  // absolute bit position of the first staged word
   uint32_t np;
   uint32_t staged;    // decode-table entries p0 .. p0+np-1 are in shared memory
-  uint32_t skip;      // pruned: nothing was copied
+  uint32_t skip;      // pruned: the job is dropped, nothing is copied
   uint32_t cls;       // filter: 1 = the tile misses [lo, hi], 2 = lies inside it, 0 = undecided
+  uint32_t end;       // no job: the producer has no more work for this CTA
 };
 
 struct ScanArgs {
@@ -96,32 +98,69 @@ __device__ __forceinline__ Aux ldg_aux(const Aux* a) {
   return r;
 }
 
-// Model bounds of positions [x0, x1] of a partition: prediction at both ends (monotone in x) +- the
-// residual range [-2^(b-1), 2^(b-1) - 1] of width b. False for a binary64 partition, b > 62, or
-// bounds that would leave the value domain (wrap-around).
-__device__ __forceinline__ bool part_bounds(int dtype, const Aux& a, uint64_t x0, uint64_t x1,
-                                            uint64_t* vlo_out, uint64_t* vhi_out) {
+// Model bounds of positions [x0, x1] of an exact partition: the value w = pred + r satisfies
+// pmin - 2^(b-1) <= w <= pmax + 2^(b-1) - 1 as a signed integer, with the prediction taken at both
+// ends (it is monotone in x) and r in the zigzag range of width b. Returned as a set of unsigned
+// values: kind 1 = [vlo, vhi]; kind 2 = [0, vhi] together with [vlo, 2^64 - 1] (a 64-bit range that
+// straddles zero as a signed number); kind 0 = no bound (binary64 partition, b > 62, or an
+// extreme range). A 32-bit column's values are w itself, in [0, 2^32), so its range is clamped.
+__device__ __forceinline__ int part_bounds(int dtype, const Aux& a, uint64_t x0, uint64_t x1,
+                                           uint64_t* vlo_out, uint64_t* vhi_out) {
   const uint32_t b = w3_b(a.word3);
-  if (!w3_exact(a.word3) || b > 62) return false;
+  if (!w3_exact(a.word3) || b > 62) return 0;
   int32_t sh = w3_s(a.word3);
   sh = (sh > 0 ? sh : 0) & 63;
-  int64_t p0v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x0) >> sh;
-  int64_t p1v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x1) >> sh;
+  const int64_t p0v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x0) >> sh;
+  const int64_t p1v = (int64_t)((uint64_t)a.A + (uint64_t)a.B * x1) >> sh;
   const int64_t pmin = p0v < p1v ? p0v : p1v, pmax = p0v < p1v ? p1v : p0v;
   const int64_t half = b ? (int64_t)1 << (b - 1) : 0;
-  if (pmin < half) return false;  // the lower bound would drop below zero
-  const uint64_t vhi = (uint64_t)pmax + (uint64_t)(half ? half - 1 : 0);
-  if (dtype == LECO_U32 && vhi > 0xFFFFFFFFull) return false;
-  *vlo_out = (uint64_t)(pmin - half);
-  *vhi_out = vhi;
-  return true;
+  if (pmin < INT64_MIN + half || pmax > INT64_MAX - half) return 0;
+  const int64_t L = pmin - half, U = pmax + (half ? half - 1 : 0);
+  if (dtype == LECO_U32) {
+    const int64_t lo = L > 0 ? L : 0, hi = U < 0xFFFFFFFFll ? U : 0xFFFFFFFFll;
+    if (lo > hi) return 0;
+    *vlo_out = (uint64_t)lo;
+    *vhi_out = (uint64_t)hi;
+    return 1;
+  }
+  *vlo_out = (uint64_t)L;
+  *vhi_out = (uint64_t)U;
+  return (L < 0 && U >= 0) ? 2 : 1;
+}
+
+// Union of a tile's running bound set (kind k, [lo, hi]) with one partition's (kind pk, [plo, phi]).
+__device__ __forceinline__ int bounds_union(int k, uint64_t* lo, uint64_t* hi, int pk, uint64_t plo, uint64_t phi) {
+  if (k == 0 || pk == 0) return 0;
+  if (k == 1 && pk == 1) {
+    *lo = min(*lo, plo);
+    *hi = max(*hi, phi);
+    return 1;
+  }
+  if (k == 1) {  // make the running set the wrapped one
+    const uint64_t t0 = *lo, t1 = *hi;
+    *lo = plo;
+    *hi = phi;
+    plo = t0;
+    phi = t1;
+    pk = 1;
+  }
+  if (pk == 2) {
+    *hi = max(*hi, phi);
+    *lo = min(*lo, plo);
+  } else if (plo < *lo) {  // [plo, phi] lies in [0, max(hi, phi)] (plo >= 0)
+    *hi = max(*hi, phi);
+  }
+  return *hi < *lo - 1 ? 2 : 0;  // the two pieces met: no bound left
 }
 
 // 0 = may meet [lo, hi], 1 = certainly misses, 2 = certainly inside
-__device__ __forceinline__ int classify(bool ok, uint64_t vlo, uint64_t vhi, uint64_t lo, uint64_t hi) {
-  if (!ok) return 0;
-  if (vhi < lo || vlo > hi) return 1;
-  if (vlo >= lo && vhi <= hi) return 2;
+__device__ __forceinline__ int classify(int kind, uint64_t vlo, uint64_t vhi, uint64_t lo, uint64_t hi) {
+  if (kind == 1) {
+    if (vhi < lo || vlo > hi) return 1;
+    if (vlo >= lo && vhi <= hi) return 2;
+    return 0;
+  }
+  if (kind == 2 && lo > vhi && hi < vlo) return 1;
   return 0;
 }
 
@@ -275,8 +314,8 @@ __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, 
       int cls = (int)mt.cls;
       if (MODE == kFilter && cls == 0 && !(g.flags & LECO_FILTER_DECODE_ALL)) {
         uint64_t vlo = 0, vhi = 0;
-        const bool ok = part_bounds(c.dtype, a, gp - a.start, gp + 32ull * ng - 1 - a.start, &vlo, &vhi);
-        cls = classify(ok, vlo, vhi, g.lo, g.hi);
+        const int kind = part_bounds(c.dtype, a, gp - a.start, gp + 32ull * ng - 1 - a.start, &vlo, &vhi);
+        cls = classify(kind, vlo, vhi, g.lo, g.hi);
       }
       if (w3_b(a.word3) > 32)
         run_groups<MODE, true>(g, acc, words, a, gp, ng, mt.bit_base, lane, cls);
@@ -307,8 +346,9 @@ __device__ __forceinline__ TileMeta meta_from(const TileDesc& d, int mode, const
   mt.bit_base = d.g0 * 8;
   mt.cls = 0;
   if (mode == kFilter && !(g.flags & LECO_FILTER_DECODE_ALL))
-    mt.cls = (uint32_t)classify(d.bounds != 0, d.vmin, d.vmax, g.lo, g.hi);
+    mt.cls = (uint32_t)classify((int)d.bounds, d.vmin, d.vmax, g.lo, g.hi);
   mt.skip = ((g.flags & LECO_FILTER_PRUNE) && mt.cls == 1) ? 1u : 0u;
+  mt.end = 0;
   return mt;
 }
 
@@ -338,14 +378,20 @@ __global__ void __launch_bounds__((CW + 1) * 32)
   __syncthreads();
 
   if (warp == CW) {
-    // producer: the warp's lanes fetch 32 jobs' inputs at a time, lane 0 issues the copies in order
+    // producer: the warp's lanes fetch 32 jobs' descriptors at a time and classify them in
+    // parallel; a pruned job is dropped here and never occupies a stage. In turn, lane j (which
+    // holds job j's descriptor in registers) waits for its stage to drain and issues the job's
+    // copies, so no global load sits between consecutive copies. A final job marked `end` tells
+    // the consumers to stop.
     uint64_t it = 0;
+    uint32_t s = 0, ph = 0;  // stage of copy `it` and the parity of its round (it / nst)
     bool stop = false;
     for (uint64_t k0 = blockIdx.x; k0 < njobs && !stop; k0 += 32ull * gridDim.x) {
       const uint64_t kk = k0 + (uint64_t)lane * gridDim.x;
       ScanArgs mine = g0;
       uint64_t tile = 0;
       TileDesc d = {};
+      TileMeta mt = {};
       if (kk < njobs) {
         if (MULTI) {
           const BatchItem bi = items[kk];
@@ -358,55 +404,63 @@ __global__ void __launch_bounds__((CW + 1) * 32)
           tile = g0.t_first + kk;
         }
         d = mine.c.tiles[tile];
+        mt = meta_from(d, MODE, mine);
       }
-      for (int j = 0; j < 32; j++) {
-        const uint64_t k = k0 + (uint64_t)j * gridDim.x;
-        if (k >= njobs) break;
-        const uint32_t s = (uint32_t)(it % nst);
+      uint32_t todo = __ballot_sync(0xffffffffu, kk < njobs && !mt.skip);
+      while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1;
         int ok = 1;
-        if (lane == 0) {
-          if (it >= (uint64_t)nst) ok = mbar_wait_bounded(&ctl.empty[s], (uint32_t)(((it / nst) - 1) & 1)) ? 1 : 0;
+        if (lane == (uint32_t)j) {
+          if (it >= (uint64_t)nst) ok = mbar_wait_bounded(&ctl.empty[s], ph ^ 1u) ? 1 : 0;
           if (ok && *(volatile int*)&ctl.abort) ok = 0;
           if (!ok) {
             atomicOr(g0.c.status, kStatTimeout);
             *(volatile int*)&ctl.abort = 1;
+          } else {
+            // publish the job into the drained slot, then arm the stage and issue its copies
+            Job& jb = ctl.job[s];
+            if (MULTI) jb.g = mine;  // a single-column scan's consumers take the arguments from g0
+            jb.tile = tile;
+            jb.mt = mt;
+            unsigned char* dst = stages + (size_t)s * stride;
+            const uint32_t abytes = mt.staged ? mt.np * 32u : 0u;
+            mbar_arrive_expect_tx(&ctl.full[s], d.wbytes + abytes);
+            bulk_g2s(dst, reinterpret_cast<const char*>(mine.c.words) + d.g0, d.wbytes, &ctl.full[s]);
+            if (abytes) bulk_g2s(dst + stage_bytes, mine.c.aux + mt.p0, abytes, &ctl.full[s]);
           }
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
+        ok = __shfl_sync(0xffffffffu, ok, j);
         if (!ok) {
           stop = true;
           break;
         }
-        // lane j publishes its job into the free stage slot
-        if (lane == (uint32_t)j) {
-          Job& jb = ctl.job[s];
-          jb.g = mine;
-          jb.tile = tile;
-          jb.mt = meta_from(d, MODE, mine);
-        }
-        __syncwarp();
-        if (lane == 0) {
-          const Job& jb = ctl.job[s];
-          unsigned char* dst = stages + (size_t)s * stride;
-          const TileDesc dd = jb.g.c.tiles[jb.tile];
-          const uint32_t abytes = (jb.mt.staged && !jb.mt.skip) ? jb.mt.np * 32u : 0u;
-          const uint32_t wb = jb.mt.skip ? 0u : dd.wbytes;
-          mbar_arrive_expect_tx(&ctl.full[s], wb + abytes);
-          if (wb) bulk_g2s(dst, reinterpret_cast<const char*>(jb.g.c.words) + dd.g0, wb, &ctl.full[s]);
-          if (abytes) bulk_g2s(dst + stage_bytes, jb.g.c.aux + jb.mt.p0, abytes, &ctl.full[s]);
-          ctl.issued = it + 1;
-        }
-        __syncwarp();
         it++;
+        if (++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    if (lane == 0) {
+      ctl.issued = it;  // copies issued (each one's stage is armed)
+      bool ok = !stop;
+      if (ok && it >= (uint64_t)nst) ok = mbar_wait_bounded(&ctl.empty[s], ph ^ 1u);
+      if (ok) {
+        ctl.job[s].mt.end = 1u;
+        mbar_arrive(&ctl.full[s]);
+      } else if (!stop) {
+        atomicOr(g0.c.status, kStatTimeout);
+        *(volatile int*)&ctl.abort = 1;
       }
     }
   } else {
     Acc acc;
     uint64_t it = 0;
+    uint32_t s = 0, ph = 0;
     const uint32_t per_warp = (uint32_t)(kScanTile / CW);
-    for (uint64_t k = blockIdx.x; k < njobs; k += gridDim.x, it++) {
-      const uint32_t s = (uint32_t)(it % nst);
-      const bool ok = mbar_wait_bounded(&ctl.full[s], (uint32_t)((it / nst) & 1));
+    for (;;) {
+      const bool ok = mbar_wait_bounded(&ctl.full[s], ph);
       if (!ok || *(volatile int*)&ctl.abort) {
         if (lane == 0) {
           atomicOr(g0.c.status, kStatTimeout);
@@ -415,8 +469,9 @@ __global__ void __launch_bounds__((CW + 1) * 32)
         break;
       }
       const TileMeta mt = ctl.job[s].mt;
-      if (!mt.skip && !(MODE == kFilter && mt.cls == 1)) {
-        const ScanArgs g = ctl.job[s].g;
+      if (mt.end) break;
+      if (!(MODE == kFilter && mt.cls == 1)) {
+        const ScanArgs g = MULTI ? ctl.job[s].g : g0;
         const uint64_t tile = ctl.job[s].tile;
         const unsigned char* base = stages + (size_t)s * stride;
         const uint32_t* words = reinterpret_cast<const uint32_t*>(base);
@@ -434,6 +489,11 @@ __global__ void __launch_bounds__((CW + 1) * 32)
       if (lane == 0) {
         mbar_arrive(&ctl.empty[s]);
         ctl.consumed[warp] = it + 1;
+      }
+      it++;
+      if (++s == nst) {
+        s = 0;
+        ph ^= 1u;
       }
     }
     if (MODE == kFilter) {
@@ -497,20 +557,26 @@ __device__ TileDesc tile_desc_one(const ColumnView& c, uint64_t t) {
     d.g0 = g0;
     d.wbytes = (uint32_t)(g1 - g0);
     d.pad = 0;
-    uint64_t vmin = ~0ull, vmax = 0;
-    bool ok = true;
-    for (uint64_t p = p0; p <= p1 && ok; p++) {
+    uint64_t vmin = 0, vmax = 0;
+    int kind = 0;
+    for (uint64_t p = p0; p <= p1; p++) {
       const Aux a = p == p0 ? a0 : (p == p1 ? a1 : ldg_aux(c.aux + p));
       const uint64_t ps = max(i0, a.start);
       const uint64_t pe = min(i1, pstart(c, p + 1));
       uint64_t lo = 0, hi = 0;
-      ok = part_bounds(c.dtype, a, ps - a.start, pe - 1 - a.start, &lo, &hi);
-      vmin = min(vmin, lo);
-      vmax = max(vmax, hi);
+      const int pk = part_bounds(c.dtype, a, ps - a.start, pe - 1 - a.start, &lo, &hi);
+      if (p == p0) {
+        kind = pk;
+        vmin = lo;
+        vmax = hi;
+      } else {
+        kind = bounds_union(kind, &vmin, &vmax, pk, lo, hi);
+      }
+      if (kind == 0) break;
     }
-    d.bounds = ok ? 1u : 0u;
-    d.vmin = ok ? vmin : 0;
-    d.vmax = ok ? vmax : ~0ull;
+    d.bounds = (uint32_t)kind;
+    d.vmin = kind ? vmin : 0;
+    d.vmax = kind ? vmax : ~0ull;
     return d;
   }
 }

@@ -45,11 +45,11 @@ constexpr uint64_t kScanTile = 4096;
 struct TileDesc {
   uint64_t p0;      // first partition touching the tile
   uint64_t g0;      // byte offset of the staged word range in the residual stream (16-aligned)
-  uint64_t vmin;    // every value of the tile lies in [vmin, vmax] (unsigned) when bounds == 1
-  uint64_t vmax;
+  uint64_t vmin;    // bounds == 1: every value of the tile lies in [vmin, vmax] (unsigned);
+  uint64_t vmax;    // bounds == 2: in [0, vmax] or [vmin, 2^64 - 1] (vmax < vmin); 0: unknown
   uint32_t np;      // partitions touching the tile
   uint32_t wbytes;  // bytes of the staged word range (multiple of 16)
-  uint32_t bounds;  // 1: [vmin, vmax] is valid
+  uint32_t bounds;
   uint32_t pad;
 };
 static_assert(sizeof(TileDesc) == 48, "tile descriptor layout");

@@ -43,6 +43,11 @@ def _cases():
     yield "for_L1024", W.cfg1(100_000), 1024, 0, 64
     yield "ts_u32_L512", W.timestamps_u32(150_001, seed=12), 512, 1, 32
     yield "ts_u32_const_L33", W.timestamps_u32(70_001, seed=13), 33, 0, 32
+    # model ranges that cross zero as signed numbers (64-bit: values on both sides of 2^64 = 0)
+    # and 32-bit ranges whose residual band dips below zero (clamped bounds)
+    yield "wrap_zero_u64_L512", W.linear_noise(100_003, -(1 << 30), 21_000, 4096, seed=14), 512, 1, 64
+    yield "low_u64_L1024", W.random_u64(60_001, 15, bits=20), 1024, 1, 64
+    yield "low_u32_L1024", W.random_u64(60_001, 16, bits=20), 1024, 1, 32
 
 
 CASES = list(_cases())
@@ -103,7 +108,9 @@ def test_decode_range_lookup_filter(lc, case):
     assert lc.leco_sync(col) == lc.LECO_OK
     rec, words = oracle.encode_fixed(v, L, model)
     res = torch.zeros(3, dtype=torch.int64, device="cuda")
-    bounds = [W.filter_bounds(v), (0, (1 << 64) - 1), (5, 4), (int(v[n // 2]), int(v[n // 2]))]
+    top = (1 << 64) - 1
+    bounds = [W.filter_bounds(v), (0, top), (5, 4), (int(v[n // 2]), int(v[n // 2])),
+              (0, 1 << 20), (top - (1 << 20), top), (1 << 40, 1 << 50), (1 << 31, (1 << 32) - 1)]
     for lo, hi in bounds:
         want = oracle.filter_sum(rec, words, n, lo, hi, bits)
         assert want == exact_sum(v, lo, hi)
