@@ -550,10 +550,24 @@ def run_var(args):
     return 0
 
 
+def upload_columns(gen, spec, ncols, dev):
+    """Columns generated on host threads (numpy releases the GIL) and copied to the device as
+    they complete."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    out = []
+    with ThreadPoolExecutor(max(2, os.cpu_count() or 2)) as ex:
+        for v in ex.map(lambda c: gen(spec, c), range(ncols)):
+            out.append(torch.from_numpy(v.view(np.int64)).to(dev))
+    return out
+
+
 def run_batch(args):
     """Batched form: 10,000 uint64 columns, lengths log-uniform in [1K, 10M] rescaled to 3B values,
-    each linear + bounded noise with its own seed, constant or linear model (50/50), partition size
-    256/1024/4096. Encode and decode all columns in one pass (decode: one persistent launch, also as
+    each linear + noise, sorted normal or sorted lognormal with its own seed, constant or linear
+    model (50/50), partition size 256/1024/4096. Encode and decode all columns in one pass (decode: one persistent launch, also as
     a CUDA graph, with the autotuned scan shape) against one launch per column."""
     import numpy as np
     import torch
@@ -567,22 +581,11 @@ def run_batch(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    g = W.rng(41)
-    ncols = args.batch_columns
-    lens = np.exp(g.uniform(np.log(1e3), np.log(1e7), size=ncols))
-    lens = np.maximum(1000, np.rint(lens * (args.batch_total / lens.sum()))).astype(np.int64)
-    models = g.integers(0, 2, size=ncols).tolist()
-    Ls = g.choice([256, 1024, 4096], size=ncols).tolist()
-    slopes = g.integers(1, 100, size=ncols)
-    noises = g.integers(1, 2000, size=ncols)
-    gen = torch.Generator(device=dev)
-    vals = []
-    for c in range(ncols):
-        gen.manual_seed(1000 + c)
-        n = int(lens[c])
-        v = torch.arange(n, dtype=torch.int64, device=dev) * int(slopes[c]) + (1 << 30)
-        v += torch.randint(-int(noises[c]), int(noises[c]) + 1, (n,), generator=gen, dtype=torch.int64, device=dev)
-        vals.append(v)
+    spec = W.batch_spec(args.batch_columns, int(args.batch_total))
+    ncols = len(spec["lens"])
+    lens = spec["lens"]
+    models, Ls = spec["model"].tolist(), spec["L"].tolist()
+    vals = upload_columns(W.batch_column, spec, ncols, dev)
     total = int(lens.sum())
 
     def ev_time(fn, reps=1):
@@ -610,11 +613,10 @@ def run_batch(args):
     comp = sum(c.stats()["record_bytes"] + c.stats()["residual_bytes"] for c in cols)
     for c in single:
         c.free()
-    # autotune the scan on a representative column, then decode
-    mid = int(np.argsort(lens)[ncols // 2])
-    tuned = leco.leco_tune_scan(cols[mid], 0)
+    # autotune the plan's scan shape (every candidate times the whole multi-column launch), then decode
     outs = [torch.empty(int(n), dtype=torch.int64, device=dev) for n in lens]
     plan = leco.leco_batch_plan_create(cols, outs)
+    tuned = leco.leco_batch_plan_tune(plan)
     reps = max(3, min(args.steps, 20))
     leco.leco_batch_plan_run(plan)
     t_plan, _ = ev_time(lambda: leco.leco_batch_plan_run(plan), reps)
@@ -635,8 +637,8 @@ def run_batch(args):
     dec_bytes = comp + 8 * total
     enc_bytes = 8 * total + comp
     print(json.dumps({
-        "workload": f"batched: {ncols} uint64 columns, {total} values (log-uniform 1K-10M rescaled), L in {{256,1024,4096}}, "
-                    "constant/linear 50/50",
+        "workload": f"batched: {ncols} uint64 columns, {total} values (log-uniform 1K-10M rescaled; linear + noise, "
+                    "sorted normal, sorted lognormal), L in {256,1024,4096}, constant/linear 50/50",
         "results": {
             "encode_batched_ms": t_benc, "encode_batched_gbs": enc_bytes / (t_benc * 1e-3) / 1e9,
             "encode_per_column_ms": t_penc, "encode_speedup": t_penc / t_benc, "encode_identical": same,
@@ -653,7 +655,7 @@ def run_batch(args):
 
 def run_serve(args):
     """Serving form: 2,000 resident uint64 columns (lengths log-uniform 100K-50M rescaled to 2.5B
-    values, half fixed L=4096, half variable), admitted against a 40 GB budget; a Poisson stream of
+    values; half fixed L=4096 over linear + noise, half variable over piecewise-linear), admitted against a 40 GB budget; a Poisson stream of
     requests (50% lookups of log-uniform 1-4096 indices, 50% range decodes of log-uniform 1K-1M
     values) at several offered loads, continuous batching vs one launch per request. Also an
     admission-stress run with the budget at half the resident size."""
@@ -668,24 +670,16 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    g = W.rng(53)
-    ncols = args.serve_columns
-    lens = np.exp(g.uniform(np.log(1e5), np.log(5e7), size=ncols))
-    lens = np.maximum(100_000, np.rint(lens * (args.serve_total / lens.sum()))).astype(np.int64)
-    slopes = g.integers(1, 100, size=ncols)
-    noises = g.integers(1, 4000, size=ncols)
-    gen = torch.Generator(device=dev)
+    spec = W.serve_spec(args.serve_columns, int(args.serve_total))
+    ncols = len(spec["lens"])
 
     def build_columns():
+        vals = upload_columns(W.serve_column, spec, ncols, dev)
         out = []
         for c in range(ncols):
-            gen.manual_seed(7000 + c)
-            n = int(lens[c])
-            v = torch.arange(n, dtype=torch.int64, device=dev) * int(slopes[c]) + (1 << 32)
-            v += torch.randint(-int(noises[c]), int(noises[c]) + 1, (n,), generator=gen, dtype=torch.int64, device=dev)
-            pol = leco.fixed(4096) if c % 2 == 0 else leco.variable(args.tau)
-            out.append(leco.leco_encode(v, pol, leco.LECO_MODEL_LINEAR))
-            del v
+            pol = leco.variable(args.tau) if spec["variable"][c] else leco.fixed(4096)
+            out.append(leco.leco_encode(vals[c], pol, leco.LECO_MODEL_LINEAR))
+            vals[c] = None
         return out
 
     results = {}
@@ -735,7 +729,7 @@ def run_serve(args):
               "resident_bytes": st["resident_bytes"], "reserved_bytes": st["reserved_bytes"]}
     s.destroy()
     print(json.dumps({
-        "workload": f"serving: {ncols} resident uint64 columns, {int(lens.sum())} values, half fixed / half variable, "
+        "workload": f"serving: {ncols} resident uint64 columns, {int(spec['lens'].sum())} values, half fixed / half variable, "
                     "budget 40 GB; Poisson requests, 50% lookups (1-4096), 50% ranges (1K-1M)",
         "build_s": build_s, "resident_bytes": resident, "results": results, "admission_stress": stress}), flush=True)
     return 0

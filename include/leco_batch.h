@@ -52,6 +52,12 @@ leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream);
  * instantiates the graph; every call launches the graph on `stream`. */
 leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream);
 
+/* Time the plan's launch under every candidate pipeline shape (the whole multi-column decode, on
+ * `stream`, writing the plan's outputs) and keep the fastest for this plan's later runs; a graph
+ * captured with another shape is captured again on its next run. The process-wide table of
+ * leco_tune_scan is not changed. Synchronizes `stream`. Errors: INVALID_ARG, CUDA. */
+leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, leco_scan_config* best);
+
 /* Number of jobs (scan tiles) in the plan. */
 uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan);
 

@@ -170,7 +170,7 @@ leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream) {
 leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream) {
   if (!plan) return LECO_ERR_INVALID_ARG;
   if (!plan->exec) {
-    cudaError_t e = cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking);
+    cudaError_t e = plan->capture ? cudaSuccess : cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(plan->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       const cudaError_t le = launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes,
@@ -182,6 +182,62 @@ leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t strea
     if (e != cudaSuccess) return from_cuda(e);
   }
   return from_cuda(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+}
+
+leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, leco_scan_config* best) {
+  if (!plan || !best) return LECO_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return LECO_ERR_CUDA;
+  const uint32_t stages[] = {2, 3, 4, 6, 8};
+  const uint32_t warps[] = {4, 8};
+  ScanConfig chosen = plan->cfg;
+  float best_ms = -1.0f;
+  for (uint32_t cw : warps) {
+    for (uint32_t ns : stages) {
+      const ScanConfig cfg{ns, cw};
+      auto run = [&]() {
+        return launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes, cfg,
+                                   plan->d_status, st);
+      };
+      if (run() != cudaSuccess) {  // e.g. too much shared memory for the plan's widest tile: skip
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(a, st);
+      const bool ok = run() == cudaSuccess && run() == cudaSuccess;
+      cudaEventRecord(b, st);
+      if (!ok || cudaEventSynchronize(b) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      ms /= 2.0f;
+      if (best_ms < 0 || ms < best_ms) {
+        best_ms = ms;
+        chosen = cfg;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (cudaStreamSynchronize(st) != cudaSuccess || best_ms < 0) return LECO_ERR_CUDA;
+  if (chosen.stages != plan->cfg.stages || chosen.consumer_warps != plan->cfg.consumer_warps) {
+    plan->cfg = chosen;
+    if (plan->exec) {  // the captured graph holds the old launch shape: capture again on next use
+      cudaGraphExecDestroy(plan->exec);
+      plan->exec = nullptr;
+    }
+    if (plan->graph) {
+      cudaGraphDestroy(plan->graph);
+      plan->graph = nullptr;
+    }
+  }
+  best->stages = chosen.stages;
+  best->consumer_warps = chosen.consumer_warps;
+  best->ms = best_ms;
+  return LECO_OK;
 }
 
 uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan) { return plan ? plan->nitems : 0; }

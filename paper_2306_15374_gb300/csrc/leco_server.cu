@@ -50,7 +50,10 @@ struct ColSlot {
 
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t ldone = nullptr;  // the batch's lookup results are on the host
+  cudaEvent_t done = nullptr;   // all of the batch's results are on the host
+  bool lookups_done = false;    // lookup requests already completed
+  Clock::time_point mock_done;  // mock executor: when the batch counts as finished
   uint64_t* h_idx = nullptr;
   uint32_t* h_col = nullptr;
   uint64_t* h_lout = nullptr;
@@ -103,6 +106,7 @@ namespace {
 void slot_free(Slot& sl) {
   if (sl.stream) cudaStreamDestroy(sl.stream);
   if (sl.done) cudaEventDestroy(sl.done);
+  if (sl.ldone) cudaEventDestroy(sl.ldone);
   cudaFreeHost(sl.h_idx);
   cudaFreeHost(sl.h_col);
   cudaFreeHost(sl.h_lout);
@@ -124,6 +128,7 @@ cudaError_t slot_alloc(Slot& sl, const leco_server_config& c, uint64_t cap_items
   const uint64_t L = c.max_batch_lookups, rb = 8 * c.max_batch_values + 16 * (uint64_t)c.max_batch_requests;
   cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ldone, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_idx, 8 * L);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_col, 4 * L);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_lout, 8 * L);
@@ -186,6 +191,7 @@ void gpu_run(leco_server* s, Slot& sl) {
   }
   if (nl && staged_lookups && e == cudaSuccess)
     e = cudaMemcpyAsync(sl.h_lout, sl.d_lout, 8 * nl, cudaMemcpyDeviceToHost, sl.stream);
+  if (nl && e == cudaSuccess) e = cudaEventRecord(sl.ldone, sl.stream);  // lookups complete before ranges
   if (ni && e == cudaSuccess) {
     e = cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, sl.stream);
     uint32_t sb;
@@ -223,8 +229,14 @@ void batcher_loop(leco_server* s) {
     sl.reqs.clear();
     sl.off.clear();
     sl.nl = sl.nitems = sl.rbytes = sl.values = 0;
+    sl.lookups_done = false;
+    sl.err = cudaSuccess;
     uint64_t items = 0;
-    while (!s->queue.empty() && sl.reqs.size() < s->cfg.max_batch_requests) {
+    // share the queue among the free slots: with idle slots, requests spread out (no waiting
+    // behind each other's work); with one free slot, it takes everything queued (up to the caps)
+    const uint64_t share = (s->queue.size() + s->free_slots.size()) / (s->free_slots.size() + 1);
+    const uint64_t limit = std::min<uint64_t>(s->cfg.max_batch_requests, std::max<uint64_t>(1, share));
+    while (!s->queue.empty() && sl.reqs.size() < limit) {
       Req* r = s->queue.front();
       uint64_t off;
       if (r->type == 0) {
@@ -244,7 +256,10 @@ void batcher_loop(leco_server* s) {
       sl.off.push_back(off);
     }
     lk.unlock();
-    if (!s->cfg.mock) gpu_run(s, sl);
+    if (s->cfg.mock)
+      sl.mock_done = Clock::now() + std::chrono::microseconds(s->cfg.mock_batch_us);
+    else
+      gpu_run(s, sl);
     lk.lock();
     s->batches++;
     s->launches += s->cfg.mock ? 0 : (uint64_t)(sl.nl > 0) + (uint64_t)(sl.nitems > 0);
@@ -259,72 +274,106 @@ void batcher_loop(leco_server* s) {
 // host-only executor: values are a fixed function of (column, position)
 inline uint64_t mock_value(uint32_t col, uint64_t i) { return ((uint64_t)col << 40) ^ (i * 0x9E3779B97F4A7C15ull); }
 
+// true once stage 0 (the slot's lookups) or stage 1 (all its work) has finished, or failed
+bool slot_reached(leco_server* s, Slot& sl, int stage) {
+  if (sl.err != cudaSuccess) return true;
+  if (s->cfg.mock) return Clock::now() >= sl.mock_done;
+  if (stage == 0 && sl.nl == 0) return true;
+  const cudaError_t e = cudaEventQuery(stage == 0 ? sl.ldone : sl.done);
+  if (e == cudaErrorNotReady) return false;
+  if (e != cudaSuccess) sl.err = e;
+  return true;
+}
+
+// Deliver the results of the slot's requests of one type (0 lookups, 1 ranges) whose GPU work has
+// finished, then mark them done. A completed request's entry is cleared: its owner may free it.
+void deliver(leco_server* s, Slot& sl, int type) {
+  const cudaError_t e = sl.err;
+  for (size_t k = 0; k < sl.reqs.size(); k++) {
+    Req* r = sl.reqs[k];
+    if (!r || r->type != type) continue;
+    const uint64_t vb = vbytes(r->dtype);
+    if (e != cudaSuccess) {
+      r->status = e == cudaErrorLaunchTimeout ? LECO_ERR_TIMEOUT : LECO_ERR_CUDA;
+      continue;
+    }
+    if (r->direct && !s->cfg.mock && !(r->type == 0 && r->dtype == LECO_U32)) continue;  // already there
+    if (r->type == 0) {
+      const uint64_t o = sl.off[k];
+      for (uint64_t q = 0; q < r->idx.size(); q++) {
+        const uint64_t v = s->cfg.mock ? mock_value(r->col, r->idx[q]) : sl.h_lout[o + q];
+        if (vb == 4)
+          static_cast<uint32_t*>(r->out)[q] = (uint32_t)v;
+        else
+          static_cast<uint64_t*>(r->out)[q] = v;
+      }
+    } else if (s->cfg.mock) {
+      for (uint64_t q = 0; q < r->count; q++) {
+        const uint64_t v = mock_value(r->col, r->begin + q);
+        if (vb == 4)
+          static_cast<uint32_t*>(r->out)[q] = (uint32_t)v;
+        else
+          static_cast<uint64_t*>(r->out)[q] = v;
+      }
+    } else {
+      memcpy(r->out, sl.h_rout + sl.off[k], r->count * vb);
+    }
+  }
+  const Clock::time_point now = Clock::now();
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (Req*& r : sl.reqs) {
+    if (!r || r->type != type) continue;
+    r->done = true;
+    const double us = std::chrono::duration<double, std::micro>(now - r->t0).count();
+    s->lat_us.push_back(us);
+    s->completed++;
+    if (r->status != LECO_OK) s->failed++;
+    if (r->type == 0)
+      s->lookups += r->idx.size();
+    else
+      s->range_values += r->count;
+    if (r->col < s->cols.size() && s->cols[r->col].pending) s->cols[r->col].pending--;
+    if (r->detached) {
+      s->outstanding_detached--;
+      delete r;
+    }
+    r = nullptr;
+  }
+  s->cv.notify_all();
+}
+
+// Completes requests as their slots finish, in whatever order that happens: every in-flight slot
+// is polled, its lookups complete when their results have landed (before the batch's range
+// decodes), the rest when the batch is done, and the slot is then free for the batcher.
 void completer_loop(leco_server* s) {
   if (!s->cfg.mock) cudaSetDevice(s->device);
+  std::vector<int> flight;
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    s->cv.wait(lk, [&] { return !s->inflight.empty() || (s->batcher_done && s->inflight.empty()); });
-    if (s->inflight.empty()) break;
-    const int si = s->inflight.front();
-    s->inflight.pop_front();
-    Slot& sl = s->slots[si];
+    s->cv.wait(lk, [&] { return !s->inflight.empty() || s->batcher_done; });
+    if (s->inflight.empty()) break;  // the batcher has stopped and everything is delivered
+    flight.assign(s->inflight.begin(), s->inflight.end());
     lk.unlock();
-    cudaError_t e = sl.err;
-    if (s->cfg.mock) {
-      std::this_thread::sleep_for(std::chrono::microseconds(s->cfg.mock_batch_us));
-    } else if (e == cudaSuccess) {
-      e = cudaEventSynchronize(sl.done);
-    }
-    for (size_t k = 0; k < sl.reqs.size(); k++) {
-      Req* r = sl.reqs[k];
-      const uint64_t vb = vbytes(r->dtype);
-      if (e != cudaSuccess) {
-        r->status = e == cudaErrorLaunchTimeout ? LECO_ERR_TIMEOUT : LECO_ERR_CUDA;
-        continue;
+    bool progress = false;
+    for (int si : flight) {
+      Slot& sl = s->slots[si];
+      if (!sl.lookups_done && slot_reached(s, sl, 0)) {
+        deliver(s, sl, 0);
+        sl.lookups_done = true;
+        progress = true;
       }
-      if (r->direct && !s->cfg.mock && !(r->type == 0 && r->dtype == LECO_U32)) continue;  // already there
-      if (r->type == 0) {
-        const uint64_t o = sl.off[k];
-        for (uint64_t q = 0; q < r->idx.size(); q++) {
-          const uint64_t v = s->cfg.mock ? mock_value(r->col, r->idx[q]) : sl.h_lout[o + q];
-          if (vb == 4)
-            static_cast<uint32_t*>(r->out)[q] = (uint32_t)v;
-          else
-            static_cast<uint64_t*>(r->out)[q] = v;
-        }
-      } else if (s->cfg.mock) {
-        for (uint64_t q = 0; q < r->count; q++) {
-          const uint64_t v = mock_value(r->col, r->begin + q);
-          if (vb == 4)
-            static_cast<uint32_t*>(r->out)[q] = (uint32_t)v;
-          else
-            static_cast<uint64_t*>(r->out)[q] = v;
-        }
-      } else {
-        memcpy(r->out, sl.h_rout + sl.off[k], r->count * vb);
+      if (sl.lookups_done && slot_reached(s, sl, 1)) {
+        deliver(s, sl, 1);
+        std::lock_guard<std::mutex> lock(s->mu);
+        sl.reqs.clear();
+        s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), si));
+        s->free_slots.push_back(si);
+        s->cv.notify_all();
+        progress = true;
       }
     }
-    const Clock::time_point now = Clock::now();
+    if (!progress) std::this_thread::yield();
     lk.lock();
-    for (Req* r : sl.reqs) {
-      r->done = true;
-      const double us = std::chrono::duration<double, std::micro>(now - r->t0).count();
-      s->lat_us.push_back(us);
-      s->completed++;
-      if (r->status != LECO_OK) s->failed++;
-      if (r->type == 0)
-        s->lookups += r->idx.size();
-      else
-        s->range_values += r->count;
-      if (r->col < s->cols.size() && s->cols[r->col].pending) s->cols[r->col].pending--;
-      if (r->detached) {
-        s->outstanding_detached--;
-        delete r;
-      }
-    }
-    sl.reqs.clear();
-    s->free_slots.push_back(si);
-    s->cv.notify_all();
   }
 }
 

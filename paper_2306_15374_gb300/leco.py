@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
         "leco_batch_plan_run": (i32, [vp, vp]),
         "leco_batch_plan_run_graph": (i32, [vp, vp]),
         "leco_batch_plan_jobs": (u64, [vp]),
+        "leco_batch_plan_tune": (i32, [vp, vp, ctypes.POINTER(ScanConfig)]),
         "leco_batch_plan_free": (None, [vp]),
         "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
         "leco_batch_encode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
@@ -411,6 +412,13 @@ def leco_batch_plan_run(plan: BatchPlan, stream=None) -> None:
 
 def leco_batch_plan_run_graph(plan: BatchPlan, stream=None) -> None:
     _check(lib().leco_batch_plan_run_graph(plan.handle, _stream(stream)), "leco_batch_plan_run_graph")
+
+
+def leco_batch_plan_tune(plan: BatchPlan, stream=None) -> dict:
+    """Time the plan under every scan shape and keep the fastest for this plan."""
+    cfg = ScanConfig()
+    _check(lib().leco_batch_plan_tune(plan.handle, _stream(stream), ctypes.byref(cfg)), "leco_batch_plan_tune")
+    return {"stages": cfg.stages, "consumer_warps": cfg.consumer_warps, "ms": cfg.ms}
 
 
 def leco_batch_plan_jobs(plan: BatchPlan) -> int:

@@ -45,12 +45,12 @@ def test_budget_admission(lc):
 
 
 def test_results_route_to_the_right_requests(lc):
-    s = lc.leco_server_create(1 << 30, mock=True, mock_batch_us=200)
+    s = lc.leco_server_create(1 << 30, mock=True, mock_batch_us=2000)
     cols = {lc.leco_server_admit_mock(s, 100_000, lc.LECO_U64, 1000): 64,
             lc.leco_server_admit_mock(s, 50_000, lc.LECO_U32, 1000): 32}
     g = np.random.default_rng(5)
     reqs = []
-    for _ in range(200):
+    for _ in range(200):  # submitted back to back: arrivals outpace the slots, so batches form
         cid = list(cols)[int(g.integers(0, 2))]
         bits = cols[cid]
         n = 100_000 if bits == 64 else 50_000
@@ -58,17 +58,16 @@ def test_results_route_to_the_right_requests(lc):
             idx = g.integers(0, n, size=int(g.integers(1, 300)), dtype=np.uint64)
             out = np.zeros(idx.size, dtype=np.uint64 if bits == 64 else np.uint32)
             rid = lc.leco_server_submit_lookup(s, cid, idx, out)
-            want = [mock_value(cid, int(i), bits) for i in idx]
+            reqs.append((rid, out, cid, bits, [int(i) for i in idx]))
         else:
             b = int(g.integers(0, n - 10))
             cnt = int(g.integers(1, min(5000, n - b)))
             out = np.zeros(cnt, dtype=np.uint64 if bits == 64 else np.uint32)
             rid = lc.leco_server_submit_range(s, cid, b, cnt, out)
-            want = [mock_value(cid, b + k, bits) for k in range(cnt)]
-        reqs.append((rid, out, want))
-    for rid, out, want in reqs:
+            reqs.append((rid, out, cid, bits, range(b, b + cnt)))
+    for rid, out, cid, bits, pos in reqs:
         assert lc.leco_server_wait(s, rid) == lc.LECO_OK
-        assert out.tolist() == want
+        assert out.tolist() == [mock_value(cid, i, bits) for i in pos]
     st = lc.leco_server_stats_get(s)
     assert st["completed"] == 200 and st["failed"] == 0
     assert st["batches"] < 200 and st["max_batch_size"] > 1  # requests arriving together share batches

@@ -198,3 +198,44 @@ def cfg3(dist: str, n: int | None = None) -> np.ndarray:
     if dist == "b":
         return timestamps_u32(500_000_000 if n is None else n, seed=5)
     raise ValueError(dist)
+
+
+# ----------------------------------------------------------------------------- many-column workloads
+
+def batch_spec(ncols: int = 10_000, total: int = 3_000_000_000, seed: int = 41) -> dict:
+    """The many-column batch: lengths log-uniform in [1K, 10M], rescaled so they sum to `total`
+    (each at least 1K); each column one of the three fixed-partition distributions (0: linear +
+    noise as the 1M-value column, 1: sorted normal, 2: sorted lognormal, as the 200M-value ones),
+    the constant or linear model (50/50) and a partition size in {256, 1024, 4096}."""
+    g = rng(seed)
+    lens = np.exp(g.uniform(np.log(1e3), np.log(1e7), size=ncols))
+    lens = np.maximum(1000, np.rint(lens * (total / lens.sum()))).astype(np.int64)
+    return {"lens": lens, "dist": g.integers(0, 3, size=ncols), "model": g.integers(0, 2, size=ncols),
+            "L": g.choice(np.array([256, 1024, 4096]), size=ncols)}
+
+
+def batch_column(spec: dict, c: int) -> np.ndarray:
+    n, d = int(spec["lens"][c]), int(spec["dist"][c])
+    if d == 0:
+        return linear_noise(n, 1000, 37, 500, seed=1000 + c)
+    if d == 1:
+        return sorted_normal(n, float(1 << 40), float(1 << 36), seed=1000 + c)
+    return sorted_lognormal(n, 1e9, 2.0, seed=1000 + c)
+
+
+def serve_spec(ncols: int = 2_000, total: int = 2_500_000_000, seed: int = 53) -> dict:
+    """The resident columns of the serving workload: lengths log-uniform in [100K, 50M], rescaled
+    so they sum to `total` (each at least 100K); even columns fixed partitions (L = 4096) over
+    linear + noise values, odd columns variable partitions over piecewise-linear values."""
+    g = rng(seed)
+    lens = np.exp(g.uniform(np.log(1e5), np.log(5e7), size=ncols))
+    lens = np.maximum(100_000, np.rint(lens * (total / lens.sum()))).astype(np.int64)
+    return {"lens": lens, "slope": g.integers(1, 100, size=ncols), "noise": g.integers(1, 4000, size=ncols),
+            "variable": np.arange(ncols) % 2 == 1}
+
+
+def serve_column(spec: dict, c: int) -> np.ndarray:
+    n = int(spec["lens"][c])
+    if spec["variable"][c]:
+        return piecewise_linear(n, segments=max(1, n // 200_000), mean_len=200_000, seed=7000 + c)
+    return linear_noise(n, 1 << 32, int(spec["slope"][c]), int(spec["noise"][c]), seed=7000 + c)
