@@ -220,6 +220,12 @@ void leco_column_free(leco_column* col);
  * `stream` completes; the caller guarantees that no other stream still uses the column. */
 void leco_column_free_async(leco_column* col, leco_stream_t stream);
 
+/* Device memory: the library allocates from its own stream-ordered pool on each device, which keeps
+ * freed memory cached for reuse. This call returns the cached memory of the current device's pool to
+ * the driver (memory still owned by live columns stays). Synchronizes the device. Errors: CUDA.
+ * A systems facility; the paper has no counterpart. */
+leco_status leco_trim_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,7 @@ namespace leco {
 inline leco_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return LECO_OK;
   if (e == cudaErrorMemoryAllocation) return LECO_ERR_OOM;
+  if (e == cudaErrorTimeout) return LECO_ERR_TIMEOUT;  // a bounded device wait gave up (reported by the host)
   return LECO_ERR_CUDA;
 }
 

@@ -2,7 +2,8 @@
 //
 // Fit of one partition of N values (w = the value as two's complement int64):
 //  1. exact least-squares slope q = 6S/D, S = sum (2x - (N-1)) (w_x - w_0), D = N (N^2 - 1)
-//     (integer moments reduced across the group in int128; q = 0 for the constant model);
+//     (integer moments reduced across the group in int128; q = 0 for the constant model; the
+//     divisions are exact 128-by-64 long divisions where the divisor allows, see floordiv_i128);
 //  2. magnitude bound U = max|w| + (wmax - wmin) + (ceil|q| + 1) N + 4; bitlen(U) > 62 falls back
 //     to the constant model on the grid 2^11 (residuals taken mod 2^64);
 //  3. grid exponent s = min(52, 52 - bitlen(U)), slope B = round(q 2^s) (half up);
@@ -21,13 +22,62 @@ namespace {
 
 
 
-__device__ __forceinline__ i128 floordiv_i128(i128 num, i128 den) {  // den > 0
-  i128 q = num / den;
-  if ((num % den) != 0 && num < 0) q -= 1;
-  return q;
+// (u1 2^64 + u0) / v for u1 < v (so the quotient fits 64 bits), with the remainder: schoolbook
+// long division in base 2^32 after normalising v (Knuth's algorithm D with two quotient digits, in
+// the form of Warren's "divlu", Hacker's Delight §9-4). Each digit is estimated from the top two
+// dividend digits over the top divisor digit and corrected at most twice.
+__host__ __device__ __forceinline__ uint64_t divlu(uint64_t u1, uint64_t u0, uint64_t v, uint64_t* rem) {
+  const uint64_t base = 1ull << 32;
+#ifdef __CUDA_ARCH__
+  const int sh = __clzll((long long)v);  // v > 0
+#else
+  const int sh = __builtin_clzll(v);
+#endif
+  v <<= sh;
+  const uint64_t vn1 = v >> 32, vn0 = v & 0xFFFFFFFFull;
+  const uint64_t un32 = sh ? (u1 << sh) | (u0 >> (64 - sh)) : u1;
+  const uint64_t un10 = u0 << sh;
+  const uint64_t un1 = un10 >> 32, un0 = un10 & 0xFFFFFFFFull;
+  uint64_t q1 = un32 / vn1, rhat = un32 - q1 * vn1;
+  while (q1 >= base || q1 * vn0 > base * rhat + un1) {
+    q1--;
+    rhat += vn1;
+    if (rhat >= base) break;
+  }
+  const uint64_t un21 = un32 * base + un1 - q1 * v;
+  uint64_t q0 = un21 / vn1;
+  rhat = un21 - q0 * vn1;
+  while (q0 >= base || q0 * vn0 > base * rhat + un0) {
+    q0--;
+    rhat += vn1;
+    if (rhat >= base) break;
+  }
+  *rem = (un21 * base + un0 - q0 * v) >> sh;
+  return q1 * base + q0;
 }
 
-__device__ __forceinline__ i128 round_half_up_i128(i128 num, i128 den) {  // den > 0
+// floor(num / den) for den > 0, exactly. Divisors below 2^64 (every fit of a partition up to 2^21
+// values) take two native 64-bit divisions and one 128-by-64 long division; wider divisors use
+// the generic 128-bit routine, whose bit-serial latency would otherwise stall a whole CTA per
+// fitted partition.
+__host__ __device__ __forceinline__ i128 floordiv_i128(i128 num, i128 den) {
+  if ((den >> 64) == 0 && num != ((i128)1 << 127)) {
+    const uint64_t d = (uint64_t)den;
+    const bool neg = num < 0;
+    const u128 u = neg ? (u128)0 - (u128)num : (u128)num;
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    const uint64_t qh = hi / d;
+    uint64_t r = 0;
+    const uint64_t ql = divlu(hi - qh * d, lo, d, &r);
+    const u128 q = ((u128)qh << 64) | ql;
+    return neg ? -(i128)q - (r != 0 ? 1 : 0) : (i128)q;
+  }
+  i128 t = num / den;
+  if ((num % den) != 0 && num < 0) t -= 1;
+  return t;
+}
+
+__host__ __device__ __forceinline__ i128 round_half_up_i128(i128 num, i128 den) {  // den > 0
   return floordiv_i128(2 * num + den, 2 * den);
 }
 
@@ -55,7 +105,7 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   const i128 D = lin ? (i128)N * ((i128)N * (i128)N - 1) : (i128)1;
   const i128 sixS = lin ? 6 * S : (i128)0;
   const i128 a6 = sixS < 0 ? -sixS : sixS;
-  const i128 Q = (a6 + D - 1) / D;
+  const i128 Q = floordiv_i128(a6 + D - 1, D);  // ceil(|6S| / D)
   const i128 amx = mx < 0 ? -(i128)mx : (i128)mx;
   const i128 amn = mn < 0 ? -(i128)mn : (i128)mn;
   const i128 M = amx > amn ? amx : amn;
@@ -63,7 +113,7 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   const int eU = bitlen_u128((u128)U);
   if (eU > 62) {
     const i128 t = (i128)mn + (((i128)mx - (i128)mn + 1) / 2);
-    const i128 tg = floordiv_i128(t, (i128)2048);
+    const i128 tg = t >> 11;  // floor(t / 2^11)
     P.fallback = 1;
     P.s = -11;
     P.B = 0;
@@ -103,7 +153,7 @@ __device__ FitResult finish_fit(const FitParams& P, int64_t lo, int64_t hi, uint
     shift = t;
     A = t * ((i128)1 << s);
   } else {
-    const i128 tg = floordiv_i128(t, (i128)1 << (-s));
+    const i128 tg = t >> (-s);  // floor(t / 2^-s)
     shift = tg * ((i128)1 << (-s));
     A = tg;
   }
@@ -116,10 +166,6 @@ __device__ FitResult finish_fit(const FitParams& P, int64_t lo, int64_t hi, uint
   return R;
 }
 
-__device__ __forceinline__ int64_t line_at(int64_t B, int32_t s, uint32_t x) {
-  const int64_t bx = B * (int64_t)x;
-  return s >= 0 ? (bx >> s) : (bx << (-s));
-}
 
 // Group fit: GROUP threads (a warp, or a whole CTA when GROUP > 32) fit [a, a+N). Returns the
 // result in every thread of the group. sm: shared scratch (only used when GROUP > 32).
@@ -131,23 +177,85 @@ struct FitShared {
   FitResult R;
 };
 
+// Pass 1 over one group member's positions x = rank, rank + GROUP, ... < N of the values v (the
+// partition's first value at v[0]): min, max and (linear model) S = sum u_x w_x with
+// u_x = 2x - (N-1), where w is the value as two's complement int64. S equals
+// sum u_x (w_x - w_0) because the u_x sum to zero. Each term is split as u w_hi 2^32 + u w_lo with
+// 32 x 32 -> 64-bit products, accumulated in 64 bits over at most 64 terms (|u| < 2^24: each
+// partial stays below 2^62), then folded into 128 bits.
+template <int GROUP, typename T>
+__device__ __forceinline__ void fit_pass1(const T* __restrict__ v, uint32_t N, bool lin, uint32_t rank, i128* S_out,
+                                          int64_t* mx_out, int64_t* mn_out) {
+  int64_t mx = INT64_MIN, mn = INT64_MAX;
+  i128 S = 0;
+  if (lin) {
+    const int64_t nm1 = (int64_t)N - 1;
+    for (uint32_t x0 = rank; x0 < N; x0 += 64u * GROUP) {
+      const uint32_t xe = N - x0 > 64u * GROUP ? x0 + 64u * GROUP : N;
+      int64_t acc_hi = 0, acc_lo = 0;
+      int32_t u = (int32_t)(2 * (int64_t)x0 - nm1);
+#pragma unroll 4
+      for (uint32_t x = x0; x < xe; x += GROUP, u += 2 * GROUP) {
+        const int64_t w = (int64_t)__ldg(v + x);
+        mx = max(mx, w);
+        mn = min(mn, w);
+        if (sizeof(T) == 8) acc_hi += (int64_t)u * (int64_t)(int32_t)(w >> 32);
+        acc_lo += (int64_t)u * (int64_t)(uint32_t)w;
+      }
+      S += (i128)acc_hi * ((i128)1 << 32) + (i128)acc_lo;
+    }
+  } else {
+#pragma unroll 4
+    for (uint32_t x = rank; x < N; x += GROUP) {
+      const int64_t w = (int64_t)__ldg(v + x);
+      mx = max(mx, w);
+      mn = min(mn, w);
+    }
+  }
+  *S_out = S;
+  *mx_out = mx;
+  *mn_out = mn;
+}
+
+// Pass 2: range [lo, hi] of the residuals w_x - line(x) with line(x) = (B x) >> s (s >= 0) or
+// (B x) << -s, B x taken mod 2^64 and stepped by B GROUP from one position to the next.
+template <int GROUP, typename T>
+__device__ __forceinline__ void fit_pass2(const T* __restrict__ v, uint32_t N, int64_t B, int32_t s, uint32_t rank,
+                                          int64_t* lo_out, int64_t* hi_out) {
+  int64_t lo = INT64_MAX, hi = INT64_MIN;
+  uint64_t F = (uint64_t)B * rank;
+  const uint64_t dF = (uint64_t)B * GROUP;
+  if (s >= 0) {
+#pragma unroll 4
+    for (uint32_t x = rank; x < N; x += GROUP, F += dF) {
+      const int64_t r = (int64_t)__ldg(v + x) - ((int64_t)F >> s);
+      lo = min(lo, r);
+      hi = max(hi, r);
+    }
+  } else {
+    for (uint32_t x = rank; x < N; x += GROUP, F += dF) {
+      const int64_t r = (int64_t)__ldg(v + x) - (int64_t)(F << (-s));
+      lo = min(lo, r);
+      hi = max(hi, r);
+    }
+  }
+  *lo_out = lo;
+  *hi_out = hi;
+}
+
 template <int GROUP>
 __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint64_t a, uint32_t N,
                                int model, uint32_t rank, FitShared* sm) {
   const bool lin = model == LECO_MODEL_LINEAR && N >= 2;
-  const int64_t w0 = (int64_t)load_value(values, dtype, a);
-  i128 S = 0;
-  int64_t mx = INT64_MIN, mn = INT64_MAX;
-  const int64_t nm1 = (int64_t)N - 1;
-  for (uint32_t x = rank; x < N; x += GROUP) {
-    const int64_t w = (int64_t)load_value(values, dtype, a + x);
-    mx = max(mx, w);
-    mn = min(mn, w);
-    if (lin) {
-      const int64_t u = 2 * (int64_t)x - nm1;
-      S += (i128)u * ((i128)w - (i128)w0);
-    }
-  }
+  const bool u32 = dtype == LECO_U32;
+  const uint32_t* v32 = static_cast<const uint32_t*>(values) + a;
+  const uint64_t* v64 = static_cast<const uint64_t*>(values) + a;
+  i128 S;
+  int64_t mx, mn;
+  if (u32)
+    fit_pass1<GROUP>(v32, N, lin, rank, &S, &mx, &mn);
+  else
+    fit_pass1<GROUP>(v64, N, lin, rank, &S, &mx, &mn);
   S = warp_sum_i128(S);
   mx = warp_max_i64(mx);
   mn = warp_min_i64(mn);
@@ -184,17 +292,15 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
   uint64_t zmax = 0;
   if (P.fallback) {
     for (uint32_t x = rank; x < N; x += GROUP) {
-      const uint64_t v = load_value(values, dtype, a + x);
+      const uint64_t v = u32 ? (uint64_t)__ldg(v32 + x) : __ldg(v64 + x);
       zmax = max(zmax, zz_encode((int64_t)(v - (uint64_t)P.fb_shift)));
     }
     zmax = warp_max_u64(zmax);
   } else {
-    for (uint32_t x = rank; x < N; x += GROUP) {
-      const int64_t w = (int64_t)load_value(values, dtype, a + x);
-      const int64_t r = w - line_at(P.B, P.s, x);
-      lo = min(lo, r);
-      hi = max(hi, r);
-    }
+    if (u32)
+      fit_pass2<GROUP>(v32, N, P.B, P.s, rank, &lo, &hi);
+    else
+      fit_pass2<GROUP>(v64, N, P.B, P.s, rank, &lo, &hi);
     lo = warp_min_i64(lo);
     hi = warp_max_i64(hi);
   }

@@ -2,12 +2,17 @@
 // decode-table build and residual packing.
 #include "fit.cuh"
 #include "leco_internal.cuh"
+#include "tma.cuh"
 
 namespace leco {
 
 namespace {
 
 constexpr int kFitBlock = 256;
+constexpr int kFitWarps = kFitBlock / 32;
+// CTAs of kFitBlock threads per SM for the fit (registers capped to fit them): the fit is bound by
+// instruction issue, so more resident warps beat keeping every partition in flight inside L2
+constexpr int kFitCtasPerSm = 4;
 
 __device__ __forceinline__ uint64_t part_begin(const uint64_t* starts, uint32_t L, uint64_t n,
                                                uint64_t p) {
@@ -16,18 +21,135 @@ __device__ __forceinline__ uint64_t part_begin(const uint64_t* starts, uint32_t 
   return s < n ? s : n;
 }
 
-// one CTA per partition (grid-stride)
-__global__ void __launch_bounds__(kFitBlock)
+// ------------------------------------------------------------------------------ staged partitions
+//
+// The fit and the packing read each partition's values twice or more, so a CTA stages the
+// partition in shared memory first: one 1-D bulk copy (TMA) of the 16-byte-aligned byte range
+// around it, completing on an mbarrier, double-buffered so the copy of the CTA's next partition
+// runs while the current one is processed. A partition the copy cannot take (the aligned range
+// would leave the array, or it does not fit a buffer) is read with plain loads: into the buffer
+// when it fits, else straight from global memory by the body.
+
+constexpr uint32_t kStageData = 32768;             // partition bytes one buffer holds
+constexpr uint32_t kStageBuf = kStageData + 32;    // + alignment lead and tail
+
+// the value at position x of a partition staged in shared memory (raw values of the column's type)
+__device__ __forceinline__ int64_t staged_value(const unsigned char* stage, int dtype, uint32_t x) {
+  return dtype == LECO_U32 ? (int64_t)reinterpret_cast<const uint32_t*>(stage)[x]
+                           : reinterpret_cast<const int64_t*>(stage)[x];
+}
+
+struct PartSrc {
+  const void* values;  // the column's values
+  uint64_t n;          // values in the column
+  uint64_t a;          // first position of the partition
+  uint32_t N;          // its length
+  int dtype;
+};
+
+// aligned byte range [g0, g0 + bytes) of the column holding the partition (at most cap value bytes);
+// lead = the partition's offset inside it
+__device__ __forceinline__ bool stage_plan(const PartSrc& s, uint32_t cap, uint64_t* g0, uint32_t* bytes,
+                                           uint32_t* lead) {
+  const uint64_t vb = s.dtype == LECO_U32 ? 4 : 8;
+  if (s.N == 0 || (uint64_t)s.N * vb > cap || (reinterpret_cast<uintptr_t>(s.values) & 15u)) return false;
+  const uint64_t b0 = s.a * vb, b1 = (s.a + s.N) * vb;
+  const uint64_t a0 = b0 & ~15ull, a1 = (b1 + 15) & ~15ull;
+  if (a1 > s.n * vb) return false;
+  *g0 = a0;
+  *bytes = (uint32_t)(a1 - a0);
+  *lead = (uint32_t)(b0 - a0);
+  return true;
+}
+
+// every thread decides (identically) whether the copy is used; thread 0 issues it
+__device__ __forceinline__ bool stage_issue(const PartSrc& s, uint32_t cap, unsigned char* dst, uint64_t* full) {
+  uint64_t g0;
+  uint32_t bytes, lead;
+  if (!stage_plan(s, cap, &g0, &bytes, &lead)) return false;
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(full, bytes);
+    bulk_g2s(dst, static_cast<const char*>(s.values) + g0, bytes, full);
+  }
+  return true;
+}
+
+// Runs body(p, src, stage) for partitions p = blockIdx.x, + gridDim.x, ... < P, where stage is the
+// partition's values in shared memory (raw, the column's type; partitions of at most cap bytes,
+// cap <= kStageData) or nullptr. NBUF = 2 copies the
+// CTA's next partition while the current one is processed; NBUF = 1 keeps the CTA small (more CTAs
+// per SM hide each other's copies instead). body must end with a __syncthreads(). On a copy that
+// never lands the CTA records kStatTimeout in *err and stops.
+template <int NBUF, typename GetPart, typename Body>
+__device__ void for_each_staged(uint64_t P, uint32_t cap, GetPart get, Body body, unsigned char* ring, uint64_t* full,
+                                uint32_t* err) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NBUF; k++) mbar_init(&full[k], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t ph = 0, armed = 0;  // bit k: buffer k's mbarrier parity / a copy into buffer k is pending
+  uint32_t buf = 0;
+  uint64_t p = blockIdx.x;
+  if (p < P && stage_issue(get(p), cap, ring, &full[0])) armed = 1u;
+  for (; p < P; p += gridDim.x, buf = NBUF == 2 ? buf ^ 1u : 0u) {
+    // the buffer written next was released by the previous body's closing barrier
+    const uint32_t nb = NBUF == 2 ? buf ^ 1u : 0u;
+    const uint64_t pn = p + gridDim.x;
+    if (NBUF == 2) {
+      armed &= ~(1u << nb);
+      if (pn < P && stage_issue(get(pn), cap, ring + nb * kStageBuf, &full[nb])) armed |= 1u << nb;
+    }
+    const PartSrc s = get(p);
+    unsigned char* b = ring + buf * kStageBuf;
+    const unsigned char* st = nullptr;
+    if ((armed >> buf) & 1u) {
+      const bool ok = mbar_wait_bounded(&full[buf], (ph >> buf) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0 && err) atomicOr(err, kStatTimeout);
+        if (NBUF == 2 && ((armed >> nb) & 1u)) mbar_wait_bounded(&full[nb], (ph >> nb) & 1u);
+        return;
+      }
+      ph ^= 1u << buf;
+      uint64_t g0;
+      uint32_t bytes, lead;
+      stage_plan(s, cap, &g0, &bytes, &lead);
+      st = b + lead;
+    } else if ((uint64_t)s.N * (s.dtype == LECO_U32 ? 4 : 8) <= cap) {
+      if (s.dtype == LECO_U32) {
+        uint32_t* d = reinterpret_cast<uint32_t*>(b);
+        for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
+          d[x] = __ldg(static_cast<const uint32_t*>(s.values) + s.a + x);
+      } else {
+        uint64_t* d = reinterpret_cast<uint64_t*>(b);
+        for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
+          d[x] = __ldg(static_cast<const uint64_t*>(s.values) + s.a + x);
+      }
+      __syncthreads();
+      st = b;
+    }
+    body(p, s, st);
+    if (NBUF == 1) {  // the single buffer is free again: start the CTA's next partition
+      armed = 0;
+      if (pn < P && stage_issue(get(pn), cap, ring, &full[0])) armed = 1u;
+    }
+  }
+}
+
+// One warp per partition (grid-stride over warps): the fit's reductions are warp shuffles and its
+// parameter solve runs on one lane, so a warp waiting on its solve stalls only itself while the
+// SM's other warps stream their partitions; the second pass re-reads the partition from L2.
+__global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
     k_fit(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
           uint32_t L, uint64_t m, int model, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
           uint32_t* __restrict__ max_b) {
-  __shared__ FitShared sm;
-  for (uint64_t p = blockIdx.x; p < m; p += gridDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
+  for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < m; p += nw) {
     const uint64_t a = part_begin(starts, L, n, p);
-    const uint64_t e = part_begin(starts, L, n, p + 1);
-    const uint32_t N = (uint32_t)(e - a);
-    const FitResult R = fit_range<kFitBlock>(values, dtype, a, N, model, threadIdx.x, &sm);
-    if (threadIdx.x == 0) {
+    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
+    const FitResult R = fit_range<32>(values, dtype, a, N, model, lane, nullptr);
+    if (lane == 0) {
       Record r;
       r.theta0 = R.theta0;
       r.theta1 = R.theta1;
@@ -189,75 +311,112 @@ __global__ void k_build_aux(const Record* __restrict__ rec, uint64_t m, uint64_t
 
 // ------------------------------------------------------------------------------ packing
 
-// Gather packing: thread per output word. The word's bits [64w, 64w+64) are filled from the
-// fields that overlap it (first partition by a search over the offsets), each field recomputed
-// from the input value and the partition's prediction. No atomics, no pre-zeroing.
-__device__ uint64_t pack_word(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
-                              const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t total_bits,
-                              uint64_t w) {
-  {
-    const uint64_t bit0 = w * 64;
-    if (bit0 >= total_bits) return 0;
-    uint64_t lo = 0, hi = m;  // largest p with off(p) <= bit0
-    while (hi - lo > 1) {
-      const uint64_t mid = (lo + hi) >> 1;
-      if (w3_off(__ldg(&aux[mid].word3)) <= bit0)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    uint64_t acc = 0;
-    const uint64_t end = bit0 + 64;
-    for (uint64_t p = lo; p < m; p++) {
-      const Aux a = aux[p];
-      const uint64_t off = w3_off(a.word3);
-      if (off >= end) break;
-      const uint32_t b = w3_b(a.word3);
-      if (b == 0) continue;
-      const uint64_t pe = p + 1 < m ? aux[p + 1].start : n;
-      const uint32_t N = (uint32_t)(pe - a.start);
-      uint32_t x = bit0 > off ? (uint32_t)(bit0 - off) / b : 0u;  // < 2^30 bits per partition
-      uint64_t fpos = off + (uint64_t)x * b;
-      for (; x < N && fpos < end; x++, fpos += b) {
-        const uint64_t v = load_value(values, dtype, a.start + x);
-        const int64_t pred = predict_aux(a, rec, p, x);
-        const uint64_t z = zz_encode((int64_t)(v - (uint64_t)pred));
-        if (fpos >= bit0)
-          acc |= z << (uint32_t)(fpos - bit0);
-        else
-          acc |= z >> (uint32_t)(bit0 - fpos);
-      }
-      if (x < N) break;
-    }
-    return acc;
-  }
+// Packing, one CTA per partition (staged as for the fit). Phase 1 turns each staged value into its
+// zigzag residual under the partition's prediction, in shared memory (over the value itself for a
+// 64-bit column, into a second region for a 32-bit one). Phase 2 has each thread assemble output
+// words of the partition's bit range [off, off + N b) from those residuals. A word inside that
+// range belongs to this partition alone and is stored; a word the range covers only in part holds a
+// partition boundary (or the end of the stream), was zeroed beforehand, and is OR-ed into.
+constexpr uint32_t kZzOffset32 = (kStageData / 2 + 32 + 127) & ~127u;  // 32-bit columns: residuals after the values
+constexpr uint32_t kPackSmem64 = kStageBuf;
+constexpr uint32_t kPackSmem32 = kZzOffset32 + kStageData;
+
+// value bytes a staged partition may have: 64-bit residuals replace 64-bit values in place; a 32-bit
+// column's values (up to 4096 of them) leave room for their residuals after them
+__device__ __forceinline__ uint32_t pack_stage_cap(int dtype) { return dtype == LECO_U32 ? kStageData / 2 : kStageData; }
+
+__device__ __forceinline__ uint64_t residual_at(const Record* __restrict__ rec, const Aux& a, uint64_t p, uint32_t x,
+                                                uint64_t v) {
+  return zz_encode((int64_t)(v - (uint64_t)predict_aux(a, rec, p, x)));
 }
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned char* st, unsigned char* ring,
+                                               const Record* __restrict__ rec, const Aux* __restrict__ aux,
+                                               uint64_t p, uint64_t* __restrict__ words) {
+  const Aux a = aux[p];
+  const uint32_t b = w3_b(a.word3);
+  if (b) {
+    const uint64_t off = w3_off(a.word3), endb = off + (uint64_t)s.N * b;
+    // phase 1: residuals into shared memory (staged partitions only; others recompute per field)
+    uint64_t* zs = nullptr;
+    if (st) {
+      zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32)
+                               : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
+      for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
+        zs[x] = residual_at(rec, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
+      __syncthreads();
+    }
+    // phase 2: output words
+    for (uint64_t w = (off >> 6) + threadIdx.x; w <= ((endb - 1) >> 6); w += blockDim.x) {
+      const uint64_t wb = w << 6;
+      const uint64_t lo = wb > off ? wb : off, hi = wb + 64 < endb ? wb + 64 : endb;
+      uint32_t x = (uint32_t)(lo - off) / b;  // first field overlapping the word (< 2^30 bits in)
+      uint64_t acc = 0;
+      for (uint64_t f = off + (uint64_t)x * b; f < hi; f += b, x++) {
+        const uint64_t z = zs ? zs[x] : residual_at(rec, a, p, x, load_value(s.values, s.dtype, s.a + x));
+        acc |= f >= wb ? z << (uint32_t)(f - wb) : z >> (uint32_t)(wb - f);
+      }
+      if (lo == wb && hi == wb + 64)
+        words[w] = acc;
+      else
+        atomicOr((unsigned long long*)&words[w], (unsigned long long)acc);
+    }
+  }
+  __syncthreads();  // the stage buffer is refilled for the next partition
+}
+
+constexpr int kPackBlock = 128;
+
+__global__ void __launch_bounds__(kPackBlock)
     k_pack(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
-           const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t total_bits,
-           uint64_t* __restrict__ words, uint64_t nwords) {
-  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
-       w += (uint64_t)gridDim.x * blockDim.x)
-    words[w] = pack_word(values, dtype, rec, aux, m, n, total_bits, w);
+           const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t* __restrict__ words,
+           uint32_t* __restrict__ err) {
+  __shared__ __align__(8) uint64_t full[1];
+  extern __shared__ __align__(128) unsigned char ring[];
+  auto get = [&](uint64_t p) {
+    PartSrc s;
+    s.values = values;
+    s.n = n;
+    s.a = aux[p].start;
+    s.N = (uint32_t)((p + 1 < m ? aux[p + 1].start : n) - s.a);
+    s.dtype = dtype;
+    return s;
+  };
+  auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
+    pack_partition(s, st, ring, rec, aux, p, words);
+  };
+  for_each_staged<1>(m, pack_stage_cap(dtype), get, body, ring, full, err);
+}
+
+// Zero the words that packing OR-s into: each word holding a partition's first bit, and the words
+// from the end of the stream on (the tail word and the zero padding). Every other word lies inside
+// one partition's bit range and is written whole.
+__global__ void k_zero_bounds(const Aux* __restrict__ aux, uint64_t m, uint64_t total_bits, uint64_t nwords,
+                              uint64_t* __restrict__ words) {
+  const uint64_t tail = total_bits >> 6;
+  const uint64_t count = m + (nwords > tail ? nwords - tail : 0);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = i < m ? (w3_off(aux[i].word3) >> 6) : tail + (i - m);
+    if (w < nwords) words[w] = 0;
+  }
 }
 
 // ------------------------------------------------------------------------------ batched encode
 
-// CTA per partition of every column: the partition's column by a search over part_base
-__global__ void __launch_bounds__(kFitBlock)
+// one warp per partition of every column (the column by a search over part_base)
+__global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
     k_fit_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base, uint32_t ncols,
                 uint64_t P, int dtype, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
                 uint32_t* __restrict__ max_b) {
-  __shared__ FitShared sm;
-  for (uint64_t p = blockIdx.x; p < P; p += gridDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
+  for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < P; p += nw) {
     const uint32_t c = find_col(part_base, ncols, p);
     const EncCol col = cols[c];
     const uint64_t a = (p - part_base[c]) * (uint64_t)col.L;
-    const uint64_t e = a + col.L < col.n ? a + col.L : col.n;
-    const uint32_t N = (uint32_t)(e - a);
-    const FitResult R = fit_range<kFitBlock>(col.values, dtype, a, N, col.model, threadIdx.x, &sm);
-    if (threadIdx.x == 0) {
+    const uint32_t N = (uint32_t)((a + col.L < col.n ? a + col.L : col.n) - a);
+    const FitResult R = fit_range<32>(col.values, dtype, a, N, col.model, lane, nullptr);
+    if (lane == 0) {
       Record r;
       r.theta0 = R.theta0;
       r.theta1 = R.theta1;
@@ -295,18 +454,43 @@ __global__ void k_aux_multi(const Record* __restrict__ rec, const EncCol* __rest
   }
 }
 
-__global__ void __launch_bounds__(256)
+// CTA per partition of every column (the column by a search over part_base)
+__global__ void __launch_bounds__(kPackBlock)
     k_pack_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
-                 const uint64_t* __restrict__ word_base, const uint64_t* __restrict__ col_bits, uint32_t ncols,
-                 uint64_t W, int dtype, const Record* __restrict__ rec, const Aux* __restrict__ aux,
-                 uint64_t* __restrict__ words) {
-  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < W;
-       w += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = find_col(word_base, ncols, w);
+                 const uint64_t* __restrict__ word_base, uint32_t ncols, uint64_t P, int dtype,
+                 const Record* __restrict__ rec, const Aux* __restrict__ aux, uint64_t* __restrict__ words,
+                 uint32_t* __restrict__ err) {
+  __shared__ __align__(8) uint64_t full[1];
+  extern __shared__ __align__(128) unsigned char ring[];
+  auto get = [&](uint64_t p) {
+    const uint32_t c = find_col(part_base, ncols, p);
+    PartSrc s;
+    s.values = cols[c].values;
+    s.n = cols[c].n;
+    s.a = aux[p].start;
+    s.N = (uint32_t)((p + 1 < part_base[c + 1] ? aux[p + 1].start : s.n) - s.a);
+    s.dtype = dtype;
+    return s;
+  };
+  auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
+    const uint32_t c = find_col(part_base, ncols, p);
     const uint64_t p0 = part_base[c];
-    words[w] = pack_word(cols[c].values, dtype, rec + p0, aux + p0, part_base[c + 1] - p0, cols[c].n, col_bits[c],
-                         w - word_base[c]);
+    pack_partition(s, st, ring, rec + p0, aux + p0, p - p0, words + word_base[c]);
+  };
+  for_each_staged<1>(P, pack_stage_cap(dtype), get, body, ring, full, err);
+}
+
+// k_zero_bounds for every column: thread per partition, then each column's tail words
+__global__ void k_zero_bounds_multi(const Aux* __restrict__ aux, const uint64_t* __restrict__ part_base,
+                                    const uint64_t* __restrict__ word_base, const uint64_t* __restrict__ col_bits,
+                                    uint32_t ncols, uint64_t P, uint64_t* __restrict__ words) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P; p += stride) {
+    const uint32_t c = find_col(part_base, ncols, p);
+    words[word_base[c] + (w3_off(aux[p].word3) >> 6)] = 0;
   }
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < ncols; c += stride)
+    for (uint64_t w = word_base[c] + (col_bits[c] >> 6); w < word_base[c + 1]; w++) words[w] = 0;
 }
 
 int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
@@ -330,13 +514,23 @@ int sm_count() {
   return cached[dev];
 }
 
+// persistent grid: as many CTAs as fit on the GPU at once with the staging ring (grid-stride over work)
+template <typename K>
+int resident_grid(K kern, int block, uint64_t work, uint32_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, block, smem) != cudaSuccess || nb < 1) nb = 1;
+  const uint64_t cap = (uint64_t)sm_count() * nb;
+  return (int)(work < cap ? work : cap);
+}
+
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
                        uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
-                       uint32_t* max_b, cudaStream_t st) {
+                       uint32_t* max_b, uint32_t* err, cudaStream_t st) {
+  (void)err;  // the fit waits on nothing
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess || m == 0) return e;
-  const uint64_t cap = (uint64_t)sm_count() * 16;
-  const int grid = (int)(m < cap ? m : cap);
+  const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
   k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
   return cudaGetLastError();
 }
@@ -378,20 +572,27 @@ cudaError_t launch_build_aux(const Record* rec, uint64_t m, uint64_t n, Aux* aux
 }
 
 cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux,
-                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
-                        uint64_t nwords, cudaStream_t st) {
+                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words, uint64_t nwords, uint32_t* err,
+                        cudaStream_t st) {
   if (nwords == 0) return cudaSuccess;
-  k_pack<<<grid_for(nwords, 256, 8), 256, 0, st>>>(values, dtype, rec, aux, m, n, total_bits, words,
-                                                   nwords);
+  const uint64_t tail = total_bits >> 6;
+  k_zero_bounds<<<grid_for(m + (nwords > tail ? nwords - tail : 0), 256, 8), 256, 0, st>>>(aux, m, total_bits, nwords,
+                                                                                         words);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || m == 0) return e;
+  const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
+  k_pack<<<resident_grid(k_pack, kPackBlock, m, smem), kPackBlock, smem, st>>>(values, dtype, rec, aux, m, n, words,
+                                                                               err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
-                             Record* rec, uint64_t* lenbits, uint32_t* max_b, cudaStream_t st) {
+                             Record* rec, uint64_t* lenbits, uint32_t* max_b, uint32_t* err, cudaStream_t st) {
+  (void)err;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t) * (ncols ? ncols : 1), st);
   if (e != cudaSuccess || P == 0) return e;
-  const uint64_t cap = (uint64_t)sm_count() * 16;
-  k_fit_multi<<<(int)(P < cap ? P : cap), kFitBlock, 0, st>>>(cols, part_base, ncols, P, dtype, rec, lenbits, max_b);
+  const int grid = grid_for((P + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
+  k_fit_multi<<<grid, kFitBlock, 0, st>>>(cols, part_base, ncols, P, dtype, rec, lenbits, max_b);
   return cudaGetLastError();
 }
 
@@ -418,11 +619,16 @@ cudaError_t launch_aux_multi(const Record* rec, const EncCol* cols, const uint64
 }
 
 cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
-                              const uint64_t* col_bits, uint32_t ncols, uint64_t W, int dtype, const Record* rec,
-                              const Aux* aux, uint64_t* words, cudaStream_t st) {
+                              const uint64_t* col_bits, uint32_t ncols, uint64_t P, uint64_t W, int dtype,
+                              const Record* rec, const Aux* aux, uint64_t* words, uint32_t* err, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
-  k_pack_multi<<<grid_for(W, 256, 8), 256, 0, st>>>(cols, part_base, word_base, col_bits, ncols, W, dtype, rec, aux,
-                                                    words);
+  k_zero_bounds_multi<<<grid_for(P > ncols ? P : ncols, 256, 8), 256, 0, st>>>(aux, part_base, word_base, col_bits,
+                                                                                ncols, P, words);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || P == 0) return e;
+  const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
+  k_pack_multi<<<resident_grid(k_pack_multi, kPackBlock, P, smem), kPackBlock, smem, st>>>(
+      cols, part_base, word_base, ncols, P, dtype, rec, aux, words, err);
   return cudaGetLastError();
 }
 

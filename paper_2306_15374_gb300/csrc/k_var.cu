@@ -229,7 +229,7 @@ int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
 
 template <typename T>
 cudaError_t dalloc(T** p, uint64_t elems, cudaStream_t st) {
-  return cudaMallocAsync((void**)p, (elems ? elems : 1) * sizeof(T), st);
+  return dev_alloc((void**)p, (elems ? elems : 1) * sizeof(T), st);
 }
 
 }  // namespace

@@ -13,6 +13,29 @@ using namespace leco;
 
 namespace {
 
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
 constexpr uint32_t kMagic = 0x4F43454Cu;  // "LECO"
 constexpr uint32_t kVersion = 1;
 constexpr uint64_t kHeaderBytes = 64;
@@ -28,7 +51,7 @@ leco_status alloc_meta(leco_column* c, cudaStream_t st) {
   const uint64_t tiles_b = align256(sizeof(TileDesc) * (scan_tiles(c->n) + 1));
   c->meta_bytes = 2 * rec_b + starts_b + tiles_b + 256;
   void* p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, c->meta_bytes, st);
+  cudaError_t e = dev_alloc(&p, c->meta_bytes, st);
   if (e != cudaSuccess) return from_cuda(e);
   char* b = (char*)p;
   c->meta_block = p;
@@ -61,7 +84,7 @@ leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t
   const uint64_t m = c->m;
   const uint64_t scr_elems = m + offsets_scratch_elems(m) + 2;
   uint64_t* scr = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&scr, scr_elems * 8, st);
+  cudaError_t e = dev_alloc((void**)&scr, scr_elems * 8, st);
   if (e != cudaSuccess) return from_cuda(e);
   uint64_t* lenbits = scr;
   uint64_t* off_scr = scr + m;
@@ -70,11 +93,17 @@ leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t
   const uint64_t* starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
   uint64_t hres[2] = {0, 0};
   uint64_t& total = hres[0];
-  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, d_maxb, st);
+  uint32_t flags = 0;
+  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, d_maxb, c->status, st);
   if (e == cudaSuccess)
     e = launch_offsets(c->rec, lenbits, m, off_scr, offsets_scratch_elems(m), d_total, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hres, d_total, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, c->status, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && (flags & kStatTimeout)) {
+    cudaFreeAsync(scr, st);
+    return LECO_ERR_TIMEOUT;  // a staging copy never landed: the fit is incomplete
+  }
   if (e == cudaSuccess && total >= (1ull << 48)) e = cudaErrorInvalidValue;
   if (e == cudaSuccess) {
     c->total_bits = total;
@@ -82,12 +111,12 @@ leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t
     c->stage_bytes = stage_word_bytes(c->max_b);
     c->nwords = stream_words(total);
     c->words_bytes = c->nwords * 8;
-    e = cudaMallocAsync((void**)&c->words, c->words_bytes, st);
+    e = dev_alloc((void**)&c->words, c->words_bytes, st);
   }
   if (e == cudaSuccess) e = launch_build_aux(c->rec, m, c->n, c->aux, c->status, st);
   if (e == cudaSuccess) e = launch_tile_desc(view_of(c), c->tiles, st);
   if (e == cudaSuccess)
-    e = launch_pack(d_values, c->dtype, c->rec, c->aux, m, c->n, total, c->words, c->nwords, st);
+    e = launch_pack(d_values, c->dtype, c->rec, c->aux, m, c->n, total, c->words, c->nwords, c->status, st);
   cudaFreeAsync(scr, st);
   if (e == cudaErrorInvalidValue) return LECO_ERR_INVALID_ARG;
   return from_cuda(e);
@@ -170,7 +199,25 @@ bool validate_host(const BlobHeader& h, const Record* rec, const uint64_t* start
 
 }  // namespace
 
+namespace leco {
+
+cudaError_t dev_alloc(void** p, uint64_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = pool_for_current_device();
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+}  // namespace leco
+
 extern "C" {
+
+leco_status leco_trim_memory(void) {
+  cudaMemPool_t pool = pool_for_current_device();
+  if (!pool) return LECO_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return LECO_ERR_CUDA;
+  return from_cuda(cudaMemPoolTrimTo(pool, 0));
+}
+
 
 const char* leco_status_string(leco_status s) {
   switch (s) {
@@ -233,7 +280,7 @@ leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
     c->tau = policy.tau;
     c->L = 0;
     uint64_t* tmp = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&tmp, 8 * (n + 1), st);
+    cudaError_t e = dev_alloc((void**)&tmp, 8 * (n + 1), st);
     if (e != cudaSuccess) {
       delete c;
       return from_cuda(e);
@@ -456,7 +503,7 @@ leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t
   leco_status s = alloc_meta(c, st);
   if (s == LECO_OK) {
     c->words_bytes = 8 * c->nwords;
-    s = from_cuda(cudaMallocAsync((void**)&c->words, c->words_bytes, st));
+    s = from_cuda(dev_alloc((void**)&c->words, c->words_bytes, st));
   }
   if (s == LECO_OK && h.m)
     s = from_cuda(cudaMemcpyAsync(c->rec, rec.data(), 32 * h.m, cudaMemcpyHostToDevice, st));

@@ -50,7 +50,7 @@ leco_status leco_tune_scan(const leco_column* col, uint32_t op, uint64_t lo, uin
   const ColumnView v = view_of(col);
   const uint64_t vb = col->dtype == LECO_U32 ? 4 : 8;
   void* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, op == 0 ? (col->n ? col->n * vb : 8) : sizeof(leco_sum_result), st);
+  cudaError_t e = dev_alloc(&buf, op == 0 ? (col->n ? col->n * vb : 8) : sizeof(leco_sum_result), st);
   if (e != cudaSuccess) return from_cuda(e);
   cudaEvent_t a = nullptr, b = nullptr;
   cudaEventCreate(&a);
@@ -306,11 +306,11 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   std::vector<uint32_t> max_b(ncols);
   std::vector<ColumnView> views(ncols);
   uint64_t W = 0;
-  cudaError_t e = cudaMallocAsync((void**)&meta, 2 * rec_b + tiles_b + stat_b, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&scr, 8 * scr_words, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_ec, sizeof(EncCol) * ncols, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_bases, 8 * 3 * (uint64_t)(ncols + 1), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_views, sizeof(ColumnView) * ncols, st);
+  cudaError_t e = dev_alloc((void**)&meta, 2 * rec_b + tiles_b + stat_b, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&scr, 8 * scr_words, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&d_ec, sizeof(EncCol) * ncols, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&d_bases, 8 * 3 * (uint64_t)(ncols + 1), st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&d_views, sizeof(ColumnView) * ncols, st);
   Record* rec = reinterpret_cast<Record*>(meta);
   Aux* aux = reinterpret_cast<Aux*>(meta + rec_b);
   TileDesc* tiles = reinterpret_cast<TileDesc*>(meta + 2 * rec_b);
@@ -327,11 +327,14 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_part, part_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_tile, tile_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   // fit every partition of every column, then column-relative offsets and per-column totals
-  if (e == cudaSuccess) e = launch_fit_multi(d_ec, d_part, ncols, P, dtype, rec, lenbits, d_maxb, st);
+  if (e == cudaSuccess) e = launch_fit_multi(d_ec, d_part, ncols, P, dtype, rec, lenbits, d_maxb, status, st);
   if (e == cudaSuccess) e = launch_offsets_multi(rec, lenbits, d_part, ncols, P, offs, d_colbits, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(col_bits.data(), d_colbits, 8 * ncols, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(max_b.data(), d_maxb, 4 * ncols, cudaMemcpyDeviceToHost, st);
+  uint32_t fit_flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&fit_flags, status, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && (fit_flags & kStatTimeout)) e = cudaErrorTimeout;  // a staging copy never landed
   if (e == cudaSuccess) {
     word_base[0] = 0;
     for (uint32_t c = 0; c < ncols; c++) {
@@ -340,7 +343,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
     }
     W = word_base[ncols];
   }
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&words, 8 * W, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&words, 8 * W, st);
   if (e == cudaSuccess) {
     for (uint32_t c = 0; c < ncols; c++) {
       ColumnView& v = views[c];
@@ -361,7 +364,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_views, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_aux_multi(rec, d_ec, d_part, ncols, P, aux, st);
   if (e == cudaSuccess) e = launch_tile_desc_multi(d_views, d_tile, ncols, T, tiles, st);
-  if (e == cudaSuccess) e = launch_pack_multi(d_ec, d_part, d_word, d_colbits, ncols, W, dtype, rec, aux, words, st);
+  if (e == cudaSuccess) e = launch_pack_multi(d_ec, d_part, d_word, d_colbits, ncols, P, W, dtype, rec, aux, words, status, st);
   if (e == cudaSuccess) {
     sh = new (std::nothrow) leco_shared_blocks();
     if (!sh) e = cudaErrorMemoryAllocation;

@@ -220,15 +220,15 @@ struct EncCol {
 // batched encode (k_encode.cu, k_scan.cu): arrays of all columns back to back; part_base /
 // word_base / tile_base hold each column's first partition / word / scan tile (ncols + 1 entries)
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
-                             Record* rec, uint64_t* lenbits, uint32_t* max_b, cudaStream_t st);
+                             Record* rec, uint64_t* lenbits, uint32_t* max_b, uint32_t* err, cudaStream_t st);
 uint64_t offsets_multi_scratch_elems(uint64_t P);
 cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base, uint32_t ncols,
                                  uint64_t P, uint64_t* scratch, uint64_t* col_bits, cudaStream_t st);
 cudaError_t launch_aux_multi(const Record* rec, const EncCol* cols, const uint64_t* part_base, uint32_t ncols,
                              uint64_t P, Aux* aux, cudaStream_t st);
 cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
-                              const uint64_t* col_bits, uint32_t ncols, uint64_t W, int dtype, const Record* rec,
-                              const Aux* aux, uint64_t* words, cudaStream_t st);
+                              const uint64_t* col_bits, uint32_t ncols, uint64_t P, uint64_t W, int dtype,
+                              const Record* rec, const Aux* aux, uint64_t* words, uint32_t* err, cudaStream_t st);
 cudaError_t launch_tile_desc_multi(const ColumnView* views, const uint64_t* tile_base, uint32_t ncols, uint64_t T,
                                    TileDesc* tiles, cudaStream_t st);
 
@@ -253,15 +253,15 @@ void scan_config_store(int op, int dtype, uint32_t stage_bytes, ScanConfig cfg);
 // encode pipeline (k_encode.cu)
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
                        uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
-                       uint32_t* max_b, cudaStream_t st);
+                       uint32_t* max_b, uint32_t* err, cudaStream_t st);
 cudaError_t launch_offsets(Record* rec, const uint64_t* lenbits, uint64_t m, uint64_t* scratch,
                            uint64_t scratch_elems, uint64_t* total_out, cudaStream_t st);
 uint64_t offsets_scratch_elems(uint64_t m);
 cudaError_t launch_build_aux(const Record* rec, uint64_t m, uint64_t n, Aux* aux, uint32_t* status,
                              cudaStream_t st);
 cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux,
-                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
-                        uint64_t nwords, cudaStream_t st);
+                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words, uint64_t nwords, uint32_t* err,
+                        cudaStream_t st);
 
 // scans (k_scan.cu) and lookups (k_decode.cu)
 cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st);
@@ -285,5 +285,9 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
                           int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st);
 
 int sm_count();
+// Stream-ordered device allocation from the library's own memory pool on the current device. The
+// pool keeps freed memory for reuse (no release threshold), so repeated encodes do not map and
+// unmap pages at every synchronization; leco_trim_memory hands the cached memory back.
+cudaError_t dev_alloc(void** p, uint64_t bytes, cudaStream_t st);
 
 }  // namespace leco

@@ -66,20 +66,27 @@ extern "C" leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t 
   uint64_t* off_scr = lenbits + kNoAllocMaxParts;
   uint64_t* res = off_scr + (kNoAllocMaxParts + kNoAllocMaxParts / 2048 + 2);  // [total, max b]
   Record* rec = static_cast<Record*>(d_records);
-  // every scratch word this call reads is written first by this call (launch_fit zeroes max b)
-  cudaError_t e = launch_fit(d_values, dtype, n, nullptr, L, m, model, rec, lenbits,
-                             reinterpret_cast<uint32_t*>(res + 1), st);
+  // every scratch word this call reads is written first by this call (launch_fit zeroes max b; the
+  // word after it records a staging copy that timed out)
+  uint32_t* err = reinterpret_cast<uint32_t*>(res + 1) + 1;
+  cudaError_t e = cudaMemsetAsync(err, 0, 4, st);
+  if (e == cudaSuccess)
+    e = launch_fit(d_values, dtype, n, nullptr, L, m, model, rec, lenbits, reinterpret_cast<uint32_t*>(res + 1), err,
+                   st);
   if (e == cudaSuccess) e = launch_offsets(rec, lenbits, m, off_scr, offsets_scratch_elems(m), res, st);
   uint64_t total = 0;
+  uint32_t flags = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, res, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LECO_ERR_OOM : LECO_ERR_CUDA;
+  if (flags & kStatTimeout) return LECO_ERR_TIMEOUT;
   if (total >= (1ull << 48)) return LECO_ERR_INVALID_ARG;
   const uint64_t nwords = stream_words(total);
   *nwords_out = nwords;
   if (nwords > words_cap) return LECO_ERR_INVALID_ARG;  // *nwords_out tells the size needed
   e = launch_build_aux(rec, m, n, aux, nullptr, st);
   if (e == cudaSuccess)
-    e = launch_pack(d_values, dtype, rec, aux, m, n, total, static_cast<uint64_t*>(d_words), nwords, st);
+    e = launch_pack(d_values, dtype, rec, aux, m, n, total, static_cast<uint64_t*>(d_words), nwords, err, st);
   return e == cudaSuccess ? LECO_OK : LECO_ERR_CUDA;
 }

@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
         "leco_batch_plan_run": (i32, [vp, vp]),
         "leco_batch_plan_run_graph": (i32, [vp, vp]),
         "leco_batch_plan_jobs": (u64, [vp]),
+        "leco_trim_memory": (i32, []),
         "leco_batch_plan_tune": (i32, [vp, vp, ctypes.POINTER(ScanConfig)]),
         "leco_batch_plan_free": (None, [vp]),
         "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
@@ -357,6 +358,11 @@ def leco_tune_scan(col: Column, op: int = 0, lo: int = 0, hi: int = (1 << 64) - 
     _check(lib().leco_tune_scan(col.handle, int(op), int(lo), int(hi), _stream(stream), ctypes.byref(cfg)),
            "leco_tune_scan")
     return {"stages": cfg.stages, "consumer_warps": cfg.consumer_warps, "ms": cfg.ms}
+
+
+def leco_trim_memory() -> None:
+    """Return the device memory the library's pool keeps cached to the driver (current device)."""
+    _check(lib().leco_trim_memory(), "leco_trim_memory")
 
 
 def leco_tune_save(path: str) -> None:

@@ -137,3 +137,18 @@ def test_tuner_keeps_results_identical(lc, tmp_path):
     text = open(path).read()
     assert '"stages"' in text and '"consumer_warps"' in text
     lc.leco_tune_load(path)
+
+
+def test_trim_memory_keeps_live_columns(lc):
+    """Freed columns' memory stays cached in the library's pool until trimmed; trimming leaves live
+    columns intact."""
+    import torch
+
+    v = W.cfg1(500_000)
+    keep = lc.leco_encode(to_dev(v), lc.fixed(1024), 1)
+    for _ in range(3):
+        lc.leco_encode(to_dev(v), lc.fixed(1024), 1).free()
+    lc.leco_trim_memory()
+    out = torch.empty(len(v), dtype=torch.int64, device="cuda")
+    lc.leco_decode_all(keep, out)
+    assert (from_dev(out) == v).all()
