@@ -167,8 +167,8 @@ __device__ FitResult finish_fit(const FitParams& P, int64_t lo, int64_t hi, uint
 }
 
 
-// Group fit: GROUP threads (a warp, or a whole CTA when GROUP > 32) fit [a, a+N). Returns the
-// result in every thread of the group. sm: shared scratch (only used when GROUP > 32).
+// Group fit: GROUP threads (one thread, a warp, or a whole CTA when GROUP > 32) fit [a, a+N).
+// Returns the result in every thread of the group. sm: shared scratch (only used when GROUP > 32).
 struct FitShared {
   i128 S[32];
   int64_t mx[32], mn[32];
@@ -256,12 +256,16 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
     fit_pass1<GROUP>(v32, N, lin, rank, &S, &mx, &mn);
   else
     fit_pass1<GROUP>(v64, N, lin, rank, &S, &mx, &mn);
-  S = warp_sum_i128(S);
-  mx = warp_max_i64(mx);
-  mn = warp_min_i64(mn);
+  if (GROUP > 1) {
+    S = warp_sum_i128(S);
+    mx = warp_max_i64(mx);
+    mn = warp_min_i64(mn);
+  }
   const uint32_t lane = rank & 31u;
   FitParams P;
-  if (GROUP == 32) {
+  if (GROUP == 1) {
+    P = solve_params(S, mx, mn, N, lin);
+  } else if (GROUP == 32) {
     if (lane == 0) P = solve_params(S, mx, mn, N, lin);
     P.B = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)P.B, 0);
     P.fb_shift = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)P.fb_shift, 0);
@@ -295,17 +299,21 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
       const uint64_t v = u32 ? (uint64_t)__ldg(v32 + x) : __ldg(v64 + x);
       zmax = max(zmax, zz_encode((int64_t)(v - (uint64_t)P.fb_shift)));
     }
-    zmax = warp_max_u64(zmax);
+    if (GROUP > 1) zmax = warp_max_u64(zmax);
   } else {
     if (u32)
       fit_pass2<GROUP>(v32, N, P.B, P.s, rank, &lo, &hi);
     else
       fit_pass2<GROUP>(v64, N, P.B, P.s, rank, &lo, &hi);
-    lo = warp_min_i64(lo);
-    hi = warp_max_i64(hi);
+    if (GROUP > 1) {
+      lo = warp_min_i64(lo);
+      hi = warp_max_i64(hi);
+    }
   }
   FitResult R;
-  if (GROUP == 32) {
+  if (GROUP == 1) {
+    R = finish_fit(P, lo, hi, zmax);
+  } else if (GROUP == 32) {
     if (lane == 0) R = finish_fit(P, lo, hi, zmax);
     R.theta0 = __shfl_sync(0xffffffffu, R.theta0, 0);
     R.theta1 = __shfl_sync(0xffffffffu, R.theta1, 0);

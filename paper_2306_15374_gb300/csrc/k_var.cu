@@ -8,7 +8,8 @@
 // compacts them.
 //
 // Merge, round-synchronous: each round computes for every adjacent pair the size of the merged
-// partition with the full regressor (S_M + len * b) and its gain over the two apart; every pair
+// partition with the full regressor (S_M + len * b; pairs sorted by length onto a thread, a warp or a
+// CTA each) and its gain over the two apart; every pair
 // with a positive gain whose priority (gain, SplitMix64 of its start) beats both neighbouring
 // pairs merges, all at once. Pair sizes are cached: only pairs touching a partition merged in the
 // previous round are refitted. Rounds repeat until none merges.
@@ -100,51 +101,89 @@ __global__ void k_scatter_starts(const uint64_t* __restrict__ bitmap, uint64_t n
   }
 }
 
-// sizes of single partitions (initial round): warp per partition
-__global__ void k_part_size(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
-                            uint64_t m, int model, uint64_t* __restrict__ sz) {
-  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t p = warp; p < m; p += nw) {
-    const uint64_t a = st[p], e = st[p + 1];
-    const FitResult R = fit_range<32>(values, dtype, a, (uint32_t)(e - a), model, threadIdx.x & 31u, nullptr);
-    if ((threadIdx.x & 31u) == 0) sz[p] = kSmBits + (e - a) * (uint64_t)R.b;
+// Sizes S_M + len * b of spans [st[j], st[j + w]) (w = 1: partitions; w = 2: adjacent pairs) by the
+// full fit. The spans to fit are first sorted into three work lists by length, so that each is fitted
+// by a group of matching size: one thread for short spans (32 of them share a warp, and with it the
+// single-lane parameter solve), a warp for medium ones, a CTA for long ones. A list's order is free:
+// every span's size is independent of the others.
+constexpr uint32_t kTinySpan = 256;
+
+struct SpanLists {
+  uint64_t* tiny;       // [0, counts[0])
+  uint64_t* medium;     // [0, counts[1])
+  uint64_t* lng;        // [0, counts[2])
+  unsigned long long* counts;
+};
+
+// append j to list k with one atomic per warp and list
+__device__ __forceinline__ void list_push(const SpanLists& L, int k, bool take, uint64_t j) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t mask = __ballot_sync(0xffffffffu, take);
+  if (!mask) return;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if ((int)lane == leader) base = atomicAdd(&L.counts[k], (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (take) {
+    uint64_t* list = k == 0 ? L.tiny : (k == 1 ? L.medium : L.lng);
+    list[base + __popc(mask & ((1u << lane) - 1u))] = j;
   }
 }
 
-// merged sizes of dirty pairs up to kLongPair values: warp per pair
-__global__ void k_pair_size_warp(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
-                                 uint64_t m, int model, uint32_t cap, const uint8_t* __restrict__ dirty,
-                                 uint64_t* __restrict__ msz) {
-  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t j = warp; j + 1 < m; j += nw) {
-    if (!dirty[j]) continue;
-    const uint64_t a = st[j], e = st[j + 2];
-    const uint64_t len = e - a;
-    if (len > cap) {
-      if ((threadIdx.x & 31u) == 0) msz[j] = kNone;
-      continue;
+// dirty == nullptr: every span. A span longer than cap gets no fit (out[j] = kNone).
+__global__ void k_classify(const uint64_t* __restrict__ st, uint64_t count, uint32_t w, uint32_t cap,
+                           const uint8_t* __restrict__ dirty, uint64_t* __restrict__ out, SpanLists L) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x; j0 < count; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;  // whole warps iterate together (list_push is warp-wide)
+    bool t = false, md = false, lg = false;
+    if (j < count && (!dirty || dirty[j])) {
+      const uint64_t len = st[j + w] - st[j];
+      if (len > cap)
+        out[j] = kNone;
+      else
+        (len <= kTinySpan ? t : (len <= kLongPair ? md : lg)) = true;
     }
-    if (len > kLongPair) continue;
-    const FitResult R = fit_range<32>(values, dtype, a, (uint32_t)len, model, threadIdx.x & 31u, nullptr);
-    if ((threadIdx.x & 31u) == 0) msz[j] = kSmBits + len * (uint64_t)R.b;
+    list_push(L, 0, t, j);
+    list_push(L, 1, md, j);
+    list_push(L, 2, lg, j);
   }
 }
 
-// merged sizes of dirty pairs longer than kLongPair: CTA per pair
+__global__ void k_span_size_thread(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
+                                   uint32_t w, int model, SpanLists L, uint64_t* __restrict__ out) {
+  const uint64_t cnt = L.counts[0];
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = L.tiny[i];
+    const uint64_t a = st[j], len = st[j + w] - a;
+    const FitResult R = fit_range<1>(values, dtype, a, (uint32_t)len, model, 0, nullptr);
+    out[j] = kSmBits + len * (uint64_t)R.b;
+  }
+}
+
+__global__ void k_span_size_warp(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
+                                 uint32_t w, int model, SpanLists L, uint64_t* __restrict__ out) {
+  const uint64_t cnt = L.counts[1];
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < cnt; i += nw) {
+    const uint64_t j = L.medium[i];
+    const uint64_t a = st[j], len = st[j + w] - a;
+    const FitResult R = fit_range<32>(values, dtype, a, (uint32_t)len, model, threadIdx.x & 31u, nullptr);
+    if ((threadIdx.x & 31u) == 0) out[j] = kSmBits + len * (uint64_t)R.b;
+  }
+}
+
 __global__ void __launch_bounds__(256)
-    k_pair_size_block(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
-                      uint64_t m, int model, uint32_t cap, const uint8_t* __restrict__ dirty,
-                      uint64_t* __restrict__ msz) {
+    k_span_size_block(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st, uint32_t w,
+                      int model, SpanLists L, uint64_t* __restrict__ out) {
   __shared__ FitShared sm;
-  for (uint64_t j = blockIdx.x; j + 1 < m; j += gridDim.x) {
-    if (!dirty[j]) continue;
-    const uint64_t a = st[j], e = st[j + 2];
-    const uint64_t len = e - a;
-    if (len > cap || len <= kLongPair) continue;
+  const uint64_t cnt = L.counts[2];
+  for (uint64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const uint64_t j = L.lng[i];
+    const uint64_t a = st[j], len = st[j + w] - a;
     const FitResult R = fit_range<256>(values, dtype, a, (uint32_t)len, model, threadIdx.x, &sm);
-    if (threadIdx.x == 0) msz[j] = kSmBits + len * (uint64_t)R.b;
+    if (threadIdx.x == 0) out[j] = kSmBits + len * (uint64_t)R.b;
   }
 }
 
@@ -232,6 +271,25 @@ cudaError_t dalloc(T** p, uint64_t elems, cudaStream_t st) {
   return dev_alloc((void**)p, (elems ? elems : 1) * sizeof(T), st);
 }
 
+// spans longer than kLongPair among those of a column of n values: partitions are disjoint, and
+// of adjacent pairs every other one is
+inline uint64_t long_span_cap(uint64_t n) { return 2 * (n / kLongPair + 1); }
+
+// sizes of the `count` spans [st[j], st[j + w]) selected by dirty (nullptr: all) into out; the lists
+// hold `count` entries each (tiny, medium) and long_span_cap(n) (long)
+cudaError_t span_sizes(const void* values, int dtype, uint64_t n, const uint64_t* st, uint64_t count, uint32_t w,
+                       uint32_t cap, int model, const uint8_t* dirty, uint64_t* out, const SpanLists& L,
+                       cudaStream_t stm) {
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(L.counts, 0, 3 * sizeof(unsigned long long), stm);
+  if (e != cudaSuccess) return e;
+  k_classify<<<grid_for(count, 256, 8), 256, 0, stm>>>(st, count, w, cap, dirty, out, L);
+  k_span_size_thread<<<grid_for(count, 256, 8), 256, 0, stm>>>(values, dtype, st, w, model, L, out);
+  k_span_size_warp<<<grid_for(count * 32, 256, 8), 256, 0, stm>>>(values, dtype, st, w, model, L, out);
+  k_span_size_block<<<grid_for(long_span_cap(n), 1, 4), 256, 0, stm>>>(values, dtype, st, w, model, L, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // Runs split + merge; writes m+1 starts to starts_out (capacity n+1) and m to *m_out.
@@ -295,17 +353,20 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
     ok = ok && dalloc(&scr, scr_elems + 1, st) == cudaSuccess;
     ok = ok && dalloc(&dirty_a, m0, st) == cudaSuccess && dalloc(&dirty_b, m0, st) == cudaSuccess;
     ok = ok && dalloc(&sel, m0, st) == cudaSuccess && dalloc(&d_nsel, 1, st) == cudaSuccess;
+    SpanLists lists;
+    lists.tiny = lists.medium = lists.lng = nullptr;
+    lists.counts = nullptr;
+    ok = ok && dalloc(&lists.tiny, m0, st) == cudaSuccess && dalloc(&lists.medium, m0, st) == cudaSuccess;
+    ok = ok && dalloc(&lists.lng, long_span_cap(n), st) == cudaSuccess && dalloc(&lists.counts, 3, st) == cudaSuccess;
     uint64_t* cur_st = starts_out;
     uint64_t* nxt_st = st_b;
     if (ok && m > 1) {
-      k_part_size<<<grid_for(m * 32, 256, 8), 256, 0, st>>>(values, dtype, cur_st, m, model, sz_a);
+      e = span_sizes(values, dtype, n, cur_st, m, 1, ~0u, model, nullptr, sz_a, lists, st);
       k_fill_u8<<<grid_for(m, 256, 8), 256, 0, st>>>(dirty_a, m, 1);
-      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGetLastError();
       while (e == cudaSuccess && m > 1) {
-        k_pair_size_warp<<<grid_for(m * 32, 256, 8), 256, 0, st>>>(values, dtype, cur_st, m, model, cap,
-                                                                     dirty_a, msz_a);
-        k_pair_size_block<<<grid_for(m, 1, 4), 256, 0, st>>>(values, dtype, cur_st, m, model, cap,
-                                                             dirty_a, msz_a);
+        e = span_sizes(values, dtype, n, cur_st, m - 1, 2, cap, model, dirty_a, msz_a, lists, st);
+        if (e != cudaSuccess) break;
         cudaMemsetAsync(d_nsel, 0, 8, st);
         k_select<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, m, sel, d_nsel);
         unsigned long long nsel = 0;
@@ -346,6 +407,10 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
     cudaFreeAsync(dirty_b, st);
     cudaFreeAsync(sel, st);
     cudaFreeAsync(d_nsel, st);
+    cudaFreeAsync(lists.tiny, st);
+    cudaFreeAsync(lists.medium, st);
+    cudaFreeAsync(lists.lng, st);
+    cudaFreeAsync(lists.counts, st);
     if (e == cudaSuccess) *m_out = m;
   }
 done:
