@@ -258,7 +258,7 @@ __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const ui
 #pragma unroll 4
     for (uint32_t k = 0; k < ng; k++) {
       const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
-      *o = (uint32_t)(uint64_t)(F >> sh) + (uint32_t)r;
+      *o = (uint32_t)(uint64_t)((int64_t)F >> sh) + (uint32_t)r;  // floor: arithmetic shift
       o += 32;
       F += B32;
       bit += b32;

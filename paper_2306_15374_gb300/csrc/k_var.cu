@@ -13,6 +13,10 @@
 // with a positive gain whose priority (gain, SplitMix64 of its start) beats both neighbouring
 // pairs merges, all at once. Pair sizes are cached: only pairs touching a partition merged in the
 // previous round are refitted. Rounds repeat until none merges.
+#include <math.h>
+
+#include <type_traits>
+
 #include "fit.cuh"
 #include "leco_internal.cuh"
 
@@ -27,40 +31,58 @@ constexpr uint64_t kChunk = 1ull << 16;
 constexpr uint64_t kNone = ~0ull;        // no merged size (pair longer than the cap)
 constexpr uint32_t kLongPair = 1u << 14; // pairs longer than this are fitted by a whole CTA
 
-__global__ void k_split(const void* __restrict__ values, int dtype, uint64_t n, uint32_t cap,
-                        double thresh, uint64_t* __restrict__ bitmap) {
-  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
-  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
-       c += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t a = c * kChunk;
-    const uint64_t e = min(a + kChunk, n);
-    uint64_t i = a;
-    uint64_t word = 1ull;  // position a opens a partition (a % 64 == 0)
-    uint64_t wi = a >> 6;
-    int64_t prev = (int64_t)load_value(values, dtype, a);
-    i128 dmax = 0, dmin = 0;
-    int cur = 0;
-    for (uint64_t j = a + 1; j < e; j++) {
+// One chunk's greedy sweep. NARROW: every value of the chunk lies in (-2^62, 2^62) as int64, so the
+// differences and their running extremes fit 64 bits (their range below 2^64, taken unsigned);
+// otherwise 128-bit. The threshold test C <= tau S_M is done on integers: for an integer C and a
+// real t, C <= t exactly when C <= floor(t). Values are read eight at a time ahead of the sweep's
+// dependency chain.
+template <bool NARROW, typename T>
+__device__ __forceinline__ void split_chunk(const T* __restrict__ v, uint64_t a, uint64_t e, uint32_t cap,
+                                            int64_t tfloor, uint64_t* __restrict__ bitmap) {
+  using D = typename std::conditional<NARROW, int64_t, i128>::type;
+  uint64_t i = a;
+  uint64_t word = 1ull;  // position a opens a partition (a % 64 == 0)
+  uint64_t wi = a >> 6;
+  int64_t prev = (int64_t)v[a];
+  D dmax = 0, dmin = 0;
+  int cur = 0;
+  int64_t nxt[8];  // the next batch, loaded while the current one is swept
+#pragma unroll
+  for (int u = 0; u < 8; u++) nxt[u] = a + 1 + u < e ? (int64_t)__ldg(v + a + 1 + u) : 0;
+  for (uint64_t j0 = a + 1; j0 < e; j0 += 8) {
+    int64_t buf[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      buf[u] = nxt[u];
+      nxt[u] = j0 + 8 + u < e ? (int64_t)__ldg(v + j0 + 8 + u) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint64_t j = j0 + u;
+      if (j >= e) break;
       if ((j & 63) == 0) {
         bitmap[wi++] = word;
         word = 0;
       }
-      const int64_t w = (int64_t)load_value(values, dtype, j);
+      const int64_t w = buf[u];
       bool take = (j - i) < cap;
-      i128 nmax = dmax, nmin = dmin;
+      D nmax = dmax, nmin = dmin;
       int next = 0;
       if (take) {
-        const i128 d = (i128)w - (i128)prev;
+        const D d = (D)w - (D)prev;
         if (j == i + 1) {
           nmax = d;
           nmin = d;
         } else {
-          if (d > nmax) nmax = d;
-          if (d < nmin) nmin = d;
+          nmax = d > nmax ? d : nmax;
+          nmin = d < nmin ? d : nmin;
         }
-        next = bitlen_u128((u128)(nmax - nmin));
+        if (NARROW)
+          next = bitlen_u64((uint64_t)nmax - (uint64_t)nmin);
+        else
+          next = bitlen_u128((u128)(nmax - nmin));
         const int64_t C = (int64_t)(j + 1 - i) * next - (int64_t)(j - i) * cur;
-        take = (double)C <= thresh;
+        take = C <= tfloor;
       }
       if (take) {
         cur = next;
@@ -75,7 +97,40 @@ __global__ void k_split(const void* __restrict__ values, int dtype, uint64_t n, 
       }
       prev = w;
     }
-    bitmap[wi] = word;
+  }
+  bitmap[wi] = word;
+}
+
+// narrow[c] = every value of chunk c lies in (-2^62, 2^62) as int64 (a CTA per chunk)
+template <typename T>
+__global__ void k_chunk_narrow(const T* __restrict__ v, uint64_t n, uint8_t* __restrict__ narrow) {
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  const int64_t lim = (int64_t)1 << 62;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint64_t a = c * kChunk, e = min(a + kChunk, n);
+    int bad = 0;
+    if (sizeof(T) == 8)
+      for (uint64_t j = a + threadIdx.x; j < e; j += blockDim.x) {
+        const int64_t w = (int64_t)__ldg(v + j);
+        bad |= (w <= -lim || w >= lim) ? 1 : 0;
+      }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) narrow[c] = bad ? 0 : 1;
+  }
+}
+
+template <typename T>
+__global__ void k_split(const T* __restrict__ values, uint64_t n, uint32_t cap, int64_t tfloor,
+                        const uint8_t* __restrict__ narrow, uint64_t* __restrict__ bitmap) {
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = c * kChunk;
+    const uint64_t e = min(a + kChunk, n);
+    if (narrow[c])
+      split_chunk<true>(values, a, e, cap, tfloor, bitmap);
+    else
+      split_chunk<false>(values, a, e, cap, tfloor, bitmap);
   }
 }
 
@@ -319,7 +374,19 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
     LECO_TRY(dalloc(&scan_scratch, scan_elems + 1, st));
     LECO_TRY(dalloc(&d_total, 1, st));
     const uint64_t nchunks = (n + kChunk - 1) / kChunk;
-    k_split<<<grid_for(nchunks, 64, 32), 64, 0, st>>>(values, dtype, n, cap, thresh, bitmap);
+    // C <= tau * S_M for an integer C: C <= floor(tau * S_M) (thresh >= 0, below 2^62 here). The
+    // sweeps are serial per chunk, so each gets a warp of its own SM slot (one-warp blocks)
+    const int64_t tfloor = thresh < 4.0e18 ? (int64_t)floor(thresh) : INT64_MAX;
+    uint8_t* narrow = reinterpret_cast<uint8_t*>(cnt);  // scratch: cnt is not used until the popcount
+    if (dtype == LECO_U32) {
+      k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint32_t*>(values), n, narrow);
+      k_split<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(static_cast<const uint32_t*>(values), n, cap, tfloor, narrow,
+                                                         bitmap);
+    } else {
+      k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint64_t*>(values), n, narrow);
+      k_split<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(static_cast<const uint64_t*>(values), n, cap, tfloor, narrow,
+                                                         bitmap);
+    }
     LECO_TRY(cudaGetLastError());
     k_popc<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, cnt);
     LECO_TRY(cudaGetLastError());

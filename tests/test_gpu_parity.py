@@ -48,6 +48,15 @@ def _cases():
     yield "wrap_zero_u64_L512", W.linear_noise(100_003, -(1 << 30), 21_000, 4096, seed=14), 512, 1, 64
     yield "low_u64_L1024", W.random_u64(60_001, 15, bits=20), 1024, 1, 64
     yield "low_u32_L1024", W.random_u64(60_001, 16, bits=20), 1024, 1, 32
+    # ramps falling to 0 and staying there: the fitted line dips below zero (negative predictions)
+    # on a fine grid (s > 32), so the 32-bit decode must floor with an arithmetic shift; partitions
+    # of 32, 64 and 96 values reach the one-group, the paired and the mixed decode loops
+    def ramp(period, top, step, seed):
+        x = np.arange(70_001) % period
+        return np.maximum(0, top - step * x).astype(np.uint64) + W.random_u64(70_001, seed, bits=2)
+    yield "neg_pred_u32_L32", ramp(32, 100, 8, 17), 32, 1, 32
+    yield "neg_pred_u32_L96", ramp(96, 300, 8, 18), 96, 1, 32
+    yield "neg_pred_u64_L64", ramp(64, 200, 8, 19), 64, 1, 64
 
 
 CASES = list(_cases())
