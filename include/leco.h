@@ -193,6 +193,13 @@ leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, ui
  * last leco_sync (and clear it), else LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
 leco_status leco_sync(const leco_column* col, leco_stream_t stream);
 
+/* Failure-detection self-test: one kernel waits on a shared-memory barrier that nothing completes,
+ * with the same bounded wait the scan and pack kernels use, limited to limit_us microseconds
+ * (1 .. 1000000). Returns LECO_ERR_TIMEOUT when the wait gave up and reported it (the expected
+ * outcome: the device stays usable), LECO_OK if the barrier completed, INVALID_ARG or CUDA on
+ * errors. Synchronizes `stream`. A systems facility; the paper has no counterpart. */
+leco_status leco_selftest_wait_timeout(uint32_t limit_us, leco_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------ */
 /* Column metadata and lifetime */
 

@@ -624,7 +624,25 @@ cudaError_t launch_scan(const ScanArgs& g, const ColumnView* cols, const BatchIt
   return launch_scan_cfg<MODE, 8, MULTI>(g, cols, items, nitems, stage_bytes, cfg, st);
 }
 
+// One CTA waits on an mbarrier that nothing arrives at: the bounded wait must give up after limit_ns
+// and record kStatTimeout, the same path a scan takes when a copy never lands.
+__global__ void k_wait_selftest(uint64_t limit_ns, uint32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatTimeout);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, uint32_t* status, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st) {
   const uint64_t nt = scan_tiles(c.n);

@@ -7,11 +7,19 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "column.cuh"
 
 using namespace leco;
 
 namespace {
+
+// a named range on the profiler timeline for the duration of one C-ABI call (no cost without a tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr int kMaxDevices = 64;
 std::mutex g_pool_mu;
@@ -211,6 +219,22 @@ cudaError_t dev_alloc(void** p, uint64_t bytes, cudaStream_t st) {
 
 extern "C" {
 
+leco_status leco_selftest_wait_timeout(uint32_t limit_us, leco_stream_t stream) {
+  if (limit_us < 1 || limit_us > 1000000) return LECO_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* d = nullptr;
+  cudaError_t e = dev_alloc((void**)&d, 4, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  uint32_t flags = 0;
+  e = cudaMemsetAsync(d, 0, 4, st);
+  if (e == cudaSuccess) e = launch_wait_selftest((uint64_t)limit_us * 1000ull, d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d, 4, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return LECO_ERR_CUDA;
+  return (flags & kStatTimeout) ? LECO_ERR_TIMEOUT : LECO_OK;
+}
+
 leco_status leco_trim_memory(void) {
   cudaMemPool_t pool = pool_for_current_device();
   if (!pool) return LECO_ERR_CUDA;
@@ -238,6 +262,7 @@ uint32_t leco_version(void) { return 10000u; }
 leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtype,
                                leco_partition_policy policy, leco_model model,
                                uint64_t* d_starts_out, uint64_t* m_out, leco_stream_t stream) {
+  NvtxRange nvtx_range("leco_var_partition");
   if (!d_starts_out || !m_out || (n && !d_values) || !valid_dtype(dtype) || !valid_model(model))
     return LECO_ERR_INVALID_ARG;
   if (policy.kind != LECO_PART_VAR || !(policy.tau >= 0.0 && policy.tau <= 1.0) ||
@@ -251,6 +276,7 @@ leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtyp
 leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
                         leco_partition_policy policy, leco_model model, leco_stream_t stream,
                         leco_column** out) {
+  NvtxRange nvtx_range("leco_encode");
   if (!out) return LECO_ERR_INVALID_ARG;
   *out = nullptr;
   if ((n && !d_values) || !valid_dtype(dtype) || !valid_model(model)) return LECO_ERR_INVALID_ARG;
@@ -310,6 +336,7 @@ leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
 leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype dtype,
                                     const uint64_t* d_starts, uint64_t m, leco_model model,
                                     leco_stream_t stream, leco_column** out) {
+  NvtxRange nvtx_range("leco_encode_with_starts");
   if (!out) return LECO_ERR_INVALID_ARG;
   *out = nullptr;
   if ((n && !d_values) || !d_starts || !valid_dtype(dtype) || !valid_model(model))
@@ -345,12 +372,14 @@ leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype
 }
 
 leco_status leco_decode_all(const leco_column* col, void* d_out, leco_stream_t stream) {
+  NvtxRange nvtx_range("leco_decode_all");
   if (!col || (col->n && !d_out)) return LECO_ERR_INVALID_ARG;
   return from_cuda(launch_decode(view_of(col), 0, col->n, d_out, (cudaStream_t)stream));
 }
 
 leco_status leco_decode_range(const leco_column* col, uint64_t begin, uint64_t count, void* d_out,
                               leco_stream_t stream) {
+  NvtxRange nvtx_range("leco_decode_range");
   if (!col || (count && !d_out) || begin > col->n || count > col->n - begin)
     return LECO_ERR_INVALID_ARG;
   return from_cuda(launch_decode(view_of(col), begin, count, d_out, (cudaStream_t)stream));
@@ -358,12 +387,14 @@ leco_status leco_decode_range(const leco_column* col, uint64_t begin, uint64_t c
 
 leco_status leco_random_access(const leco_column* col, const uint64_t* d_idx, uint64_t k,
                                void* d_out, leco_stream_t stream) {
+  NvtxRange nvtx_range("leco_random_access");
   if (!col || (k && (!d_idx || !d_out))) return LECO_ERR_INVALID_ARG;
   return from_cuda(launch_random_access(view_of(col), d_idx, k, d_out, (cudaStream_t)stream));
 }
 
 leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, uint32_t flags,
                             leco_sum_result* d_out, leco_stream_t stream) {
+  NvtxRange nvtx_range("leco_filter_sum");
   if (!col || !d_out || (flags & ~(LECO_FILTER_PRUNE | LECO_FILTER_DECODE_ALL))) return LECO_ERR_INVALID_ARG;
   return from_cuda(launch_filter_sum(view_of(col), lo, hi, flags, d_out, (cudaStream_t)stream));
 }
@@ -453,6 +484,7 @@ leco_status leco_serialize(const leco_column* col, void* host_buf, uint64_t cap,
 
 leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t stream,
                              leco_column** out) {
+  NvtxRange nvtx_range("leco_deserialize");
   if (!out || !host_buf) return LECO_ERR_INVALID_ARG;
   *out = nullptr;
   if (bytes < kHeaderBytes) return LECO_ERR_CORRUPT;

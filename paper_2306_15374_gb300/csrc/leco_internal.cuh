@@ -265,6 +265,7 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
 
 // scans (k_scan.cu) and lookups (k_decode.cu)
 cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st);
+cudaError_t launch_wait_selftest(uint64_t limit_ns, uint32_t* status, cudaStream_t st);
 cudaError_t launch_decode(const ColumnView& c, uint64_t begin, uint64_t count, void* out,
                           cudaStream_t st);
 cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,

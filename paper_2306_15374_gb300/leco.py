@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
         "leco_batch_plan_run_graph": (i32, [vp, vp]),
         "leco_batch_plan_jobs": (u64, [vp]),
         "leco_trim_memory": (i32, []),
+        "leco_selftest_wait_timeout": (i32, [u32, vp]),
         "leco_batch_plan_tune": (i32, [vp, vp, ctypes.POINTER(ScanConfig)]),
         "leco_batch_plan_free": (None, [vp]),
         "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
@@ -358,6 +359,11 @@ def leco_tune_scan(col: Column, op: int = 0, lo: int = 0, hi: int = (1 << 64) - 
     _check(lib().leco_tune_scan(col.handle, int(op), int(lo), int(hi), _stream(stream), ctypes.byref(cfg)),
            "leco_tune_scan")
     return {"stages": cfg.stages, "consumer_warps": cfg.consumer_warps, "ms": cfg.ms}
+
+
+def leco_selftest_wait_timeout(limit_us: int, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status (LECO_ERR_TIMEOUT is the expected one)."""
+    return int(lib().leco_selftest_wait_timeout(int(limit_us), _stream(stream)))
 
 
 def leco_trim_memory() -> None:

@@ -67,3 +67,5 @@ def test_host_side_argument_errors(built):
     assert L.leco_deserialize(b"LECO", 4, None, ctypes.byref(h)) == leco.LECO_ERR_CORRUPT
     assert L.leco_deserialize(b"\0" * 64, 64, None, ctypes.byref(h)) == leco.LECO_ERR_CORRUPT
     assert L.leco_filter_sum(None, 0, 1, 0, None, None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_selftest_wait_timeout(0, None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_selftest_wait_timeout(2_000_000, None) == leco.LECO_ERR_INVALID_ARG
