@@ -11,13 +11,16 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// partition holding position i (< n): fixed i / L, variable largest p with starts[p] <= i
+// partition holding position i (< n): fixed i / L; variable: largest p with starts[p] <= i, searched
+// among the partitions touching i's scan tile (its descriptor names the first and how many), so a
+// lookup costs one descriptor load and a search over a few starts instead of over all of them
 __device__ __forceinline__ uint64_t find_part(const ColumnView& c, uint64_t i) {
   if (!c.starts) {
     if (c.n <= 0xFFFFFFFFull) return (uint32_t)i / c.L;
     return i / c.L;
   }
-  uint64_t lo = 0, hi = c.m;
+  const TileDesc* d = c.tiles + i / kScanTile;
+  uint64_t lo = __ldg(&d->p0), hi = lo + __ldg(&d->np);
   while (hi - lo > 1) {
     const uint64_t mid = (lo + hi) >> 1;
     if (__ldg(c.starts + mid) <= i)
