@@ -95,6 +95,9 @@ def lib() -> ctypes.CDLL:
         "orc_var_merge_seq": (u64, [vp, vp, u64, i32, u64, u64, vp]),
         "orc_var_merge_round": (u64, [vp, vp, u64, i32, u64, u64, vp]),
         "orc_splitmix64": (u64, [u64]),
+        "orc_search_samples": (u64, [u64, u64, dbl, u64, vp]),
+        "orc_sample_size_bits": (u64, [vp, vp, u64, u64, u64, i32]),
+        "orc_search_partition_size": (u64, [vp, u64, u64, dbl, u64, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -195,6 +198,31 @@ def var_partition(values, tau: float = 0.1, model: int = MODEL_LINEAR, variant: 
     else:
         raise ValueError(variant)
     return st
+
+
+def search_samples(n: int, N: int, frac: float = 0.01, seed: int = 0) -> np.ndarray:
+    """Starts of the subsequences of length N sampled for the partition-size search (§3.2.1)."""
+    kmax = max(1, int(frac * n / N)) if n > N else 1
+    out = np.zeros(kmax, dtype=np.uint64)
+    k = lib().orc_search_samples(n, N, float(frac), int(seed), _p(out))
+    return out[:k].copy()
+
+
+def sample_size_bits(values, starts, N: int, L: int, model: int = MODEL_LINEAR) -> int:
+    v = _u64(values)
+    st = _u64(starts)
+    return int(lib().orc_sample_size_bits(_p(v), _p(st), st.size, N, L, model))
+
+
+def search_partition_size(values, N: int = 10000, frac: float = 0.01, seed: int = 0,
+                          model: int = MODEL_LINEAR):
+    """Fixed partition size search (§3.2.1): (L, sample size in bits at L, sizes evaluated)."""
+    v = _u64(values)
+    bits = ctypes.c_uint64(0)
+    ne = ctypes.c_uint64(0)
+    L = lib().orc_search_partition_size(_p(v), v.size, N, float(frac), int(seed), model, ctypes.byref(bits),
+                                        ctypes.byref(ne))
+    return int(L), int(bits.value), int(ne.value)
 
 
 def splitmix64(x: int) -> int:

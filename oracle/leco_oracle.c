@@ -38,6 +38,11 @@
  *      bitlen(max d - min d) over the inner differences, S_M = 256 bits (one record).
  *   R8 var merge: (seq) the paper's left-to-right passes; (round) all pairs whose gain is a local
  *      maximum merged at once per round, equal gains ordered by a SplitMix64 hash of the position.
+ *   R9 partition-size search (§3.2.1): samples are k = max(1, floor(frac n / N)) subsequences of
+ *      length N starting at SplitMix64(seed + i) mod (n - N + 1); sizes of fixed partitions cut from
+ *      each subsequence's start; exponential phase over powers of two that ends after the first size
+ *      above its predecessor's; back search probing best +- step (step from half the best L,
+ *      halved when neither probe is smaller); stop when the step is 0 or a move gains < 0.01 %.
  */
 #include <math.h>
 #include <stdint.h>
@@ -671,4 +676,112 @@ uint64_t orc_var_merge_round(const uint64_t* v, uint64_t* starts, uint64_t m, in
   free(nsz);
   if (rounds_out) *rounds_out = rounds;
   return m;
+}
+
+/* ------------------------------------------------------------ partition-size search (§3.2.1) */
+
+/*
+ * Sample of the column for the fixed-partition size search (§3.2.1, step 1): subsequences of
+ * length N (the largest partition size searched) whose starts are SplitMix64(seed + i) mod
+ * (n - N + 1) for i = 0 .. k-1, with k = max(1, floor(frac * n / N)), so at most a fraction frac of
+ * the values (plus one subsequence) is sampled. A column of at most N values is its own only
+ * sample (N is then n). Writes the k starts; returns k.
+ */
+uint64_t orc_search_samples(uint64_t n, uint64_t N, double frac, uint64_t seed, uint64_t* starts_out) {
+  if (n <= N) {
+    starts_out[0] = 0;
+    return 1;
+  }
+  uint64_t k = (uint64_t)(frac * (double)n / (double)N);
+  if (k < 1) k = 1;
+  for (uint64_t i = 0; i < k; i++) starts_out[i] = orc_splitmix64(seed + i) % (n - N + 1);
+  return k;
+}
+
+/* Compressed size (bits) of the samples under fixed partitions of size L: each subsequence is cut
+ * into partitions of L values from its own start (the last may be short), each costing
+ * S_M + len * b (§3, the size function). */
+uint64_t orc_sample_size_bits(const uint64_t* v, const uint64_t* starts, uint64_t k, uint64_t N, uint64_t L,
+                              int model) {
+  uint64_t total = 0;
+  for (uint64_t s = 0; s < k; s++)
+    for (uint64_t a = 0; a < N; a += L) {
+      const uint64_t len = a + L <= N ? L : N - a;
+      total += orc_partition_size_bits(v + starts[s] + a, len, model);
+    }
+  return total;
+}
+
+/*
+ * The search (§3.2.1, steps 2-3), in this reading:
+ *  - exponential phase: L = 1, 2, 4, ... (powers of two up to N, then N itself), stopping after the
+ *    first size above its predecessor's: the sizes are U-shaped in L, so that step is past the
+ *    minimum;
+ *  - back search: from the best L so far, probe L - step and L + step (inside [1, N]) with step
+ *    starting at half the best L; move to the smaller size when it is smaller, else halve the step;
+ *  - stop when the step reaches 0, or when a move improves the size by less than 0.01 %
+ *    (old - new < old / 10^4, in integers).
+ * Sizes are cached per L. Returns the chosen L; *best_bits gets its sample size and *evals the
+ * number of distinct L evaluated.
+ */
+uint64_t orc_search_partition_size(const uint64_t* v, uint64_t n, uint64_t N, double frac, uint64_t seed,
+                                   int model, uint64_t* best_bits, uint64_t* evals) {
+  if (n == 0) {
+    if (best_bits) *best_bits = 0;
+    if (evals) *evals = 0;
+    return 1;
+  }
+  if (n < N) N = n;
+  uint64_t kmax = (uint64_t)(frac * (double)n / (double)N);
+  if (kmax < 1) kmax = 1;
+  uint64_t* starts = (uint64_t*)malloc(sizeof(uint64_t) * kmax);
+  uint64_t* cache = (uint64_t*)calloc(N + 1, sizeof(uint64_t)); /* 0 = not evaluated */
+  if (!starts || !cache) orc_die("out of memory");
+  const uint64_t k = orc_search_samples(n, N, frac, seed, starts);
+  uint64_t ne = 0;
+#define SIZE_AT(LL) (cache[LL] ? cache[LL] : (ne++, cache[LL] = orc_sample_size_bits(v, starts, k, N, LL, model) + 1))
+  /* cache holds size + 1 so that 0 marks "not evaluated" */
+  uint64_t best = 1, best_s = SIZE_AT(1);
+  uint64_t prev_s = best_s;
+  for (uint64_t L = 2;; L *= 2) {
+    const uint64_t LL = L < N ? L : N;
+    const uint64_t s = SIZE_AT(LL);
+    if (s < best_s) {
+      best_s = s;
+      best = LL;
+    }
+    if (s > prev_s || LL == N) break;
+    prev_s = s;
+  }
+  for (uint64_t step = best / 2; step > 0;) {
+    uint64_t cand = best, cand_s = best_s;
+    if (best > step) {
+      const uint64_t s = SIZE_AT(best - step);
+      if (s < cand_s) {
+        cand_s = s;
+        cand = best - step;
+      }
+    }
+    if (best + step <= N) {
+      const uint64_t s = SIZE_AT(best + step);
+      if (s < cand_s) {
+        cand_s = s;
+        cand = best + step;
+      }
+    }
+    if (cand == best) {
+      step /= 2;
+      continue;
+    }
+    const int small_gain = (best_s - cand_s) * 10000 < best_s - 1; /* cached sizes are size + 1 */
+    best = cand;
+    best_s = cand_s;
+    if (small_gain) break;
+  }
+#undef SIZE_AT
+  free(starts);
+  free(cache);
+  if (best_bits) *best_bits = best_s - 1;
+  if (evals) *evals = ne;
+  return best;
 }

@@ -490,3 +490,71 @@ def test_split_merge_vs_brute_force_optimum(orc):
             got = sum(_sizes(orc, v, st, 1))
             assert got >= best
             assert got <= best + 256 * n  # never worse than one partition per value beyond optimum
+
+
+# ----------------------------------------------------------------------------- partition-size search (§3.2.1)
+
+def test_size_search_worked_case(orc):
+    """Eight values, a 2^40 jump after the fourth, N = 8 (the column is its own sample). By hand:
+    L = 1: 8 zero-width partitions, 2048 bits; L = 2: 4 exact lines, 1024; L = 4: two exact lines,
+    512; L = 8: one partition across the jump, b >= 40, over 512: the exponential phase stops there
+    with best L = 4. Back search from 4 with step 2 probes 2 (cached) and 6, then step 1 probes 3
+    and 5; every one of those holds the jump inside a partition or has three partitions, so all
+    exceed 512 and L = 4 stands. Distinct sizes evaluated: 1, 2, 4, 8, 6, 3, 5."""
+    j = 1 << 40
+    v = np.array([0, 1, 2, 3, j, j + 1, j + 2, j + 3], dtype=np.uint64)
+    L, bits, evals = orc.search_partition_size(v, 8, 1.0, 0, orc.MODEL_LINEAR)
+    assert (L, bits, evals) == (4, 512, 7)
+
+
+def test_size_search_exactly_linear_takes_the_largest_size(orc):
+    """Exactly linear data fits with zero-width residuals at every size, so the size is S_M per
+    partition and the fewest partitions win: L = N, one 256-bit record per sample."""
+    v = np.arange(200_000, dtype=np.uint64) * 13 + 7
+    for N in (1000, 4096):
+        L, bits, _ = orc.search_partition_size(v, N, 0.05, 3, orc.MODEL_LINEAR)
+        k = len(orc.search_samples(len(v), N, 0.05, 3))
+        assert (L, bits) == (N, 256 * k)
+
+
+def test_size_search_samples(orc):
+    """k = floor(frac n / N) subsequences (at least one), starts in [0, n - N], deterministic;
+    a column no longer than N is its own sample."""
+    st = orc.search_samples(1_000_000, 1000, 0.01, 5)
+    assert len(st) == 10 and (st <= 1_000_000 - 1000).all()
+    assert (st == orc.search_samples(1_000_000, 1000, 0.01, 5)).all()
+    assert not (st == orc.search_samples(1_000_000, 1000, 0.01, 6)).all()
+    assert orc.search_samples(500, 1000, 0.01, 5).tolist() == [0]
+    assert len(orc.search_samples(50_000, 1000, 0.001, 1)) == 1
+
+
+def test_size_search_lands_on_a_local_minimum_near_the_optimum(orc):
+    """On quadratic data with noise (partition size trades record overhead against residual width)
+    the result is a local minimum over L +- 1 (the back search ends with step 1) and within 0.5 % of
+    the brute-force optimum over every L in [1, N]."""
+    x = np.arange(40_000, dtype=np.float64)
+    for c, nb, N in ((2e-3, 4, 256), (5e-4, 6, 512)):
+        v = (x * x * c).astype(np.uint64) + W.random_u64(40_000, 5, bits=nb)
+        st = orc.search_samples(len(v), N, 0.5, 7)
+        sizes = [orc.sample_size_bits(v, st, N, L) for L in range(1, N + 1)]
+        L, bits, _ = orc.search_partition_size(v, N, 0.5, 7)
+        assert bits == sizes[L - 1]
+        assert bits <= min(sizes[L - 2] if L > 1 else bits, sizes[L] if L < N else bits)
+        assert bits <= 1.005 * min(sizes)
+
+
+def test_size_search_passes_a_tie_in_the_exponential_phase(orc):
+    """Only a size above its predecessor's ends the exponential phase. N = 32 values in four groups of
+    eight, each two exact 4-value lines with a jump of 0xA0000000 between them: L = 4 costs eight
+    zero-width records, 2048 bits; L = 8 costs four records plus 32 values of width 32, also 2048;
+    L = 16 and L = 32 are cheaper still (1568 and 1312). The search must walk past the tie to 32."""
+    J = 0xA0000000
+    v = []
+    for g in range(4):
+        base = (1 << 40) + g * 3 * J
+        v += [base + k for k in range(4)] + [base + J + k for k in range(4)]
+    v = np.array(v, dtype=np.uint64)
+    st = np.array([0], dtype=np.uint64)
+    s = {L: orc.sample_size_bits(v, st, 32, L) for L in (4, 8, 16, 32)}
+    assert s == {4: 2048, 8: 2048, 16: 1568, 32: 1312}
+    assert orc.search_partition_size(v, 32, 1.0, 0)[:2] == (32, 1312)
