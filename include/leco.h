@@ -64,12 +64,13 @@ typedef enum { LECO_U32 = 0, LECO_U64 = 1 } leco_dtype;
 /* §3.1 model family members built here: constant (FOR, §2) and linear. */
 typedef enum { LECO_MODEL_CONSTANT = 0, LECO_MODEL_LINEAR = 1 } leco_model;
 
-typedef enum { LECO_PART_FIXED = 0, LECO_PART_VAR = 1 } leco_part_kind;
+typedef enum { LECO_PART_FIXED = 0, LECO_PART_VAR = 1, LECO_PART_AUTO = 2 } leco_part_kind;
 
 /* Partition policy (§3.2). Fixed: partition j = positions [j L, (j+1) L) (§3.2.1), part_size = L
  * (1 .. 2^24). Variable: split + merge (§3.2.2); part_size caps a partition's length (1 .. 2^24,
  * 0 = 2^24); tau in [0, 1] is the split threshold coefficient (C <= tau * S_M with S_M = 256 bits,
- * one record). */
+ * one record). Auto: fixed partitions whose size leco_search_partition_size picks (§3.2.1) over
+ * 1 .. part_size (0 = 10000, at most 16384) from a 1% sample with seed 0. */
 typedef struct {
   int32_t kind;       /* leco_part_kind */
   uint32_t part_size; /* fixed: L; variable: length cap */
@@ -192,6 +193,19 @@ leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, ui
 /* Synchronize `stream`, then return the first device-side error recorded on the column since the
  * last leco_sync (and clear it), else LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
 leco_status leco_sync(const leco_column* col, leco_stream_t stream);
+
+/* Fixed partition-size search (§3.2.1): sample k = max(1, floor(sample_frac n / max_len))
+ * subsequences of max_len values (starts SplitMix64(seed + i) mod (n - max_len + 1); a column of at
+ * most max_len values is its own sample), then search L in 1 .. max_len for the smallest compressed
+ * size of the sample under fixed partitions: an exponential phase over powers of two that ends after
+ * the first size above its predecessor's, then a back search with halving steps, stopping when a move
+ * gains less than 0.01 %. d_values: n values of dtype (device). max_len: 1 .. 16384 (0 = 10000);
+ * sample_frac in (0, 1] (0 = 0.01). Writes the size to *best_L and, when non-NULL, the sample's size
+ * in bits at that L to *best_bits and the number of sizes evaluated to *evals. Synchronizes `stream`
+ * once per size evaluated. Errors: INVALID_ARG, OOM, CUDA. */
+leco_status leco_search_partition_size(const void* d_values, uint64_t n, leco_dtype dtype, leco_model model,
+                                       uint32_t max_len, double sample_frac, uint64_t seed, leco_stream_t stream,
+                                       uint32_t* best_L, uint64_t* best_bits, uint64_t* evals);
 
 /* Failure-detection self-test: one kernel waits on a shared-memory barrier that nothing completes,
  * with the same bounded wait the scan and pack kernels use, limited to limit_us microseconds

@@ -15,7 +15,9 @@
 // previous round are refitted. Rounds repeat until none merges.
 #include <math.h>
 
+#include <map>
 #include <type_traits>
+#include <vector>
 
 #include "fit.cuh"
 #include "leco_internal.cuh"
@@ -242,6 +244,40 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Fixed-partition size search (§3.2.1): total S_M + len * b over partitions of L values cut from
+// each of k sampled subsequences of N values (starts[s]), the last of each possibly short.
+// Thread per partition for L <= kTinySpan, warp per partition above; one atomic per warp.
+__global__ void k_sample_sizes_thread(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ starts,
+                                      uint64_t k, uint32_t N, uint32_t L, int model,
+                                      unsigned long long* __restrict__ total) {
+  const uint64_t P = (N + L - 1) / L, count = k * P;
+  uint64_t acc = 0;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < count; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = t / P, j = t - s * P;
+    const uint32_t len = (uint32_t)min((uint64_t)L, (uint64_t)N - j * L);
+    const FitResult R = fit_range<1>(values, dtype, starts[s] + j * L, len, model, 0, nullptr);
+    acc += kSmBits + (uint64_t)len * R.b;
+  }
+  acc = warp_sum_u64(acc);
+  if ((threadIdx.x & 31u) == 0 && acc) atomicAdd(total, (unsigned long long)acc);
+}
+
+__global__ void k_sample_sizes_warp(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ starts,
+                                    uint64_t k, uint32_t N, uint32_t L, int model,
+                                    unsigned long long* __restrict__ total) {
+  const uint64_t P = (N + L - 1) / L, count = k * P;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint64_t acc = 0;
+  for (uint64_t t = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; t < count; t += nw) {
+    const uint64_t s = t / P, j = t - s * P;
+    const uint32_t len = (uint32_t)min((uint64_t)L, (uint64_t)N - j * L);
+    const FitResult R = fit_range<32>(values, dtype, starts[s] + j * L, len, model, lane, nullptr);
+    acc += kSmBits + (uint64_t)len * R.b;
+  }
+  if (lane == 0 && acc) atomicAdd(total, (unsigned long long)acc);
+}
+
 __device__ __forceinline__ bool pair_gain(const uint64_t* sz, const uint64_t* msz, uint64_t j, int64_t* g) {
   if (msz[j] == kNone) return false;
   *g = (int64_t)(sz[j] + sz[j + 1]) - (int64_t)msz[j];
@@ -346,6 +382,100 @@ cudaError_t span_sizes(const void* values, int dtype, uint64_t n, const uint64_t
 }
 
 }  // namespace
+
+// Fixed partition-size search (§3.2.1), in the reading the oracle states (R9): SplitMix64-placed
+// sample subsequences, an exponential phase over powers of two that ends after the first size above
+// its predecessor's, then a back search with halving steps, stopping when a move gains < 0.01 %.
+cudaError_t search_partition_size(const void* values, int dtype, uint64_t n, int model, uint32_t N, double frac,
+                                  uint64_t seed, uint32_t* best_L, uint64_t* best_bits, uint64_t* evals,
+                                  cudaStream_t st) {
+  *best_L = 1;
+  *best_bits = 0;
+  *evals = 0;
+  if (n == 0) return cudaSuccess;
+  if (n < N) N = (uint32_t)n;
+  std::vector<uint64_t> h_starts;
+  if (n <= N) {
+    h_starts.push_back(0);
+  } else {
+    uint64_t k = (uint64_t)(frac * (double)n / (double)N);
+    if (k < 1) k = 1;
+    for (uint64_t i = 0; i < k; i++) h_starts.push_back(splitmix64(seed + i) % (n - N + 1));
+  }
+  const uint64_t k = h_starts.size();
+  uint64_t* d_starts = nullptr;
+  unsigned long long* d_total = nullptr;
+  cudaError_t e = dalloc(&d_starts, k, st);
+  if (e == cudaSuccess) e = dalloc(&d_total, 1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_starts, h_starts.data(), 8 * k, cudaMemcpyHostToDevice, st);
+  std::map<uint32_t, uint64_t> cache;
+  auto size_at = [&](uint32_t L) -> uint64_t {
+    auto it = cache.find(L);
+    if (it != cache.end()) return it->second;
+    unsigned long long total = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_total, 0, 8, st);
+    const uint64_t parts = k * ((N + L - 1) / L);
+    if (e == cudaSuccess) {
+      if (L <= kTinySpan)
+        k_sample_sizes_thread<<<grid_for(parts, 256, 8), 256, 0, st>>>(values, dtype, d_starts, k, N, L, model, d_total);
+      else
+        k_sample_sizes_warp<<<grid_for(parts * 32, 256, 8), 256, 0, st>>>(values, dtype, d_starts, k, N, L, model,
+                                                                          d_total);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cache[L] = total;
+    return total;
+  };
+  uint32_t best = 1;
+  uint64_t best_s = size_at(1), prev_s = best_s;
+  for (uint64_t L = 2; e == cudaSuccess; L *= 2) {  // exponential phase
+    const uint32_t LL = (uint32_t)(L < N ? L : N);
+    const uint64_t s = size_at(LL);
+    if (s < best_s) {
+      best_s = s;
+      best = LL;
+    }
+    if (s > prev_s || LL == N) break;
+    prev_s = s;
+  }
+  for (uint32_t step = best / 2; step > 0 && e == cudaSuccess;) {  // back search
+    uint32_t cand = best;
+    uint64_t cand_s = best_s;
+    if (best > step) {
+      const uint64_t s = size_at(best - step);
+      if (s < cand_s) {
+        cand_s = s;
+        cand = best - step;
+      }
+    }
+    if (best + step <= N) {
+      const uint64_t s = size_at(best + step);
+      if (s < cand_s) {
+        cand_s = s;
+        cand = best + step;
+      }
+    }
+    if (cand == best) {
+      step /= 2;
+      continue;
+    }
+    const bool small_gain = (best_s - cand_s) * 10000 < best_s;
+    best = cand;
+    best_s = cand_s;
+    if (small_gain) break;
+  }
+  if (d_starts) cudaFreeAsync(d_starts, st);
+  if (d_total) cudaFreeAsync(d_total, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    *best_L = best;
+    *best_bits = best_s;
+    *evals = cache.size();
+  }
+  return e;
+}
 
 // Runs split + merge; writes m+1 starts to starts_out (capacity n+1) and m to *m_out.
 cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,

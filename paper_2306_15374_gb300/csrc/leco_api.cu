@@ -219,6 +219,23 @@ cudaError_t dev_alloc(void** p, uint64_t bytes, cudaStream_t st) {
 
 extern "C" {
 
+leco_status leco_search_partition_size(const void* d_values, uint64_t n, leco_dtype dtype, leco_model model,
+                                       uint32_t max_len, double sample_frac, uint64_t seed, leco_stream_t stream,
+                                       uint32_t* best_L, uint64_t* best_bits, uint64_t* evals) {
+  NvtxRange nvtx_range("leco_search_partition_size");
+  if (!best_L || (n && !d_values) || !valid_dtype(dtype) || !valid_model(model)) return LECO_ERR_INVALID_ARG;
+  if (max_len == 0) max_len = 10000;
+  if (sample_frac == 0.0) sample_frac = 0.01;
+  if (max_len > 16384 || !(sample_frac > 0.0 && sample_frac <= 1.0)) return LECO_ERR_INVALID_ARG;
+  uint64_t bits = 0, ne = 0;
+  const cudaError_t e = search_partition_size(d_values, dtype, n, model, max_len, sample_frac, seed, best_L, &bits,
+                                              &ne, (cudaStream_t)stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (best_bits) *best_bits = bits;
+  if (evals) *evals = ne;
+  return LECO_OK;
+}
+
 leco_status leco_selftest_wait_timeout(uint32_t limit_us, leco_stream_t stream) {
   if (limit_us < 1 || limit_us > 1000000) return LECO_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -290,6 +307,18 @@ leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
   c->home = st;
   cudaGetDevice(&c->device);
   leco_status s = LECO_OK;
+  if (policy.kind == LECO_PART_AUTO) {  // fixed partitions of the searched size (§3.2.1)
+    uint32_t L = 1;
+    s = leco_search_partition_size(d_values, n, dtype, model, policy.part_size, 0.01, 0, stream, &L, nullptr,
+                                   nullptr);
+    if (s != LECO_OK) {
+      delete c;
+      return s;
+    }
+    policy.kind = LECO_PART_FIXED;
+    policy.part_size = L;
+    c->kind = LECO_PART_FIXED;
+  }
   if (policy.kind == LECO_PART_FIXED) {
     if (policy.part_size < 1 || policy.part_size > kMaxPartLen) {
       delete c;

@@ -282,6 +282,9 @@ cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint6
                                  cudaStream_t st);
 
 // variable partitioner (k_var.cu)
+cudaError_t search_partition_size(const void* values, int dtype, uint64_t n, int model, uint32_t N, double frac,
+                                  uint64_t seed, uint32_t* best_L, uint64_t* best_bits, uint64_t* evals,
+                                  cudaStream_t st);
 cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
                           int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st);
 

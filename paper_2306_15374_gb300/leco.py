@@ -28,6 +28,7 @@ LECO_MODEL_CONSTANT = 0
 LECO_MODEL_LINEAR = 1
 LECO_PART_FIXED = 0
 LECO_PART_VAR = 1
+LECO_PART_AUTO = 2
 LECO_FILTER_PRUNE = 1
 LECO_FILTER_DECODE_ALL = 2
 
@@ -87,6 +88,11 @@ def variable(tau: float = 0.03, cap: int = 0) -> PartitionPolicy:
     return PartitionPolicy(LECO_PART_VAR, int(cap), float(tau))
 
 
+def auto(max_len: int = 0) -> PartitionPolicy:
+    """Fixed partitions of the size the §3.2.1 search picks over 1 .. max_len (0 = 10000)."""
+    return PartitionPolicy(LECO_PART_AUTO, int(max_len), 0.0)
+
+
 _lib = None
 
 
@@ -126,6 +132,8 @@ def lib() -> ctypes.CDLL:
         "leco_batch_plan_run_graph": (i32, [vp, vp]),
         "leco_batch_plan_jobs": (u64, [vp]),
         "leco_trim_memory": (i32, []),
+        "leco_search_partition_size": (i32, [vp, u64, i32, i32, u32, ctypes.c_double, u64, vp,
+                                             ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "leco_selftest_wait_timeout": (i32, [u32, vp]),
         "leco_batch_plan_tune": (i32, [vp, vp, ctypes.POINTER(ScanConfig)]),
         "leco_batch_plan_free": (None, [vp]),
@@ -364,6 +372,17 @@ def leco_tune_scan(col: Column, op: int = 0, lo: int = 0, hi: int = (1 << 64) - 
 def leco_selftest_wait_timeout(limit_us: int, stream=None) -> int:
     """Run the bounded-wait self-test; returns the status (LECO_ERR_TIMEOUT is the expected one)."""
     return int(lib().leco_selftest_wait_timeout(int(limit_us), _stream(stream)))
+
+
+def leco_search_partition_size(values, model: int = 1, max_len: int = 0, sample_frac: float = 0.0, seed: int = 0,
+                               stream=None):
+    """Fixed partition-size search (§3.2.1) on a device column: (L, sample bits at L, sizes evaluated)."""
+    L, bits, ne = ctypes.c_uint32(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().leco_search_partition_size(_dev(values), values.numel(), _dtype_of(values), int(model), int(max_len),
+                                            float(sample_frac), int(seed),
+                                            _stream(stream), ctypes.byref(L), ctypes.byref(bits), ctypes.byref(ne)),
+           "leco_search_partition_size")
+    return int(L.value), int(bits.value), int(ne.value)
 
 
 def leco_trim_memory() -> None:

@@ -69,3 +69,9 @@ def test_host_side_argument_errors(built):
     assert L.leco_filter_sum(None, 0, 1, 0, None, None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_selftest_wait_timeout(0, None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_selftest_wait_timeout(2_000_000, None) == leco.LECO_ERR_INVALID_ARG
+    L32, b64 = ctypes.c_uint32(0), ctypes.c_uint64(0)
+    assert L.leco_search_partition_size(None, 0, 1, 1, 20000, 0.01, 0, None, ctypes.byref(L32), None,
+                                        None) == leco.LECO_ERR_INVALID_ARG  # max_len above 16384
+    assert L.leco_search_partition_size(None, 0, 1, 1, 100, 1.5, 0, None, ctypes.byref(L32), None,
+                                        None) == leco.LECO_ERR_INVALID_ARG  # fraction above 1
+    assert L.leco_search_partition_size(None, 0, 1, 1, 100, 0.01, 0, None, None, None, None) == leco.LECO_ERR_INVALID_ARG

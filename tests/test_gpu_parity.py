@@ -289,6 +289,41 @@ def test_var_compression_close_to_sequential_merge(lc):
         assert gpu_bytes <= 1.02 * seq_bytes
 
 
+# ----------------------------------------------------------------------------- partition-size search (§3.2.1)
+
+def _search_cases():
+    x = np.arange(600_000, dtype=np.float64)
+    yield "cfg1_2M", W.cfg1(2_000_000), 64, 10000, 0.01
+    yield "quadratic", (x * x * 2e-5).astype(np.uint64) + W.random_u64(600_000, 5, bits=6), 64, 4096, 0.02
+    yield "lognormal", W.sorted_lognormal(2_000_000, 1e9, 2.0, seed=3), 64, 10000, 0.01
+    yield "timestamps_u32", W.timestamps_u32(1_000_000, seed=4), 32, 2000, 0.05
+    yield "random", W.random_u64(300_000, 6), 64, 1000, 0.01
+    yield "short_column", W.cfg1(700), 64, 10000, 0.01
+    yield "adversarial", W.adversarial_u64(100_000, seed=7), 64, 300, 0.2
+
+
+SEARCH = list(_search_cases())
+
+
+@pytest.mark.parametrize("case", SEARCH, ids=[c[0] for c in SEARCH])
+def test_partition_size_search_matches_oracle(lc, case):
+    """Same sample, same sizes, same search path: the GPU picks the oracle's L with the same sample
+    size in bits and the same number of sizes evaluated; the auto policy then encodes byte for byte
+    like the fixed policy at that L."""
+    _, v, bits, N, frac = case
+    for model in (1, 0):
+        want = oracle.search_partition_size(v, N, frac, 11, model)
+        got = lc.leco_search_partition_size(to_dev(v, bits), model, max_len=N, sample_frac=frac, seed=11)
+        assert got == want, model
+    if N <= 10000 and frac == 0.01:
+        L = oracle.search_partition_size(v, N, 0.01, 0, 1)[0]
+        col = lc.leco_encode(to_dev(v, bits), lc.auto(N), 1)
+        rec_b, words_b, _ = lc.leco_column_export(col)
+        rec, words = oracle.encode_fixed(v, L, 1)
+        assert rec_b == rec.tobytes() and words_b == words.tobytes()
+        assert col.stats()["partitions"] == (len(v) + L - 1) // L
+
+
 # ----------------------------------------------------------------------------- full size
 
 @pytest.mark.parametrize("dist", ["a", "b", "c"])
