@@ -54,6 +54,7 @@ def parse_args():
                     help="fix: the 3 x 200M fixed-partition columns (default); var: the variable-partition "
                          "columns (200M piecewise-linear uint64, 500M uint32 timestamps)")
     ap.add_argument("--tau", type=float, default=0.03)
+    ap.add_argument("--tau-sweep", default="", help="var workload: comma-separated tau values to sweep (CR vs tau)")
     return ap.parse_args()
 
 
@@ -542,6 +543,26 @@ def run_var(args):
             "filter_ms": t_fil, "filter_gbs": (comp + 24) / (t_fil * 1e-3) / 1e9,
             "filter_prune_ms": t_pru, "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6,
         }
+        if args.tau_sweep:
+            # compression against tau (the partitioner's one knob, swept over the paper's range)
+            sweep = []
+            for tau in [float(t) for t in args.tau_sweep.split(",")]:
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                c = leco.leco_encode(dv, leco.variable(tau), leco.LECO_MODEL_LINEAR)
+                b.record(stream)
+                torch.cuda.synchronize()
+                sc = c.stats()
+                cb = sc["record_bytes"] + sc["residual_bytes"] + 8 * (sc["partitions"] + 1)
+                sweep.append({"tau": tau, "partitions": sc["partitions"], "ratio": cb / (n * vb),
+                              "partition_encode_ms": a.elapsed_time(b)})
+                c.free()
+            L_auto, _, n_eval = leco.leco_search_partition_size(dv, leco.LECO_MODEL_LINEAR)
+            auto = leco.leco_encode(dv, leco.auto(), leco.LECO_MODEL_LINEAR)
+            out[name]["tau_sweep"] = sweep
+            out[name]["fixed_searched_size"] = {"L": L_auto, "sizes_evaluated": n_eval, "ratio": auto.stats()["ratio"]}
+            auto.free()
         for c in (col, fix):
             c.free()
         del dv, o
