@@ -157,37 +157,75 @@ def step_bytes(comp_bytes, n, k):
 
 # ----------------------------------------------------------------------------- CPU oracle arm
 
-def cpu_oracle_run(cols, lookups_frac, reps=1):
-    """Time the oracle (one thread) on prepared samples; returns (bytes, seconds)."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def cpu_oracle_run(cols, lookups_frac, reps=1, threads=1):
+    """Time the oracle on prepared samples: decode, filter-sum and lookups of every sample piece.
+    threads > 1 runs the pieces on a thread pool (the oracle is C behind ctypes, which releases the
+    GIL, and shares no state between calls): partition-parallel on that many cores. Returns
+    (algorithmic bytes, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
 
-    total_b, total_t = 0, 0.0
-    for s in cols:
+    def work(s):
         v, rec, words, idx, lo, hi = s["v"], s["rec"], s["words"], s["idx"], s["lo"], s["hi"]
-        comp = oracle.compressed_bytes(rec, words)
+        d = oracle.decode(rec, words, len(v))
+        oracle.filter_sum(rec, words, len(v), lo, hi)
+        oracle.lookup(rec, words, len(v), idx, L=L)
+        return d
+
+    pieces = [p for c in cols for p in c["pieces"]]
+    total_b = 0
+    for c in cols:
+        dec, filt, look = step_bytes(c["comp"], c["n"], c["k"])
+        total_b += (dec + filt + look) * reps
+    outs = []
+    t0 = time.perf_counter()
+    if threads <= 1:
         for _ in range(reps):
-            t0 = time.perf_counter()
-            d = oracle.decode(rec, words, len(v))
-            oracle.filter_sum(rec, words, len(v), lo, hi)
-            oracle.lookup(rec, words, len(v), idx, L=L)
-            total_t += time.perf_counter() - t0
-            dec, filt, look = step_bytes(comp, len(v), len(idx))
-            total_b += dec + filt + look
-            assert (d == v).all()
+            outs = [work(p) for p in pieces]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            for _ in range(reps):
+                outs = list(ex.map(work, pieces))
+    total_t = time.perf_counter() - t0
+    for p, d in zip(pieces, outs):
+        assert (d == p["v"]).all()
     return total_b, total_t
 
 
-def prepare_cpu_samples(columns, every, lookups, n):
+def prepare_cpu_samples(columns, every, lookups, n, parts=1):
+    """Every `every`-th partition of each column, encoded by the oracle; split into `parts` pieces of
+    whole partitions (each encoded on its own) so the pieces can be decoded in parallel. The work
+    (partitions decoded, values filtered, lookups) is the same for any number of pieces."""
+    import numpy as np
+
     import oracle
     import workloads as W
 
     out = []
     for d, v in columns.items():
         s = sample_partitions(v, every)
-        rec, words = oracle.encode_fixed(s, L, oracle.MODEL_LINEAR)
         k = max(1, int(lookups * len(s) / n))
         lo, hi = W.filter_bounds(v)
-        out.append(dict(v=s, rec=rec, words=words, idx=W.uniform_indices(k, len(s), seed=7), lo=lo, hi=hi))
+        idx = W.uniform_indices(k, len(s), seed=7)
+        m = len(s) // L
+        bounds = np.linspace(0, m, max(1, min(parts, m)) + 1).astype(np.int64) * L
+        pieces, comp = [], 0
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            sv = s[a:b]
+            rec, words = oracle.encode_fixed(sv, L, oracle.MODEL_LINEAR)
+            comp += oracle.compressed_bytes(rec, words)
+            sel = idx[(idx >= a) & (idx < b)] - np.uint64(a)
+            pieces.append(dict(v=sv, rec=rec, words=words, idx=sel, lo=lo, hi=hi))
+        out.append(dict(pieces=pieces, comp=comp, n=len(s), k=k))
     return out
 
 
@@ -203,27 +241,29 @@ def run_reference(args):
     oracle.build()
     columns = {d: W.cfg2(d, args.n) for d in DISTS}
     every = args.sample_every
-    samples = prepare_cpu_samples(columns, every, args.lookups, args.n)
+    cores = host_cores()
+    samples = prepare_cpu_samples(columns, every, args.lookups, args.n, parts=cores)
     # keep the whole run within about 90 s of oracle time: thin the per-step sample if needed
-    _, t1 = cpu_oracle_run(samples, None)
+    _, t1 = cpu_oracle_run(samples, None, threads=cores)
     budget = 90.0
     if (args.steps + args.warmup) * t1 > budget:
         every = int(every * (args.steps + args.warmup) * t1 / budget) + 1
-        samples = prepare_cpu_samples(columns, every, args.lookups, args.n)
+        samples = prepare_cpu_samples(columns, every, args.lookups, args.n, parts=cores)
     args.sample_every = every
     del columns
     for _ in range(args.warmup):
-        cpu_oracle_run(samples, None)
-    b, t = cpu_oracle_run(samples, None, reps=args.steps)
+        cpu_oracle_run(samples, None, threads=cores)
+    b, t = cpu_oracle_run(samples, None, reps=args.steps, threads=cores)
     value = b / t / 1e9
-    nsamp = sum(len(s["v"]) for s in samples)
+    nsamp = sum(c["n"] for c in samples)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"every {args.sample_every}th partition"},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{nsamp} values: every {args.sample_every}th 4096-value partition of each column"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{nsamp} values: every {args.sample_every}th 4096-value partition of each column, "
+                                   f"partition-parallel on {cores} threads"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -403,11 +443,15 @@ def run_leco(args):
         import oracle
 
         oracle.build()
-        samples = prepare_cpu_samples(columns, args.sample_every, args.lookups, n)
-        b, t = cpu_oracle_run(samples, None)
-        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sum(len(s['v']) for s in samples)} values: every {args.sample_every}th "
-                         f"4096-value partition of each column; decode + filter-sum + proportional lookups"}
+        cores = host_cores()
+        samples = prepare_cpu_samples(columns, args.sample_every, args.lookups, n, parts=cores)
+        b1, t1 = cpu_oracle_run(samples, None, threads=1)
+        b, t = cpu_oracle_run(samples, None, threads=cores)
+        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "single_thread_value": b1 / t1 / 1e9,
+               "sample": f"{sum(c['n'] for c in samples)} values: every {args.sample_every}th "
+                         f"4096-value partition of each column; decode + filter-sum + proportional lookups, "
+                         f"partition-parallel on {cores} threads (single_thread_value: the same on one)"}
 
     value = whole_job_gbs(step_b, world, ms)
     line = {
