@@ -67,6 +67,8 @@ struct Slot {
   std::vector<Req*> reqs;
   std::vector<uint64_t> off;  // lookups: first value; ranges: byte offset
   uint64_t nl = 0, nitems = 0, rbytes = 0, values = 0;
+  uint32_t* d_stat = nullptr;  // device errors of the batch's range decode (kStat* flags)
+  uint32_t* h_stat = nullptr;  // pinned copy, read when the batch is done
   cudaError_t err = cudaSuccess;
 };
 
@@ -86,7 +88,6 @@ struct leco_server {
   std::vector<ColSlot> cols;
   std::vector<ColumnView> h_views;
   ColumnView* d_views = nullptr;
-  uint32_t* d_status = nullptr;
   uint32_t stage_bytes = 64;
   uint64_t resident = 0, reserved = 0;
   uint64_t cap_items = 0;
@@ -117,6 +118,8 @@ void slot_free(Slot& sl) {
   cudaFree(sl.d_lout);
   cudaFree(sl.d_items);
   cudaFree(sl.d_rout);
+  cudaFree(sl.d_stat);
+  cudaFreeHost(sl.h_stat);
 }
 
 uint64_t slot_device_bytes(const leco_server_config& c, uint64_t cap_items) {
@@ -139,6 +142,8 @@ cudaError_t slot_alloc(Slot& sl, const leco_server_config& c, uint64_t cap_items
   if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_lout, 8 * L);
   if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_items, sizeof(BatchItem) * cap_items);
   if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_rout, rb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_stat, 16);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_stat, 16);
   return e;
 }
 
@@ -192,16 +197,20 @@ void gpu_run(leco_server* s, Slot& sl) {
   if (nl && staged_lookups && e == cudaSuccess)
     e = cudaMemcpyAsync(sl.h_lout, sl.d_lout, 8 * nl, cudaMemcpyDeviceToHost, sl.stream);
   if (nl && e == cudaSuccess) e = cudaEventRecord(sl.ldone, sl.stream);  // lookups complete before ranges
+  *sl.h_stat = 0;
   if (ni && e == cudaSuccess) {
-    e = cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, sl.stream);
+    e = cudaMemsetAsync(sl.d_stat, 0, 4, sl.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, sl.stream);
     uint32_t sb;
     {
       std::lock_guard<std::mutex> lock(s->mu);
       sb = s->stage_bytes;
     }
     if (e == cudaSuccess)
-      e = launch_batch_decode(s->d_views, sl.d_items, ni, sb, scan_config_lookup(0, LECO_U64, sb), s->d_status,
+      e = launch_batch_decode(s->d_views, sl.d_items, ni, sb, scan_config_lookup(0, LECO_U64, sb), sl.d_stat,
                               sl.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_stat, sl.d_stat, 4, cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess && staged_ranges)
       e = cudaMemcpyAsync(sl.h_rout, sl.d_rout, sl.rbytes, cudaMemcpyDeviceToHost, sl.stream);
     for (size_t k = 0; k < sl.reqs.size() && e == cudaSuccess; k++) {
@@ -295,6 +304,10 @@ void deliver(leco_server* s, Slot& sl, int type) {
     const uint64_t vb = vbytes(r->dtype);
     if (e != cudaSuccess) {
       r->status = e == cudaErrorLaunchTimeout ? LECO_ERR_TIMEOUT : LECO_ERR_CUDA;
+      continue;
+    }
+    if (type == 1 && !s->cfg.mock && (*sl.h_stat & kStatTimeout)) {  // a bounded wait of the decode gave up
+      r->status = LECO_ERR_TIMEOUT;
       continue;
     }
     if (r->direct && !s->cfg.mock && !(r->type == 0 && r->dtype == LECO_U32)) continue;  // already there
@@ -466,13 +479,10 @@ leco_status leco_server_create(const leco_server_config* cfg_in, leco_server** o
     }
     s->h_views.resize(cfg.max_columns);
     cudaError_t e = cudaMalloc((void**)&s->d_views, sizeof(ColumnView) * cfg.max_columns);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_status, 256);
-    if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, 256);
     for (uint32_t i = 0; i < cfg.max_inflight && e == cudaSuccess; i++) e = slot_alloc(s->slots[i], cfg, s->cap_items);
     if (e != cudaSuccess) {
       for (Slot& sl : s->slots) slot_free(sl);
       cudaFree(s->d_views);
-      cudaFree(s->d_status);
       delete s;
       return from_cuda(e);
     }
@@ -699,7 +709,6 @@ void leco_server_destroy(leco_server* s) {
       if (c.used && c.col) leco_column_free(c.col);
     for (Slot& sl : s->slots) slot_free(sl);
     cudaFree(s->d_views);
-    cudaFree(s->d_status);
   }
   delete s;
 }
