@@ -61,8 +61,8 @@ def parse_args():
 KSCAN_SRCS = [os.path.join(ROOT, "paper_2306_15374_gb300", "csrc", f) for f in ("k_scan.cu", "leco_internal.cuh", "tma.cuh")]
 # DRAM read + write per decode launch from one ncu capture of this workload (mean of columns a, b, c;
 # see profiles/k_tilescan_decode_filter_fix200M.md), valid only for the kernel sources it was taken on.
-DECODE_TRAFFIC = {"sha256": "e9b75c13c9836f92e73c699cbba1a37e195d3a36aba62fd8635b52a0a63355fe",
-                  "bytes_per_launch": (1893808896 + 1973340672 + 1845788928) / 3}
+DECODE_TRAFFIC = {"sha256": "7033c1e297e0998641914e6aee95f22ca681fdffbfdca79ee626b33a17ee64af",
+                  "bytes_per_launch": (1893106432 + 1972573440 + 1845003008) / 3}
 
 
 def decode_traffic():

@@ -58,6 +58,11 @@ leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t strea
  * leco_tune_scan is not changed. Synchronizes `stream`. Errors: INVALID_ARG, CUDA. */
 leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, leco_scan_config* best);
 
+/* Synchronize `stream`, then return the first device-side error the plan's runs recorded since the
+ * last call (LECO_ERR_TIMEOUT when a bounded wait inside the decode gave up) and clear it, else
+ * LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
+leco_status leco_batch_plan_sync(leco_batch_plan* plan, leco_stream_t stream);
+
 /* Number of jobs (scan tiles) in the plan. */
 uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan);
 

@@ -240,6 +240,18 @@ leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, le
   return LECO_OK;
 }
 
+leco_status leco_batch_plan_sync(leco_batch_plan* plan, leco_stream_t stream) {
+  if (!plan) return LECO_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LECO_ERR_CUDA;
+  uint32_t flags = 0;
+  if (cudaMemcpy(&flags, plan->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LECO_ERR_CUDA;
+  if (flags && cudaMemset(plan->d_status, 0, 4) != cudaSuccess) return LECO_ERR_CUDA;
+  if (flags & kStatTimeout) return LECO_ERR_TIMEOUT;
+  if (flags & kStatCorrupt) return LECO_ERR_CORRUPT;
+  if (flags & kStatIndexRange) return LECO_ERR_INDEX_RANGE;
+  return LECO_OK;
+}
+
 uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan) { return plan ? plan->nitems : 0; }
 
 void leco_batch_plan_free(leco_batch_plan* plan) {

@@ -131,6 +131,7 @@ def lib() -> ctypes.CDLL:
         "leco_batch_plan_run": (i32, [vp, vp]),
         "leco_batch_plan_run_graph": (i32, [vp, vp]),
         "leco_batch_plan_jobs": (u64, [vp]),
+        "leco_batch_plan_sync": (i32, [vp, vp]),
         "leco_trim_memory": (i32, []),
         "leco_search_partition_size": (i32, [vp, u64, i32, i32, u32, ctypes.c_double, u64, vp,
                                              ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
@@ -450,6 +451,11 @@ def leco_batch_plan_tune(plan: BatchPlan, stream=None) -> dict:
     cfg = ScanConfig()
     _check(lib().leco_batch_plan_tune(plan.handle, _stream(stream), ctypes.byref(cfg)), "leco_batch_plan_tune")
     return {"stages": cfg.stages, "consumer_warps": cfg.consumer_warps, "ms": cfg.ms}
+
+
+def leco_batch_plan_sync(plan: BatchPlan, stream=None) -> int:
+    """Synchronize and return (and clear) the first device error of the plan's runs (LECO_OK if none)."""
+    return int(lib().leco_batch_plan_sync(plan.handle, _stream(stream)))
 
 
 def leco_batch_plan_jobs(plan: BatchPlan) -> int:

@@ -63,6 +63,7 @@ def test_batch_plan_decodes_every_column(lc):
         torch.cuda.synchronize()
         for (v, bits, _), o in zip(cols, outs):
             assert (from_dev(o)[: len(v)] == v).all()
+    assert lc.leco_batch_plan_sync(plan) == lc.LECO_OK
     best = lc.leco_batch_plan_tune(plan)  # a new shape recaptures the graph; results are unchanged
     assert best["stages"] in (2, 3, 4, 6, 8) and best["consumer_warps"] in (4, 8) and best["ms"] > 0
     for runner in (lc.leco_batch_plan_run, lc.leco_batch_plan_run_graph):
