@@ -356,3 +356,85 @@ def test_full_size_cfg2(lc, dist):
         r = from_dev(res)
         assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == want
     assert lc.leco_sync(col) == lc.LECO_OK
+
+
+# ----------------------------------------------------------------------------- tiny columns, concurrency
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_tiny_columns(lc, bits):
+    """n in {2, L-1, L, L+1, 2L+1} with L = 37, both models: fixed encode byte-identical to the
+    oracle, variable boundaries equal to the oracle's round variant, decode, lookups and the full-range
+    sum exact. 64-bit columns include the extremes (width-64 partitions)."""
+    import torch
+
+    L = 37
+    tdt = torch.int32 if bits == 32 else torch.int64
+    for n in (2, L - 1, L, L + 1, 2 * L + 1):
+        v = W.random_u64(n, seed=n, bits=bits) if bits == 32 else W.adversarial_u64(n, seed=n)
+        for model in (0, 1):
+            col = lc.leco_encode(to_dev(v, bits), lc.fixed(L), model)
+            rec_b, words_b, _ = lc.leco_column_export(col)
+            rec, words = oracle.encode_fixed(v, L, model)
+            assert rec_b == rec.tobytes() and words_b == words.tobytes(), (n, model)
+            vcol = lc.leco_encode(to_dev(v, bits), lc.variable(0.03), model)
+            starts = np.frombuffer(lc.leco_column_export(vcol)[2], dtype=np.uint64)
+            assert (starts == oracle.var_partition(v, 0.03, model)).all(), (n, model)
+            for c in (col, vcol):
+                out = torch.empty(n, dtype=tdt, device="cuda")
+                lc.leco_decode_all(c, out)
+                assert (from_dev(out) == v).all()
+                idx = np.array([0, n - 1, n // 2, 1], dtype=np.uint64)
+                o2 = torch.empty(len(idx), dtype=tdt, device="cuda")
+                lc.leco_random_access(c, to_dev(idx), o2)
+                assert (from_dev(o2) == v[idx]).all()
+                res = torch.zeros(3, dtype=torch.int64, device="cuda")
+                lc.leco_filter_sum(c, 0, (1 << 64) - 1, res)
+                r = from_dev(res)
+                assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == exact_sum(v, 0, (1 << 64) - 1)
+                assert lc.leco_sync(c) == lc.LECO_OK
+
+
+def test_concurrent_host_threads_on_separate_streams(lc):
+    """Columns are immutable after encode and the library's shared state (memory pool, tuning table)
+    is locked: four host threads, each on its own stream, encode, decode, look up and filter their
+    own columns at the same time and get exact results."""
+    import threading
+
+    import torch
+
+    errors = []
+
+    def worker(k):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                v = W.linear_noise(2_000_000 + 1000 * k, 1 << 20, 5 + k, 300, seed=20 + k)
+                dv = to_dev(v)
+                for policy in (lc.fixed(1024), lc.variable(0.03)):
+                    col = lc.leco_encode(dv, policy, 1)
+                    out = torch.empty_like(dv)
+                    lc.leco_decode_all(col, out)
+                    idx = to_dev(W.uniform_indices(100_000, len(v), seed=k))
+                    o2 = torch.empty(idx.numel(), dtype=torch.int64, device="cuda")
+                    lc.leco_random_access(col, idx, o2)
+                    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+                    lo, hi = W.filter_bounds(v)
+                    lc.leco_filter_sum(col, lo, hi, res)
+                    s.synchronize()
+                    if not torch.equal(out, dv) or not torch.equal(o2, dv[idx]):
+                        errors.append((k, "values"))
+                    r = from_dev(res)
+                    if (int(r[0]), int(r[1]) | (int(r[2]) << 64)) != exact_sum(v, lo, hi):
+                        errors.append((k, "sum"))
+                    if lc.leco_sync(col, s) != lc.LECO_OK:
+                        errors.append((k, "status"))
+                    col.free()
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append((k, repr(e)))
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors
