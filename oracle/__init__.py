@@ -22,6 +22,9 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 
 MODEL_CONSTANT = 0
 MODEL_LINEAR = 1
+MODEL_POLY = 2  # per-partition choice among constant, linear, quadratic and cubic (R10)
+POLY_MIN_LEN = 64
+POLY_MAX_LEN = 16384
 METRIC_TILDE = 0
 METRIC_DELTA = 1
 SM_BITS = 256  # model size S_M: one 32-byte record
@@ -45,6 +48,20 @@ class _Fit(ctypes.Structure):
         ("b", ctypes.c_int32),
         ("fallback", ctypes.c_int32),
         ("shift", ctypes.c_int64),
+    ]
+
+
+class _PolyFit(ctypes.Structure):
+    _fields_ = [
+        ("c", ctypes.c_double * 4),
+        ("K", ctypes.c_int64 * 4),
+        ("sj", ctypes.c_int32 * 4),
+        ("T", ctypes.c_int64),
+        ("S", ctypes.c_int32),
+        ("b", ctypes.c_int32),
+        ("valid", ctypes.c_int32),
+        ("degree", ctypes.c_int32),
+        ("size", ctypes.c_uint64),
     ]
 
 
@@ -83,6 +100,10 @@ def lib() -> ctypes.CDLL:
         "orc_predict": (i64, [dbl, dbl, u64]),
         "orc_fit_partition": (None, [vp, u64, i32, ctypes.POINTER(_Fit)]),
         "orc_partition_size_bits": (u64, [vp, u64, i32]),
+        "orc_fit_poly": (None, [vp, u64, i32, ctypes.POINTER(_PolyFit)]),
+        "orc_choose_kind": (i32, [vp, u64, ctypes.POINTER(u64)]),
+        "orc_gram_p_parts": (None, [i32, u64, u64, ctypes.POINTER(u64), ctypes.POINTER(i64)]),
+        "orc_gram_norm_parts": (None, [i32, u64, ctypes.POINTER(u64), ctypes.POINTER(i64)]),
         "orc_words_for_bits": (u64, [u64]),
         "orc_encode": (u64, [vp, u64, vp, u64, i32, vp, vp, u64]),
         "orc_decode": (None, [vp, u64, vp, u64, i32, vp]),
@@ -143,6 +164,41 @@ def fit(values, model: int = MODEL_LINEAR) -> dict:
 def partition_size_bits(values, model: int = MODEL_LINEAR) -> int:
     v = _u64(values)
     return int(lib().orc_partition_size_bits(_p(v), v.size, model))
+
+
+def fit_poly(values, degree: int) -> dict:
+    """One polynomial candidate (R10): c (least-squares coefficients on p1..p3), K and sj (grid
+    coefficients and their exponents), S, T, b, valid, size."""
+    v = _u64(values)
+    f = _PolyFit()
+    lib().orc_fit_poly(_p(v), v.size, degree, ctypes.byref(f))
+    return {"c": list(f.c), "K": list(f.K), "sj": list(f.sj), "S": f.S, "T": f.T, "b": f.b,
+            "valid": f.valid, "degree": f.degree, "size": f.size}
+
+
+def choose_model(values) -> tuple[int, int]:
+    """(kind, size in bits) the polynomial model picks for one partition: kind 0 constant,
+    1 linear, 2 quadratic, 3 cubic."""
+    v = _u64(values)
+    size = ctypes.c_uint64(0)
+    k = lib().orc_choose_kind(_p(v), v.size, ctypes.byref(size))
+    return int(k), int(size.value)
+
+
+def _i128(lo, hi) -> int:
+    return (int(hi.value) << 64) | int(lo.value)
+
+
+def gram_p(j: int, N: int, x: int) -> int:
+    lo, hi = ctypes.c_uint64(0), ctypes.c_int64(0)
+    lib().orc_gram_p_parts(j, N, x, ctypes.byref(lo), ctypes.byref(hi))
+    return _i128(lo, hi)
+
+
+def gram_norm(j: int, N: int) -> int:
+    lo, hi = ctypes.c_uint64(0), ctypes.c_int64(0)
+    lib().orc_gram_norm_parts(j, N, ctypes.byref(lo), ctypes.byref(hi))
+    return _i128(lo, hi)
 
 
 # ------------------------------------------------------------------ partitions (§3.2)
@@ -256,7 +312,7 @@ def encode(values, starts, model: int = MODEL_LINEAR):
     st = _u64(starts)
     m = max(st.size - 1, 0)
     rec = np.zeros(m, dtype=RECORD_DTYPE)
-    cap = words_for_bits(64 * v.size)
+    cap = words_for_bits(64 * v.size + 320 * m)
     words = np.zeros(cap, dtype=np.uint64)
     nw = lib().orc_encode(_p(v), v.size, _p(st), m, model, _p(rec), _p(words), cap)
     if nw == 0:
@@ -312,6 +368,10 @@ def rec_grid(word3) -> np.ndarray:
 
 def rec_exact(word3) -> np.ndarray:
     return (np.asarray(word3, dtype=np.uint64) >> np.uint64(62)) & np.uint64(1)
+
+
+def rec_poly(word3) -> np.ndarray:
+    return (np.asarray(word3, dtype=np.uint64) >> np.uint64(63)) & np.uint64(1)
 
 
 def compressed_bytes(records, words) -> int:

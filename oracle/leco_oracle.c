@@ -43,6 +43,25 @@
  *      each subsequence's start; exponential phase over powers of two that ends after the first size
  *      above its predecessor's; back search probing best +- step (step from half the best L,
  *      halved when neither probe is smaller); stop when the step is 0 or a move gains < 0.01 %.
+ *  R10 polynomial model (§3.1 lists polynomial terms; §4 compares constant, linear and polynomials
+ *      up to degree three, choosing per partition): with model 2 each partition takes the smallest
+ *      of four candidates by exact size S + len * b, ties to the earlier one: constant (R5 with
+ *      q = 0), linear (R5), quadratic, cubic (S = 256 bits for the first two; 576 for the
+ *      polynomials, whose five 64-bit words sit in the stream ahead of the residuals).
+ *      A polynomial of degree d in {2, 3} is fitted on the discrete orthogonal polynomials of the
+ *      partition, x' = 2x - (N-1): p1 = x', p2 = 3x'^2 - (N^2-1), p3 = 5x'^3 - (3N^2-7)x'.
+ *      Least squares gives c_j = S_j / |p_j|^2 with the exact integer S_j = sum p_j(x)(w_x - w_0);
+ *      c_j is one binary64 division of the two integers, each converted from sign and magnitude
+ *      as +-(double(hi) * 2^64 + double(lo)). Each coefficient has its own grid: sj = min(62, 61 - e)
+ *      with |c_j| < 2^e, K_j = round(c_j 2^sj) (half up), sj < 0 rejects the candidate; S = max sj,
+ *      capped so that every term K_j 2^(S - sj) p_j(x) stays below 2^124 (the finer grids are
+ *      coarsened to the cap). Prediction pred(x) = T + floor(F(x) / 2^S) mod 2^64 with
+ *      F = sum K_j 2^(S - sj) p_j(x) (an exact integer, no floating point), T the minimax intercept
+ *      of the residuals w - floor(F / 2^S). A candidate needs 64 <= N <= 16384,
+ *      max w - min w < 2^62 and every such residual inside int64. Record: theta0 = theta1 = 0,
+ *      word3 bit 63 set, exact bit 0, s = 0; stream at off: T, K1, K2, K3 (64 bits each, K3 = 0
+ *      for the quadratic), the exponent word s1 | s2 << 8 | s3 << 16, then residual k at
+ *      off + 320 + b k. Variable partitioning and the size search keep the linear size (§3.2).
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +73,7 @@ typedef unsigned __int128 u128;
 
 #define ORC_MODEL_CONSTANT 0
 #define ORC_MODEL_LINEAR 1
+#define ORC_MODEL_POLY 2
 
 /* One 32-byte partition header (§3.3 storage format, with this format's offset/grid fields). */
 typedef struct {
@@ -142,6 +162,7 @@ int64_t orc_predict(double theta0, double theta1, uint64_t x) {
  */
 void orc_fit_partition(const uint64_t* v, uint64_t N, int model, orc_fit* out) {
   memset(out, 0, sizeof(*out));
+  if (model != ORC_MODEL_CONSTANT && model != ORC_MODEL_LINEAR) orc_die("model");
   if (N == 0) orc_die("empty partition");
   if (N > ((uint64_t)1 << 24)) orc_die("partition longer than 2^24");
 
@@ -260,13 +281,186 @@ void orc_fit_partition(const uint64_t* v, uint64_t N, int model, orc_fit* out) {
   free(r0);
 }
 
-/* residual that the decoder must add back: v - pred mod 2^64, as int64 (R3) */
-static int64_t residual_of(uint64_t v, double theta0, double theta1, uint64_t x) {
-  return (int64_t)(v - (uint64_t)orc_predict(theta0, theta1, x));
+/* ------------------------------------------------------------ polynomial model (§3.1, §4, R10) */
+
+#define ORC_POLY_MIN_LEN 64
+#define ORC_POLY_MAX_LEN 16384
+
+/* Gram polynomial p_j (j = 1, 2, 3) of N points at x, on x' = 2x - (N-1) (R10). */
+i128 orc_gram_p(int j, uint64_t N, uint64_t x) {
+  i128 xp = (i128)(2 * (int64_t)x) - (i128)(N - 1);
+  i128 n2 = (i128)N * (i128)N;
+  if (j == 1) return xp;
+  if (j == 2) return 3 * xp * xp - (n2 - 1);
+  if (j == 3) return 5 * xp * xp * xp - (3 * n2 - 7) * xp;
+  orc_die("gram polynomial degree");
+  return 0;
 }
 
-/* Total bits of one partition under the model: the §3 size term S_M + len * b with S_M = 256. */
+/* |p_j|^2 = sum over x < N of p_j(x)^2, closed forms (R10) */
+i128 orc_gram_norm(int j, uint64_t N) {
+  i128 n = (i128)N, n2 = n * n;
+  if (j == 1) return n * (n2 - 1) / 3;
+  if (j == 2) return 4 * n * (n2 - 1) * (n2 - 4) / 5;
+  if (j == 3) return 4 * n * (n2 - 1) * (n2 - 4) * (n2 - 9) / 7;
+  orc_die("gram polynomial degree");
+  return 0;
+}
+
+/* integer to binary64 from sign and magnitude: +-(double(hi) * 2^64 + double(lo)) with hi, lo the
+   halves of |v| (each conversion and the sum rounded to nearest: the same on every host) */
+static double i128_to_double(i128 v) {
+  u128 mag = v < 0 ? (u128)0 - (u128)v : (u128)v;
+  double d = (double)(uint64_t)(mag >> 64) * 18446744073709551616.0 + (double)(uint64_t)mag;
+  return v < 0 ? -d : d;
+}
+
+/* Everything one polynomial candidate decides (exposed for the pins). */
+typedef struct {
+  double c[4];      /* c[1..3]: least-squares coefficients on p_1..p_3 (c[3] = 0 for degree 2) */
+  int64_t K[4];     /* K[1..3]: grid coefficients, c_j ~ K_j 2^-sj[j] */
+  int32_t sj[4];    /* sj[1..3]: each coefficient's grid exponent, 0..62 */
+  int64_t T;        /* minimax intercept */
+  int32_t S;        /* max sj: F is evaluated on the grid 2^-S */
+  int32_t b;        /* residual width */
+  int32_t valid;    /* 0: the candidate does not apply (R10 conditions) */
+  int32_t degree;
+  uint64_t size;    /* 576 + N b when valid */
+} orc_poly_fit;
+
+/* bits a term K_j 2^(S - sj) p_j may be shifted by and stay below 2^124: |K_j| <= 2^61 and, for
+   N <= 16384, |p_1| < 2^14, |p_2| < 2^29, |p_3| < 2^43 */
+static const int32_t poly_headroom[4] = {0, 49, 34, 20};
+
+/* floor(sum_j K_j p_j(x) 2^-sj / 1) = floor(F(x) / 2^S), F = sum_j K_j 2^(S - sj) p_j(x) */
+static i128 poly_line(const int64_t* K, const int32_t* sj, int32_t S, uint64_t N, uint64_t x) {
+  i128 F = 0;
+  for (int j = 1; j <= 3; j++) F += (i128)K[j] * ((i128)1 << (S - sj[j])) * orc_gram_p(j, N, x);
+  return floordiv128(F, (i128)1 << S);
+}
+
+/*
+ * One polynomial candidate of degree 2 or 3 (R10), steps in order:
+ *  1. applicability: 64 <= N <= 16384 and max w - min w < 2^62;
+ *  2. exact moments S_j = sum p_j(x) (w_x - w_0) and least-squares coefficients c_j = S_j / |p_j|^2;
+ *  3. grid exponents: sj = min(62, 61 - e_j) with |c_j| < 2^e_j (0 when c_j = 0; a negative one
+ *     rejects the candidate), S = min(max sj, min over nonzero c_j of sj + headroom_j), each sj
+ *     lowered to at most S, and K_j = round(c_j 2^sj) (half up);
+ *  4. residuals r0_x = w_x - floor(F(x) / 2^S) (all inside int64), lo = min, hi = max;
+ *  5. minimax intercept T = lo + ceil((hi - lo) / 2), width b = bitlen(max zigzag(r0 - T)).
+ */
+void orc_fit_poly(const uint64_t* v, uint64_t N, int degree, orc_poly_fit* out) {
+  memset(out, 0, sizeof(*out));
+  out->degree = degree;
+  if (degree < 2 || degree > 3) orc_die("polynomial degree");
+  if (N < ORC_POLY_MIN_LEN || N > ORC_POLY_MAX_LEN) return;
+  i128 w0 = (int64_t)v[0], wmax = w0, wmin = w0;
+  for (uint64_t x = 0; x < N; x++) {
+    i128 w = (int64_t)v[x];
+    if (w > wmax) wmax = w;
+    if (w < wmin) wmin = w;
+  }
+  if (wmax - wmin >= ((i128)1 << 62)) return;
+
+  int32_t S = 0, cap = INT32_MAX;
+  for (int j = 1; j <= degree; j++) {
+    i128 Sj = 0;
+    for (uint64_t x = 0; x < N; x++) Sj += orc_gram_p(j, N, x) * ((i128)(int64_t)v[x] - w0);
+    out->c[j] = i128_to_double(Sj) / i128_to_double(orc_gram_norm(j, N));
+    if (out->c[j] != 0.0) {
+      int e;
+      frexp(out->c[j], &e); /* |c| < 2^e */
+      int sj = 61 - e;
+      if (sj > 62) sj = 62;
+      if (sj < 0) return;
+      out->sj[j] = sj;
+      if (sj > S) S = sj;
+      if (sj + poly_headroom[j] < cap) cap = sj + poly_headroom[j];
+    }
+  }
+  if (S > cap) S = cap;
+  out->S = S;
+  for (int j = 1; j <= degree; j++) {
+    if (out->sj[j] > S) out->sj[j] = S;
+    double y = ldexp(out->c[j], out->sj[j]); /* exact: a power-of-two scale */
+    double f = floor(y);
+    out->K[j] = (int64_t)f + (y - f >= 0.5 ? 1 : 0);
+  }
+
+  i128 lo = 0, hi = 0;
+  for (uint64_t x = 0; x < N; x++) {
+    i128 r = (i128)(int64_t)v[x] - poly_line(out->K, out->sj, S, N, x);
+    if (r > INT64_MAX || r < INT64_MIN) return;
+    if (x == 0 || r < lo) lo = r;
+    if (x == 0 || r > hi) hi = r;
+  }
+  i128 t = lo + (hi - lo + 1) / 2;
+  uint64_t z1 = zigzag64((int64_t)(lo - t)), z2 = zigzag64((int64_t)(hi - t));
+  out->T = (int64_t)t;
+  out->b = bitlen_u64(z1 > z2 ? z1 : z2);
+  out->valid = 1;
+  out->size = 576 + N * (uint64_t)out->b;
+}
+
+/* The candidate a partition takes under model 2 (R10). */
+typedef struct {
+  int32_t kind; /* 0 constant, 1 linear, 2 quadratic, 3 cubic */
+  int32_t pad;
+  uint64_t size;
+  orc_fit fit;       /* kinds 0, 1 */
+  orc_poly_fit poly; /* kinds 2, 3 */
+} orc_choice;
+
+void orc_choose_model(const uint64_t* v, uint64_t N, orc_choice* out) {
+  memset(out, 0, sizeof(*out));
+  orc_fit f;
+  orc_fit_partition(v, N, ORC_MODEL_CONSTANT, &f);
+  out->kind = 0;
+  out->fit = f;
+  out->size = 256 + N * (uint64_t)f.b;
+  orc_fit_partition(v, N, ORC_MODEL_LINEAR, &f);
+  if (256 + N * (uint64_t)f.b < out->size) {
+    out->kind = 1;
+    out->fit = f;
+    out->size = 256 + N * (uint64_t)f.b;
+  }
+  for (int d = 2; d <= 3; d++) {
+    orc_poly_fit q;
+    orc_fit_poly(v, N, d, &q);
+    if (q.valid && q.size < out->size) {
+      out->kind = d;
+      out->poly = q;
+      out->size = q.size;
+    }
+  }
+}
+
+/* ctypes helpers for the pins: 128-bit results as two 64-bit halves, the choice as kind + size */
+void orc_gram_p_parts(int j, uint64_t N, uint64_t x, uint64_t* lo, int64_t* hi) {
+  i128 v = orc_gram_p(j, N, x);
+  *lo = (uint64_t)v;
+  *hi = (int64_t)(v >> 64);
+}
+void orc_gram_norm_parts(int j, uint64_t N, uint64_t* lo, int64_t* hi) {
+  i128 v = orc_gram_norm(j, N);
+  *lo = (uint64_t)v;
+  *hi = (int64_t)(v >> 64);
+}
+int orc_choose_kind(const uint64_t* v, uint64_t N, uint64_t* size) {
+  orc_choice c;
+  orc_choose_model(v, N, &c);
+  *size = c.size;
+  return c.kind;
+}
+
+/* Total bits of one partition under the model: the §3 size term S_M + len * b with S_M = 256
+   (model 2: the chosen candidate's size, R10). */
 uint64_t orc_partition_size_bits(const uint64_t* v, uint64_t N, int model) {
+  if (model == ORC_MODEL_POLY) {
+    orc_choice c;
+    orc_choose_model(v, N, &c);
+    return c.size;
+  }
   orc_fit f;
   orc_fit_partition(v, N, model, &f);
   return 256 + N * (uint64_t)f.b;
@@ -307,8 +501,9 @@ uint64_t orc_words_for_bits(uint64_t total_bits) {
 
 /*
  * Fit every partition [starts[p], starts[p+1]) and pack the residuals (§3.3 Encoder).
- * First pass fits and sums len*b into the offsets; the second packs. Returns the padded word
- * count, or 0 when cap_words is too small (words[] is not touched then). records needs m entries.
+ * First pass fits (model 2: chooses, R10) and sums each partition's stream bits into the offsets;
+ * the second packs. Returns the padded word count, or 0 when cap_words is too small (words[] is not
+ * touched then). records needs m entries.
  */
 uint64_t orc_encode(const uint64_t* v, uint64_t n, const uint64_t* starts, uint64_t m, int model,
                     orc_record* records, uint64_t* words, uint64_t cap_words) {
@@ -319,38 +514,66 @@ uint64_t orc_encode(const uint64_t* v, uint64_t n, const uint64_t* starts, uint6
     return nw;
   }
   if (starts[0] != 0 || starts[m] != n) orc_die("bad partition bounds");
-  orc_fit* fits = (orc_fit*)malloc(sizeof(orc_fit) * m);
-  if (!fits) orc_die("oom");
+  if (model != ORC_MODEL_CONSTANT && model != ORC_MODEL_LINEAR && model != ORC_MODEL_POLY) orc_die("model");
+  orc_choice* ch = (orc_choice*)malloc(sizeof(orc_choice) * m);
+  if (!ch) orc_die("oom");
   uint64_t off = 0;
   for (uint64_t p = 0; p < m; p++) {
     uint64_t a = starts[p], e = starts[p + 1];
     if (e <= a) orc_die("empty partition");
-    orc_fit_partition(v + a, e - a, model, &fits[p]);
-    records[p].theta0 = fits[p].theta0;
-    records[p].theta1 = fits[p].theta1;
+    if (model == ORC_MODEL_POLY) {
+      orc_choose_model(v + a, e - a, &ch[p]);
+    } else {
+      memset(&ch[p], 0, sizeof(ch[p]));
+      ch[p].kind = model;
+      orc_fit_partition(v + a, e - a, model, &ch[p].fit);
+    }
     records[p].start = a;
-    records[p].word3 = make_word3(off, fits[p].b, fits[p].s, fits[p].exact);
-    off += (e - a) * (uint64_t)fits[p].b;
+    if (ch[p].kind >= 2) {
+      records[p].theta0 = 0.0;
+      records[p].theta1 = 0.0;
+      records[p].word3 = make_word3(off, ch[p].poly.b, 0, 0) | ((uint64_t)1 << 63);
+      off += 320 + (e - a) * (uint64_t)ch[p].poly.b;
+    } else {
+      records[p].theta0 = ch[p].fit.theta0;
+      records[p].theta1 = ch[p].fit.theta1;
+      records[p].word3 = make_word3(off, ch[p].fit.b, ch[p].fit.s, ch[p].fit.exact);
+      off += (e - a) * (uint64_t)ch[p].fit.b;
+    }
   }
   if (off >= ((uint64_t)1 << 48)) orc_die("stream longer than 2^48 bits");
   uint64_t nw = orc_words_for_bits(off);
   if (cap_words < nw) {
-    free(fits);
+    free(ch);
     return 0;
   }
   memset(words, 0, nw * sizeof(uint64_t));
   for (uint64_t p = 0; p < m; p++) {
-    uint64_t a = starts[p], e = starts[p + 1];
+    uint64_t a = starts[p], e = starts[p + 1], N = e - a;
     uint64_t pos = records[p].word3 & (((uint64_t)1 << 48) - 1);
-    int b = fits[p].b;
-    for (uint64_t x = 0; x < e - a; x++) {
-      int64_t r = residual_of(v[a + x], records[p].theta0, records[p].theta1, x);
-      uint64_t z = zigzag64(r);
+    int b;
+    if (ch[p].kind >= 2) {
+      const orc_poly_fit* q = &ch[p].poly;
+      put_field(words, pos, 64, (uint64_t)q->T);
+      for (int j = 1; j <= 3; j++) put_field(words, pos + 64 * (uint64_t)j, 64, (uint64_t)q->K[j]);
+      put_field(words, pos + 256, 64, (uint64_t)q->sj[1] | ((uint64_t)q->sj[2] << 8) | ((uint64_t)q->sj[3] << 16));
+      pos += 320;
+      b = q->b;
+    } else {
+      b = ch[p].fit.b;
+    }
+    for (uint64_t x = 0; x < N; x++) {
+      uint64_t pred;
+      if (ch[p].kind >= 2)
+        pred = (uint64_t)ch[p].poly.T + (uint64_t)poly_line(ch[p].poly.K, ch[p].poly.sj, ch[p].poly.S, N, x);
+      else
+        pred = (uint64_t)orc_predict(records[p].theta0, records[p].theta1, x);
+      uint64_t z = zigzag64((int64_t)(v[a + x] - pred));
       if (b < 64 && (z >> b) != 0) orc_die("residual wider than b");
       put_field(words, pos + x * (uint64_t)b, b, z);
     }
   }
-  free(fits);
+  free(ch);
   return nw;
 }
 
@@ -359,12 +582,32 @@ uint64_t orc_encode(const uint64_t* v, uint64_t n, const uint64_t* starts, uint6
 static int rec_b(const orc_record* r) { return (int)((r->word3 >> 48) & 0x7F); }
 static uint64_t rec_off(const orc_record* r) { return r->word3 & (((uint64_t)1 << 48) - 1); }
 
-/* value at local index x of partition p: floor prediction + unzigzag(bits [off + b x, +b)) */
-static uint64_t decode_one(const orc_record* r, const uint64_t* words, uint64_t x) {
+static int rec_poly(const orc_record* r) { return (int)(r->word3 >> 63); }
+
+/* Value at local index x of a partition of N values: prediction + unzigzag(bits [off + b x, +b)).
+   A polynomial partition (R10) reads T, K1..K3 and the exponent word at off, its residuals from
+   off + 320. */
+static uint64_t decode_one(const orc_record* r, const uint64_t* words, uint64_t N, uint64_t x) {
   int b = rec_b(r);
-  uint64_t z = get_field(words, rec_off(r) + x * (uint64_t)b, b);
-  int64_t pred = orc_predict(r->theta0, r->theta1, x);
-  return (uint64_t)pred + (uint64_t)unzigzag64(z);
+  uint64_t pos = rec_off(r);
+  uint64_t pred;
+  if (rec_poly(r)) {
+    int64_t K[4] = {0, 0, 0, 0};
+    int32_t sj[4] = {0, 0, 0, 0}, S = 0;
+    uint64_t T = get_field(words, pos, 64);
+    uint64_t E = get_field(words, pos + 256, 64);
+    for (int j = 1; j <= 3; j++) {
+      K[j] = (int64_t)get_field(words, pos + 64 * (uint64_t)j, 64);
+      sj[j] = (int32_t)((E >> (8 * (j - 1))) & 0xFF);
+      if (sj[j] > S) S = sj[j];
+    }
+    pred = T + (uint64_t)poly_line(K, sj, S, N, x);
+    pos += 320;
+  } else {
+    pred = (uint64_t)orc_predict(r->theta0, r->theta1, x);
+  }
+  uint64_t z = get_field(words, pos + x * (uint64_t)b, b);
+  return pred + (uint64_t)unzigzag64(z);
 }
 
 /* Range decompression = the point decode applied to every position (§3.3). out: n values. */
@@ -374,7 +617,7 @@ void orc_decode(const orc_record* records, uint64_t m, const uint64_t* words, ui
     uint64_t a = records[p].start;
     uint64_t e = p + 1 < m ? records[p + 1].start : n;
     for (uint64_t i = a; i < e; i++) {
-      uint64_t val = decode_one(&records[p], words, i - a);
+      uint64_t val = decode_one(&records[p], words, e - a, i - a);
       out[i] = dtype_bits == 32 ? (val & 0xFFFFFFFFu) : val;
     }
   }
@@ -410,7 +653,8 @@ uint64_t orc_lookup(const orc_record* records, uint64_t m, const uint64_t* words
       continue;
     }
     uint64_t p = find_partition(records, m, L, i);
-    uint64_t val = decode_one(&records[p], words, i - records[p].start);
+    uint64_t e = p + 1 < m ? records[p + 1].start : n;
+    uint64_t val = decode_one(&records[p], words, e - records[p].start, i - records[p].start);
     out[q] = dtype_bits == 32 ? (val & 0xFFFFFFFFu) : val;
   }
   return bad;
@@ -428,7 +672,7 @@ void orc_filter_sum(const orc_record* records, uint64_t m, const uint64_t* words
     uint64_t a = records[p].start;
     uint64_t e = p + 1 < m ? records[p + 1].start : n;
     for (uint64_t i = a; i < e; i++) {
-      uint64_t val = decode_one(&records[p], words, i - a);
+      uint64_t val = decode_one(&records[p], words, e - a, i - a);
       if (dtype_bits == 32) val &= 0xFFFFFFFFu;
       if (val >= lo && val <= hi) {
         count++;

@@ -558,3 +558,190 @@ def test_size_search_passes_a_tie_in_the_exponential_phase(orc):
     s = {L: orc.sample_size_bits(v, st, 32, L) for L in (4, 8, 16, 32)}
     assert s == {4: 2048, 8: 2048, 16: 1568, 32: 1312}
     assert orc.search_partition_size(v, 32, 1.0, 0)[:2] == (32, 1312)
+
+
+# ------------------------------------------------------------------ polynomial model (§3.1, §4, R10)
+
+def _poly_words(records_json):
+    import oracle
+
+    rec = np.zeros(len(records_json), dtype=oracle.RECORD_DTYPE)
+    for k, r in enumerate(records_json):
+        rec[k]["theta0"], rec[k]["theta1"], rec[k]["start"] = r["theta0"], r["theta1"], r["start"]
+        rec[k]["word3"] = (r["offset"] | (r["width"] << 48) | ((r["grid"] & 0x7F) << 55) | (r["exact"] << 62)
+                           | (r["poly"] << 63))
+    return rec
+
+
+def test_hand_packed_poly_stream_decodes(orc):
+    g = json.load(open(os.path.join(GOLDEN, "hand_packed_poly_stream.json")))
+    rec = _poly_words(g["records"])
+    words = np.array(g["words"], dtype=np.uint64)
+    assert orc.decode(rec, words, g["n"]).tolist() == g["expected"]
+    vals, bad = orc.lookup(rec, words, g["n"], [5, 2, 0, 3, 6], L=0)
+    assert vals.tolist() == [7, 489, 487, 505, 0] and bad == 1
+    cnt, tot = orc.filter_sum(rec, words, g["n"], 7, 500)
+    assert (cnt, tot) == (3, 487 + 489 + 7)
+
+
+def test_gram_polynomials_are_orthogonal_with_stated_norms(orc):
+    """p_j has degree j with leading coefficient (1, 3, 5) in x' = 2x - (N-1) (so its j-th forward
+    difference is j! * lead * 2^j), is orthogonal to 1 and to the others over x < N, and its
+    squared norm equals the closed form the fit divides by: that fixes the basis uniquely."""
+    for N in (4, 5, 7, 64, 100, 1000):
+        P = [[orc.gram_p(j, N, x) for x in range(N)] for j in (1, 2, 3)]
+        for j, lead in ((1, 1), (2, 3), (3, 5)):
+            d = P[j - 1]
+            for _ in range(j):
+                d = [b - a for a, b in zip(d, d[1:])]
+            assert set(d) == {math.factorial(j) * lead * 2 ** j}, (N, j)
+        for j in range(3):
+            assert sum(P[j]) == 0
+            for k in range(j + 1, 3):
+                assert sum(a * b for a, b in zip(P[j], P[k])) == 0, (N, j, k)
+            assert sum(a * a for a in P[j]) == orc.gram_norm(j + 1, N), (N, j)
+
+
+def _exact_ls_shape(w, degree):
+    """Least squares of degree d over x = 0..N-1 in the monomial basis, solved in exact rationals by
+    Gauss-Jordan on the normal equations; returns the fitted values minus their mean."""
+    N = len(w)
+    A = [[Fraction(sum(x ** (i + j) for x in range(N))) for j in range(degree + 1)] for i in range(degree + 1)]
+    y = [Fraction(sum(int(w[x]) * x ** i for x in range(N))) for i in range(degree + 1)]
+    M = [row + [r] for row, r in zip(A, y)]
+    n = degree + 1
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        M[c] = [v / M[c][c] for v in M[c]]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c]
+                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    coef = [M[i][n] for i in range(n)]
+    f = [sum(coef[i] * x ** i for i in range(n)) for x in range(N)]
+    mean = sum(f) / N
+    return [v - mean for v in f]
+
+
+@pytest.mark.parametrize("degree", [2, 3])
+def test_poly_coefficients_are_least_squares(orc, degree):
+    """sum_j c_j p_j(x) equals the exact rational least-squares fit (minus its mean) of the same
+    degree, up to binary64 rounding of the coefficients."""
+    g = W.rng(31)
+    for trial in range(4):
+        N = int(g.integers(64, 160))
+        x = np.arange(N)
+        w = (1 << 36) + int(g.integers(-1000, 1000)) * x + int(g.integers(-50, 50)) * x * x \
+            + int(g.integers(-3, 3)) * x ** 3 + g.integers(-(1 << 12), 1 << 12, size=N)
+        f = orc.fit_poly(w.astype(np.uint64), degree)
+        assert f["valid"] == 1 and f["degree"] == degree
+        want = _exact_ls_shape(w, degree)
+        scale = max(abs(float(v)) for v in want) + 1.0
+        for xx in range(N):
+            got = sum(f["c"][j] * orc.gram_p(j, N, xx) for j in range(1, degree + 1))
+            assert abs(got - float(want[xx])) <= 1e-9 * scale, (trial, xx)
+        if degree == 2:
+            assert f["c"][3] == 0.0 and f["K"][3] == 0
+
+
+def test_poly_intercept_is_minimax_and_width_is_the_residual_range(orc):
+    """Given the grid coefficients, T minimises the widest zigzag residual over every integer
+    intercept near it (brute force), and b is the bit length of that widest residual."""
+    g = W.rng(32)
+    for trial in range(6):
+        N = 64 + trial * 17
+        x = np.arange(N)
+        w = 5_000_000 + 300 * x - 4 * x * x + g.integers(-700, 700, size=N)
+        for degree in (2, 3):
+            f = orc.fit_poly(w.astype(np.uint64), degree)
+            assert f["valid"]
+            base = [int(w[xx]) - math.floor(sum(Fraction(f["K"][j] * orc.gram_p(j, N, xx), 1 << f["sj"][j])
+                                                 for j in (1, 2, 3)))
+                    for xx in range(N)]
+            widest = {t: max(zz(r - t) for r in base) for t in range(f["T"] - 40, f["T"] + 41)}
+            assert widest[f["T"]] == min(widest.values())
+            assert f["b"] == bitlen(widest[f["T"]])
+            assert f["size"] == 576 + N * f["b"]
+
+
+def test_exact_polynomials_compress_to_at_most_two_bits(orc):
+    """Integer quadratics and cubics are fitted up to the grid rounding: the residual range is a few
+    units, so b <= 2, and the model picks the polynomial of the data's degree (a tie between the
+    quadratic and the cubic goes to the quadratic)."""
+    for N in (64, 1000, 4096, 16384):
+        x = np.arange(N, dtype=object)
+        quad = [(1 << 40) + 1000 * int(t) - 7 * int(t) ** 2 for t in x]
+        cubic = [(1 << 40) - 1000 * int(t) + 3 * int(t) ** 2 + int(t) ** 3 // 1 for t in x]
+        for vals, degree in ((quad, 2), (cubic, 3)):
+            v = np.array(vals, dtype=np.uint64)
+            f = orc.fit_poly(v, degree)
+            assert f["valid"] and f["b"] <= 2, (N, degree, f["b"])
+            kind, size = orc.choose_model(v)
+            assert kind == degree and size == 576 + N * f["b"], (N, degree, kind)
+            assert orc.fit(v, orc.MODEL_LINEAR)["b"] > 8
+
+
+def test_poly_candidate_applicability(orc):
+    g = W.rng(33)
+    x = np.arange(20000)
+    w = (1 << 40) + 3 * x * x + g.integers(0, 100, size=x.size)
+    assert orc.fit_poly(w[:63].astype(np.uint64), 3)["valid"] == 0
+    assert orc.fit_poly(w[:64].astype(np.uint64), 3)["valid"] == 1
+    assert orc.fit_poly(w[:16384].astype(np.uint64), 3)["valid"] == 1
+    assert orc.fit_poly(w[:16385].astype(np.uint64), 3)["valid"] == 0
+    wide = np.zeros(100, dtype=np.uint64)
+    wide[50] = np.uint64(1 << 62)  # max - min = 2^62: the polynomial does not apply
+    assert orc.fit_poly(wide, 2)["valid"] == 0
+    wide[50] = np.uint64((1 << 62) - 1)
+    assert orc.fit_poly(wide, 2)["valid"] == 1
+    # every candidate rejected: the constant or linear record, as the models alone would write it
+    kind, size = orc.choose_model(w[:63].astype(np.uint64))
+    assert kind in (0, 1) and size == min(orc.partition_size_bits(w[:63], 0), orc.partition_size_bits(w[:63], 1))
+
+
+def _sine_mix(n, seed):
+    g = W.rng(seed)
+    x = np.arange(n, dtype=np.float64)
+    v = (1 << 32) + 1e6 * np.sin(x / 700.0) + 3e5 * np.sin(x / 97.0) + g.integers(-50, 50, size=n)
+    return v.astype(np.int64).astype(np.uint64)
+
+
+@pytest.mark.parametrize("L", [100, 1024, 4096])
+def test_poly_model_never_loses_to_constant_or_linear(orc, L):
+    """Per partition the polynomial model's size is at most the constant's and the linear's; a
+    partition that keeps the constant or the line has exactly the record that model writes; the
+    column round-trips through decode, lookups and filter-sum."""
+    g = W.rng(34)
+    cols = [_sine_mix(20000, 3), W.cfg1()[:20000], g.integers(0, 1 << 64, size=20000, dtype=np.uint64),
+            np.repeat(g.integers(0, 1 << 40, size=200, dtype=np.uint64), 100)]
+    for v in cols:
+        n = len(v)
+        rec, words = orc.encode_fixed(v, L, orc.MODEL_POLY)
+        rc, _ = orc.encode_fixed(v, L, orc.MODEL_CONSTANT)
+        rl, _ = orc.encode_fixed(v, L, orc.MODEL_LINEAR)
+        poly = orc.rec_poly(rec["word3"]).astype(bool)
+        for p in range(len(rec)):
+            a, e = p * L, min(n, (p + 1) * L)
+            k, size = orc.choose_model(v[a:e])
+            assert size <= min(orc.partition_size_bits(v[a:e], 0), orc.partition_size_bits(v[a:e], 1))
+            assert bool(poly[p]) == (k >= 2)
+            if k < 2:
+                ref = (rc if k == 0 else rl)[p]
+                assert rec[p]["theta0"] == ref["theta0"] and rec[p]["theta1"] == ref["theta1"]
+                assert int(rec[p]["word3"]) >> 48 == int(ref["word3"]) >> 48
+            else:
+                assert rec[p]["theta0"] == 0.0 and rec[p]["theta1"] == 0.0 and orc.rec_exact(rec[p]["word3"]) == 0
+        assert (orc.decode(rec, words, n) == v).all()
+        idx = g.integers(0, n, size=500)
+        assert (orc.lookup(rec, words, n, idx, L=L)[0] == v[idx]).all()
+        lo, hi = np.sort(v)[n // 3], np.sort(v)[2 * n // 3]
+        want = [int(t) for t in v if lo <= t <= hi]
+        assert orc.filter_sum(rec, words, n, int(lo), int(hi)) == (len(want), sum(want) % (1 << 128))
+    # the sine mixture is where the polynomials pay: fewer bytes than the line at short partitions
+    v = cols[0]
+    rp, wp = orc.encode_fixed(v, L, orc.MODEL_POLY)
+    rl, wl = orc.encode_fixed(v, L, orc.MODEL_LINEAR)
+    assert orc.compressed_bytes(rp, wp) <= orc.compressed_bytes(rl, wl)
+    if L == 100:
+        assert orc.compressed_bytes(rp, wp) < 0.85 * orc.compressed_bytes(rl, wl)
