@@ -3,7 +3,8 @@
  *
  * LeCo (Liu, Zeng & Zhang, "LeCo: Lightweight Compression via Learning Serial Correlations")
  * compresses an integer column by splitting it into partitions (§3.2), fitting one regression
- * model per partition (§3.1: constant = FOR, or linear) and bit-packing the residuals ("deltas")
+ * model per partition (§3.1: constant = FOR, linear, or a polynomial of degree <= 3 chosen per
+ * partition) and bit-packing the residuals ("deltas")
  * at a fixed width per partition (§3.3). This library runs encode, full decode, range decode,
  * batched point lookups and a fused filter + sum scan on one CUDA GPU (sm_103a).
  *
@@ -24,7 +25,7 @@
  * Stored format (§3.3 storage format, with this library's readings):
  *  - One 32-byte record per partition: {double theta0, double theta1, uint64 start, uint64 word3}
  *    with word3 = bit offset (bits 0..47) | width b (48..54) | grid exponent s (55..61, two's
- *    complement) | exact flag (62) | 0 (63).
+ *    complement) | exact flag (62) | polynomial flag (63).
  *  - Residuals: zigzag-coded, b bits each, packed LSB-first into one stream of little-endian
  *    64-bit words shared by all partitions; partition p starts at its bit offset, offsets dense.
  *    The stream carries at least two zero padding words and is a multiple of 16 bytes.
@@ -34,6 +35,13 @@
  *    decoder). When the exact flag is set the encoder guarantees that this equals
  *    (A + B i') >> s with the integers A = theta0 * 2^s, B = theta1 * 2^s (s < 0: no shift), which
  *    is what the device evaluates.
+ *  - Polynomial partitions (flag 63; LECO_MODEL_POLY): theta0 = theta1 = 0, exact = 0, s = 0, and
+ *    the partition's bits start with five 64-bit words T, K1, K2, K3 (two's complement) and
+ *    E = s1 | s2 << 8 | s3 << 16 (each s_j in 0..62), followed by its residuals (residual i' at
+ *    offset + 320 + b i'). With N the partition length, x' = 2 i' - (N - 1) and the Gram
+ *    polynomials p1 = x', p2 = 3 x'^2 - (N^2 - 1), p3 = 5 x'^3 - (3 N^2 - 7) x', the prediction is
+ *    pred(i') = T + floor(sum_j K_j p_j(i') 2^-s_j) mod 2^64, evaluated exactly in integers.
+ *    A polynomial partition holds 64 .. 16384 values.
  */
 #ifndef LECO_H
 #define LECO_H
@@ -61,8 +69,12 @@ typedef enum {
 
 typedef enum { LECO_U32 = 0, LECO_U64 = 1 } leco_dtype;
 
-/* §3.1 model family members built here: constant (FOR, §2) and linear. */
-typedef enum { LECO_MODEL_CONSTANT = 0, LECO_MODEL_LINEAR = 1 } leco_model;
+/* §3.1 model family members built here: constant (FOR, §2), linear, and the polynomial model:
+ * each partition takes whichever of constant, linear, quadratic and cubic (least squares on the
+ * Gram polynomials, coefficients on binary grids) gives it the smallest exact size (record and
+ * coefficient bits + len * b; ties to the simpler model). Variable partitioning and the
+ * partition-size search size partitions with the linear model under LECO_MODEL_POLY. */
+typedef enum { LECO_MODEL_CONSTANT = 0, LECO_MODEL_LINEAR = 1, LECO_MODEL_POLY = 2 } leco_model;
 
 typedef enum { LECO_PART_FIXED = 0, LECO_PART_VAR = 1, LECO_PART_AUTO = 2 } leco_part_kind;
 
@@ -124,7 +136,7 @@ uint32_t leco_version(void);
 /* Encode (§3: Partitioner -> Regressor -> Encoder)
  *
  * d_values: n values of `dtype` (4 or 8 bytes each, contiguous) on the device, caller-owned, read
- * only. policy: fixed or variable partitions. model: constant or linear. On success *out receives
+ * only. policy: fixed, variable or auto partitions. model: constant, linear or polynomial. On success *out receives
  * a new column (free with leco_column_free). The call synchronizes `stream` once (to size the
  * residual stream) and returns with the column's encode enqueued on `stream`.
  * Errors: INVALID_ARG (NULL out, NULL d_values with n > 0, part_size out of range, tau outside
@@ -160,8 +172,9 @@ leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype
  * device looks up that array's device address (make it before any stream capture). All calls on
  * a device share the array, so calls whose GPU work overlaps (e.g. on different streams) race;
  * nothing of it needs clearing between calls. The call synchronizes `stream` once to size the
- * stream; INVALID_ARG when words_cap < *nwords_out (nothing packed then), CUDA on a runtime
- * failure. No cudaMalloc, cudaFree or allocating library routine is called. */
+ * stream; INVALID_ARG when words_cap < *nwords_out (nothing packed then) or for LECO_MODEL_POLY
+ * (constant and linear only), CUDA on a runtime failure. No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
 leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t n, leco_dtype dtype, uint32_t L,
                                       leco_model model, void* d_records, void* d_words,
                                       uint64_t words_cap, uint64_t* nwords_out,

@@ -27,6 +27,7 @@ struct leco_column {
   leco::Aux* aux = nullptr;
   uint64_t* starts = nullptr;  // variable only
   leco::TileDesc* tiles = nullptr;   // scan tile descriptors
+  leco::PolyAux* poly = nullptr;     // polynomial decode table (LECO_MODEL_POLY columns)
   uint32_t* status = nullptr;
   uint32_t max_b = 0;          // widest partition
   uint32_t stage_bytes = 0;    // shared-memory bytes per staged scan tile
@@ -58,6 +59,7 @@ inline ColumnView view_of(const leco_column* c) {
   v.words = c->words;
   v.starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
   v.tiles = c->tiles;
+  v.poly = c->poly;
   v.stage_bytes = c->stage_bytes;
   v.status = c->status;
   return v;

@@ -342,5 +342,258 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
   return R;
 }
 
+// ------------------------------------------------------------------------------ polynomial model
+//
+// §3.1 names polynomial terms among the model family; §4 chooses per partition among constant,
+// linear and polynomials up to degree three. This fit follows one exact reading of that choice:
+//  1. one pass: min, max, and S_j = sum p_j(x) w_x (j = 1..3) over the Gram polynomials of the
+//     partition, p1 = x', p2 = 3x'^2 - (N^2-1), p3 = 5x'^3 - (3N^2-7)x' with x' = 2x - (N-1); the p_j
+//     are orthogonal to 1 and to each other over x < N, so S_j / |p_j|^2 is the least-squares
+//     coefficient c_j of p_j for any degree that includes it (and S_1 is the line's moment);
+//  2. one lane solves the constant and linear parameters (as for those models) and, when
+//     64 <= N <= 16384 and max - min < 2^62, the quadratic and cubic grids: c_j as one binary64
+//     division of the two integers (each converted from sign and magnitude), s_j = min(62, 61 - e_j)
+//     with |c_j| < 2^e_j, S = max s_j capped so that every K_j 2^(S - s_j) p_j stays below 2^124,
+//     K_j = round(c_j 2^s_j) half up;
+//  3. a second pass: the linear residual range (or the fallback's widest zigzag residual) and, per
+//     polynomial, the range of w_x - floor(F(x) / 2^S) (F = sum K_j 2^(S - s_j) p_j(x), exact);
+//  4. one lane sizes the four candidates (256 + N b for constant and linear, 576 + N b for the
+//     polynomials, whose minimax intercept T and width follow from their range as for the line) and
+//     keeps the smallest, ties to the earlier.
+
+// headroom (bits) of K_j 2^(S - s_j) p_j below 2^124: |K_j| <= 2^61, |p_j| < 2^14, 2^29, 2^43
+__host__ __device__ constexpr int32_t poly_headroom(int j) { return j == 1 ? 49 : (j == 2 ? 34 : 20); }
+
+// |p_j|^2 over N points: N(N^2-1)/3, 4N(N^2-1)(N^2-4)/5, 4N(N^2-1)(N^2-4)(N^2-9)/7
+__device__ __forceinline__ i128 gram_norm(int j, uint32_t N) {
+  const i128 n = N, n2 = n * n;
+  const i128 base = n * (n2 - 1);
+  if (j == 1) return floordiv_i128(base, 3);
+  if (j == 2) return floordiv_i128(4 * base * (n2 - 4), 5);
+  return floordiv_i128(4 * base * (n2 - 4) * (n2 - 9), 7);
+}
+
+// binary64 from sign and magnitude: +-(double(hi) 2^64 + double(lo)), each step rounded to nearest
+__device__ __forceinline__ double i128_to_f64(i128 v) {
+  const u128 mag = v < 0 ? (u128)0 - (u128)v : (u128)v;
+  const double d = __dadd_rn(__dmul_rn(__ull2double_rn((uint64_t)(mag >> 64)), 18446744073709551616.0),
+                             __ull2double_rn((uint64_t)mag));
+  return v < 0 ? -d : d;
+}
+
+// F(x) = sum_j K_j 2^(S - s_j) p_j(x) expanded in powers of the local index x (all exact):
+// p1 = 2x + (1-N), p2 = 12x^2 + (12-12N)x + (2N^2-6N+4),
+// p3 = 40x^3 + (60-60N)x^2 + (24N^2-60N+44)x + (-2N^3+12N^2-22N+12).
+__host__ __device__ __forceinline__ PolyAux poly_aux_from(const int64_t* K, const int32_t* sj, int32_t S, uint32_t N) {
+  const i128 n = N;
+  const i128 G1 = (i128)K[0] * ((i128)1 << (S - sj[0]));
+  const i128 G2 = (i128)K[1] * ((i128)1 << (S - sj[1]));
+  const i128 G3 = (i128)K[2] * ((i128)1 << (S - sj[2]));
+  i128 a[4];
+  a[3] = 40 * G3;
+  a[2] = 12 * G2 + (60 - 60 * n) * G3;
+  a[1] = 2 * G1 + (12 - 12 * n) * G2 + (24 * n * n - 60 * n + 44) * G3;
+  a[0] = (1 - n) * G1 + (2 * n * n - 6 * n + 4) * G2 + (-2 * n * n * n + 12 * n * n - 22 * n + 12) * G3;
+  PolyAux r;
+  for (int k = 0; k < 4; k++) {
+    r.a[k][0] = (uint64_t)(u128)a[k];
+    r.a[k][1] = (uint64_t)((u128)a[k] >> 64);
+  }
+  return r;
+}
+
+__device__ __forceinline__ i128 poly_horner(const PolyAux& q, uint64_t x) {
+  const u128 X = x;
+  u128 F = ((u128)q.a[3][1] << 64) | q.a[3][0];
+  F = F * X + (((u128)q.a[2][1] << 64) | q.a[2][0]);
+  F = F * X + (((u128)q.a[1][1] << 64) | q.a[1][0]);
+  F = F * X + (((u128)q.a[0][1] << 64) | q.a[0][0]);
+  return (i128)F;
+}
+
+// one polynomial candidate's grid (lane 0 of the fitting warp)
+struct PolyGrid {
+  int64_t K[3];
+  int32_t sj[3];
+  int32_t S;
+  int32_t valid;
+};
+
+__device__ PolyGrid poly_grid(const i128* Sm, uint32_t N, int degree) {
+  PolyGrid g;
+  g.valid = 0;
+  g.S = 0;
+  double c[3] = {0.0, 0.0, 0.0};
+  int32_t cap = 1 << 30;
+  for (int j = 0; j < 3; j++) {
+    g.K[j] = 0;
+    g.sj[j] = 0;
+  }
+  for (int j = 0; j < degree; j++) {
+    c[j] = __ddiv_rn(i128_to_f64(Sm[j]), i128_to_f64(gram_norm(j + 1, N)));
+    if (c[j] != 0.0) {
+      int e;
+      frexp(c[j], &e);  // |c| < 2^e
+      int32_t sj = 61 - e;
+      if (sj > 62) sj = 62;
+      if (sj < 0) return g;
+      g.sj[j] = sj;
+      g.S = max(g.S, sj);
+      cap = min(cap, sj + poly_headroom(j + 1));
+    }
+  }
+  g.S = min(g.S, cap);
+  for (int j = 0; j < degree; j++) {
+    g.sj[j] = min(g.sj[j], g.S);
+    const double y = __dmul_rn(c[j], pow2(g.sj[j]));  // exact: a power-of-two scale
+    const double f = floor(y);
+    g.K[j] = __double2ll_rz(f) + (__dsub_rn(y, f) >= 0.5 ? 1 : 0);
+  }
+  g.valid = 1;
+  return g;
+}
+
+// What the polynomial model chose for one partition: kind 0 constant, 1 linear (R: the record's
+// theta, s and b exactly as those models write them), 2 quadratic, 3 cubic (pc: its block).
+struct FitChoice {
+  FitResult R;
+  PolyCoef pc;
+  uint32_t kind;
+  uint32_t b;
+};
+
+__device__ __forceinline__ int64_t poly_value_at(const uint32_t* v32, const uint64_t* v64, bool u32, uint32_t x) {
+  return u32 ? (int64_t)__ldg(v32 + x) : (int64_t)__ldg(v64 + x);
+}
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v) { return __shfl_sync(0xffffffffu, (unsigned long long)v, 0); }
+
+// The polynomial model's fit of [a, a+N) by one warp (lane = rank); the result in every lane.
+__device__ FitChoice fit_choose_warp(const void* __restrict__ values, int dtype, uint64_t a, uint32_t N, uint32_t lane) {
+  const bool u32 = dtype == LECO_U32;
+  const uint32_t* v32 = static_cast<const uint32_t*>(values) + a;
+  const uint64_t* v64 = static_cast<const uint64_t*>(values) + a;
+  const bool poly_len = N >= kPolyMinLen && N <= kPolyMaxLen;
+
+  // pass 1
+  int64_t mx = INT64_MIN, mn = INT64_MAX;
+  i128 Sm[3] = {0, 0, 0};
+  const int64_t nm1 = (int64_t)N - 1;
+  const int64_t n2m1 = (int64_t)N * N - 1, c3 = 3 * (int64_t)N * N - 7;
+  for (uint32_t x = lane; x < N; x += 32) {
+    const int64_t w = poly_value_at(v32, v64, u32, x);
+    mx = max(mx, w);
+    mn = min(mn, w);
+    const int64_t xp = 2 * (int64_t)x - nm1;
+    Sm[0] += (i128)xp * w;
+    if (poly_len) {
+      const int64_t xp2 = xp * xp;
+      Sm[1] += (i128)(3 * xp2 - n2m1) * w;
+      Sm[2] += (i128)((5 * xp2 - c3) * xp) * w;
+    }
+  }
+  for (int j = 0; j < 3; j++) Sm[j] = warp_sum_i128(Sm[j]);
+  mx = warp_max_i64(mx);
+  mn = warp_min_i64(mn);
+
+  // solve (lane 0), then broadcast
+  FitParams PC, PL;
+  PolyGrid G[2];
+  if (lane == 0) {
+    PC = solve_params(Sm[0], mx, mn, N, false);
+    PL = solve_params(Sm[0], mx, mn, N, N >= 2);
+    const bool elig = poly_len && (i128)mx - (i128)mn < ((i128)1 << 62);
+    G[0].valid = G[1].valid = 0;
+    if (elig) {
+      G[0] = poly_grid(Sm, N, 2);
+      G[1] = poly_grid(Sm, N, 3);
+    }
+  }
+  PL.B = (int64_t)shfl_u64((uint64_t)PL.B);
+  PL.fb_shift = (int64_t)shfl_u64((uint64_t)PL.fb_shift);
+  PL.s = __shfl_sync(0xffffffffu, PL.s, 0);
+  PL.fallback = __shfl_sync(0xffffffffu, PL.fallback, 0);
+  PolyAux Q[2];
+  int valid[2];
+  for (int d = 0; d < 2; d++) {
+    valid[d] = __shfl_sync(0xffffffffu, G[d].valid, 0);
+    if (valid[d]) {
+      if (lane == 0) Q[d] = poly_aux_from(G[d].K, G[d].sj, G[d].S, N);
+      for (int k = 0; k < 4; k++) {
+        Q[d].a[k][0] = shfl_u64(Q[d].a[k][0]);
+        Q[d].a[k][1] = shfl_u64(Q[d].a[k][1]);
+      }
+      G[d].S = __shfl_sync(0xffffffffu, G[d].S, 0);
+    }
+  }
+
+  // pass 2
+  int64_t lo = INT64_MAX, hi = INT64_MIN;
+  uint64_t zmax = 0;
+  int64_t plo[2] = {INT64_MAX, INT64_MAX}, phi[2] = {INT64_MIN, INT64_MIN};
+  int bad[2] = {0, 0};
+  for (uint32_t x = lane; x < N; x += 32) {
+    const int64_t w = poly_value_at(v32, v64, u32, x);
+    if (PL.fallback) {
+      zmax = max(zmax, zz_encode((int64_t)((uint64_t)w - (uint64_t)PL.fb_shift)));
+    } else {
+      const uint64_t F = (uint64_t)PL.B * x;
+      const int64_t r = w - (PL.s >= 0 ? ((int64_t)F >> PL.s) : (int64_t)(F << (-PL.s)));
+      lo = min(lo, r);
+      hi = max(hi, r);
+    }
+    for (int d = 0; d < 2; d++) {
+      if (!valid[d]) continue;
+      const i128 r = (i128)w - (poly_horner(Q[d], x) >> G[d].S);
+      if (r > (i128)INT64_MAX || r < (i128)INT64_MIN) {
+        bad[d] = 1;
+      } else {
+        plo[d] = min(plo[d], (int64_t)r);
+        phi[d] = max(phi[d], (int64_t)r);
+      }
+    }
+  }
+  lo = warp_min_i64(lo);
+  hi = warp_max_i64(hi);
+  zmax = warp_max_u64(zmax);
+  for (int d = 0; d < 2; d++) {
+    plo[d] = warp_min_i64(plo[d]);
+    phi[d] = warp_max_i64(phi[d]);
+    bad[d] = __any_sync(0xffffffffu, bad[d]);
+  }
+
+  // size the candidates (lane 0), then broadcast
+  FitChoice C;
+  if (lane == 0) {
+    C.R = finish_fit(PC, mn, mx, zmax);  // a constant fallback implies the linear one: same zmax
+    C.kind = 0;
+    C.b = C.R.b;
+    uint64_t best = kSmBits + (uint64_t)N * C.R.b;
+    const FitResult RL = finish_fit(PL, lo, hi, zmax);
+    if (kSmBits + (uint64_t)N * RL.b < best) {
+      best = kSmBits + (uint64_t)N * RL.b;
+      C.R = RL;
+      C.kind = 1;
+      C.b = RL.b;
+    }
+    for (int d = 0; d < 2; d++) {
+      if (!valid[d] || bad[d]) continue;
+      const i128 t = (i128)plo[d] + (((i128)phi[d] - (i128)plo[d] + 1) / 2);
+      const uint64_t z = max(zz_encode((int64_t)((i128)plo[d] - t)), zz_encode((int64_t)((i128)phi[d] - t)));
+      const uint32_t b = (uint32_t)bitlen_u64(z);
+      const uint64_t size = kSmBits + kPolyBlockBits + (uint64_t)N * b;
+      if (size < best) {
+        best = size;
+        C.kind = 2 + d;
+        C.b = b;
+        C.pc.T = (int64_t)t;
+        for (int j = 0; j < 3; j++) C.pc.K[j] = G[d].K[j];
+        C.pc.E = (uint64_t)G[d].sj[0] | ((uint64_t)G[d].sj[1] << 8) | ((uint64_t)G[d].sj[2] << 16);
+      }
+    }
+  }
+  return C;  // meaningful in lane 0 (the only lane that writes the partition's outputs)
+}
+
 }  // namespace
 }  // namespace leco

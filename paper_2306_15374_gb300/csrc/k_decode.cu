@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kBlock)
         atomicOr(c.status, kStatIndexRange);
         continue;
       }
-      const int64_t pred = predict_aux(a[u], c.rec, p[u], i[u] - a[u].start);
+      const int64_t pred = predict_aux(a[u], c.rec, c.poly, p[u], i[u] - a[u].start);
       out[q] = (T)((uint64_t)pred + (uint64_t)zz_decode(z[u]));
     }
   }
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kBlock)
     const uint64_t x = i - a.start;
     const uint32_t b = w3_b(a.word3);
     const uint64_t z = read_field(c.words, w3_off(a.word3) + x * b, b);
-    const uint64_t v = (uint64_t)predict_aux(a, c.rec, p, x) + (uint64_t)zz_decode(z);
+    const uint64_t v = (uint64_t)predict_aux(a, c.rec, c.poly, p, x) + (uint64_t)zz_decode(z);
     out[q] = c.dtype == LECO_U32 ? (v & 0xFFFFFFFFull) : v;
   }
 }

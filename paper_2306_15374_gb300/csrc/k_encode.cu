@@ -162,6 +162,39 @@ __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
   }
 }
 
+// The polynomial model: one warp per partition chooses among constant, linear, quadratic and
+// cubic by exact size (fit_choose_warp); a polynomial partition's stream bits include its block.
+__global__ void __launch_bounds__(kFitBlock)
+    k_fit_poly(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
+               uint32_t L, uint64_t m, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
+               PolyCoef* __restrict__ pcoef, uint32_t* __restrict__ max_b) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
+  for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < m; p += nw) {
+    const uint64_t a = part_begin(starts, L, n, p);
+    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
+    const FitChoice C = fit_choose_warp(values, dtype, a, N, lane);
+    if (lane == 0) {
+      Record r;
+      r.start = a;
+      if (C.kind >= 2) {
+        r.theta0 = 0.0;
+        r.theta1 = 0.0;
+        r.word3 = make_w3(0, C.b, 0, 0) | kPolyFlag;
+        pcoef[p] = C.pc;
+        lenbits[p] = kPolyBlockBits + (uint64_t)N * C.b;
+      } else {
+        r.theta0 = C.R.theta0;
+        r.theta1 = C.R.theta1;
+        r.word3 = make_w3(0, C.R.b, C.R.s, 1);
+        lenbits[p] = (uint64_t)N * C.R.b;
+      }
+      rec[p] = r;
+      if (C.b) atomicMax(max_b, C.b);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------ exclusive scan
 
 constexpr int kPrefixBlock = 256;
@@ -300,12 +333,33 @@ __device__ Aux aux_of(const Record& r, uint64_t N) {
   }
 }
 
-__global__ void k_build_aux(const Record* __restrict__ rec, uint64_t m, uint64_t n, Aux* __restrict__ aux) {
+// decode-table entry and polynomial table row of a polynomial partition (block pc, N values)
+__device__ Aux poly_entry(const Record& r, const PolyCoef& pc, uint32_t N, PolyAux* row) {
+  int32_t sj[3], S = 0;
+  for (int j = 0; j < 3; j++) {
+    sj[j] = (int32_t)((pc.E >> (8 * j)) & 0xFF);
+    S = max(S, sj[j]);
+  }
+  *row = poly_aux_from(pc.K, sj, S, N);
+  Aux a;
+  a.A = pc.T;
+  a.B = 0;
+  a.start = r.start;
+  a.word3 = make_w3(w3_off(r.word3) + kPolyBlockBits, w3_b(r.word3), S, 0) | kPolyFlag;
+  return a;
+}
+
+__global__ void k_build_aux(const Record* __restrict__ rec, const PolyCoef* __restrict__ pcoef, uint64_t m,
+                            uint64_t n, Aux* __restrict__ aux, PolyAux* __restrict__ poly) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const Record r = rec[p];
     const uint64_t e = p + 1 < m ? rec[p + 1].start : n;
-    aux[p] = aux_of(r, e > r.start ? e - r.start : 0);
+    const uint64_t N = e > r.start ? e - r.start : 0;
+    if (w3_poly(r.word3) && pcoef && poly)
+      aux[p] = poly_entry(r, pcoef[p], (uint32_t)N, poly + p);
+    else
+      aux[p] = aux_of(r, N);
   }
 }
 
@@ -325,36 +379,54 @@ constexpr uint32_t kPackSmem32 = kZzOffset32 + kStageData;
 // column's values (up to 4096 of them) leave room for their residuals after them
 __device__ __forceinline__ uint32_t pack_stage_cap(int dtype) { return dtype == LECO_U32 ? kStageData / 2 : kStageData; }
 
-__device__ __forceinline__ uint64_t residual_at(const Record* __restrict__ rec, const Aux& a, uint64_t p, uint32_t x,
-                                                uint64_t v) {
-  return zz_encode((int64_t)(v - (uint64_t)predict_aux(a, rec, p, x)));
+__device__ __forceinline__ uint64_t residual_at(const Record* __restrict__ rec, const PolyAux* __restrict__ poly,
+                                                const Aux& a, uint64_t p, uint32_t x, uint64_t v) {
+  return zz_encode((int64_t)(v - (uint64_t)predict_aux(a, rec, poly, p, x)));
+}
+
+// contribution of a 64-bit field at bit f to the output word starting at bit wb
+__device__ __forceinline__ uint64_t place64(uint64_t z, uint64_t f, uint64_t wb) {
+  if (f >= wb + 64 || f + 64 <= wb) return 0;
+  return f >= wb ? z << (uint32_t)(f - wb) : z >> (uint32_t)(wb - f);
 }
 
 __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned char* st, unsigned char* ring,
                                                const Record* __restrict__ rec, const Aux* __restrict__ aux,
+                                               const PolyCoef* __restrict__ pcoef, const PolyAux* __restrict__ poly,
                                                uint64_t p, uint64_t* __restrict__ words) {
   const Aux a = aux[p];
   const uint32_t b = w3_b(a.word3);
-  if (b) {
-    const uint64_t off = w3_off(a.word3), endb = off + (uint64_t)s.N * b;
+  const bool pl = w3_poly(a.word3) != 0;
+  const uint64_t off = w3_off(a.word3), endb = off + (uint64_t)s.N * b;
+  const uint64_t off0 = pl ? off - kPolyBlockBits : off;  // first bit of the partition (its block)
+  if (endb > off0) {
     // phase 1: residuals into shared memory (staged partitions only; others recompute per field)
     uint64_t* zs = nullptr;
-    if (st) {
+    if (st && b) {
       zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32)
                                : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
       for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
-        zs[x] = residual_at(rec, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
+        zs[x] = residual_at(rec, poly, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
       __syncthreads();
     }
-    // phase 2: output words
-    for (uint64_t w = (off >> 6) + threadIdx.x; w <= ((endb - 1) >> 6); w += blockDim.x) {
+    // phase 2: output words of [off0, endb): the polynomial block's five words, then the fields
+    for (uint64_t w = (off0 >> 6) + threadIdx.x; w <= ((endb - 1) >> 6); w += blockDim.x) {
       const uint64_t wb = w << 6;
-      const uint64_t lo = wb > off ? wb : off, hi = wb + 64 < endb ? wb + 64 : endb;
-      uint32_t x = (uint32_t)(lo - off) / b;  // first field overlapping the word (< 2^30 bits in)
+      const uint64_t lo = wb > off0 ? wb : off0, hi = wb + 64 < endb ? wb + 64 : endb;
       uint64_t acc = 0;
-      for (uint64_t f = off + (uint64_t)x * b; f < hi; f += b, x++) {
-        const uint64_t z = zs ? zs[x] : residual_at(rec, a, p, x, load_value(s.values, s.dtype, s.a + x));
-        acc |= f >= wb ? z << (uint32_t)(f - wb) : z >> (uint32_t)(wb - f);
+      if (pl && lo < off) {
+        const PolyCoef& pc = pcoef[p];
+        acc |= place64((uint64_t)pc.T, off0, wb) | place64((uint64_t)pc.K[0], off0 + 64, wb) |
+               place64((uint64_t)pc.K[1], off0 + 128, wb) | place64((uint64_t)pc.K[2], off0 + 192, wb) |
+               place64(pc.E, off0 + 256, wb);
+      }
+      if (b && hi > off) {
+        const uint64_t l2 = lo > off ? lo : off;
+        uint32_t x = (uint32_t)(l2 - off) / b;  // first field overlapping the word (< 2^30 bits in)
+        for (uint64_t f = off + (uint64_t)x * b; f < hi; f += b, x++) {
+          const uint64_t z = zs ? zs[x] : residual_at(rec, poly, a, p, x, load_value(s.values, s.dtype, s.a + x));
+          acc |= f >= wb ? z << (uint32_t)(f - wb) : z >> (uint32_t)(wb - f);
+        }
       }
       if (lo == wb && hi == wb + 64)
         words[w] = acc;
@@ -369,8 +441,8 @@ constexpr int kPackBlock = 128;
 
 __global__ void __launch_bounds__(kPackBlock)
     k_pack(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
-           const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t* __restrict__ words,
-           uint32_t* __restrict__ err) {
+           const Aux* __restrict__ aux, const PolyCoef* __restrict__ pcoef, const PolyAux* __restrict__ poly,
+           uint64_t m, uint64_t n, uint64_t* __restrict__ words, uint32_t* __restrict__ err) {
   __shared__ __align__(8) uint64_t full[1];
   extern __shared__ __align__(128) unsigned char ring[];
   auto get = [&](uint64_t p) {
@@ -383,9 +455,14 @@ __global__ void __launch_bounds__(kPackBlock)
     return s;
   };
   auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
-    pack_partition(s, st, ring, rec, aux, p, words);
+    pack_partition(s, st, ring, rec, aux, pcoef, poly, p, words);
   };
   for_each_staged<1>(m, pack_stage_cap(dtype), get, body, ring, full, err);
+}
+
+// first stream bit of a partition: its residuals, or the block ahead of them for a polynomial one
+__device__ __forceinline__ uint64_t part_first_bit(const Aux& a) {
+  return w3_off(a.word3) - (w3_poly(a.word3) ? kPolyBlockBits : 0);
 }
 
 // Zero the words that packing OR-s into: each word holding a partition's first bit, and the words
@@ -396,7 +473,7 @@ __global__ void k_zero_bounds(const Aux* __restrict__ aux, uint64_t m, uint64_t 
   const uint64_t tail = total_bits >> 6;
   const uint64_t count = m + (nwords > tail ? nwords - tail : 0);
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t w = i < m ? (w3_off(aux[i].word3) >> 6) : tail + (i - m);
+    const uint64_t w = i < m ? (part_first_bit(aux[i]) >> 6) : tail + (i - m);
     if (w < nwords) words[w] = 0;
   }
 }
@@ -475,7 +552,7 @@ __global__ void __launch_bounds__(kPackBlock)
   auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
     const uint32_t c = find_col(part_base, ncols, p);
     const uint64_t p0 = part_base[c];
-    pack_partition(s, st, ring, rec + p0, aux + p0, p - p0, words + word_base[c]);
+    pack_partition(s, st, ring, rec + p0, aux + p0, nullptr, nullptr, p - p0, words + word_base[c]);
   };
   for_each_staged<1>(P, pack_stage_cap(dtype), get, body, ring, full, err);
 }
@@ -487,7 +564,7 @@ __global__ void k_zero_bounds_multi(const Aux* __restrict__ aux, const uint64_t*
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P; p += stride) {
     const uint32_t c = find_col(part_base, ncols, p);
-    words[word_base[c] + (w3_off(aux[p].word3) >> 6)] = 0;
+    words[word_base[c] + (part_first_bit(aux[p]) >> 6)] = 0;
   }
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < ncols; c += stride)
     for (uint64_t w = word_base[c] + (col_bits[c] >> 6); w < word_base[c + 1]; w++) words[w] = 0;
@@ -525,11 +602,19 @@ int resident_grid(K kern, int block, uint64_t work, uint32_t smem) {
 }
 
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
-                       uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
+                       uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits, PolyCoef* pcoef,
                        uint32_t* max_b, uint32_t* err, cudaStream_t st) {
   (void)err;  // the fit waits on nothing
+  if (model == LECO_MODEL_POLY && !pcoef) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess || m == 0) return e;
+  if (model == LECO_MODEL_POLY) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fit_poly, kFitBlock, 0) != cudaSuccess || nb < 1) nb = 1;
+    const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, nb);
+    k_fit_poly<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, rec, lenbits, pcoef, max_b);
+    return cudaGetLastError();
+  }
   const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
   k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
   return cudaGetLastError();
@@ -563,17 +648,17 @@ cudaError_t launch_offsets(Record* rec, const uint64_t* lenbits, uint64_t m, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_aux(const Record* rec, uint64_t m, uint64_t n, Aux* aux, uint32_t* status,
-                             cudaStream_t st) {
+cudaError_t launch_build_aux(const Record* rec, const PolyCoef* pcoef, uint64_t m, uint64_t n, Aux* aux,
+                             PolyAux* poly, uint32_t* status, cudaStream_t st) {
   (void)status;
   if (m == 0) return cudaSuccess;
-  k_build_aux<<<grid_for(m, 256, 8), 256, 0, st>>>(rec, m, n, aux);
+  k_build_aux<<<grid_for(m, 256, 8), 256, 0, st>>>(rec, pcoef, m, n, aux, poly);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux,
-                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words, uint64_t nwords, uint32_t* err,
-                        cudaStream_t st) {
+cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux, const PolyCoef* pcoef,
+                        const PolyAux* poly, uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
+                        uint64_t nwords, uint32_t* err, cudaStream_t st) {
   if (nwords == 0) return cudaSuccess;
   const uint64_t tail = total_bits >> 6;
   k_zero_bounds<<<grid_for(m + (nwords > tail ? nwords - tail : 0), 256, 8), 256, 0, st>>>(aux, m, total_bits, nwords,
@@ -581,8 +666,8 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || m == 0) return e;
   const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
-  k_pack<<<resident_grid(k_pack, kPackBlock, m, smem), kPackBlock, smem, st>>>(values, dtype, rec, aux, m, n, words,
-                                                                               err);
+  k_pack<<<resident_grid(k_pack, kPackBlock, m, smem), kPackBlock, smem, st>>>(values, dtype, rec, aux, pcoef, poly,
+                                                                               m, n, words, err);
   return cudaGetLastError();
 }
 

@@ -222,7 +222,7 @@ __device__ __forceinline__ uint64_t value_at(const ScanArgs& g, const uint32_t* 
   const uint32_t b = w3_b(a.word3);
   const uint32_t bit = (uint32_t)(w3_off(a.word3) + (uint64_t)b * x - mt.bit_base);
   const uint64_t z = b <= 32 ? (uint64_t)field32(words, bit, (uint32_t)low_mask(b)) : field64(words, bit, low_mask(b));
-  return (uint64_t)predict_aux(a, c.rec, q, x) + (uint64_t)zz_decode(z);
+  return (uint64_t)predict_aux(a, c.rec, c.poly, q, x) + (uint64_t)zz_decode(z);
 }
 
 // Tight loop over ng whole 32-value groups of one exact partition (the common case). Lane j

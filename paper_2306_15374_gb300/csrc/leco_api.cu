@@ -57,7 +57,8 @@ leco_status alloc_meta(leco_column* c, cudaStream_t st) {
   const uint64_t rec_b = align256(32 * (c->m ? c->m : 1));
   const uint64_t starts_b = c->kind == LECO_PART_VAR ? align256(8 * (c->m + 1)) : 0;
   const uint64_t tiles_b = align256(sizeof(TileDesc) * (scan_tiles(c->n) + 1));
-  c->meta_bytes = 2 * rec_b + starts_b + tiles_b + 256;
+  const uint64_t poly_b = c->model == LECO_MODEL_POLY ? align256(sizeof(PolyAux) * (c->m ? c->m : 1)) : 0;
+  c->meta_bytes = 2 * rec_b + starts_b + tiles_b + 256 + poly_b;
   void* p = nullptr;
   cudaError_t e = dev_alloc(&p, c->meta_bytes, st);
   if (e != cudaSuccess) return from_cuda(e);
@@ -68,6 +69,7 @@ leco_status alloc_meta(leco_column* c, cudaStream_t st) {
   c->starts = starts_b ? (uint64_t*)(b + 2 * rec_b) : nullptr;
   c->tiles = (TileDesc*)(b + 2 * rec_b + starts_b);
   c->status = (uint32_t*)(b + 2 * rec_b + starts_b + tiles_b);
+  c->poly = poly_b ? (PolyAux*)(b + 2 * rec_b + starts_b + tiles_b + 256) : nullptr;
   return from_cuda(cudaMemsetAsync(c->status, 0, 256, st));
 }
 
@@ -90,19 +92,23 @@ void release(leco_column* c, cudaStream_t st) {
 // fit + offsets + pack of an already partitioned column (c->m, c->starts or c->L set)
 leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t st) {
   const uint64_t m = c->m;
-  const uint64_t scr_elems = m + offsets_scratch_elems(m) + 2;
+  const bool poly = c->model == LECO_MODEL_POLY;
+  const uint64_t pc_elems = poly ? (sizeof(PolyCoef) / 8) * (m ? m : 1) : 0;
+  const uint64_t scr_elems = m + offsets_scratch_elems(m) + 2 + pc_elems;
   uint64_t* scr = nullptr;
   cudaError_t e = dev_alloc((void**)&scr, scr_elems * 8, st);
   if (e != cudaSuccess) return from_cuda(e);
   uint64_t* lenbits = scr;
   uint64_t* off_scr = scr + m;
-  uint64_t* d_total = scr + scr_elems - 2;  // [total bits, max width]
-  uint32_t* d_maxb = reinterpret_cast<uint32_t*>(scr + scr_elems - 1);
+  uint64_t* d_total = scr + m + offsets_scratch_elems(m);  // [total bits, max width]
+  uint32_t* d_maxb = reinterpret_cast<uint32_t*>(d_total + 1);
+  PolyCoef* pcoef = poly ? reinterpret_cast<PolyCoef*>(d_total + 2) : nullptr;
   const uint64_t* starts = c->kind == LECO_PART_VAR ? c->starts : nullptr;
   uint64_t hres[2] = {0, 0};
   uint64_t& total = hres[0];
   uint32_t flags = 0;
-  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, d_maxb, c->status, st);
+  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, pcoef, d_maxb, c->status,
+                 st);
   if (e == cudaSuccess)
     e = launch_offsets(c->rec, lenbits, m, off_scr, offsets_scratch_elems(m), d_total, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hres, d_total, 16, cudaMemcpyDeviceToHost, st);
@@ -116,22 +122,27 @@ leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t
   if (e == cudaSuccess) {
     c->total_bits = total;
     c->max_b = (uint32_t)hres[1];
-    c->stage_bytes = stage_word_bytes(c->max_b);
+    c->stage_bytes = stage_word_bytes(c->max_b) + (poly ? kPolyStageExtra : 0);
     c->nwords = stream_words(total);
     c->words_bytes = c->nwords * 8;
     e = dev_alloc((void**)&c->words, c->words_bytes, st);
   }
-  if (e == cudaSuccess) e = launch_build_aux(c->rec, m, c->n, c->aux, c->status, st);
+  if (e == cudaSuccess) e = launch_build_aux(c->rec, pcoef, m, c->n, c->aux, c->poly, c->status, st);
   if (e == cudaSuccess) e = launch_tile_desc(view_of(c), c->tiles, st);
   if (e == cudaSuccess)
-    e = launch_pack(d_values, c->dtype, c->rec, c->aux, m, c->n, total, c->words, c->nwords, c->status, st);
+    e = launch_pack(d_values, c->dtype, c->rec, c->aux, pcoef, c->poly, m, c->n, total, c->words, c->nwords,
+                    c->status, st);
   cudaFreeAsync(scr, st);
   if (e == cudaErrorInvalidValue) return LECO_ERR_INVALID_ARG;
   return from_cuda(e);
 }
 
 bool valid_dtype(int d) { return d == LECO_U32 || d == LECO_U64; }
-bool valid_model(int m) { return m == LECO_MODEL_CONSTANT || m == LECO_MODEL_LINEAR; }
+bool valid_model(int m) { return m == LECO_MODEL_CONSTANT || m == LECO_MODEL_LINEAR || m == LECO_MODEL_POLY; }
+
+// the model that sizes partitions for the variable partitioner and the size search: the polynomial
+// model's choice is made per partition after partitioning, with the line's sizes before it
+int sizing_model(int m) { return m == LECO_MODEL_POLY ? LECO_MODEL_LINEAR : m; }
 
 // ---------------------------------------------------------------------------- CRC-32 (IEEE 802.3)
 
@@ -173,13 +184,52 @@ uint64_t blob_bytes(const leco_column* c) {
   return kHeaderBytes + 32 * c->m + (c->kind == LECO_PART_VAR ? 8 * (c->m + 1) : 0) + 8 * c->nwords;
 }
 
+// 64-bit field at bit pos of a stream held on the host (pos + 64 <= 64 * nwords)
+uint64_t host_field64(const uint64_t* words, uint64_t pos) {
+  const uint64_t w = pos >> 6;
+  const uint32_t o = (uint32_t)(pos & 63);
+  return o ? (words[w] >> o) | (words[w + 1] << (64 - o)) : words[w];
+}
+
+// a polynomial partition's block {T, K1, K2, K3, E} read from the stream at bit pos
+PolyCoef host_poly_block(const uint64_t* words, uint64_t pos) {
+  PolyCoef pc;
+  pc.T = (int64_t)host_field64(words, pos);
+  for (int j = 0; j < 3; j++) pc.K[j] = (int64_t)host_field64(words, pos + 64 * (uint64_t)(j + 1));
+  pc.E = host_field64(words, pos + 256);
+  return pc;
+}
+
+// a block the decoder can evaluate exactly: exponents 0..62 in the low three bytes, |K_j| <= 2^61,
+// and each nonzero term K_j 2^(S - s_j) p_j below 2^124 (S = the largest exponent)
+bool poly_block_ok(const PolyCoef& pc) {
+  if (pc.E >> 24) return false;
+  int32_t sj[3], S = 0;
+  for (int j = 0; j < 3; j++) {
+    sj[j] = (int32_t)((pc.E >> (8 * j)) & 0xFF);
+    if (sj[j] > 62) return false;
+    S = sj[j] > S ? sj[j] : S;
+  }
+  const int32_t room[3] = {49, 34, 20};
+  for (int j = 0; j < 3; j++) {
+    const int64_t k = pc.K[j];
+    if (k > (1ll << 61) || k < -(1ll << 61)) return false;
+    if (k && S - sj[j] > room[j]) return false;
+  }
+  return true;
+}
+
 // host-side consistency of records/starts/words (everything a kernel indexes with)
 bool validate_host(const BlobHeader& h, const Record* rec, const uint64_t* starts,
                    const uint64_t* words) {
   uint64_t off = 0;
   for (uint64_t p = 0; p < h.m; p++) {
     const Record& r = rec[p];
-    if (r.word3 >> 63) return false;
+    const bool pl = w3_poly(r.word3) != 0;
+    uint64_t t0 = 0, t1 = 0;
+    memcpy(&t0, &r.theta0, 8);
+    memcpy(&t1, &r.theta1, 8);
+    if (pl && (h.model != LECO_MODEL_POLY || w3_exact(r.word3) || w3_s(r.word3) != 0 || t0 || t1)) return false;
     const uint32_t b = w3_b(r.word3);
     if (b > 64) return false;
     const uint64_t a = r.start;
@@ -193,6 +243,12 @@ bool validate_host(const BlobHeader& h, const Record* rec, const uint64_t* start
     }
     if (e <= a || e - a > kMaxPartLen) return false;
     if (w3_off(r.word3) != off) return false;
+    if (pl) {
+      if (e - a < kPolyMinLen || e - a > kPolyMaxLen) return false;
+      if (off + kPolyBlockBits > 64 * (h.nwords - 1)) return false;
+      if (!poly_block_ok(host_poly_block(words, off))) return false;
+      off += kPolyBlockBits;
+    }
     off += (e - a) * b;
     if (off >= (1ull << 48)) return false;
   }
@@ -228,8 +284,8 @@ leco_status leco_search_partition_size(const void* d_values, uint64_t n, leco_dt
   if (sample_frac == 0.0) sample_frac = 0.01;
   if (max_len > 16384 || !(sample_frac > 0.0 && sample_frac <= 1.0)) return LECO_ERR_INVALID_ARG;
   uint64_t bits = 0, ne = 0;
-  const cudaError_t e = search_partition_size(d_values, dtype, n, model, max_len, sample_frac, seed, best_L, &bits,
-                                              &ne, (cudaStream_t)stream);
+  const cudaError_t e = search_partition_size(d_values, dtype, n, sizing_model(model), max_len, sample_frac, seed,
+                                              best_L, &bits, &ne, (cudaStream_t)stream);
   if (e != cudaSuccess) return from_cuda(e);
   if (best_bits) *best_bits = bits;
   if (evals) *evals = ne;
@@ -286,7 +342,7 @@ leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtyp
       policy.part_size > kMaxPartLen)
     return LECO_ERR_INVALID_ARG;
   const uint32_t cap = policy.part_size ? policy.part_size : kMaxPartLen;
-  return from_cuda(var_partition(d_values, dtype, n, policy.tau, cap, model, d_starts_out, m_out,
+  return from_cuda(var_partition(d_values, dtype, n, policy.tau, cap, sizing_model(model), d_starts_out, m_out,
                                  (cudaStream_t)stream));
 }
 
@@ -559,7 +615,11 @@ leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t
   c->tau = h.tau;
   c->home = st;
   for (uint64_t p = 0; p < h.m; p++) c->max_b = c->max_b > w3_b(rec[p].word3) ? c->max_b : w3_b(rec[p].word3);
-  c->stage_bytes = stage_word_bytes(c->max_b);
+  c->stage_bytes = stage_word_bytes(c->max_b) + (h.model == LECO_MODEL_POLY ? kPolyStageExtra : 0);
+  // polynomial blocks, taken from the validated stream for the decode-table build
+  std::vector<PolyCoef> pcoef(h.model == LECO_MODEL_POLY ? h.m : 0);
+  for (uint64_t p = 0; p < pcoef.size(); p++)
+    if (w3_poly(rec[p].word3)) pcoef[p] = host_poly_block(words.data(), w3_off(rec[p].word3));
   cudaGetDevice(&c->device);
   leco_status s = alloc_meta(c, st);
   if (s == LECO_OK) {
@@ -572,8 +632,15 @@ leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t
     s = from_cuda(cudaMemcpyAsync(c->starts, starts.data(), 8 * (h.m + 1), cudaMemcpyHostToDevice, st));
   if (s == LECO_OK)
     s = from_cuda(cudaMemcpyAsync(c->words, words.data(), 8 * h.nwords, cudaMemcpyHostToDevice, st));
-  if (s == LECO_OK) s = from_cuda(launch_build_aux(c->rec, c->m, c->n, c->aux, c->status, st));
+  PolyCoef* d_pcoef = nullptr;
+  if (s == LECO_OK && !pcoef.empty()) {
+    s = from_cuda(dev_alloc((void**)&d_pcoef, sizeof(PolyCoef) * pcoef.size(), st));
+    if (s == LECO_OK)
+      s = from_cuda(cudaMemcpyAsync(d_pcoef, pcoef.data(), sizeof(PolyCoef) * pcoef.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (s == LECO_OK) s = from_cuda(launch_build_aux(c->rec, d_pcoef, c->m, c->n, c->aux, c->poly, c->status, st));
   if (s == LECO_OK) s = from_cuda(launch_tile_desc(view_of(c), c->tiles, st));
+  if (d_pcoef) cudaFreeAsync(d_pcoef, st);
   // the host vectors die at return: finish the copies first
   if (s == LECO_OK) s = from_cuda(cudaStreamSynchronize(st));
   if (s != LECO_OK) {

@@ -368,6 +368,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
       v.words = words + word_base[c];
       v.starts = nullptr;
       v.tiles = tiles + tile_base[c];
+      v.poly = nullptr;  // the batched encode takes constant and linear columns
       v.stage_bytes = stage_word_bytes(max_b[c]);
       v.status = status + c;
     }

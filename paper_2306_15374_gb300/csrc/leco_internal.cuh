@@ -21,13 +21,16 @@ struct Record {
   double theta0;
   double theta1;
   uint64_t start;
-  uint64_t word3;  // off:48 | b:7 | s:7 | exact:1 | 0:1
+  uint64_t word3;  // off:48 | b:7 | s:7 | exact:1 | poly:1
 };
 static_assert(sizeof(Record) == 32, "record layout");
 
 // Device decode table, derived from the records when a column is created: the same header with
 // theta replaced by the grid integers (A, B) when the exact flag was verified. word3 keeps the
 // canonical layout; its exact bit is cleared when verification failed (binary64 path then).
+// A polynomial partition's entry has A = T, B = 0, the poly bit, exact = 0, s = the common grid
+// exponent S of its coefficients and off moved past its coefficient block to its first residual;
+// its prediction comes from the PolyAux table.
 struct Aux {
   int64_t A;
   int64_t B;
@@ -35,6 +38,33 @@ struct Aux {
   uint64_t word3;
 };
 static_assert(sizeof(Aux) == 32, "aux layout");
+
+// Polynomial model (§3.1; §4's per-partition choice among constant, linear and polynomials up to
+// degree three). A polynomial partition's stream bits begin with a block of five 64-bit words
+// {T, K1, K2, K3, E = s1 | s2 << 8 | s3 << 16}; its prediction is
+// T + floor(sum_j K_j p_j(x) 2^-s_j) mod 2^64 over the Gram polynomials of its N values on
+// x' = 2x - (N-1): p1 = x', p2 = 3x'^2 - (N^2-1), p3 = 5x'^3 - (3N^2-7)x'.
+constexpr uint32_t kPolyBlockBits = 320;
+constexpr uint32_t kPolyMinLen = 64;
+constexpr uint32_t kPolyMaxLen = 16384;
+// extra staged bytes a scan tile can need for the blocks of polynomial partitions that start
+// inside it (at most kScanTile / kPolyMinLen of them)
+constexpr uint32_t kPolyStageExtra = 4096 / kPolyMinLen * (kPolyBlockBits / 8);
+
+// the block as the encoder writes it (one per partition; used only for polynomial partitions)
+struct PolyCoef {
+  int64_t T;
+  int64_t K[3];
+  uint64_t E;
+};
+static_assert(sizeof(PolyCoef) == 40, "poly coefficient layout");
+
+// Decode-side form: F(x) = a0 + a1 x + a2 x^2 + a3 x^3 = sum_j K_j 2^(S - s_j) p_j(x) expanded in
+// the local index (exact 128-bit integers), so that pred(x) = T + (F(x) >> S).
+struct PolyAux {
+  uint64_t a[4][2];  // a_k as (low, high) 64-bit halves of a two's complement 128-bit integer
+};
+static_assert(sizeof(PolyAux) == 64, "poly aux layout");
 
 // Scan tiles: tile t covers positions [t kScanTile, (t+1) kScanTile). Positions are encoded in order
 // with dense bit offsets, so a tile's residuals are one contiguous bit range; its descriptor is
@@ -72,6 +102,8 @@ __host__ __device__ __forceinline__ int32_t w3_s(uint64_t w3) {
   return s >= 64 ? s - 128 : s;
 }
 __host__ __device__ __forceinline__ uint32_t w3_exact(uint64_t w3) { return (uint32_t)(w3 >> 62) & 1u; }
+__host__ __device__ __forceinline__ uint32_t w3_poly(uint64_t w3) { return (uint32_t)(w3 >> 63); }
+constexpr uint64_t kPolyFlag = 1ull << 63;
 __host__ __device__ __forceinline__ uint64_t make_w3(uint64_t off, uint32_t b, int32_t s, uint32_t exact) {
   return (off & kOffMask) | ((uint64_t)(b & 0x7F) << 48) | ((uint64_t)((uint32_t)s & 0x7F) << 55) |
          ((uint64_t)(exact & 1) << 62);
@@ -116,14 +148,29 @@ __device__ __forceinline__ int64_t predict_f64(double theta0, double theta1, uin
   return __double2ll_rd(y);
 }
 
-// prediction from the decode table (integer grid when exact, else binary64 from the record)
+// F(x) of a polynomial partition by Horner's rule in 128-bit two's complement arithmetic (exact:
+// the true F is below 2^126 in magnitude, so wrap-around in the intermediate steps cancels)
+__device__ __forceinline__ i128 poly_eval(const PolyAux* __restrict__ poly, uint64_t p, uint64_t x) {
+  const ulonglong2* q = reinterpret_cast<const ulonglong2*>(poly + p);
+  const ulonglong2 c0 = __ldg(q), c1 = __ldg(q + 1), c2 = __ldg(q + 2), c3 = __ldg(q + 3);
+  const u128 X = x;
+  u128 F = ((u128)c3.y << 64) | c3.x;
+  F = F * X + (((u128)c2.y << 64) | c2.x);
+  F = F * X + (((u128)c1.y << 64) | c1.x);
+  F = F * X + (((u128)c0.y << 64) | c0.x);
+  return (i128)F;
+}
+
+// prediction from the decode table (integer grid when exact, the polynomial table for a
+// polynomial partition, else binary64 from the record)
 __device__ __forceinline__ int64_t predict_aux(const Aux& a, const Record* __restrict__ rec,
-                                               uint64_t p, uint64_t x) {
+                                               const PolyAux* __restrict__ poly, uint64_t p, uint64_t x) {
   if (w3_exact(a.word3)) {
     const int32_t s = w3_s(a.word3);
     const int64_t f = a.A + a.B * (int64_t)x;
     return s > 0 ? (f >> s) : f;
   }
+  if (w3_poly(a.word3)) return (int64_t)((uint64_t)a.A + (uint64_t)(poly_eval(poly, p, x) >> w3_s(a.word3)));
   return predict_f64(__ldg(&rec[p].theta0), __ldg(&rec[p].theta1), x);
 }
 
@@ -187,6 +234,7 @@ struct ColumnView {
   const uint64_t* words;
   const uint64_t* starts;      // variable: m+1 entries; fixed: nullptr
   const TileDesc* tiles;       // scan_tiles(n) descriptors
+  const PolyAux* poly;         // m entries when the column may hold polynomial partitions, else nullptr
   uint32_t stage_bytes;        // stage_word_bytes(max width of the column)
   uint32_t* status;
 };
@@ -250,18 +298,20 @@ ScanConfig scan_config_for(const ColumnView& c, int op);
 ScanConfig scan_config_lookup(int op, int dtype, uint32_t stage_bytes);
 void scan_config_store(int op, int dtype, uint32_t stage_bytes, ScanConfig cfg);
 
-// encode pipeline (k_encode.cu)
+// encode pipeline (k_encode.cu). pcoef / poly: per-partition polynomial blocks (written by the fit
+// of a LECO_MODEL_POLY column, read by the decode-table build and the packer) and the derived
+// polynomial decode table; both nullptr for constant and linear columns.
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
-                       uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits,
+                       uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits, PolyCoef* pcoef,
                        uint32_t* max_b, uint32_t* err, cudaStream_t st);
 cudaError_t launch_offsets(Record* rec, const uint64_t* lenbits, uint64_t m, uint64_t* scratch,
                            uint64_t scratch_elems, uint64_t* total_out, cudaStream_t st);
 uint64_t offsets_scratch_elems(uint64_t m);
-cudaError_t launch_build_aux(const Record* rec, uint64_t m, uint64_t n, Aux* aux, uint32_t* status,
-                             cudaStream_t st);
-cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux,
-                        uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words, uint64_t nwords, uint32_t* err,
-                        cudaStream_t st);
+cudaError_t launch_build_aux(const Record* rec, const PolyCoef* pcoef, uint64_t m, uint64_t n, Aux* aux,
+                             PolyAux* poly, uint32_t* status, cudaStream_t st);
+cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux, const PolyCoef* pcoef,
+                        const PolyAux* poly, uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
+                        uint64_t nwords, uint32_t* err, cudaStream_t st);
 
 // scans (k_scan.cu) and lookups (k_decode.cu)
 cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st);

@@ -71,8 +71,8 @@ extern "C" leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t 
   uint32_t* err = reinterpret_cast<uint32_t*>(res + 1) + 1;
   cudaError_t e = cudaMemsetAsync(err, 0, 4, st);
   if (e == cudaSuccess)
-    e = launch_fit(d_values, dtype, n, nullptr, L, m, model, rec, lenbits, reinterpret_cast<uint32_t*>(res + 1), err,
-                   st);
+    e = launch_fit(d_values, dtype, n, nullptr, L, m, model, rec, lenbits, nullptr,
+                   reinterpret_cast<uint32_t*>(res + 1), err, st);
   if (e == cudaSuccess) e = launch_offsets(rec, lenbits, m, off_scr, offsets_scratch_elems(m), res, st);
   uint64_t total = 0;
   uint32_t flags = 0;
@@ -85,8 +85,9 @@ extern "C" leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t 
   const uint64_t nwords = stream_words(total);
   *nwords_out = nwords;
   if (nwords > words_cap) return LECO_ERR_INVALID_ARG;  // *nwords_out tells the size needed
-  e = launch_build_aux(rec, m, n, aux, nullptr, st);
+  e = launch_build_aux(rec, nullptr, m, n, aux, nullptr, nullptr, st);
   if (e == cudaSuccess)
-    e = launch_pack(d_values, dtype, rec, aux, m, n, total, static_cast<uint64_t*>(d_words), nwords, err, st);
+    e = launch_pack(d_values, dtype, rec, aux, nullptr, nullptr, m, n, total, static_cast<uint64_t*>(d_words), nwords,
+                    err, st);
   return e == cudaSuccess ? LECO_OK : LECO_ERR_CUDA;
 }

@@ -26,6 +26,7 @@ LECO_U32 = 0
 LECO_U64 = 1
 LECO_MODEL_CONSTANT = 0
 LECO_MODEL_LINEAR = 1
+LECO_MODEL_POLY = 2  # per partition: constant, linear, quadratic or cubic, by exact size
 LECO_PART_FIXED = 0
 LECO_PART_VAR = 1
 LECO_PART_AUTO = 2

@@ -35,6 +35,7 @@ def make_blob(records: np.ndarray, words: np.ndarray, n: int, L: int, dtype: int
     b = (records["word3"].astype(np.uint64) >> np.uint64(48)) & np.uint64(0x7F)
     ends = np.append(records["start"][1:].astype(np.uint64), np.uint64(n)) if m else np.zeros(0, np.uint64)
     total_bits = int(((ends - records["start"].astype(np.uint64)) * b).sum()) if m else 0
+    total_bits += 320 * int((records["word3"].astype(np.uint64) >> np.uint64(63)).sum()) if m else 0  # poly blocks
     header = struct.pack("<IIQQQBBBBIdQII", LECO_MAGIC, LECO_VERSION, n, m, len(words), dtype, kind,
                          model, 0, L if kind == 0 else 0, tau, total_bits, zlib.crc32(body), 0)
     assert len(header) == 64

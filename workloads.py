@@ -121,6 +121,21 @@ def timestamps_u32(n: int, step: int = 1000, period: int = 86400, amp: int = 300
     return (t & 0xFFFFFFFF).astype(np.uint64)
 
 
+def sine_mixture(n: int, base: int = 1 << 40, a1: float = 1e9, p1: float = 1e6, a2: float = 1e7,
+                 p2: float = 4e4, noise: int = 128, seed: int = 0, stream: int = 0) -> np.ndarray:
+    """Two superposed sine signals plus uniform noise, the sensor-like shape where higher-order
+    models pay (§4's mixture-of-sines data set): v_i = base + floor(a1 sin(2 pi i/p1) +
+    a2 sin(2 pi i/p2)) + U{-noise..noise}. Generated in chunks of 2^24 values."""
+    g = rng(seed, stream)
+    out = np.empty(n, dtype=np.uint64)
+    step = 1 << 24
+    for a in range(0, n, step):
+        i = np.arange(a, min(n, a + step), dtype=np.float64)
+        s = np.floor(a1 * np.sin(2 * np.pi * i / p1) + a2 * np.sin(2 * np.pi * i / p2)).astype(np.int64)
+        out[a:a + i.size] = (base + s + g.integers(-noise, noise + 1, size=i.size, dtype=np.int64)).astype(np.uint64)
+    return out
+
+
 # ----------------------------------------------------------------------------- small / adversarial
 
 def random_u64(n: int, seed: int = 0, stream: int = 0, bits: int = 64) -> np.ndarray:
