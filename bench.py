@@ -50,9 +50,10 @@ def parse_args():
     ap.add_argument("--serve-columns", type=int, default=2000)
     ap.add_argument("--serve-total", type=float, default=2.5e9)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--workload", choices=["fix", "var", "batch", "serve"], default="fix",
+    ap.add_argument("--workload", choices=["fix", "var", "batch", "serve", "poly"], default="fix",
                     help="fix: the 3 x 200M fixed-partition columns (default); var: the variable-partition "
-                         "columns (200M piecewise-linear uint64, 500M uint32 timestamps)")
+                         "columns (200M piecewise-linear uint64, 500M uint32 timestamps); batch: 10,000 columns; "
+                         "serve: the serving loop; poly: the polynomial model against the line on a 200M sine mixture")
     ap.add_argument("--tau", type=float, default=0.03)
     ap.add_argument("--tau-sweep", default="", help="var workload: comma-separated tau values to sweep (CR vs tau)")
     return ap.parse_args()
@@ -61,8 +62,8 @@ def parse_args():
 KSCAN_SRCS = [os.path.join(ROOT, "paper_2306_15374_gb300", "csrc", f) for f in ("k_scan.cu", "leco_internal.cuh", "tma.cuh")]
 # DRAM read + write per decode launch from one ncu capture of this workload (mean of columns a, b, c;
 # see profiles/k_tilescan_decode_filter_fix200M.md), valid only for the kernel sources it was taken on.
-DECODE_TRAFFIC = {"sha256": "7033c1e297e0998641914e6aee95f22ca681fdffbfdca79ee626b33a17ee64af",
-                  "bytes_per_launch": (1893106432 + 1972573440 + 1845003008) / 3}
+DECODE_TRAFFIC = {"sha256": "ff7f4eab1768ba7ebddb3dab63b9f6dbd2309688335bf8d43df1eb4b50a4659a",
+                  "bytes_per_launch": (1893852160 + 1972840704 + 1844824320) / 3}
 
 
 def decode_traffic():
@@ -615,6 +616,77 @@ def run_var(args):
     return 0
 
 
+def run_poly(args):
+    """Polynomial model (per-partition choice among constant, linear, quadratic and cubic) against
+    the linear model on a 200M-value uint64 sine mixture, fixed partitions of 4096: compression,
+    encode, decode, filter-sum and 10M lookups per model (not the default workload)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2306_15374_gb300 as pkg
+
+    pkg.build()
+    from paper_2306_15374_gb300 import leco
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    L = 4096
+    v = W.sine_mixture(args.n)
+    n = len(v)
+    dv = torch.from_numpy(v.view(np.int64)).to(dev)
+    k = args.lookups
+    idx = torch.from_numpy(W.uniform_indices(k, n, seed=11).view(np.int64)).to(dev)
+    lo, hi = W.filter_bounds(v)
+    reps = max(3, min(args.steps, 50))
+    peak, _ = measured_peaks()
+
+    def timed(fn, r=reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(r):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / r
+
+    out = {}
+    for name, model in (("linear", leco.LECO_MODEL_LINEAR), ("poly", leco.LECO_MODEL_POLY)):
+        enc_ms = timed(lambda: leco.leco_encode(dv, leco.fixed(L), model).free(), r=3)
+        col = leco.leco_encode(dv, leco.fixed(L), model)
+        st = col.stats()
+        comp = st["record_bytes"] + st["residual_bytes"]
+        rec_b, _, _ = leco.leco_column_export(col)
+        w3 = np.frombuffer(rec_b, dtype=np.uint64)[3::4]  # word3 of each 32-byte record
+        npoly = int((w3 >> np.uint64(63)).sum())
+        o = torch.empty(n, dtype=torch.int64, device=dev)
+        ok_ = torch.empty(k, dtype=torch.int64, device=dev)
+        res = torch.zeros(3, dtype=torch.int64, device=dev)
+        t_dec = timed(lambda: leco.leco_decode_all(col, o))
+        ok = bool(torch.equal(o, dv))
+        t_fil = timed(lambda: leco.leco_filter_sum(col, lo, hi, res))
+        t_ra = timed(lambda: leco.leco_random_access(col, idx, ok_))
+        ok = ok and bool(torch.equal(ok_, dv[idx]))
+        out[name] = {
+            "ratio": comp / (8 * n), "compressed_bytes": comp, "polynomial_partitions": npoly,
+            "partitions": st["partitions"], "encode_ms": enc_ms, "encode_gbs": (8 * n + comp) / (enc_ms * 1e-3) / 1e9,
+            "decode_ms": t_dec, "decode_gbs": (comp + 8 * n) / (t_dec * 1e-3) / 1e9,
+            "decode_frac_hbm": (comp + 8 * n) / (t_dec * 1e-3) / 1e9 / peak,
+            "filter_ms": t_fil, "filter_gbs": (comp + 24) / (t_fil * 1e-3) / 1e9,
+            "filter_frac_hbm": (comp + 24) / (t_fil * 1e-3) / 1e9 / peak,
+            "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6, "results_equal_input": ok,
+        }
+        col.free()
+        del o, ok_
+    print(json.dumps({"workload": f"LeCo-Poly vs linear: {n} uint64 sine mixture (two sines + noise), L={L}",
+                      "peak_gbs": peak, "results": out}), flush=True)
+    return 0
+
+
 def upload_columns(gen, spec, ncols, dev):
     """Columns generated on host threads (numpy releases the GIL) and copied to the device as
     they complete."""
@@ -808,6 +880,8 @@ def main():
         return run_serve(args)
     if args.workload == "batch" and args.impl != "reference":
         return run_batch(args)
+    if args.workload == "poly" and args.impl != "reference":
+        return run_poly(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_leco(args)

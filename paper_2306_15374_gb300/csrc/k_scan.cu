@@ -205,7 +205,10 @@ __device__ __forceinline__ void emit(const ScanArgs& g, Acc& acc, uint64_t i, ui
   }
 }
 
-// one position decoded from scratch (partition search, multiply): boundary groups only
+// one position decoded from scratch (partition search, multiply): boundary groups only. ANY_MODEL:
+// the column may hold polynomial partitions (single-column scans of constant and linear columns
+// leave that branch out)
+template <bool ANY_MODEL>
 __device__ __forceinline__ uint64_t value_at(const ScanArgs& g, const uint32_t* words, const Aux* saux,
                                              const TileMeta& mt, uint64_t i, uint64_t q) {
   const ColumnView& c = g.c;
@@ -222,7 +225,8 @@ __device__ __forceinline__ uint64_t value_at(const ScanArgs& g, const uint32_t* 
   const uint32_t b = w3_b(a.word3);
   const uint32_t bit = (uint32_t)(w3_off(a.word3) + (uint64_t)b * x - mt.bit_base);
   const uint64_t z = b <= 32 ? (uint64_t)field32(words, bit, (uint32_t)low_mask(b)) : field64(words, bit, low_mask(b));
-  return (uint64_t)predict_aux(a, c.rec, c.poly, q, x) + (uint64_t)zz_decode(z);
+  const int64_t pred = ANY_MODEL ? predict_aux(a, c.rec, c.poly, q, x) : predict_aux_line(a, c.rec, q, x);
+  return (uint64_t)pred + (uint64_t)zz_decode(z);
 }
 
 // Tight loop over ng whole 32-value groups of one exact partition (the common case). Lane j
@@ -285,7 +289,68 @@ __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const ui
   }
 }
 
-template <int MODE>
+// Tight loop over ng whole 32-value groups of one polynomial partition (§3.1 polynomial terms):
+// lane j's prediction T + (F(x) >> S) steps by forward differences of the cubic F over strides of
+// 32 positions, exactly in 128-bit two's complement arithmetic (the differences start from F at
+// x, x + 32, x + 64, x + 96 by Horner's rule). F and its differences are carried multiplied by
+// 2^(64-S) modulo 2^128: floor(F / 2^S) mod 2^64 is then the high half of the carried value, so
+// the loop shifts nothing. Filter runs have no model bounds: every value is compared.
+template <int MODE, bool WIDE>
+__device__ __forceinline__ void run_groups_poly(const ScanArgs& g, Acc& acc, const uint32_t* words,
+                                                const Aux& a, uint64_t q, uint64_t i0, uint32_t ng,
+                                                uint64_t bit_base, uint32_t lane) {
+  const uint32_t b = w3_b(a.word3);
+  const int32_t S = w3_s(a.word3) & 63;
+  const uint64_t x = i0 + lane - a.start;
+  const ulonglong2* row = reinterpret_cast<const ulonglong2*>(g.c.poly + q);
+  u128 c[4];
+  for (int k = 0; k < 4; k++) {
+    const ulonglong2 h = __ldg(row + k);
+    c[k] = ((u128)h.y << 64) | h.x;
+  }
+  // F(x) and its forward differences over the stride h = 32, in closed form:
+  // D1 = a1 h + a2 (2xh + h^2) + a3 (3x^2 h + 3x h^2 + h^3), D2 = a2 2h^2 + a3 (6x h^2 + 6h^3),
+  // D3 = a3 6h^3 (x < 2^14, so every bracket fits 64 bits)
+  const uint64_t h = 32;
+  const uint32_t up = 64u - (uint32_t)S;  // 2..64
+  u128 F = (((c[3] * x + c[2]) * x + c[1]) * x + c[0]) << up;
+  u128 D1 = (c[1] * h + c[2] * (2 * x * h + h * h) + c[3] * (3 * x * x * h + 3 * x * h * h + h * h * h)) << up;
+  u128 D2 = (c[2] * (2 * h * h) + c[3] * (6 * x * h * h + 6 * h * h * h)) << up;
+  const u128 D3 = (c[3] * (6 * h * h * h)) << up;
+  uint32_t bit = (uint32_t)(w3_off(a.word3) + (uint64_t)b * x - bit_base);
+  const uint32_t b32 = 32u * b;
+  const uint64_t mask64 = low_mask(b);
+  const uint32_t mask32 = (uint32_t)mask64;
+  const uint64_t T = (uint64_t)a.A;
+  if (MODE == kDecode64 || MODE == kDecode32) {
+    const uint64_t o0 = i0 + lane - g.begin;
+    for (uint32_t k = 0; k < ng; k++) {
+      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+      const uint64_t v = T + (uint64_t)(F >> 64) + (uint64_t)r;
+      if (MODE == kDecode64)
+        reinterpret_cast<uint64_t*>(g.out)[o0 + 32ull * k] = v;
+      else
+        reinterpret_cast<uint32_t*>(g.out)[o0 + 32ull * k] = (uint32_t)v;
+      F += D1;
+      D1 += D2;
+      D2 += D3;
+      bit += b32;
+    }
+  } else {
+    const uint64_t vmask = g.c.dtype == LECO_U32 ? 0xFFFFFFFFull : ~0ull;
+    for (uint32_t k = 0; k < ng; k++) {
+      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+      const uint64_t v = (T + (uint64_t)(F >> 64) + (uint64_t)r) & vmask;
+      if (v >= g.lo && v <= g.hi) acc.add(v);
+      F += D1;
+      D1 += D2;
+      D2 += D3;
+      bit += b32;
+    }
+  }
+}
+
+template <int MODE, bool POLY>
 __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, const uint32_t* words,
                              const Aux* saux, Acc& acc, uint32_t per_warp) {
   const ColumnView& c = g.c;
@@ -322,11 +387,18 @@ __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, 
       else
         run_groups<MODE, false>(g, acc, words, a, gp, ng, mt.bit_base, lane, cls);
       gp += 32ull * ng;
+    } else if (POLY && ng && w3_poly(a.word3)) {
+      if (w3_b(a.word3) > 32)
+        run_groups_poly<MODE, true>(g, acc, words, a, q, gp, ng, mt.bit_base, lane);
+      else
+        run_groups_poly<MODE, false>(g, acc, words, a, q, gp, ng, mt.bit_base, lane);
+      gp += 32ull * ng;
     } else {
-      // a group that crosses a partition end, a partial last group, or a binary64 partition:
-      // each lane decodes its position from scratch
+      // a group that crosses a partition end, a partial last group, a binary64 partition, or a
+      // polynomial partition in a kernel without the polynomial loop: each lane decodes its
+      // position from scratch
       const uint64_t i = gp + lane;
-      if (i < wend) emit<MODE>(g, acc, i, value_at(g, words, saux, mt, i, q), vmask);
+      if (i < wend) emit<MODE>(g, acc, i, value_at<POLY>(g, words, saux, mt, i, q), vmask);
       gp += 32;
     }
   }
@@ -355,7 +427,10 @@ __device__ __forceinline__ TileMeta meta_from(const TileDesc& d, int mode, const
 // Persistent scan. One producer warp (the last) and CW consumer warps; nst stages of stage_bytes
 // word bytes + the decode-table slot. MULTI: jobs come from a work table (column, tile, range,
 // output) over several columns; otherwise every tile of [g.begin, g.end) of the one column g.c.
-template <int MODE, int CW, bool MULTI>
+// POLY: the column (or a column of the batch) may hold polynomial partitions, decoded by their own
+// loop (a separate instantiation, so that constant and linear columns keep the smaller register
+// budget).
+template <int MODE, int CW, bool MULTI, bool POLY>
 __global__ void __launch_bounds__((CW + 1) * 32)
     k_tilescan(const ScanArgs g0, const ColumnView* __restrict__ cols, const BatchItem* __restrict__ items,
                uint64_t nitems, uint32_t nst, uint32_t stage_bytes) {
@@ -478,11 +553,11 @@ __global__ void __launch_bounds__((CW + 1) * 32)
         const Aux* saux = reinterpret_cast<const Aux*>(base + stage_bytes);
         if (MODE == kDecodeAny) {
           if (g.c.dtype == LECO_U32)
-            process_tile<kDecode32>(g, tile, mt, words, saux, acc, per_warp);
+            process_tile<kDecode32, POLY>(g, tile, mt, words, saux, acc, per_warp);
           else
-            process_tile<kDecode64>(g, tile, mt, words, saux, acc, per_warp);
+            process_tile<kDecode64, POLY>(g, tile, mt, words, saux, acc, per_warp);
         } else {
-          process_tile<MODE>(g, tile, mt, words, saux, acc, per_warp);
+          process_tile<MODE, POLY>(g, tile, mt, words, saux, acc, per_warp);
         }
       }
       __syncwarp();
@@ -581,6 +656,108 @@ __device__ TileDesc tile_desc_one(const ColumnView& c, uint64_t t) {
   }
 }
 
+__device__ __forceinline__ i128 shfl_down_i128(i128 v, int o) {
+  const uint64_t lo = __shfl_down_sync(0xffffffffu, (unsigned long long)(uint64_t)(u128)v, o);
+  const uint64_t hi = __shfl_down_sync(0xffffffffu, (unsigned long long)(uint64_t)((u128)v >> 64), o);
+  return (i128)(((u128)hi << 64) | lo);
+}
+
+__device__ __forceinline__ i128 shfl_lane0_i128(i128 v) {
+  const uint64_t lo = __shfl_sync(0xffffffffu, (unsigned long long)(uint64_t)(u128)v, 0);
+  const uint64_t hi = __shfl_sync(0xffffffffu, (unsigned long long)(uint64_t)((u128)v >> 64), 0);
+  return (i128)(((u128)hi << 64) | lo);
+}
+
+// Bounds of the values at local positions [xa, xb) of polynomial partition p (warp-collective; the
+// result in every lane): each lane enumerates floor(F(x) / 2^S) for x = xa + lane + 32k by forward
+// differences of F, the warp takes the exact min and max, and the residual range of width b widens
+// them: T + min - 2^(b-1) <= w <= T + max + 2^(b-1) - 1. Kinds as part_bounds.
+__device__ int poly_part_bounds(const ColumnView& c, const Aux& a, uint64_t p, uint64_t xa, uint64_t xb,
+                                uint32_t lane, uint64_t* vlo_out, uint64_t* vhi_out) {
+  const uint32_t b = w3_b(a.word3);
+  const int32_t S = w3_s(a.word3) & 63;
+  const ulonglong2* row = reinterpret_cast<const ulonglong2*>(c.poly + p);
+  u128 cf[4];
+  for (int k = 0; k < 4; k++) {
+    const ulonglong2 h = __ldg(row + k);
+    cf[k] = ((u128)h.y << 64) | h.x;
+  }
+  const uint64_t x = xa + lane, h = 32;
+  u128 F = ((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0];
+  u128 D1 = cf[1] * h + cf[2] * (2 * x * h + h * h) + cf[3] * (3 * x * x * h + 3 * x * h * h + h * h * h);
+  u128 D2 = cf[2] * (2 * h * h) + cf[3] * (6 * x * h * h + 6 * h * h * h);
+  const u128 D3 = cf[3] * (6 * h * h * h);
+  i128 qmin = ((i128)1 << 126), qmax = -((i128)1 << 126);
+  for (uint64_t xx = x; xx < xb; xx += 32) {
+    const i128 q = (i128)F >> S;
+    qmin = q < qmin ? q : qmin;
+    qmax = q > qmax ? q : qmax;
+    F += D1;
+    D1 += D2;
+    D2 += D3;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const i128 m0 = shfl_down_i128(qmin, o), m1 = shfl_down_i128(qmax, o);
+    qmin = m0 < qmin ? m0 : qmin;
+    qmax = m1 > qmax ? m1 : qmax;
+  }
+  qmin = shfl_lane0_i128(qmin);
+  qmax = shfl_lane0_i128(qmax);
+  if (b > 62 || xa >= xb) return 0;
+  const i128 half = b ? (i128)1 << (b - 1) : 0;
+  const i128 L = (i128)a.A + qmin - half, U = (i128)a.A + qmax + (half ? half - 1 : 0);
+  if (L < (i128)INT64_MIN || U > (i128)INT64_MAX) return 0;
+  if (c.dtype == LECO_U32) {
+    const i128 lo = L > 0 ? L : 0, hi = U < (i128)0xFFFFFFFFll ? U : (i128)0xFFFFFFFFll;
+    if (lo > hi) return 0;
+    *vlo_out = (uint64_t)lo;
+    *vhi_out = (uint64_t)hi;
+    return 1;
+  }
+  *vlo_out = (uint64_t)(int64_t)L;
+  *vhi_out = (uint64_t)(int64_t)U;
+  return (L < 0 && U >= 0) ? 2 : 1;
+}
+
+// Value bounds of the tiles of a column with polynomial partitions (a warp per tile): the bounds
+// k_tile_desc leaves out for polynomial partitions (their predictions are not monotone), from the
+// exact predictions; partitions with a line keep part_bounds. Tiles without a polynomial partition
+// are left as they are.
+__global__ void k_tile_poly_bounds(const ColumnView c, TileDesc* __restrict__ tiles) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nt = scan_tiles(c.n);
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t t = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += nw) {
+    const uint64_t p0 = tiles[t].p0, np = tiles[t].np;
+    bool any = false;
+    for (uint64_t p = p0; p < p0 + np && !any; p++) any = w3_poly(ldg_aux(c.aux + p).word3) != 0;
+    if (!any) continue;
+    const uint64_t i0 = t * kScanTile, i1 = min(i0 + kScanTile, c.n);
+    int kind = 0;
+    uint64_t vmin = 0, vmax = 0;
+    for (uint64_t p = p0; p < p0 + np; p++) {
+      const Aux a = ldg_aux(c.aux + p);
+      const uint64_t ps = max(i0, a.start), pe = min(i1, pstart(c, p + 1));
+      uint64_t lo = 0, hi = 0;
+      const int pk = w3_poly(a.word3) ? poly_part_bounds(c, a, p, ps - a.start, pe - a.start, lane, &lo, &hi)
+                                      : part_bounds(c.dtype, a, ps - a.start, pe - 1 - a.start, &lo, &hi);
+      if (p == p0) {
+        kind = pk;
+        vmin = lo;
+        vmax = hi;
+      } else {
+        kind = bounds_union(kind, &vmin, &vmax, pk, lo, hi);
+      }
+      if (kind == 0) break;
+    }
+    if (lane == 0) {
+      tiles[t].bounds = (uint32_t)kind;
+      tiles[t].vmin = kind ? vmin : 0;
+      tiles[t].vmax = kind ? vmax : ~0ull;
+    }
+  }
+}
+
 __global__ void k_tile_desc(const ColumnView c, TileDesc* __restrict__ tiles) {
   const uint64_t nt = scan_tiles(c.n);
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt;
@@ -597,12 +774,12 @@ __global__ void k_tile_desc_multi(const ColumnView* __restrict__ views, const ui
   }
 }
 
-template <int MODE, int CW, bool MULTI>
+template <int MODE, int CW, bool MULTI, bool POLY>
 cudaError_t launch_scan_cfg(const ScanArgs& g, const ColumnView* cols, const BatchItem* items,
                             uint64_t nitems, uint32_t stage_bytes, ScanConfig cfg, cudaStream_t st) {
   const uint32_t nst = cfg.stages < 2 ? 2u : (cfg.stages > (uint32_t)kMaxStages ? (uint32_t)kMaxStages : cfg.stages);
   const uint32_t smem = kCtrlBytes + nst * (stage_bytes + kAuxBytes);
-  auto kern = k_tilescan<MODE, CW, MULTI>;
+  auto kern = k_tilescan<MODE, CW, MULTI, POLY>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
@@ -616,12 +793,19 @@ cudaError_t launch_scan_cfg(const ScanArgs& g, const ColumnView* cols, const Bat
   return cudaGetLastError();
 }
 
+// poly: the column (a single-column scan: it has a polynomial table) or some column of the batch
+// may hold polynomial partitions
 template <int MODE, bool MULTI>
 cudaError_t launch_scan(const ScanArgs& g, const ColumnView* cols, const BatchItem* items, uint64_t nitems,
-                        uint32_t stage_bytes, ScanConfig cfg, cudaStream_t st) {
+                        uint32_t stage_bytes, ScanConfig cfg, bool poly, cudaStream_t st) {
+  if (poly) {
+    if (cfg.consumer_warps == 4)
+      return launch_scan_cfg<MODE, 4, MULTI, true>(g, cols, items, nitems, stage_bytes, cfg, st);
+    return launch_scan_cfg<MODE, 8, MULTI, true>(g, cols, items, nitems, stage_bytes, cfg, st);
+  }
   if (cfg.consumer_warps == 4)
-    return launch_scan_cfg<MODE, 4, MULTI>(g, cols, items, nitems, stage_bytes, cfg, st);
-  return launch_scan_cfg<MODE, 8, MULTI>(g, cols, items, nitems, stage_bytes, cfg, st);
+    return launch_scan_cfg<MODE, 4, MULTI, false>(g, cols, items, nitems, stage_bytes, cfg, st);
+  return launch_scan_cfg<MODE, 8, MULTI, false>(g, cols, items, nitems, stage_bytes, cfg, st);
 }
 
 // One CTA waits on an mbarrier that nothing arrives at: the bounded wait must give up after limit_ns
@@ -649,6 +833,10 @@ cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t 
   if (nt == 0) return cudaSuccess;
   const uint64_t want = (nt + 127) / 128, cap = (uint64_t)sm_count() * 8;
   k_tile_desc<<<(int)(want < cap ? want : cap), 128, 0, st>>>(c, tiles);
+  if (c.poly) {
+    const uint64_t wb = (nt + 7) / 8;
+    k_tile_poly_bounds<<<(int)(wb < cap ? wb : cap), 256, 0, st>>>(c, tiles);
+  }
   return cudaGetLastError();
 }
 
@@ -678,8 +866,9 @@ cudaError_t launch_decode_cfg(const ColumnView& c, uint64_t begin, uint64_t coun
   g.lo = g.hi = 0;
   g.flags = 0;
   g.res = nullptr;
-  return c.dtype == LECO_U32 ? launch_scan<kDecode32, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, st)
-                             : launch_scan<kDecode64, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, st);
+  const bool poly = c.poly != nullptr;
+  return c.dtype == LECO_U32 ? launch_scan<kDecode32, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, poly, st)
+                             : launch_scan<kDecode64, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, poly, st);
 }
 
 cudaError_t launch_filter_sum(const ColumnView& c, uint64_t lo, uint64_t hi, uint32_t flags,
@@ -702,16 +891,16 @@ cudaError_t launch_filter_sum_cfg(const ColumnView& c, uint64_t lo, uint64_t hi,
   g.hi = hi;
   g.flags = flags;
   g.res = out;
-  return launch_scan<kFilter, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, st);
+  return launch_scan<kFilter, false>(g, nullptr, nullptr, 0, c.stage_bytes, cfg, c.poly != nullptr, st);
 }
 
 cudaError_t launch_batch_decode(const ColumnView* d_cols, const BatchItem* d_items, uint64_t nitems,
-                                uint32_t stage_bytes, ScanConfig cfg, uint32_t* status, cudaStream_t st) {
+                                uint32_t stage_bytes, ScanConfig cfg, bool poly, uint32_t* status, cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
   ScanArgs g;
   memset(&g, 0, sizeof(g));
   g.c.status = status;
-  return launch_scan<kDecodeAny, true>(g, d_cols, d_items, nitems, stage_bytes, cfg, st);
+  return launch_scan<kDecodeAny, true>(g, d_cols, d_items, nitems, stage_bytes, cfg, poly, st);
 }
 
 }  // namespace leco

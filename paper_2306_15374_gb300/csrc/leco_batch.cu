@@ -20,6 +20,7 @@ struct leco_batch_plan {
   uint64_t nitems = 0;
   uint32_t stage_bytes = 64;
   ScanConfig cfg{4, 8};
+  bool poly = false;  // some column has polynomial partitions
   int device = 0;
   cudaStream_t capture = nullptr;
   cudaGraph_t graph = nullptr;
@@ -120,10 +121,12 @@ leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* 
   std::vector<BatchItem> items;
   uint32_t stage_bytes = 64;
   int dtype = LECO_U32;
+  bool any_poly = false;
   for (uint32_t c = 0; c < ncols; c++) {
     const leco_column* col = cols[c];
     if (!col || col->device != dev || (col->n && !d_outs[c])) return LECO_ERR_INVALID_ARG;
     views[c] = view_of(col);
+    any_poly = any_poly || col->poly != nullptr;
     stage_bytes = col->stage_bytes > stage_bytes ? col->stage_bytes : stage_bytes;
     if (col->dtype == LECO_U64) dtype = LECO_U64;
     const uint64_t vb = col->dtype == LECO_U32 ? 4 : 8;
@@ -144,6 +147,7 @@ leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* 
   p->device = dev;
   p->nitems = items.size();
   p->stage_bytes = stage_bytes;
+  p->poly = any_poly;
   p->cfg = scan_config_lookup(0, dtype, stage_bytes);
   cudaError_t e = cudaMalloc((void**)&p->d_cols, sizeof(ColumnView) * (ncols ? ncols : 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_items, sizeof(BatchItem) * (items.empty() ? 1 : items.size()));
@@ -164,7 +168,7 @@ leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* 
 leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream) {
   if (!plan) return LECO_ERR_INVALID_ARG;
   return from_cuda(launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes, plan->cfg,
-                                       plan->d_status, (cudaStream_t)stream));
+                                       plan->poly, plan->d_status, (cudaStream_t)stream));
 }
 
 leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream) {
@@ -174,7 +178,7 @@ leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t strea
     if (e == cudaSuccess) e = cudaStreamBeginCapture(plan->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       const cudaError_t le = launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes,
-                                                 plan->cfg, plan->d_status, plan->capture);
+                                                 plan->cfg, plan->poly, plan->d_status, plan->capture);
       e = cudaStreamEndCapture(plan->capture, &plan->graph);
       if (le != cudaSuccess) e = le;
     }
@@ -198,7 +202,7 @@ leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, le
       const ScanConfig cfg{ns, cw};
       auto run = [&]() {
         return launch_batch_decode(plan->d_cols, plan->d_items, plan->nitems, plan->stage_bytes, cfg,
-                                   plan->d_status, st);
+                                   plan->poly, plan->d_status, st);
       };
       if (run() != cudaSuccess) {  // e.g. too much shared memory for the plan's widest tile: skip
         cudaGetLastError();

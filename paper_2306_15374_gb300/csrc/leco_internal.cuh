@@ -161,17 +161,23 @@ __device__ __forceinline__ i128 poly_eval(const PolyAux* __restrict__ poly, uint
   return (i128)F;
 }
 
-// prediction from the decode table (integer grid when exact, the polynomial table for a
-// polynomial partition, else binary64 from the record)
-__device__ __forceinline__ int64_t predict_aux(const Aux& a, const Record* __restrict__ rec,
-                                               const PolyAux* __restrict__ poly, uint64_t p, uint64_t x) {
+// prediction of a constant or linear partition from the decode table (integer grid when exact,
+// else binary64 from the record)
+__device__ __forceinline__ int64_t predict_aux_line(const Aux& a, const Record* __restrict__ rec, uint64_t p,
+                                                    uint64_t x) {
   if (w3_exact(a.word3)) {
     const int32_t s = w3_s(a.word3);
     const int64_t f = a.A + a.B * (int64_t)x;
     return s > 0 ? (f >> s) : f;
   }
-  if (w3_poly(a.word3)) return (int64_t)((uint64_t)a.A + (uint64_t)(poly_eval(poly, p, x) >> w3_s(a.word3)));
   return predict_f64(__ldg(&rec[p].theta0), __ldg(&rec[p].theta1), x);
+}
+
+// prediction of any partition (the polynomial table for a polynomial one)
+__device__ __forceinline__ int64_t predict_aux(const Aux& a, const Record* __restrict__ rec,
+                                               const PolyAux* __restrict__ poly, uint64_t p, uint64_t x) {
+  if (w3_poly(a.word3)) return (int64_t)((uint64_t)a.A + (uint64_t)(poly_eval(poly, p, x) >> w3_s(a.word3)));
+  return predict_aux_line(a, rec, p, x);
 }
 
 __device__ __forceinline__ uint64_t load_value(const void* __restrict__ v, int dtype, uint64_t i) {
@@ -326,8 +332,9 @@ cudaError_t launch_decode_cfg(const ColumnView& c, uint64_t begin, uint64_t coun
                               ScanConfig cfg, cudaStream_t st);
 cudaError_t launch_lookup_multi(const ColumnView* views, const uint32_t* col, const uint64_t* idx, uint64_t k,
                                 uint64_t* out, cudaStream_t st);
+// poly: some column of the batch may hold polynomial partitions (a column with a polynomial table)
 cudaError_t launch_batch_decode(const ColumnView* d_cols, const BatchItem* d_items, uint64_t nitems,
-                                uint32_t stage_bytes, ScanConfig cfg, uint32_t* status, cudaStream_t st);
+                                uint32_t stage_bytes, ScanConfig cfg, bool poly, uint32_t* status, cudaStream_t st);
 cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint64_t k, void* out,
                                  cudaStream_t st);
 

@@ -89,6 +89,7 @@ struct leco_server {
   std::vector<ColumnView> h_views;
   ColumnView* d_views = nullptr;
   uint32_t stage_bytes = 64;
+  bool poly = false;  // some admitted column has polynomial partitions
   uint64_t resident = 0, reserved = 0;
   uint64_t cap_items = 0;
   std::vector<Slot> slots;
@@ -203,12 +204,14 @@ void gpu_run(leco_server* s, Slot& sl) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, sl.stream);
     uint32_t sb;
+    bool poly;
     {
       std::lock_guard<std::mutex> lock(s->mu);
       sb = s->stage_bytes;
+      poly = s->poly;
     }
     if (e == cudaSuccess)
-      e = launch_batch_decode(s->d_views, sl.d_items, ni, sb, scan_config_lookup(0, LECO_U64, sb), sl.d_stat,
+      e = launch_batch_decode(s->d_views, sl.d_items, ni, sb, scan_config_lookup(0, LECO_U64, sb), poly, sl.d_stat,
                               sl.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_stat, sl.d_stat, 4, cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess && staged_ranges)
@@ -435,6 +438,7 @@ leco_status admit_common(leco_server* s, leco_column* col, uint64_t n, int dtype
     if (cudaMemcpy(s->d_views + id, &s->h_views[id], sizeof(ColumnView), cudaMemcpyHostToDevice) != cudaSuccess)
       return LECO_ERR_CUDA;
     s->stage_bytes = std::max(s->stage_bytes, col->stage_bytes);
+    s->poly = s->poly || col->poly != nullptr;
   }
   ColSlot& c = s->cols[id];
   c.col = col;

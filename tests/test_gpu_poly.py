@@ -236,3 +236,44 @@ def test_poly_never_larger_than_linear(lc):
         b = lc.leco_encode(to_dev(v), lc.fixed(L), 1).stats()
         c = lc.leco_encode(to_dev(v), lc.fixed(L), 0).stats()
         assert a["total_bytes"] <= min(b["total_bytes"], c["total_bytes"])
+
+
+def test_poly_columns_in_batched_decode_and_server(lc):
+    """A batch plan (and its CUDA graph) over polynomial and linear columns takes the batched scan
+    with the polynomial loop; a server with a polynomial column answers lookups and range decodes
+    with the column's values."""
+    import torch
+
+    vals = [W.sine_mixture(150_001, seed=20), W.cfg1(120_000), W.sine_mixture(90_000, p2=7e3, seed=21)]
+    cols = [lc.leco_encode(to_dev(vals[0]), lc.fixed(4096), POLY), lc.leco_encode(to_dev(vals[1]), lc.fixed(1024), 1),
+            lc.leco_encode(to_dev(vals[2]), lc.variable(0.03), POLY)]
+    outs = [torch.full((len(v),), -1, dtype=torch.int64, device="cuda") for v in vals]
+    plan = lc.leco_batch_plan_create(cols, outs)
+    for runner in (lc.leco_batch_plan_run, lc.leco_batch_plan_run_graph):
+        for o in outs:
+            o.fill_(-1)
+        runner(plan)
+        torch.cuda.synchronize()
+        for v, o in zip(vals, outs):
+            assert (from_dev(o) == v).all()
+    plan.free()
+    s = lc.leco_server_create(4 << 30, max_batch_values=1 << 20, max_batch_lookups=1 << 14)
+    ids = [lc.leco_server_admit(s, c) for c in cols]
+    g = W.rng(22)
+    reqs = []
+    for k in range(200):
+        c = int(g.integers(0, 3))
+        n = len(vals[c])
+        if k % 2:
+            idx = g.integers(0, n, size=int(g.integers(1, 2000)), dtype=np.uint64)
+            out = np.empty(len(idx), dtype=np.uint64)
+            reqs.append((lc.leco_server_submit_lookup(s, ids[c], idx, out), out, vals[c][idx]))
+        else:
+            cnt = int(g.integers(1, 50_000))
+            b = int(g.integers(0, n - cnt + 1))
+            out = np.empty(cnt, dtype=np.uint64)
+            reqs.append((lc.leco_server_submit_range(s, ids[c], b, cnt, out), out, vals[c][b:b + cnt]))
+    for rid, out, want in reqs:
+        assert lc.leco_server_wait(s, rid) == lc.LECO_OK
+        assert np.array_equal(out, want)
+    s.destroy()
