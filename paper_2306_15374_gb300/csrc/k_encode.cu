@@ -379,9 +379,11 @@ constexpr uint32_t kPackSmem32 = kZzOffset32 + kStageData;
 // column's values (up to 4096 of them) leave room for their residuals after them
 __device__ __forceinline__ uint32_t pack_stage_cap(int dtype) { return dtype == LECO_U32 ? kStageData / 2 : kStageData; }
 
+template <bool POLY>
 __device__ __forceinline__ uint64_t residual_at(const Record* __restrict__ rec, const PolyAux* __restrict__ poly,
                                                 const Aux& a, uint64_t p, uint32_t x, uint64_t v) {
-  return zz_encode((int64_t)(v - (uint64_t)predict_aux(a, rec, poly, p, x)));
+  const int64_t pred = POLY ? predict_aux(a, rec, poly, p, x) : predict_aux_line(a, rec, p, x);
+  return zz_encode((int64_t)(v - (uint64_t)pred));
 }
 
 // contribution of a 64-bit field at bit f to the output word starting at bit wb
@@ -390,13 +392,16 @@ __device__ __forceinline__ uint64_t place64(uint64_t z, uint64_t f, uint64_t wb)
   return f >= wb ? z << (uint32_t)(f - wb) : z >> (uint32_t)(wb - f);
 }
 
+// POLY: the column may hold polynomial partitions (a separate instantiation keeps the constant and
+// linear packer as small as before)
+template <bool POLY>
 __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned char* st, unsigned char* ring,
                                                const Record* __restrict__ rec, const Aux* __restrict__ aux,
                                                const PolyCoef* __restrict__ pcoef, const PolyAux* __restrict__ poly,
                                                uint64_t p, uint64_t* __restrict__ words) {
   const Aux a = aux[p];
   const uint32_t b = w3_b(a.word3);
-  const bool pl = w3_poly(a.word3) != 0;
+  const bool pl = POLY && w3_poly(a.word3) != 0;
   const uint64_t off = w3_off(a.word3), endb = off + (uint64_t)s.N * b;
   const uint64_t off0 = pl ? off - kPolyBlockBits : off;  // first bit of the partition (its block)
   if (endb > off0) {
@@ -406,7 +411,7 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
       zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32)
                                : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
       for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
-        zs[x] = residual_at(rec, poly, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
+        zs[x] = residual_at<POLY>(rec, poly, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
       __syncthreads();
     }
     // phase 2: output words of [off0, endb): the polynomial block's five words, then the fields
@@ -424,7 +429,7 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
         const uint64_t l2 = lo > off ? lo : off;
         uint32_t x = (uint32_t)(l2 - off) / b;  // first field overlapping the word (< 2^30 bits in)
         for (uint64_t f = off + (uint64_t)x * b; f < hi; f += b, x++) {
-          const uint64_t z = zs ? zs[x] : residual_at(rec, poly, a, p, x, load_value(s.values, s.dtype, s.a + x));
+          const uint64_t z = zs ? zs[x] : residual_at<POLY>(rec, poly, a, p, x, load_value(s.values, s.dtype, s.a + x));
           acc |= f >= wb ? z << (uint32_t)(f - wb) : z >> (uint32_t)(wb - f);
         }
       }
@@ -439,6 +444,7 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
 
 constexpr int kPackBlock = 128;
 
+template <bool POLY>
 __global__ void __launch_bounds__(kPackBlock)
     k_pack(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
            const Aux* __restrict__ aux, const PolyCoef* __restrict__ pcoef, const PolyAux* __restrict__ poly,
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(kPackBlock)
     return s;
   };
   auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
-    pack_partition(s, st, ring, rec, aux, pcoef, poly, p, words);
+    pack_partition<POLY>(s, st, ring, rec, aux, pcoef, poly, p, words);
   };
   for_each_staged<1>(m, pack_stage_cap(dtype), get, body, ring, full, err);
 }
@@ -552,7 +558,7 @@ __global__ void __launch_bounds__(kPackBlock)
   auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
     const uint32_t c = find_col(part_base, ncols, p);
     const uint64_t p0 = part_base[c];
-    pack_partition(s, st, ring, rec + p0, aux + p0, nullptr, nullptr, p - p0, words + word_base[c]);
+    pack_partition<false>(s, st, ring, rec + p0, aux + p0, nullptr, nullptr, p - p0, words + word_base[c]);
   };
   for_each_staged<1>(P, pack_stage_cap(dtype), get, body, ring, full, err);
 }
@@ -666,8 +672,12 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || m == 0) return e;
   const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
-  k_pack<<<resident_grid(k_pack, kPackBlock, m, smem), kPackBlock, smem, st>>>(values, dtype, rec, aux, pcoef, poly,
-                                                                               m, n, words, err);
+  if (pcoef)
+    k_pack<true><<<resident_grid(k_pack<true>, kPackBlock, m, smem), kPackBlock, smem, st>>>(
+        values, dtype, rec, aux, pcoef, poly, m, n, words, err);
+  else
+    k_pack<false><<<resident_grid(k_pack<false>, kPackBlock, m, smem), kPackBlock, smem, st>>>(
+        values, dtype, rec, aux, nullptr, nullptr, m, n, words, err);
   return cudaGetLastError();
 }
 
