@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
         "orc_delta_bits": (i32, [vp, u64, u64]),
         "orc_split_cost": (i64, [vp, u64, u64, i32]),
         "orc_var_split": (u64, [vp, u64, dbl, u64, u64, u64, i32, vp]),
+        "orc_var_split_seeded": (u64, [vp, u64, dbl, u64, u64, u64, i32, vp]),
+        "orc_chunk_seed": (u64, [vp, u64, u64]),
         "orc_var_merge_seq": (u64, [vp, vp, u64, i32, u64, u64, vp]),
         "orc_var_merge_round": (u64, [vp, vp, u64, i32, u64, u64, vp]),
         "orc_splitmix64": (u64, [u64]),
@@ -214,11 +216,18 @@ def fixed_starts(n: int, L: int) -> np.ndarray:
 
 
 def var_split(values, tau: float = 0.1, sm_bits: int = SM_BITS, cap: int = DEFAULT_CAP,
-              chunk: int = DEFAULT_CHUNK, metric: int = METRIC_TILDE) -> np.ndarray:
+              chunk: int = DEFAULT_CHUNK, metric: int = METRIC_TILDE, seeded: bool = False) -> np.ndarray:
+    """Split phase (§3.2.2, R7); seeded: partitions grow from each chunk's seed both ways (R11)."""
     v = _u64(values)
     out = np.zeros(v.size + 1, dtype=np.uint64)
-    m = lib().orc_var_split(_p(v), v.size, float(tau), sm_bits, cap, chunk, metric, _p(out))
+    f = lib().orc_var_split_seeded if seeded else lib().orc_var_split
+    m = f(_p(v), v.size, float(tau), sm_bits, cap, chunk, metric, _p(out))
     return out[: m + 1].copy()
+
+
+def chunk_seed(values, a: int, e: int) -> int:
+    v = _u64(values)
+    return int(lib().orc_chunk_seed(_p(v), a, e))
 
 
 def var_merge_seq(values, starts, model: int = MODEL_LINEAR, sm_bits: int = SM_BITS,
@@ -242,11 +251,11 @@ def var_merge_round(values, starts, model: int = MODEL_LINEAR, sm_bits: int = SM
 
 
 def var_partition(values, tau: float = 0.1, model: int = MODEL_LINEAR, variant: str = "round",
-                  cap: int = DEFAULT_CAP, chunk: int = DEFAULT_CHUNK) -> np.ndarray:
+                  cap: int = DEFAULT_CAP, chunk: int = DEFAULT_CHUNK, seeded: bool = False) -> np.ndarray:
     """Split then merge (§3.2.2). variant 'round' uses chunked split + round merge; 'seq' the
-    paper's literal single sweep + sequential merge passes."""
+    paper's literal single sweep + sequential merge passes. seeded: the seeded split (R11)."""
     if variant == "round":
-        st = var_split(values, tau, SM_BITS, cap, chunk)
+        st = var_split(values, tau, SM_BITS, cap, chunk, seeded=seeded)
         st, _ = var_merge_round(values, st, model, SM_BITS, cap)
     elif variant == "seq":
         st = var_split(values, tau, SM_BITS, cap, 0)

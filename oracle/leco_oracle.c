@@ -62,6 +62,12 @@
  *      word3 bit 63 set, exact bit 0, s = 0; stream at off: T, K1, K2, K3 (64 bits each, K3 = 0
  *      for the quadratic), the exponent word s1 | s2 << 8 | s3 << 16, then residual k at
  *      off + 320 + b k. Variable partitioning and the size search keep the linear size (§3.2).
+ *  R11 seeded split (§3.2.2, selecting good starting positions: for a degree-k regressor, start
+ *      where the (k+1)-th order deltas are smallest): each chunk has one seed, the first window of
+ *      three values whose second-order delta has the shortest zigzag code; partitions grow from it
+ *      to the right with the greedy rule and, with the same rule on the values read backwards, to
+ *      the left; the seed and the chunk edge are cuts. (One seed per chunk: the paper's precedence
+ *      among seeds growing into each other does not arise.)
  */
 #include <math.h>
 #include <stdint.h>
@@ -777,6 +783,64 @@ uint64_t orc_var_split(const uint64_t* v, uint64_t n, double tau, uint64_t sm_bi
     }
   }
   starts_out[m] = n;
+  return m;
+}
+
+/*
+ * Seed of the chunk [a, e) for the seeded split (§3.2.2 "selecting good starting positions", R11):
+ * the first k in [a, e-3] whose second-order delta w_{k+2} - 2 w_{k+1} + w_k needs the fewest bits
+ * as a zigzag code (the linear regressor's smoothest window); a for chunks of fewer than 3 values.
+ */
+uint64_t orc_chunk_seed(const uint64_t* v, uint64_t a, uint64_t e) {
+  if (e - a < 3) return a;
+  uint64_t best = a;
+  int best_bits = 1000;
+  for (uint64_t k = a; k + 2 < e; k++) {
+    i128 d2 = (i128)(int64_t)v[k + 2] - 2 * (i128)(int64_t)v[k + 1] + (i128)(int64_t)v[k];
+    u128 z = d2 >= 0 ? (u128)d2 * 2 : (u128)(-d2) * 2 - 1;
+    int bits = bitlen_u128(z);
+    if (bits < best_bits) {
+      best_bits = bits;
+      best = k;
+    }
+  }
+  return best;
+}
+
+/*
+ * Seeded split (R11): per chunk, partitions grow away from the chunk's seed in both directions:
+ * [seed, e) by the greedy sweep of orc_var_split, and [a, seed) by the same sweep run on its values
+ * in reverse order (a partition that ends where the reversed sweep opened one starts right after
+ * it). The chunk edge and the seed always start a partition. starts_out needs n+1 entries;
+ * returns m.
+ */
+uint64_t orc_var_split_seeded(const uint64_t* v, uint64_t n, double tau, uint64_t sm_bits, uint64_t cap,
+                              uint64_t chunk, int metric, uint64_t* starts_out) {
+  if (n == 0) {
+    starts_out[0] = 0;
+    return 0;
+  }
+  if (chunk == 0) chunk = n;
+  uint64_t* tmp = (uint64_t*)malloc(sizeof(uint64_t) * (chunk + 1));
+  uint64_t* rev = (uint64_t*)malloc(sizeof(uint64_t) * (chunk + 1));
+  if (!tmp || !rev) orc_die("oom");
+  uint64_t m = 0;
+  for (uint64_t a = 0; a < n; a += chunk) {
+    uint64_t e = a + chunk < n ? a + chunk : n;
+    uint64_t seed = orc_chunk_seed(v, a, e);
+    if (seed > a) {
+      uint64_t len = seed - a;
+      for (uint64_t k = 0; k < len; k++) rev[k] = v[seed - 1 - k];
+      uint64_t q = orc_var_split(rev, len, tau, sm_bits, cap, 0, metric, tmp);
+      /* reversed partition [tmp[r], tmp[r+1]) = original [seed - tmp[r+1], seed - tmp[r]) */
+      for (uint64_t r = q; r >= 1; r--) starts_out[m++] = seed - tmp[r];
+    }
+    uint64_t q = orc_var_split(v + seed, e - seed, tau, sm_bits, cap, 0, metric, tmp);
+    for (uint64_t r = 0; r < q; r++) starts_out[m++] = seed + tmp[r];
+  }
+  starts_out[m] = n;
+  free(tmp);
+  free(rev);
   return m;
 }
 

@@ -745,3 +745,54 @@ def test_poly_model_never_loses_to_constant_or_linear(orc, L):
     assert orc.compressed_bytes(rp, wp) <= orc.compressed_bytes(rl, wl)
     if L == 100:
         assert orc.compressed_bytes(rp, wp) < 0.85 * orc.compressed_bytes(rl, wl)
+
+
+# ------------------------------------------------------------------ seeded split (§3.2.2, R11)
+
+def _zz_bits(d: int) -> int:
+    return (2 * d if d >= 0 else -2 * d - 1).bit_length()
+
+
+def test_chunk_seed_is_the_first_smoothest_window(orc):
+    """Brute force: the seed is the first k whose second-order delta w_{k+2} - 2w_{k+1} + w_k has
+    the shortest zigzag code (64-bit values read as int64)."""
+    g = W.rng(40)
+    for v in (W.piecewise_linear(3000, segments=6, mean_len=500, max_k=8, seed=1), W.timestamps_u32(3000, seed=2),
+              W.adversarial_u64(500), np.array([5, 9], dtype=np.uint64), g.integers(0, 1 << 64, 400, dtype=np.uint64)):
+        w = [s64(x) for x in v]
+        for a, e in ((0, len(v)), (1, len(v) - 1), (0, min(3, len(v)))):
+            if e - a < 3:
+                assert orc.chunk_seed(v, a, e) == a
+                continue
+            bits = [_zz_bits(w[k + 2] - 2 * w[k + 1] + w[k]) for k in range(a, e - 2)]
+            assert orc.chunk_seed(v, a, e) == a + bits.index(min(bits))
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.03, 0.1, 0.5])
+def test_seeded_split_grows_greedily_both_ways(orc, tau):
+    """Right of each chunk's seed the partitions follow the greedy rule; left of it they follow the
+    same rule on the values read backwards; chunk edges and seeds are cuts."""
+    for v in (W.piecewise_linear(3000, segments=6, mean_len=500, max_k=8, seed=1),
+              W.timestamps_u32(3000, seed=2), W.adversarial_u64(500)):
+        for chunk, cap in ((0, 1 << 24), (700, 1 << 24), (0, 50)):
+            st = orc.var_split(v, tau, orc.SM_BITS, cap, chunk, seeded=True)
+            n = len(v)
+            ch = chunk or n
+            for a in range(0, n, ch):
+                e = min(n, a + ch)
+                seed = orc.chunk_seed(v, a, e)
+                inside = [int(s) for s in st if a <= s <= e]
+                assert a in inside and seed in inside
+                right = np.array([s - seed for s in inside if s >= seed], dtype=np.uint64)
+                _check_split_greedy(orc, v[seed:e], right, tau, cap, 0)
+                if seed > a:
+                    left = np.array(sorted(seed - s for s in inside if s <= seed), dtype=np.uint64)
+                    _check_split_greedy(orc, v[a:seed][::-1].copy(), left, tau, cap, 0)
+
+
+def test_seeded_split_on_a_line_is_the_plain_split(orc):
+    """On exactly linear data every second-order delta is 0: each seed is its chunk's first value,
+    so the seeded split equals the left-to-right one."""
+    v = (np.arange(200_000, dtype=np.uint64) * np.uint64(977) + np.uint64(12345))
+    for tau in (0.0, 0.1):
+        assert (orc.var_split(v, tau, seeded=True) == orc.var_split(v, tau)).all()
