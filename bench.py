@@ -588,21 +588,29 @@ def run_var(args):
             "filter_ms": t_fil, "filter_gbs": (comp + 24) / (t_fil * 1e-3) / 1e9,
             "filter_prune_ms": t_pru, "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6,
         }
+        def var_encode(tau, seeded):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c = leco.leco_encode(dv, leco.variable(tau, seeded=seeded), leco.LECO_MODEL_LINEAR)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sc = c.stats()
+            cb = sc["record_bytes"] + sc["residual_bytes"] + 8 * (sc["partitions"] + 1)
+            c.free()
+            return {"tau": tau, "partitions": sc["partitions"], "ratio": cb / (n * vb),
+                    "partition_encode_ms": a.elapsed_time(b)}
+
+        # the seeded split (each chunk grown from its smoothest point both ways, §3.2.2)
+        out[name]["seeded"] = var_encode(args.tau, True)
         if args.tau_sweep:
-            # compression against tau (the partitioner's one knob, swept over the paper's range)
+            # compression against tau (the partitioner's one knob, swept over the paper's range),
+            # left-to-right and seeded
             sweep = []
             for tau in [float(t) for t in args.tau_sweep.split(",")]:
-                torch.cuda.synchronize()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                c = leco.leco_encode(dv, leco.variable(tau), leco.LECO_MODEL_LINEAR)
-                b.record(stream)
-                torch.cuda.synchronize()
-                sc = c.stats()
-                cb = sc["record_bytes"] + sc["residual_bytes"] + 8 * (sc["partitions"] + 1)
-                sweep.append({"tau": tau, "partitions": sc["partitions"], "ratio": cb / (n * vb),
-                              "partition_encode_ms": a.elapsed_time(b)})
-                c.free()
+                r = var_encode(tau, False)
+                r["seeded"] = var_encode(tau, True)
+                sweep.append(r)
             L_auto, _, n_eval = leco.leco_search_partition_size(dv, leco.LECO_MODEL_LINEAR)
             auto = leco.leco_encode(dv, leco.auto(), leco.LECO_MODEL_LINEAR)
             out[name]["tau_sweep"] = sweep

@@ -76,13 +76,18 @@ typedef enum { LECO_U32 = 0, LECO_U64 = 1 } leco_dtype;
  * partition-size search size partitions with the linear model under LECO_MODEL_POLY. */
 typedef enum { LECO_MODEL_CONSTANT = 0, LECO_MODEL_LINEAR = 1, LECO_MODEL_POLY = 2 } leco_model;
 
-typedef enum { LECO_PART_FIXED = 0, LECO_PART_VAR = 1, LECO_PART_AUTO = 2 } leco_part_kind;
+typedef enum { LECO_PART_FIXED = 0, LECO_PART_VAR = 1, LECO_PART_AUTO = 2, LECO_PART_VAR_SEEDED = 3 } leco_part_kind;
 
 /* Partition policy (§3.2). Fixed: partition j = positions [j L, (j+1) L) (§3.2.1), part_size = L
  * (1 .. 2^24). Variable: split + merge (§3.2.2); part_size caps a partition's length (1 .. 2^24,
  * 0 = 2^24); tau in [0, 1] is the split threshold coefficient (C <= tau * S_M with S_M = 256 bits,
  * one record). Auto: fixed partitions whose size leco_search_partition_size picks (§3.2.1) over
- * 1 .. part_size (0 = 10000, at most 16384) from a 1% sample with seed 0. */
+ * 1 .. part_size (0 = 10000, at most 16384) from a 1% sample with seed 0. Variable seeded: as
+ * variable, but each 65536-value chunk's split starts at the chunk's smoothest point (§3.2.2,
+ * selecting good starting positions: the first window of three values whose second-order delta has
+ * the shortest zigzag code) and grows partitions from there in both directions (the backward
+ * direction with the same greedy rule on the values read backwards); the column is a variable
+ * partition column. */
 typedef struct {
   int32_t kind;       /* leco_part_kind */
   uint32_t part_size; /* fixed: L; variable: length cap */

@@ -103,6 +103,100 @@ __device__ __forceinline__ void split_chunk(const T* __restrict__ v, uint64_t a,
   bitmap[wi] = word;
 }
 
+// Seeded split (§3.2.2, selecting good starting positions): the greedy sweep over the count values
+// u_k = v[base + dir k] (dir = +1, or -1 to read them backwards); a partition opens at u-index k when
+// u_k is refused, and mark(k) records it (the first partition, at k = 0, is not marked). Same rule,
+// cap and integer threshold as split_chunk; values are read eight ahead of the dependency chain.
+template <bool NARROW, typename T, typename Mark>
+__device__ __forceinline__ void sweep_dir(const T* __restrict__ v, uint64_t base, int dir, uint64_t count, uint32_t cap,
+                                          int64_t tfloor, Mark mark) {
+  using D = typename std::conditional<NARROW, int64_t, i128>::type;
+  const int64_t step = dir;
+  const T* p = v + base;
+  uint64_t i = 0;
+  int64_t prev = (int64_t)__ldg(p);
+  D dmax = 0, dmin = 0;
+  int cur = 0;
+  int64_t nxt[8];
+#pragma unroll
+  for (int u = 0; u < 8; u++) nxt[u] = 1 + u < count ? (int64_t)__ldg(p + step * (int64_t)(1 + u)) : 0;
+  for (uint64_t k0 = 1; k0 < count; k0 += 8) {
+    int64_t buf[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      buf[u] = nxt[u];
+      nxt[u] = k0 + 8 + u < count ? (int64_t)__ldg(p + step * (int64_t)(k0 + 8 + u)) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint64_t k = k0 + u;
+      if (k >= count) break;
+      const int64_t w = buf[u];
+      bool take = (k - i) < cap;
+      D nmax = dmax, nmin = dmin;
+      int next = 0;
+      if (take) {
+        const D d = (D)w - (D)prev;
+        if (k == i + 1) {
+          nmax = d;
+          nmin = d;
+        } else {
+          nmax = d > nmax ? d : nmax;
+          nmin = d < nmin ? d : nmin;
+        }
+        if (NARROW)
+          next = bitlen_u64((uint64_t)nmax - (uint64_t)nmin);
+        else
+          next = bitlen_u128((u128)(nmax - nmin));
+        const int64_t C = (int64_t)(k + 1 - i) * next - (int64_t)(k - i) * cur;
+        take = C <= tfloor;
+      }
+      if (take) {
+        cur = next;
+        dmax = nmax;
+        dmin = nmin;
+      } else {
+        mark(k);
+        i = k;
+        cur = 0;
+        dmax = 0;
+        dmin = 0;
+      }
+      prev = w;
+    }
+  }
+}
+
+// seed[c] = the first k of chunk c whose second-order delta w_{k+2} - 2 w_{k+1} + w_k has the
+// shortest zigzag code (the linear regressor's smoothest window); the chunk's first position when
+// it holds fewer than 3 values. A CTA per chunk; the (bits, k) minimum is reduced over the CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_chunk_seed(const T* __restrict__ v, uint64_t n, uint64_t* __restrict__ seed) {
+  __shared__ uint64_t red[8];
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint64_t a = c * kChunk, e = min(a + kChunk, n);
+    uint64_t best = ~0ull;  // bits << 32 | (k - a): the minimum is the smallest bits, then the first k
+    for (uint64_t k = a + threadIdx.x; k + 2 < e; k += blockDim.x) {
+      const i128 d2 = (i128)(int64_t)__ldg(v + k + 2) - 2 * (i128)(int64_t)__ldg(v + k + 1) + (i128)(int64_t)__ldg(v + k);
+      const u128 z = d2 >= 0 ? (u128)d2 * 2 : (u128)(-d2) * 2 - 1;
+      const uint64_t key = ((uint64_t)bitlen_u128(z) << 32) | (k - a);
+      best = key < best ? key : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t t = __shfl_down_sync(0xffffffffu, best, o);
+      best = t < best ? t : best;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; w++) best = red[w] < best ? red[w] : best;
+      seed[c] = best == ~0ull ? a : a + (best & 0xFFFFFFFFull);
+    }
+    __syncthreads();
+  }
+}
+
 // narrow[c] = every value of chunk c lies in (-2^62, 2^62) as int64 (a CTA per chunk)
 template <typename T>
 __global__ void k_chunk_narrow(const T* __restrict__ v, uint64_t n, uint8_t* __restrict__ narrow) {
@@ -121,18 +215,40 @@ __global__ void k_chunk_narrow(const T* __restrict__ v, uint64_t n, uint8_t* __r
   }
 }
 
+// one chunk of the seeded split: partitions grow from the chunk's seed to the right, and to the
+// left by the same sweep over the values read backwards (a partition refused there at u-index k
+// starts at seed - k); the chunk edge and the seed are cuts. The thread owns the chunk's words.
+template <bool NARROW, typename T>
+__device__ __forceinline__ void split_chunk_seeded(const T* __restrict__ v, uint64_t a, uint64_t e, uint64_t seed,
+                                                   uint32_t cap, int64_t tfloor, uint64_t* __restrict__ bitmap) {
+  for (uint64_t w = a >> 6; w <= ((e - 1) >> 6); w++) bitmap[w] = 0;
+  auto set = [&](uint64_t pos) { bitmap[pos >> 6] |= 1ull << (pos & 63); };
+  set(a);
+  set(seed);
+  if (seed > a) sweep_dir<NARROW>(v, seed - 1, -1, seed - a, cap, tfloor, [&](uint64_t k) { set(seed - k); });
+  sweep_dir<NARROW>(v, seed, 1, e - seed, cap, tfloor, [&](uint64_t k) { set(seed + k); });
+}
+
+// seeds: nullptr for the left-to-right split, else each chunk's seed (k_chunk_seed)
 template <typename T>
 __global__ void k_split(const T* __restrict__ values, uint64_t n, uint32_t cap, int64_t tfloor,
-                        const uint8_t* __restrict__ narrow, uint64_t* __restrict__ bitmap) {
+                        const uint8_t* __restrict__ narrow, const uint64_t* __restrict__ seeds,
+                        uint64_t* __restrict__ bitmap) {
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
        c += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t a = c * kChunk;
     const uint64_t e = min(a + kChunk, n);
-    if (narrow[c])
+    if (seeds) {
+      if (narrow[c])
+        split_chunk_seeded<true>(values, a, e, seeds[c], cap, tfloor, bitmap);
+      else
+        split_chunk_seeded<false>(values, a, e, seeds[c], cap, tfloor, bitmap);
+    } else if (narrow[c]) {
       split_chunk<true>(values, a, e, cap, tfloor, bitmap);
-    else
+    } else {
       split_chunk<false>(values, a, e, cap, tfloor, bitmap);
+    }
   }
 }
 
@@ -479,7 +595,7 @@ cudaError_t search_partition_size(const void* values, int dtype, uint64_t n, int
 
 // Runs split + merge; writes m+1 starts to starts_out (capacity n+1) and m to *m_out.
 cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
-                          int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
+                          int model, bool seeded, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
   *m_out = 0;
   if (n == 0) {
     const uint64_t zero = 0;
@@ -490,6 +606,7 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
   const double thresh = tau * (double)kSmBits;
   const uint64_t nw = (n + 63) / 64;
   uint64_t *bitmap = nullptr, *cnt = nullptr, *pos = nullptr, *scan_scratch = nullptr, *d_total = nullptr;
+  uint64_t* seeds = nullptr;
   cudaError_t e = cudaSuccess;
   const uint64_t scan_elems = nw / 2048 + 2;
 #define LECO_TRY(x)          \
@@ -508,14 +625,19 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
     // sweeps are serial per chunk, so each gets a warp of its own SM slot (one-warp blocks)
     const int64_t tfloor = thresh < 4.0e18 ? (int64_t)floor(thresh) : INT64_MAX;
     uint8_t* narrow = reinterpret_cast<uint8_t*>(cnt);  // scratch: cnt is not used until the popcount
+    if (seeded) LECO_TRY(dalloc(&seeds, nchunks, st));
     if (dtype == LECO_U32) {
       k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint32_t*>(values), n, narrow);
+      if (seeded)
+        k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint32_t*>(values), n, seeds);
       k_split<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(static_cast<const uint32_t*>(values), n, cap, tfloor, narrow,
-                                                         bitmap);
+                                                         seeds, bitmap);
     } else {
       k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint64_t*>(values), n, narrow);
+      if (seeded)
+        k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint64_t*>(values), n, seeds);
       k_split<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(static_cast<const uint64_t*>(values), n, cap, tfloor, narrow,
-                                                         bitmap);
+                                                         seeds, bitmap);
     }
     LECO_TRY(cudaGetLastError());
     k_popc<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, cnt);
@@ -532,6 +654,8 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
     pos = nullptr;
     cudaFreeAsync(bitmap, st);
     bitmap = nullptr;
+    if (seeds) cudaFreeAsync(seeds, st);
+    seeds = nullptr;
     cudaFreeAsync(scan_scratch, st);
     scan_scratch = nullptr;
 
@@ -611,6 +735,7 @@ cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau,
     if (e == cudaSuccess) *m_out = m;
   }
 done:
+  if (seeds) cudaFreeAsync(seeds, st);
   if (bitmap) cudaFreeAsync(bitmap, st);
   if (cnt) cudaFreeAsync(cnt, st);
   if (pos) cudaFreeAsync(pos, st);

@@ -338,12 +338,12 @@ leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtyp
   NvtxRange nvtx_range("leco_var_partition");
   if (!d_starts_out || !m_out || (n && !d_values) || !valid_dtype(dtype) || !valid_model(model))
     return LECO_ERR_INVALID_ARG;
-  if (policy.kind != LECO_PART_VAR || !(policy.tau >= 0.0 && policy.tau <= 1.0) ||
+  if ((policy.kind != LECO_PART_VAR && policy.kind != LECO_PART_VAR_SEEDED) || !(policy.tau >= 0.0 && policy.tau <= 1.0) ||
       policy.part_size > kMaxPartLen)
     return LECO_ERR_INVALID_ARG;
   const uint32_t cap = policy.part_size ? policy.part_size : kMaxPartLen;
-  return from_cuda(var_partition(d_values, dtype, n, policy.tau, cap, sizing_model(model), d_starts_out, m_out,
-                                 (cudaStream_t)stream));
+  return from_cuda(var_partition(d_values, dtype, n, policy.tau, cap, sizing_model(model),
+                                 policy.kind == LECO_PART_VAR_SEEDED, d_starts_out, m_out, (cudaStream_t)stream));
 }
 
 leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
@@ -383,13 +383,14 @@ leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
     c->L = policy.part_size;
     c->m = (n + c->L - 1) / c->L;
     s = alloc_meta(c, st);
-  } else if (policy.kind == LECO_PART_VAR) {
+  } else if (policy.kind == LECO_PART_VAR || policy.kind == LECO_PART_VAR_SEEDED) {
     if (!(policy.tau >= 0.0 && policy.tau <= 1.0) || policy.part_size > kMaxPartLen) {
       delete c;
       return LECO_ERR_INVALID_ARG;
     }
     c->tau = policy.tau;
     c->L = 0;
+    c->kind = LECO_PART_VAR;  // the seeded split gives an ordinary variable partition column
     uint64_t* tmp = nullptr;
     cudaError_t e = dev_alloc((void**)&tmp, 8 * (n + 1), st);
     if (e != cudaSuccess) {

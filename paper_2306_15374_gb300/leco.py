@@ -30,6 +30,7 @@ LECO_MODEL_POLY = 2  # per partition: constant, linear, quadratic or cubic, by e
 LECO_PART_FIXED = 0
 LECO_PART_VAR = 1
 LECO_PART_AUTO = 2
+LECO_PART_VAR_SEEDED = 3  # variable, each chunk's split grown from its smoothest point both ways
 LECO_FILTER_PRUNE = 1
 LECO_FILTER_DECODE_ALL = 2
 
@@ -85,8 +86,8 @@ def fixed(L: int) -> PartitionPolicy:
     return PartitionPolicy(LECO_PART_FIXED, int(L), 0.0)
 
 
-def variable(tau: float = 0.03, cap: int = 0) -> PartitionPolicy:
-    return PartitionPolicy(LECO_PART_VAR, int(cap), float(tau))
+def variable(tau: float = 0.03, cap: int = 0, seeded: bool = False) -> PartitionPolicy:
+    return PartitionPolicy(LECO_PART_VAR_SEEDED if seeded else LECO_PART_VAR, int(cap), float(tau))
 
 
 def auto(max_len: int = 0) -> PartitionPolicy:
