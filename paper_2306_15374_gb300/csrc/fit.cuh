@@ -402,15 +402,6 @@ __host__ __device__ __forceinline__ PolyAux poly_aux_from(const int64_t* K, cons
   return r;
 }
 
-__device__ __forceinline__ i128 poly_horner(const PolyAux& q, uint64_t x) {
-  const u128 X = x;
-  u128 F = ((u128)q.a[3][1] << 64) | q.a[3][0];
-  F = F * X + (((u128)q.a[2][1] << 64) | q.a[2][0]);
-  F = F * X + (((u128)q.a[1][1] << 64) | q.a[1][0]);
-  F = F * X + (((u128)q.a[0][1] << 64) | q.a[0][0]);
-  return (i128)F;
-}
-
 // one polynomial candidate's grid (lane 0 of the fitting warp)
 struct PolyGrid {
   int64_t K[3];
@@ -462,20 +453,45 @@ struct FitChoice {
   uint32_t b;
 };
 
+// The polynomial model's fit runs as four phases, each its own kernel so that none carries the
+// others' registers: moments (a warp per partition), plan (a thread: every candidate's parameters),
+// ranges (a warp: the residual ranges under them), choice (a thread: sizes and the record).
+
+// phase 1 result: min, max and the Gram moments S_j = sum p_j(x) w_x (S_1 is the line's moment)
+struct PolyMom {
+  i128 S[3];
+  int64_t mx, mn;
+};
+static_assert(sizeof(PolyMom) == 64, "poly moments layout");
+
+// phase 2 result
+struct PolyPlan {
+  FitParams PC, PL;  // constant and linear parameters (as those models solve them)
+  PolyGrid G[2];     // quadratic and cubic grids (valid = 0: the candidate does not apply)
+  PolyAux Q[2];      // their F as 128-bit monomial coefficients
+  int32_t fast[2];   // |floor(F / 2^S)| is bounded so that every residual fits int64 (see poly_plan)
+  int32_t pad[2];
+};
+
+// phase 3 result
+struct PolyRange {
+  int64_t lo, hi;   // the line's residual range (not fallback)
+  uint64_t zmax;    // the fallback's widest zigzag residual
+  int64_t plo[2], phi[2];
+  int32_t bad[2];   // a residual outside int64: the candidate does not apply
+};
+
 __device__ __forceinline__ int64_t poly_value_at(const uint32_t* v32, const uint64_t* v64, bool u32, uint32_t x) {
   return u32 ? (int64_t)__ldg(v32 + x) : (int64_t)__ldg(v64 + x);
 }
 
-__device__ __forceinline__ uint64_t shfl_u64(uint64_t v) { return __shfl_sync(0xffffffffu, (unsigned long long)v, 0); }
-
-// The polynomial model's fit of [a, a+N) by one warp (lane = rank); the result in every lane.
-__device__ FitChoice fit_choose_warp(const void* __restrict__ values, int dtype, uint64_t a, uint32_t N, uint32_t lane) {
+// phase 1 by one warp; the result in lane 0
+__device__ PolyMom poly_moments_warp(const void* __restrict__ values, int dtype, uint64_t a, uint32_t N,
+                                     uint32_t lane) {
   const bool u32 = dtype == LECO_U32;
   const uint32_t* v32 = static_cast<const uint32_t*>(values) + a;
   const uint64_t* v64 = static_cast<const uint64_t*>(values) + a;
   const bool poly_len = N >= kPolyMinLen && N <= kPolyMaxLen;
-
-  // pass 1
   int64_t mx = INT64_MIN, mn = INT64_MAX;
   i128 Sm[3] = {0, 0, 0};
   const int64_t nm1 = (int64_t)N - 1;
@@ -492,107 +508,149 @@ __device__ FitChoice fit_choose_warp(const void* __restrict__ values, int dtype,
       Sm[2] += (i128)((5 * xp2 - c3) * xp) * w;
     }
   }
-  for (int j = 0; j < 3; j++) Sm[j] = warp_sum_i128(Sm[j]);
-  mx = warp_max_i64(mx);
-  mn = warp_min_i64(mn);
+  PolyMom M;
+  for (int j = 0; j < 3; j++) M.S[j] = warp_sum_i128(Sm[j]);
+  M.mx = warp_max_i64(mx);
+  M.mn = warp_min_i64(mn);
+  return M;
+}
 
-  // solve (lane 0), then broadcast
-  FitParams PC, PL;
-  PolyGrid G[2];
-  if (lane == 0) {
-    PC = solve_params(Sm[0], mx, mn, N, false);
-    PL = solve_params(Sm[0], mx, mn, N, N >= 2);
-    const bool elig = poly_len && (i128)mx - (i128)mn < ((i128)1 << 62);
-    G[0].valid = G[1].valid = 0;
-    if (elig) {
-      G[0] = poly_grid(Sm, N, 2);
-      G[1] = poly_grid(Sm, N, 3);
-    }
-  }
-  PL.B = (int64_t)shfl_u64((uint64_t)PL.B);
-  PL.fb_shift = (int64_t)shfl_u64((uint64_t)PL.fb_shift);
-  PL.s = __shfl_sync(0xffffffffu, PL.s, 0);
-  PL.fallback = __shfl_sync(0xffffffffu, PL.fallback, 0);
-  PolyAux Q[2];
-  int valid[2];
+// phase 2 (one thread)
+__device__ PolyPlan poly_plan(const PolyMom& M, uint32_t N) {
+  PolyPlan P;
+  P.PC = solve_params(M.S[0], M.mx, M.mn, N, false);
+  P.PL = solve_params(M.S[0], M.mx, M.mn, N, N >= 2);
+  const bool elig = N >= kPolyMinLen && N <= kPolyMaxLen && (i128)M.mx - (i128)M.mn < ((i128)1 << 62);
   for (int d = 0; d < 2; d++) {
-    valid[d] = __shfl_sync(0xffffffffu, G[d].valid, 0);
-    if (valid[d]) {
-      if (lane == 0) Q[d] = poly_aux_from(G[d].K, G[d].sj, G[d].S, N);
-      for (int k = 0; k < 4; k++) {
-        Q[d].a[k][0] = shfl_u64(Q[d].a[k][0]);
-        Q[d].a[k][1] = shfl_u64(Q[d].a[k][1]);
-      }
-      G[d].S = __shfl_sync(0xffffffffu, G[d].S, 0);
+    P.G[d].valid = 0;
+    P.fast[d] = 0;
+    if (elig) P.G[d] = poly_grid(M.S, N, 2 + d);
+    if (!P.G[d].valid) continue;
+    P.Q[d] = poly_aux_from(P.G[d].K, P.G[d].sj, P.G[d].S, N);
+    // |F(x)| <= sum_j |K_j| 2^(S - s_j) max|p_j| with max|p_1| < N, max|p_2| <= 2N^2, max|p_3| <= 2N^3;
+    // with q = floor(F / 2^S) in [-Bq, Bq], every residual w - q lies in [mn - Bq, mx + Bq]
+    const u128 n = N;
+    const u128 bnd[3] = {n, 2 * n * n, 2 * n * n * n};
+    u128 Fb = 0;
+    for (int j = 0; j < 3; j++) {
+      const int64_t k = P.G[d].K[j];
+      const u128 ak = (u128)(k < 0 ? -(i128)k : (i128)k) << (P.G[d].S - P.G[d].sj[j]);
+      Fb += ak * bnd[j];
     }
+    const i128 Bq = (i128)(Fb >> P.G[d].S) + 1;
+    P.fast[d] = Bq < ((i128)1 << 62) && (i128)M.mn - Bq > (i128)INT64_MIN && (i128)M.mx + Bq < (i128)INT64_MAX;
   }
+  return P;
+}
 
-  // pass 2
+// phase 3 by one warp; the result in lane 0. One pass: the line's residual (or the fallback's
+// zigzag residual) and both polynomials' residuals at the lane's positions x = lane + 32k, each
+// polynomial's F by forward differences over the stride 32 (exact 128-bit; x < 2^14, so every
+// bracket fits 64 bits).
+__device__ PolyRange poly_ranges_warp(const void* __restrict__ values, int dtype, uint64_t a, uint32_t N,
+                                      uint32_t lane, const PolyPlan* __restrict__ plan) {
+  const bool u32 = dtype == LECO_U32;
+  const uint32_t* v32 = static_cast<const uint32_t*>(values) + a;
+  const uint64_t* v64 = static_cast<const uint64_t*>(values) + a;
+  const int64_t B = plan->PL.B, fb = plan->PL.fb_shift;
+  const int32_t s = plan->PL.s, fallback = plan->PL.fallback;
+  bool valid[2], fast[2];
+  int32_t S[2];
+  u128 F[2], D1[2], D2[2], D3[2];
+  for (int d = 0; d < 2; d++) {
+    valid[d] = plan->G[d].valid != 0;
+    fast[d] = valid[d] && plan->fast[d];
+    S[d] = plan->G[d].S;
+    u128 c[4];
+    for (int k = 0; k < 4; k++) c[k] = valid[d] ? ((u128)plan->Q[d].a[k][1] << 64) | plan->Q[d].a[k][0] : 0;
+    const uint64_t x = lane, h = 32;
+    // fast: carried times 2^(64-S) modulo 2^128, so that floor(F / 2^S) mod 2^64 (= floor(F / 2^S),
+    // which the plan bounded inside int64) is the high half
+    const uint32_t up = fast[d] ? 64u - (uint32_t)S[d] : 0u;
+    F[d] = (((c[3] * x + c[2]) * x + c[1]) * x + c[0]) << up;
+    D1[d] = (c[1] * h + c[2] * (2 * x * h + h * h) + c[3] * (3 * x * x * h + 3 * x * h * h + h * h * h)) << up;
+    D2[d] = (c[2] * (2 * h * h) + c[3] * (6 * x * h * h + 6 * h * h * h)) << up;
+    D3[d] = (c[3] * (6 * h * h * h)) << up;
+  }
+  PolyRange R;
   int64_t lo = INT64_MAX, hi = INT64_MIN;
   uint64_t zmax = 0;
   int64_t plo[2] = {INT64_MAX, INT64_MAX}, phi[2] = {INT64_MIN, INT64_MIN};
   int bad[2] = {0, 0};
   for (uint32_t x = lane; x < N; x += 32) {
     const int64_t w = poly_value_at(v32, v64, u32, x);
-    if (PL.fallback) {
-      zmax = max(zmax, zz_encode((int64_t)((uint64_t)w - (uint64_t)PL.fb_shift)));
+    if (fallback) {
+      zmax = max(zmax, zz_encode((int64_t)((uint64_t)w - (uint64_t)fb)));
     } else {
-      const uint64_t F = (uint64_t)PL.B * x;
-      const int64_t r = w - (PL.s >= 0 ? ((int64_t)F >> PL.s) : (int64_t)(F << (-PL.s)));
+      const uint64_t Fl = (uint64_t)B * x;
+      const int64_t r = w - (s >= 0 ? ((int64_t)Fl >> s) : (int64_t)(Fl << (-s)));
       lo = min(lo, r);
       hi = max(hi, r);
     }
+#pragma unroll
     for (int d = 0; d < 2; d++) {
       if (!valid[d]) continue;
-      const i128 r = (i128)w - (poly_horner(Q[d], x) >> G[d].S);
-      if (r > (i128)INT64_MAX || r < (i128)INT64_MIN) {
-        bad[d] = 1;
+      if (fast[d]) {
+        const int64_t r = w - (int64_t)(uint64_t)(F[d] >> 64);
+        plo[d] = min(plo[d], r);
+        phi[d] = max(phi[d], r);
       } else {
-        plo[d] = min(plo[d], (int64_t)r);
-        phi[d] = max(phi[d], (int64_t)r);
+        const i128 r = (i128)w - ((i128)F[d] >> S[d]);
+        if (r > (i128)INT64_MAX || r < (i128)INT64_MIN) {
+          bad[d] = 1;
+        } else {
+          plo[d] = min(plo[d], (int64_t)r);
+          phi[d] = max(phi[d], (int64_t)r);
+        }
       }
+      F[d] += D1[d];
+      D1[d] += D2[d];
+      D2[d] += D3[d];
     }
   }
-  lo = warp_min_i64(lo);
-  hi = warp_max_i64(hi);
-  zmax = warp_max_u64(zmax);
+  R.lo = warp_min_i64(lo);
+  R.hi = warp_max_i64(hi);
+  R.zmax = warp_max_u64(zmax);
   for (int d = 0; d < 2; d++) {
-    plo[d] = warp_min_i64(plo[d]);
-    phi[d] = warp_max_i64(phi[d]);
-    bad[d] = __any_sync(0xffffffffu, bad[d]);
+    R.plo[d] = warp_min_i64(plo[d]);
+    R.phi[d] = warp_max_i64(phi[d]);
+    R.bad[d] = __any_sync(0xffffffffu, bad[d]);
   }
+  return R;
+}
 
-  // size the candidates (lane 0), then broadcast
+// phase 4 (one thread): size the four candidates (256 + N b for constant and linear, 576 + N b for
+// the polynomials, whose minimax intercept and width follow from their range as for the line) and
+// keep the smallest, ties to the earlier
+__device__ FitChoice poly_choose(const PolyMom& M, const PolyPlan& P, const PolyRange& R, uint32_t N) {
   FitChoice C;
-  if (lane == 0) {
-    C.R = finish_fit(PC, mn, mx, zmax);  // a constant fallback implies the linear one: same zmax
-    C.kind = 0;
-    C.b = C.R.b;
-    uint64_t best = kSmBits + (uint64_t)N * C.R.b;
-    const FitResult RL = finish_fit(PL, lo, hi, zmax);
-    if (kSmBits + (uint64_t)N * RL.b < best) {
-      best = kSmBits + (uint64_t)N * RL.b;
-      C.R = RL;
-      C.kind = 1;
-      C.b = RL.b;
-    }
-    for (int d = 0; d < 2; d++) {
-      if (!valid[d] || bad[d]) continue;
-      const i128 t = (i128)plo[d] + (((i128)phi[d] - (i128)plo[d] + 1) / 2);
-      const uint64_t z = max(zz_encode((int64_t)((i128)plo[d] - t)), zz_encode((int64_t)((i128)phi[d] - t)));
-      const uint32_t b = (uint32_t)bitlen_u64(z);
-      const uint64_t size = kSmBits + kPolyBlockBits + (uint64_t)N * b;
-      if (size < best) {
-        best = size;
-        C.kind = 2 + d;
-        C.b = b;
-        C.pc.T = (int64_t)t;
-        for (int j = 0; j < 3; j++) C.pc.K[j] = G[d].K[j];
-        C.pc.E = (uint64_t)G[d].sj[0] | ((uint64_t)G[d].sj[1] << 8) | ((uint64_t)G[d].sj[2] << 16);
-      }
+  C.R = finish_fit(P.PC, M.mn, M.mx, R.zmax);  // a constant fallback implies the linear one: same zmax
+  C.kind = 0;
+  C.b = C.R.b;
+  uint64_t best = kSmBits + (uint64_t)N * C.R.b;
+  const FitResult RL = finish_fit(P.PL, R.lo, R.hi, R.zmax);
+  if (kSmBits + (uint64_t)N * RL.b < best) {
+    best = kSmBits + (uint64_t)N * RL.b;
+    C.R = RL;
+    C.kind = 1;
+    C.b = RL.b;
+  }
+  for (int d = 0; d < 2; d++) {
+    if (!P.G[d].valid || R.bad[d]) continue;
+    const i128 t = (i128)R.plo[d] + (((i128)R.phi[d] - (i128)R.plo[d] + 1) / 2);
+    const uint64_t z = max(zz_encode((int64_t)((i128)R.plo[d] - t)), zz_encode((int64_t)((i128)R.phi[d] - t)));
+    const uint32_t b = (uint32_t)bitlen_u64(z);
+    const uint64_t size = kSmBits + kPolyBlockBits + (uint64_t)N * b;
+    if (size < best) {
+      best = size;
+      C.kind = 2 + d;
+      C.b = b;
+      C.pc.T = (int64_t)t;
+      for (int j = 0; j < 3; j++) C.pc.K[j] = P.G[d].K[j];
+      C.pc.E = (uint64_t)P.G[d].sj[0] | ((uint64_t)P.G[d].sj[1] << 8) | ((uint64_t)P.G[d].sj[2] << 16);
     }
   }
-  return C;  // meaningful in lane 0 (the only lane that writes the partition's outputs)
+  return C;
 }
 
 }  // namespace

@@ -162,36 +162,67 @@ __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
   }
 }
 
-// The polynomial model: one warp per partition chooses among constant, linear, quadratic and
-// cubic by exact size (fit_choose_warp); a polynomial partition's stream bits include its block.
+// The polynomial model (fit.cuh): four phases over all partitions, each its own kernel. Phases 1
+// and 3 read the values (a warp per partition), phases 2 and 4 are a thread per partition.
 __global__ void __launch_bounds__(kFitBlock)
-    k_fit_poly(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
-               uint32_t L, uint64_t m, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
-               PolyCoef* __restrict__ pcoef, uint32_t* __restrict__ max_b) {
+    k_poly_moments(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
+                   uint32_t L, uint64_t m, PolyMom* __restrict__ mom) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
   for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < m; p += nw) {
     const uint64_t a = part_begin(starts, L, n, p);
     const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
-    const FitChoice C = fit_choose_warp(values, dtype, a, N, lane);
-    if (lane == 0) {
-      Record r;
-      r.start = a;
-      if (C.kind >= 2) {
-        r.theta0 = 0.0;
-        r.theta1 = 0.0;
-        r.word3 = make_w3(0, C.b, 0, 0) | kPolyFlag;
-        pcoef[p] = C.pc;
-        lenbits[p] = kPolyBlockBits + (uint64_t)N * C.b;
-      } else {
-        r.theta0 = C.R.theta0;
-        r.theta1 = C.R.theta1;
-        r.word3 = make_w3(0, C.R.b, C.R.s, 1);
-        lenbits[p] = (uint64_t)N * C.R.b;
-      }
-      rec[p] = r;
-      if (C.b) atomicMax(max_b, C.b);
+    const PolyMom M = poly_moments_warp(values, dtype, a, N, lane);
+    if (lane == 0) mom[p] = M;
+  }
+}
+
+__global__ void k_poly_plan(const PolyMom* __restrict__ mom, const uint64_t* __restrict__ starts, uint32_t L,
+                            uint64_t n, uint64_t m, PolyPlan* __restrict__ plan) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - part_begin(starts, L, n, p));
+    plan[p] = poly_plan(mom[p], N);
+  }
+}
+
+__global__ void __launch_bounds__(kFitBlock)
+    k_poly_ranges(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
+                  uint32_t L, uint64_t m, const PolyPlan* __restrict__ plan, PolyRange* __restrict__ rng) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
+  for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < m; p += nw) {
+    const uint64_t a = part_begin(starts, L, n, p);
+    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
+    const PolyRange R = poly_ranges_warp(values, dtype, a, N, lane, plan + p);
+    if (lane == 0) rng[p] = R;
+  }
+}
+
+// the record (offset 0, set by the offset scan), stream bits, block and widest width of the choice
+__global__ void k_poly_choose(const PolyMom* __restrict__ mom, const PolyPlan* __restrict__ plan,
+                              const PolyRange* __restrict__ rng, const uint64_t* __restrict__ starts, uint32_t L,
+                              uint64_t n, uint64_t m, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
+                              PolyCoef* __restrict__ pcoef, uint32_t* __restrict__ max_b) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = part_begin(starts, L, n, p);
+    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
+    const FitChoice C = poly_choose(mom[p], plan[p], rng[p], N);
+    Record r;
+    r.start = a;
+    if (C.kind >= 2) {
+      r.theta0 = 0.0;
+      r.theta1 = 0.0;
+      r.word3 = make_w3(0, C.b, 0, 0) | kPolyFlag;
+      pcoef[p] = C.pc;
+      lenbits[p] = kPolyBlockBits + (uint64_t)N * C.b;
+    } else {
+      r.theta0 = C.R.theta0;
+      r.theta1 = C.R.theta1;
+      r.word3 = make_w3(0, C.R.b, C.R.s, 1);
+      lenbits[p] = (uint64_t)N * C.R.b;
     }
+    rec[p] = r;
+    if (C.b) atomicMax(max_b, C.b);
   }
 }
 
@@ -410,8 +441,33 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
     if (st && b) {
       zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32)
                                : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
-      for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
-        zs[x] = residual_at<POLY>(rec, poly, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
+      if (pl) {
+        // the thread's predictions T + (F(x) >> S) for x = tid, tid + blockDim, ... by forward
+        // differences of the cubic F over that stride, carried times 2^(64-S) modulo 2^128 so that
+        // the prediction's low 64 bits are the carried value's high half
+        const ulonglong2* row = reinterpret_cast<const ulonglong2*>(poly + p);
+        u128 c[4];
+        for (int k = 0; k < 4; k++) {
+          const ulonglong2 h = __ldg(row + k);
+          c[k] = ((u128)h.y << 64) | h.x;
+        }
+        const uint64_t x = threadIdx.x, h = blockDim.x;
+        const uint32_t up = 64u - ((uint32_t)w3_s(a.word3) & 63u);
+        u128 F = (((c[3] * x + c[2]) * x + c[1]) * x + c[0]) << up;
+        u128 D1 = (c[1] * h + c[2] * (2 * x * h + h * h) + c[3] * (3 * x * x * h + 3 * x * h * h + h * h * h)) << up;
+        u128 D2 = (c[2] * (2 * h * h) + c[3] * (6 * x * h * h + 6 * h * h * h)) << up;
+        const u128 D3 = (c[3] * (6 * h * h * h)) << up;
+        const uint64_t T = (uint64_t)a.A;
+        for (uint32_t xx = threadIdx.x; xx < s.N; xx += blockDim.x) {
+          zs[xx] = zz_encode((int64_t)((uint64_t)staged_value(st, s.dtype, xx) - (T + (uint64_t)(F >> 64))));
+          F += D1;
+          D1 += D2;
+          D2 += D3;
+        }
+      } else {
+        for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
+          zs[x] = residual_at<POLY>(rec, poly, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
+      }
       __syncthreads();
     }
     // phase 2: output words of [off0, endb): the polynomial block's five words, then the fields
@@ -615,11 +671,24 @@ cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess || m == 0) return e;
   if (model == LECO_MODEL_POLY) {
+    const uint64_t bm = (sizeof(PolyMom) * m + 255) & ~255ull, bp = (sizeof(PolyPlan) * m + 255) & ~255ull;
+    char* scr = nullptr;
+    e = dev_alloc((void**)&scr, bm + bp + sizeof(PolyRange) * m, st);
+    if (e != cudaSuccess) return e;
+    PolyMom* mom = reinterpret_cast<PolyMom*>(scr);
+    PolyPlan* plan = reinterpret_cast<PolyPlan*>(scr + bm);
+    PolyRange* rng = reinterpret_cast<PolyRange*>(scr + bm + bp);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fit_poly, kFitBlock, 0) != cudaSuccess || nb < 1) nb = 1;
-    const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, nb);
-    k_fit_poly<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, rec, lenbits, pcoef, max_b);
-    return cudaGetLastError();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_poly_ranges, kFitBlock, 0) != cudaSuccess || nb < 1) nb = 1;
+    const int wgrid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, nb);
+    k_poly_moments<<<grid_for((m + kFitWarps - 1) / kFitWarps, 1, 8), kFitBlock, 0, st>>>(values, dtype, n, starts,
+                                                                                         L, m, mom);
+    k_poly_plan<<<grid_for(m, 128, 8), 128, 0, st>>>(mom, starts, L, n, m, plan);
+    k_poly_ranges<<<wgrid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, plan, rng);
+    k_poly_choose<<<grid_for(m, 128, 8), 128, 0, st>>>(mom, plan, rng, starts, L, n, m, rec, lenbits, pcoef, max_b);
+    e = cudaGetLastError();
+    cudaFreeAsync(scr, st);
+    return e;
   }
   const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
   k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
