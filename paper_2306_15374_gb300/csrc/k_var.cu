@@ -21,6 +21,7 @@
 
 #include "fit.cuh"
 #include "leco_internal.cuh"
+#include "var_partition.cuh"
 
 namespace leco {
 
@@ -743,6 +744,11 @@ done:
   if (d_total) cudaFreeAsync(d_total, st);
 #undef LECO_TRY
   return e;
+}
+
+cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
+                          int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
+  return var_partition(values, dtype, n, tau, cap, model, false, starts_out, m_out, st);
 }
 
 }  // namespace leco

@@ -10,6 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "column.cuh"
+#include "var_partition.cuh"
 
 using namespace leco;
 

@@ -342,9 +342,8 @@ cudaError_t launch_random_access(const ColumnView& c, const uint64_t* idx, uint6
 cudaError_t search_partition_size(const void* values, int dtype, uint64_t n, int model, uint32_t N, double frac,
                                   uint64_t seed, uint32_t* best_L, uint64_t* best_bits, uint64_t* evals,
                                   cudaStream_t st);
-// seeded: each chunk's split grows from its seed both ways instead of from its first value
 cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
-                          int model, bool seeded, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st);
+                          int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st);
 
 int sm_count();
 // Stream-ordered device allocation from the library's own memory pool on the current device. The
