@@ -75,3 +75,22 @@ def test_host_side_argument_errors(built):
     assert L.leco_search_partition_size(None, 0, 1, 1, 100, 1.5, 0, None, ctypes.byref(L32), None,
                                         None) == leco.LECO_ERR_INVALID_ARG  # fraction above 1
     assert L.leco_search_partition_size(None, 0, 1, 1, 100, 0.01, 0, None, None, None, None) == leco.LECO_ERR_INVALID_ARG
+    # models: 0 constant, 1 linear, 2 polynomial; anything else is refused
+    assert L.leco_encode(None, 0, 1, leco.fixed(16), 3, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_encode(None, 0, 1, leco.fixed(16), -1, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks below fail first
+    assert L.leco_encode_with_starts(None, 0, 1, fake, 0, 3, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
+    # the allocation-free and the batched encode take constant and linear only
+    nw = ctypes.c_uint64(0)
+    assert L.leco_encode_fixed_noalloc(fake, 10, 1, 16, leco.LECO_MODEL_POLY, fake, fake, 100, ctypes.byref(nw),
+                                       None) == leco.LECO_ERR_INVALID_ARG
+    vals = (ctypes.c_void_p * 1)(fake)
+    ns, models, Ls = (ctypes.c_uint64 * 1)(10), (ctypes.c_int * 1)(leco.LECO_MODEL_POLY), (ctypes.c_uint32 * 1)(16)
+    outs = (ctypes.c_void_p * 1)()
+    assert L.leco_batch_encode(vals, ns, models, Ls, 1, 1, None, outs) == leco.LECO_ERR_INVALID_ARG
+    # variable partitioning takes the variable kinds (plain or seeded) and tau in [0, 1]
+    m_out = ctypes.c_uint64(0)
+    for pol in (leco.fixed(16), leco.auto(), leco.variable(1.5), leco.variable(-0.1, seeded=True)):
+        assert L.leco_var_partition(fake, 10, 1, pol, 1, fake, ctypes.byref(m_out), None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_encode(fake, 10, 1, leco.variable(2.0, seeded=True), 1, None, ctypes.byref(h)) == \
+        leco.LECO_ERR_INVALID_ARG

@@ -277,3 +277,32 @@ def test_poly_columns_in_batched_decode_and_server(lc):
         assert lc.leco_server_wait(s, rid) == lc.LECO_OK
         assert np.array_equal(out, want)
     s.destroy()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 63, 64, 65, 127, 4096, 4097])
+def test_poly_tiny_columns(lc, n):
+    """Empty and tiny columns under the polynomial model (one partition below, at and above the
+    64-value minimum, a ragged second partition): byte parity, decode, lookups, sums, round trip."""
+    import torch
+
+    v = W.sine_mixture(max(n, 1), p2=500.0, noise=2, seed=30)[:n]
+    dv = to_dev(v) if n else torch.empty(0, dtype=torch.int64, device="cuda")
+    col = lc.leco_encode(dv, lc.fixed(4096), POLY)
+    rec_b, words_b, _ = lc.leco_column_export(col)
+    rec, words = oracle.encode_fixed(v, 4096, POLY)
+    assert rec_b == rec.tobytes() and words_b == words.tobytes()
+    out = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+    lc.leco_decode_all(col, out)
+    assert (from_dev(out)[:n] == v).all()
+    if n:
+        idx = np.array([0, n - 1, n // 2], dtype=np.uint64)
+        o2 = torch.empty(3, dtype=torch.int64, device="cuda")
+        lc.leco_random_access(col, to_dev(idx), o2)
+        assert (from_dev(o2) == v[idx]).all()
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    lc.leco_filter_sum(col, 0, (1 << 64) - 1, res, flags=lc.LECO_FILTER_PRUNE)
+    r = from_dev(res)
+    assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == exact_sum(v, 0, (1 << 64) - 1)
+    blob = lc.leco_serialize(col)
+    assert lc.leco_serialize(lc.leco_deserialize(blob)) == blob
+    assert lc.leco_sync(col) == lc.LECO_OK
