@@ -74,9 +74,11 @@ leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_out
                               leco_stream_t stream);
 
 /* Fixed-partition encode of ncols columns at once (§3.2.1 partitions, §3.1 fit, §3.3 packing):
- * column c has n[c] values of `dtype` at d_vals[c] (device), model models[c] and partition size
- * L[c] (1 .. 2^24). Every stage runs over all columns in one launch (fit, offset scan, decode
- * table, tile descriptors, pack); one stream synchronization sizes the residual streams. out[c]
+ * column c has n[c] values of `dtype` at d_vals[c] (device), model models[c] (constant, linear or
+ * polynomial, mixed freely) and partition size L[c] (1 .. 2^24). Every stage runs over all columns
+ * in one launch (fit, offset scan, decode table, tile descriptors, pack; the polynomial columns' fit
+ * adds its four phases over all their partitions); one stream synchronization sizes the residual
+ * streams. out[c]
  * receives a column identical to leco_encode(d_vals[c], n[c], dtype, fixed(L[c]), models[c]);
  * the columns share their device blocks, which are released when the last of them is freed.
  * Errors: INVALID_ARG, OOM, CUDA (then no column is returned). */

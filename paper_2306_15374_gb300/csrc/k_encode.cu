@@ -163,49 +163,92 @@ __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
 }
 
 // The polynomial model (fit.cuh): four phases over all partitions, each its own kernel. Phases 1
-// and 3 read the values (a warp per partition), phases 2 and 4 are a thread per partition.
+// and 3 read the values (a warp per partition), phases 2 and 4 are a thread per partition. A map
+// says where partition p's values are: one column (OneColumn), or the polynomial columns of a
+// batch (BatchColumns; partitions of the batch's other columns are skipped).
+struct OneColumn {
+  const void* values;
+  uint64_t n;
+  const uint64_t* starts;
+  uint32_t L;
+  __device__ __forceinline__ bool get(uint64_t p, const void** v, uint64_t* a, uint32_t* N, uint32_t* slot) const {
+    *v = values;
+    *a = part_begin(starts, L, n, p);
+    *N = (uint32_t)(part_begin(starts, L, n, p + 1) - *a);
+    *slot = 0;
+    return true;
+  }
+};
+
+struct BatchColumns {
+  const EncCol* cols;
+  const uint64_t* part_base;
+  uint32_t ncols;
+  __device__ __forceinline__ bool get(uint64_t p, const void** v, uint64_t* a, uint32_t* N, uint32_t* slot) const {
+    const uint32_t c = find_col(part_base, ncols, p);
+    const EncCol col = cols[c];
+    if (col.model != LECO_MODEL_POLY) return false;
+    const uint64_t s = (p - part_base[c]) * (uint64_t)col.L;
+    *v = col.values;
+    *a = s;
+    *N = (uint32_t)((s + col.L < col.n ? s + col.L : col.n) - s);
+    *slot = c;
+    return true;
+  }
+};
+
+template <typename Map>
 __global__ void __launch_bounds__(kFitBlock)
-    k_poly_moments(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
-                   uint32_t L, uint64_t m, PolyMom* __restrict__ mom) {
+    k_poly_moments(const Map map, int dtype, uint64_t m, PolyMom* __restrict__ mom) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
   for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < m; p += nw) {
-    const uint64_t a = part_begin(starts, L, n, p);
-    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
-    const PolyMom M = poly_moments_warp(values, dtype, a, N, lane);
+    const void* v;
+    uint64_t a;
+    uint32_t N, slot;
+    if (!map.get(p, &v, &a, &N, &slot)) continue;
+    const PolyMom M = poly_moments_warp(v, dtype, a, N, lane);
     if (lane == 0) mom[p] = M;
   }
 }
 
-__global__ void k_poly_plan(const PolyMom* __restrict__ mom, const uint64_t* __restrict__ starts, uint32_t L,
-                            uint64_t n, uint64_t m, PolyPlan* __restrict__ plan) {
+template <typename Map>
+__global__ void k_poly_plan(const Map map, uint64_t m, const PolyMom* __restrict__ mom, PolyPlan* __restrict__ plan) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - part_begin(starts, L, n, p));
-    plan[p] = poly_plan(mom[p], N);
+    const void* v;
+    uint64_t a;
+    uint32_t N, slot;
+    if (map.get(p, &v, &a, &N, &slot)) plan[p] = poly_plan(mom[p], N);
   }
 }
 
+template <typename Map>
 __global__ void __launch_bounds__(kFitBlock)
-    k_poly_ranges(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
-                  uint32_t L, uint64_t m, const PolyPlan* __restrict__ plan, PolyRange* __restrict__ rng) {
+    k_poly_ranges(const Map map, int dtype, uint64_t m, const PolyPlan* __restrict__ plan, PolyRange* __restrict__ rng) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
   for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < m; p += nw) {
-    const uint64_t a = part_begin(starts, L, n, p);
-    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
-    const PolyRange R = poly_ranges_warp(values, dtype, a, N, lane, plan + p);
+    const void* v;
+    uint64_t a;
+    uint32_t N, slot;
+    if (!map.get(p, &v, &a, &N, &slot)) continue;
+    const PolyRange R = poly_ranges_warp(v, dtype, a, N, lane, plan + p);
     if (lane == 0) rng[p] = R;
   }
 }
 
 // the record (offset 0, set by the offset scan), stream bits, block and widest width of the choice
-__global__ void k_poly_choose(const PolyMom* __restrict__ mom, const PolyPlan* __restrict__ plan,
-                              const PolyRange* __restrict__ rng, const uint64_t* __restrict__ starts, uint32_t L,
-                              uint64_t n, uint64_t m, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
-                              PolyCoef* __restrict__ pcoef, uint32_t* __restrict__ max_b) {
+// (max_b[slot]: the column's)
+template <typename Map>
+__global__ void k_poly_choose(const Map map, uint64_t m, const PolyMom* __restrict__ mom,
+                              const PolyPlan* __restrict__ plan, const PolyRange* __restrict__ rng,
+                              Record* __restrict__ rec, uint64_t* __restrict__ lenbits, PolyCoef* __restrict__ pcoef,
+                              uint32_t* __restrict__ max_b) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t a = part_begin(starts, L, n, p);
-    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
+    const void* v;
+    uint64_t a;
+    uint32_t N, slot;
+    if (!map.get(p, &v, &a, &N, &slot)) continue;
     const FitChoice C = poly_choose(mom[p], plan[p], rng[p], N);
     Record r;
     r.start = a;
@@ -222,7 +265,7 @@ __global__ void k_poly_choose(const PolyMom* __restrict__ mom, const PolyPlan* _
       lenbits[p] = (uint64_t)N * C.R.b;
     }
     rec[p] = r;
-    if (C.b) atomicMax(max_b, C.b);
+    if (C.b) atomicMax(max_b + slot, C.b);
   }
 }
 
@@ -552,6 +595,7 @@ __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
   for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < P; p += nw) {
     const uint32_t c = find_col(part_base, ncols, p);
     const EncCol col = cols[c];
+    if (col.model == LECO_MODEL_POLY) continue;  // fitted by the polynomial phases
     const uint64_t a = (p - part_base[c]) * (uint64_t)col.L;
     const uint32_t N = (uint32_t)((a + col.L < col.n ? a + col.L : col.n) - a);
     const FitResult R = fit_range<32>(col.values, dtype, a, N, col.model, lane, nullptr);
@@ -581,24 +625,29 @@ __global__ void k_set_offsets_multi(Record* __restrict__ rec, const uint64_t* __
   }
 }
 
-__global__ void k_aux_multi(const Record* __restrict__ rec, const EncCol* __restrict__ cols,
-                            const uint64_t* __restrict__ part_base, uint32_t ncols, uint64_t P,
-                            Aux* __restrict__ aux) {
+__global__ void k_aux_multi(const Record* __restrict__ rec, const PolyCoef* __restrict__ pcoef,
+                            const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base, uint32_t ncols,
+                            uint64_t P, Aux* __restrict__ aux, PolyAux* __restrict__ poly) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t c = find_col(part_base, ncols, p);
     const Record r = rec[p];
     const uint64_t e = p + 1 < part_base[c + 1] ? rec[p + 1].start : cols[c].n;
-    aux[p] = aux_of(r, e > r.start ? e - r.start : 0);
+    const uint64_t N = e > r.start ? e - r.start : 0;
+    if (w3_poly(r.word3) && pcoef && poly)
+      aux[p] = poly_entry(r, pcoef[p], (uint32_t)N, poly + p);
+    else
+      aux[p] = aux_of(r, N);
   }
 }
 
 // CTA per partition of every column (the column by a search over part_base)
+template <bool POLY>
 __global__ void __launch_bounds__(kPackBlock)
     k_pack_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
                  const uint64_t* __restrict__ word_base, uint32_t ncols, uint64_t P, int dtype,
-                 const Record* __restrict__ rec, const Aux* __restrict__ aux, uint64_t* __restrict__ words,
-                 uint32_t* __restrict__ err) {
+                 const Record* __restrict__ rec, const Aux* __restrict__ aux, const PolyCoef* __restrict__ pcoef,
+                 const PolyAux* __restrict__ poly, uint64_t* __restrict__ words, uint32_t* __restrict__ err) {
   __shared__ __align__(8) uint64_t full[1];
   extern __shared__ __align__(128) unsigned char ring[];
   auto get = [&](uint64_t p) {
@@ -614,7 +663,8 @@ __global__ void __launch_bounds__(kPackBlock)
   auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
     const uint32_t c = find_col(part_base, ncols, p);
     const uint64_t p0 = part_base[c];
-    pack_partition<false>(s, st, ring, rec + p0, aux + p0, nullptr, nullptr, p - p0, words + word_base[c]);
+    pack_partition<POLY>(s, st, ring, rec + p0, aux + p0, POLY ? pcoef + p0 : nullptr, POLY ? poly + p0 : nullptr,
+                         p - p0, words + word_base[c]);
   };
   for_each_staged<1>(P, pack_stage_cap(dtype), get, body, ring, full, err);
 }
@@ -663,6 +713,30 @@ int resident_grid(K kern, int block, uint64_t work, uint32_t smem) {
   return (int)(work < cap ? work : cap);
 }
 
+// the four polynomial phases over partitions [0, m) of the map, with their scratch
+template <typename Map>
+cudaError_t launch_poly_fit(const Map& map, int dtype, uint64_t m, Record* rec, uint64_t* lenbits, PolyCoef* pcoef,
+                            uint32_t* max_b, cudaStream_t st) {
+  const uint64_t bm = (sizeof(PolyMom) * m + 255) & ~255ull, bp = (sizeof(PolyPlan) * m + 255) & ~255ull;
+  char* scr = nullptr;
+  cudaError_t e = dev_alloc((void**)&scr, bm + bp + sizeof(PolyRange) * m, st);
+  if (e != cudaSuccess) return e;
+  PolyMom* mom = reinterpret_cast<PolyMom*>(scr);
+  PolyPlan* plan = reinterpret_cast<PolyPlan*>(scr + bm);
+  PolyRange* rng = reinterpret_cast<PolyRange*>(scr + bm + bp);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_poly_ranges<Map>, kFitBlock, 0) != cudaSuccess || nb < 1)
+    nb = 1;
+  const uint64_t wb = (m + kFitWarps - 1) / kFitWarps;
+  k_poly_moments<Map><<<grid_for(wb, 1, 8), kFitBlock, 0, st>>>(map, dtype, m, mom);
+  k_poly_plan<Map><<<grid_for(m, 128, 8), 128, 0, st>>>(map, m, mom, plan);
+  k_poly_ranges<Map><<<grid_for(wb, 1, nb), kFitBlock, 0, st>>>(map, dtype, m, plan, rng);
+  k_poly_choose<Map><<<grid_for(m, 128, 8), 128, 0, st>>>(map, m, mom, plan, rng, rec, lenbits, pcoef, max_b);
+  e = cudaGetLastError();
+  cudaFreeAsync(scr, st);
+  return e;
+}
+
 cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t* starts,
                        uint32_t L, uint64_t m, int model, Record* rec, uint64_t* lenbits, PolyCoef* pcoef,
                        uint32_t* max_b, uint32_t* err, cudaStream_t st) {
@@ -670,26 +744,8 @@ cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t
   if (model == LECO_MODEL_POLY && !pcoef) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess || m == 0) return e;
-  if (model == LECO_MODEL_POLY) {
-    const uint64_t bm = (sizeof(PolyMom) * m + 255) & ~255ull, bp = (sizeof(PolyPlan) * m + 255) & ~255ull;
-    char* scr = nullptr;
-    e = dev_alloc((void**)&scr, bm + bp + sizeof(PolyRange) * m, st);
-    if (e != cudaSuccess) return e;
-    PolyMom* mom = reinterpret_cast<PolyMom*>(scr);
-    PolyPlan* plan = reinterpret_cast<PolyPlan*>(scr + bm);
-    PolyRange* rng = reinterpret_cast<PolyRange*>(scr + bm + bp);
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_poly_ranges, kFitBlock, 0) != cudaSuccess || nb < 1) nb = 1;
-    const int wgrid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, nb);
-    k_poly_moments<<<grid_for((m + kFitWarps - 1) / kFitWarps, 1, 8), kFitBlock, 0, st>>>(values, dtype, n, starts,
-                                                                                         L, m, mom);
-    k_poly_plan<<<grid_for(m, 128, 8), 128, 0, st>>>(mom, starts, L, n, m, plan);
-    k_poly_ranges<<<wgrid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, plan, rng);
-    k_poly_choose<<<grid_for(m, 128, 8), 128, 0, st>>>(mom, plan, rng, starts, L, n, m, rec, lenbits, pcoef, max_b);
-    e = cudaGetLastError();
-    cudaFreeAsync(scr, st);
-    return e;
-  }
+  if (model == LECO_MODEL_POLY) return launch_poly_fit(OneColumn{values, n, starts, L}, dtype, m, rec, lenbits, pcoef,
+                                                        max_b, st);
   const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
   k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
   return cudaGetLastError();
@@ -751,13 +807,17 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
 }
 
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
-                             Record* rec, uint64_t* lenbits, uint32_t* max_b, uint32_t* err, cudaStream_t st) {
+                             Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b, uint32_t* err,
+                             cudaStream_t st) {
   (void)err;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t) * (ncols ? ncols : 1), st);
   if (e != cudaSuccess || P == 0) return e;
   const int grid = grid_for((P + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
   k_fit_multi<<<grid, kFitBlock, 0, st>>>(cols, part_base, ncols, P, dtype, rec, lenbits, max_b);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && pcoef)
+    e = launch_poly_fit(BatchColumns{cols, part_base, ncols}, dtype, P, rec, lenbits, pcoef, max_b, st);
+  return e;
 }
 
 uint64_t offsets_multi_scratch_elems(uint64_t P) { return P + (P + kPrefixTile - 1) / kPrefixTile + 2; }
@@ -775,24 +835,29 @@ cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_aux_multi(const Record* rec, const EncCol* cols, const uint64_t* part_base, uint32_t ncols,
-                             uint64_t P, Aux* aux, cudaStream_t st) {
+cudaError_t launch_aux_multi(const Record* rec, const PolyCoef* pcoef, const EncCol* cols, const uint64_t* part_base,
+                             uint32_t ncols, uint64_t P, Aux* aux, PolyAux* poly, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
-  k_aux_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, cols, part_base, ncols, P, aux);
+  k_aux_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, pcoef, cols, part_base, ncols, P, aux, poly);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
                               const uint64_t* col_bits, uint32_t ncols, uint64_t P, uint64_t W, int dtype,
-                              const Record* rec, const Aux* aux, uint64_t* words, uint32_t* err, cudaStream_t st) {
+                              const Record* rec, const Aux* aux, const PolyCoef* pcoef, const PolyAux* poly,
+                              uint64_t* words, uint32_t* err, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
   k_zero_bounds_multi<<<grid_for(P > ncols ? P : ncols, 256, 8), 256, 0, st>>>(aux, part_base, word_base, col_bits,
                                                                                 ncols, P, words);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || P == 0) return e;
   const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
-  k_pack_multi<<<resident_grid(k_pack_multi, kPackBlock, P, smem), kPackBlock, smem, st>>>(
-      cols, part_base, word_base, ncols, P, dtype, rec, aux, words, err);
+  if (pcoef)
+    k_pack_multi<true><<<resident_grid(k_pack_multi<true>, kPackBlock, P, smem), kPackBlock, smem, st>>>(
+        cols, part_base, word_base, ncols, P, dtype, rec, aux, pcoef, poly, words, err);
+  else
+    k_pack_multi<false><<<resident_grid(k_pack_multi<false>, kPackBlock, P, smem), kPackBlock, smem, st>>>(
+        cols, part_base, word_base, ncols, P, dtype, rec, aux, nullptr, nullptr, words, err);
   return cudaGetLastError();
 }
 

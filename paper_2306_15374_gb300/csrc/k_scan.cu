@@ -723,38 +723,51 @@ __device__ int poly_part_bounds(const ColumnView& c, const Aux& a, uint64_t p, u
 // k_tile_desc leaves out for polynomial partitions (their predictions are not monotone), from the
 // exact predictions; partitions with a line keep part_bounds. Tiles without a polynomial partition
 // are left as they are.
+__device__ void tile_poly_bounds_one(const ColumnView& c, TileDesc* __restrict__ tiles, uint64_t t, uint32_t lane) {
+  const uint64_t p0 = tiles[t].p0, np = tiles[t].np;
+  bool any = false;
+  for (uint64_t p = p0; p < p0 + np && !any; p++) any = w3_poly(ldg_aux(c.aux + p).word3) != 0;
+  if (!any) return;
+  const uint64_t i0 = t * kScanTile, i1 = min(i0 + kScanTile, c.n);
+  int kind = 0;
+  uint64_t vmin = 0, vmax = 0;
+  for (uint64_t p = p0; p < p0 + np; p++) {
+    const Aux a = ldg_aux(c.aux + p);
+    const uint64_t ps = max(i0, a.start), pe = min(i1, pstart(c, p + 1));
+    uint64_t lo = 0, hi = 0;
+    const int pk = w3_poly(a.word3) ? poly_part_bounds(c, a, p, ps - a.start, pe - a.start, lane, &lo, &hi)
+                                    : part_bounds(c.dtype, a, ps - a.start, pe - 1 - a.start, &lo, &hi);
+    if (p == p0) {
+      kind = pk;
+      vmin = lo;
+      vmax = hi;
+    } else {
+      kind = bounds_union(kind, &vmin, &vmax, pk, lo, hi);
+    }
+    if (kind == 0) break;
+  }
+  if (lane == 0) {
+    tiles[t].bounds = (uint32_t)kind;
+    tiles[t].vmin = kind ? vmin : 0;
+    tiles[t].vmax = kind ? vmax : ~0ull;
+  }
+}
+
 __global__ void k_tile_poly_bounds(const ColumnView c, TileDesc* __restrict__ tiles) {
-  const uint32_t lane = threadIdx.x & 31u;
   const uint64_t nt = scan_tiles(c.n);
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t t = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += nw) {
-    const uint64_t p0 = tiles[t].p0, np = tiles[t].np;
-    bool any = false;
-    for (uint64_t p = p0; p < p0 + np && !any; p++) any = w3_poly(ldg_aux(c.aux + p).word3) != 0;
-    if (!any) continue;
-    const uint64_t i0 = t * kScanTile, i1 = min(i0 + kScanTile, c.n);
-    int kind = 0;
-    uint64_t vmin = 0, vmax = 0;
-    for (uint64_t p = p0; p < p0 + np; p++) {
-      const Aux a = ldg_aux(c.aux + p);
-      const uint64_t ps = max(i0, a.start), pe = min(i1, pstart(c, p + 1));
-      uint64_t lo = 0, hi = 0;
-      const int pk = w3_poly(a.word3) ? poly_part_bounds(c, a, p, ps - a.start, pe - a.start, lane, &lo, &hi)
-                                      : part_bounds(c.dtype, a, ps - a.start, pe - 1 - a.start, &lo, &hi);
-      if (p == p0) {
-        kind = pk;
-        vmin = lo;
-        vmax = hi;
-      } else {
-        kind = bounds_union(kind, &vmin, &vmax, pk, lo, hi);
-      }
-      if (kind == 0) break;
-    }
-    if (lane == 0) {
-      tiles[t].bounds = (uint32_t)kind;
-      tiles[t].vmin = kind ? vmin : 0;
-      tiles[t].vmax = kind ? vmax : ~0ull;
-    }
+  for (uint64_t t = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += nw)
+    tile_poly_bounds_one(c, tiles, t, threadIdx.x & 31u);
+}
+
+// the same over the tiles of a batch of columns (columns without a polynomial table are skipped)
+__global__ void k_tile_poly_bounds_multi(const ColumnView* __restrict__ views, const uint64_t* __restrict__ tile_base,
+                                         uint32_t ncols, uint64_t T, TileDesc* __restrict__ tiles) {
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t g = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < T; g += nw) {
+    const uint32_t c = find_col(tile_base, ncols, g);
+    const ColumnView v = views[c];
+    if (v.poly) tile_poly_bounds_one(v, tiles + tile_base[c], g - tile_base[c], threadIdx.x & 31u);
   }
 }
 
@@ -841,10 +854,14 @@ cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t 
 }
 
 cudaError_t launch_tile_desc_multi(const ColumnView* views, const uint64_t* tile_base, uint32_t ncols, uint64_t T,
-                                   TileDesc* tiles, cudaStream_t st) {
+                                   bool poly, TileDesc* tiles, cudaStream_t st) {
   if (T == 0) return cudaSuccess;
   const uint64_t want = (T + 127) / 128, cap = (uint64_t)sm_count() * 8;
   k_tile_desc_multi<<<(int)(want < cap ? want : cap), 128, 0, st>>>(views, tile_base, ncols, T, tiles);
+  if (poly) {
+    const uint64_t wb = (T + 7) / 8;
+    k_tile_poly_bounds_multi<<<(int)(wb < cap ? wb : cap), 256, 0, st>>>(views, tile_base, ncols, T, tiles);
+  }
   return cudaGetLastError();
 }
 

@@ -288,9 +288,11 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   for (uint32_t c = 0; c < ncols; c++) {
     out[c] = nullptr;
     if ((n[c] && !d_vals[c]) || L[c] < 1 || L[c] > kMaxPartLen ||
-        (models[c] != LECO_MODEL_CONSTANT && models[c] != LECO_MODEL_LINEAR))
+        (models[c] != LECO_MODEL_CONSTANT && models[c] != LECO_MODEL_LINEAR && models[c] != LECO_MODEL_POLY))
       return LECO_ERR_INVALID_ARG;
   }
+  bool any_poly = false;
+  for (uint32_t c = 0; c < ncols; c++) any_poly = any_poly || models[c] == LECO_MODEL_POLY;
   if (ncols == 0) return LECO_OK;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
@@ -306,12 +308,14 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   }
   const uint64_t P = part_base[ncols], T = tile_base[ncols];
   auto a256 = [](uint64_t x) { return (x + 255) & ~255ull; };
-  // shared block 0: records | decode table | tile descriptors | status words
+  // shared block 0: records | decode table | tile descriptors | status words | polynomial table
   const uint64_t rec_b = a256(32 * (P ? P : 1)), tiles_b = a256(sizeof(TileDesc) * (T ? T : 1));
   const uint64_t stat_b = a256(4ull * ncols);
+  const uint64_t poly_b = any_poly ? a256(sizeof(PolyAux) * (P ? P : 1)) : 0;
   char* meta = nullptr;
-  // scratch: lenbits | scan scratch | col_bits | max_b | tables
-  const uint64_t scr_words = P + offsets_multi_scratch_elems(P) + 2 * (uint64_t)ncols + 8;
+  // scratch: lenbits | scan scratch | col_bits | max_b | polynomial blocks
+  const uint64_t pc_words = any_poly ? (sizeof(PolyCoef) / 8) * (P ? P : 1) : 0;
+  const uint64_t scr_words = P + offsets_multi_scratch_elems(P) + 2 * (uint64_t)ncols + 8 + pc_words;
   uint64_t* scr = nullptr;
   EncCol* d_ec = nullptr;
   uint64_t* d_bases = nullptr;  // part_base | tile_base | word_base
@@ -322,7 +326,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   std::vector<uint32_t> max_b(ncols);
   std::vector<ColumnView> views(ncols);
   uint64_t W = 0;
-  cudaError_t e = dev_alloc((void**)&meta, 2 * rec_b + tiles_b + stat_b, st);
+  cudaError_t e = dev_alloc((void**)&meta, 2 * rec_b + tiles_b + stat_b + poly_b, st);
   if (e == cudaSuccess) e = dev_alloc((void**)&scr, 8 * scr_words, st);
   if (e == cudaSuccess) e = dev_alloc((void**)&d_ec, sizeof(EncCol) * ncols, st);
   if (e == cudaSuccess) e = dev_alloc((void**)&d_bases, 8 * 3 * (uint64_t)(ncols + 1), st);
@@ -331,10 +335,12 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   Aux* aux = reinterpret_cast<Aux*>(meta + rec_b);
   TileDesc* tiles = reinterpret_cast<TileDesc*>(meta + 2 * rec_b);
   uint32_t* status = reinterpret_cast<uint32_t*>(meta + 2 * rec_b + tiles_b);
+  PolyAux* poly = any_poly ? reinterpret_cast<PolyAux*>(meta + 2 * rec_b + tiles_b + stat_b) : nullptr;
   uint64_t* lenbits = scr;
   uint64_t* offs = scr + P;
   uint64_t* d_colbits = offs + offsets_multi_scratch_elems(P);
   uint32_t* d_maxb = reinterpret_cast<uint32_t*>(d_colbits + ncols);
+  PolyCoef* pcoef = any_poly ? reinterpret_cast<PolyCoef*>(scr + scr_words - pc_words) : nullptr;
   uint64_t* d_part = d_bases;
   uint64_t* d_tile = d_bases + (ncols + 1);
   uint64_t* d_word = d_bases + 2 * (ncols + 1);
@@ -343,7 +349,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_part, part_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_tile, tile_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   // fit every partition of every column, then column-relative offsets and per-column totals
-  if (e == cudaSuccess) e = launch_fit_multi(d_ec, d_part, ncols, P, dtype, rec, lenbits, d_maxb, status, st);
+  if (e == cudaSuccess) e = launch_fit_multi(d_ec, d_part, ncols, P, dtype, rec, lenbits, pcoef, d_maxb, status, st);
   if (e == cudaSuccess) e = launch_offsets_multi(rec, lenbits, d_part, ncols, P, offs, d_colbits, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(col_bits.data(), d_colbits, 8 * ncols, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(max_b.data(), d_maxb, 4 * ncols, cudaMemcpyDeviceToHost, st);
@@ -372,16 +378,18 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
       v.words = words + word_base[c];
       v.starts = nullptr;
       v.tiles = tiles + tile_base[c];
-      v.poly = nullptr;  // the batched encode takes constant and linear columns
-      v.stage_bytes = stage_word_bytes(max_b[c]);
+      const bool pc = models[c] == LECO_MODEL_POLY;
+      v.poly = pc ? poly + part_base[c] : nullptr;
+      v.stage_bytes = stage_word_bytes(max_b[c]) + (pc ? kPolyStageExtra : 0);
       v.status = status + c;
     }
     e = cudaMemcpyAsync(d_word, word_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_views, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = launch_aux_multi(rec, d_ec, d_part, ncols, P, aux, st);
-  if (e == cudaSuccess) e = launch_tile_desc_multi(d_views, d_tile, ncols, T, tiles, st);
-  if (e == cudaSuccess) e = launch_pack_multi(d_ec, d_part, d_word, d_colbits, ncols, P, W, dtype, rec, aux, words, status, st);
+  if (e == cudaSuccess) e = launch_aux_multi(rec, pcoef, d_ec, d_part, ncols, P, aux, poly, st);
+  if (e == cudaSuccess) e = launch_tile_desc_multi(d_views, d_tile, ncols, T, any_poly, tiles, st);
+  if (e == cudaSuccess)
+    e = launch_pack_multi(d_ec, d_part, d_word, d_colbits, ncols, P, W, dtype, rec, aux, pcoef, poly, words, status, st);
   if (e == cudaSuccess) {
     sh = new (std::nothrow) leco_shared_blocks();
     if (!sh) e = cudaErrorMemoryAllocation;
@@ -405,11 +413,12 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
       col->rec = rec + part_base[c];
       col->aux = aux + part_base[c];
       col->tiles = tiles + tile_base[c];
+      col->poly = v.poly ? const_cast<PolyAux*>(v.poly) : nullptr;
       col->status = status + c;
       col->max_b = max_b[c];
       col->stage_bytes = v.stage_bytes;
       col->words = words + word_base[c];
-      col->meta_bytes = 64 * col->m + sizeof(TileDesc) * scan_tiles(col->n);
+      col->meta_bytes = (v.poly ? 64 + sizeof(PolyAux) : 64) * col->m + sizeof(TileDesc) * scan_tiles(col->n);
       col->words_bytes = 8 * col->nwords;
       col->home = st;
       col->shared = sh;

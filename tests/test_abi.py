@@ -80,12 +80,12 @@ def test_host_side_argument_errors(built):
     assert L.leco_encode(None, 0, 1, leco.fixed(16), -1, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
     fake = ctypes.c_void_p(256)  # never dereferenced: the checks below fail first
     assert L.leco_encode_with_starts(None, 0, 1, fake, 0, 3, None, ctypes.byref(h)) == leco.LECO_ERR_INVALID_ARG
-    # the allocation-free and the batched encode take constant and linear only
+    # the allocation-free encode takes constant and linear only; the batched encode all three models
     nw = ctypes.c_uint64(0)
     assert L.leco_encode_fixed_noalloc(fake, 10, 1, 16, leco.LECO_MODEL_POLY, fake, fake, 100, ctypes.byref(nw),
                                        None) == leco.LECO_ERR_INVALID_ARG
     vals = (ctypes.c_void_p * 1)(fake)
-    ns, models, Ls = (ctypes.c_uint64 * 1)(10), (ctypes.c_int * 1)(leco.LECO_MODEL_POLY), (ctypes.c_uint32 * 1)(16)
+    ns, models, Ls = (ctypes.c_uint64 * 1)(10), (ctypes.c_int * 1)(3), (ctypes.c_uint32 * 1)(16)
     outs = (ctypes.c_void_p * 1)()
     assert L.leco_batch_encode(vals, ns, models, Ls, 1, 1, None, outs) == leco.LECO_ERR_INVALID_ARG
     # variable partitioning takes the variable kinds (plain or seeded) and tau in [0, 1]

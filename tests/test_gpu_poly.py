@@ -215,7 +215,7 @@ def test_poly_auto_partition_size(lc):
 
 
 def test_poly_model_limits(lc):
-    """The allocation-free encode and the batched encode take constant and linear columns only."""
+    """The allocation-free encode takes constant and linear columns only."""
     import torch
 
     v = W.sine_mixture(10_000, seed=12)
@@ -224,9 +224,45 @@ def test_poly_model_limits(lc):
     with pytest.raises(lc.LecoError) as e:
         lc.leco_encode_fixed_noalloc(to_dev(v), 1024, rec_out, words_out, POLY)
     assert e.value.status == lc.LECO_ERR_INVALID_ARG
-    with pytest.raises(lc.LecoError) as e:
-        lc.leco_batch_encode([to_dev(v)], [POLY], [1024])
-    assert e.value.status == lc.LECO_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_poly_batched_encode(lc, bits):
+    """The batched encode over columns of all three models: each column byte-identical to the
+    oracle's encoding with its model and L, and every filter mode exact (the polynomial columns'
+    tiles carry their exact bounds)."""
+    import torch
+
+    g = W.rng(40 + bits)
+    vals, models, Ls = [], [], []
+    for c in range(24):
+        n = int(np.exp(g.uniform(np.log(50), np.log(120_000)))) if c % 7 else 0
+        base = 1 << 31 if bits == 32 else 1 << 40
+        v = W.sine_mixture(n, base=base, a1=1e9, a2=1e7, p2=float(g.choice([3e3, 2e4])), seed=c)
+        vals.append(v)
+        models.append(int(c % 3))
+        Ls.append(int(g.choice([64, 100, 1024, 4096])))
+    dvals = [to_dev(v, bits) for v in vals]
+    cols = lc.leco_batch_encode(dvals, models, Ls)
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    for v, m, L, col in zip(vals, models, Ls, cols):
+        rec_b, words_b, _ = lc.leco_column_export(col)
+        rec, words = oracle.encode_fixed(v, L, m)
+        assert rec_b == rec.tobytes() and words_b == words.tobytes(), (m, L, len(v))
+        out = torch.empty(max(len(v), 1), dtype=torch.int32 if bits == 32 else torch.int64, device="cuda")
+        lc.leco_decode_all(col, out)
+        assert (from_dev(out)[: len(v)] == v).all()
+        if len(v):
+            lo, hi = W.filter_bounds(v)
+            for flags in (0, lc.LECO_FILTER_PRUNE, lc.LECO_FILTER_DECODE_ALL):
+                lc.leco_filter_sum(col, lo, hi, res, flags=flags)
+                r = from_dev(res)
+                assert (int(r[0]), int(r[1]) | (int(r[2]) << 64)) == exact_sum(v, lo, hi)
+    outs = [torch.empty(max(len(v), 1), dtype=torch.int32 if bits == 32 else torch.int64, device="cuda") for v in vals]
+    lc.leco_batch_decode(cols, outs)
+    torch.cuda.synchronize()
+    for v, o in zip(vals, outs):
+        assert (from_dev(o)[: len(v)] == v).all()
 
 
 def test_poly_never_larger_than_linear(lc):
