@@ -350,14 +350,14 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
 //     partition, p1 = x', p2 = 3x'^2 - (N^2-1), p3 = 5x'^3 - (3N^2-7)x' with x' = 2x - (N-1); the p_j
 //     are orthogonal to 1 and to each other over x < N, so S_j / |p_j|^2 is the least-squares
 //     coefficient c_j of p_j for any degree that includes it (and S_1 is the line's moment);
-//  2. one lane solves the constant and linear parameters (as for those models) and, when
+//  2. a thread solves the constant and linear parameters (as for those models) and, when
 //     64 <= N <= 16384 and max - min < 2^62, the quadratic and cubic grids: c_j as one binary64
 //     division of the two integers (each converted from sign and magnitude), s_j = min(62, 61 - e_j)
 //     with |c_j| < 2^e_j, S = max s_j capped so that every K_j 2^(S - s_j) p_j stays below 2^124,
 //     K_j = round(c_j 2^s_j) half up;
 //  3. a second pass: the linear residual range (or the fallback's widest zigzag residual) and, per
 //     polynomial, the range of w_x - floor(F(x) / 2^S) (F = sum K_j 2^(S - s_j) p_j(x), exact);
-//  4. one lane sizes the four candidates (256 + N b for constant and linear, 576 + N b for the
+//  4. a thread sizes the four candidates (256 + N b for constant and linear, 576 + N b for the
 //     polynomials, whose minimax intercept T and width follow from their range as for the line) and
 //     keeps the smallest, ties to the earlier.
 
@@ -402,7 +402,7 @@ __host__ __device__ __forceinline__ PolyAux poly_aux_from(const int64_t* K, cons
   return r;
 }
 
-// one polynomial candidate's grid (lane 0 of the fitting warp)
+// one polynomial candidate's grid (step 2)
 struct PolyGrid {
   int64_t K[3];
   int32_t sj[3];
