@@ -690,8 +690,28 @@ def run_poly(args):
         }
         col.free()
         del o, ok_
-    print(json.dumps({"workload": f"LeCo-Poly vs linear: {n} uint64 sine mixture (two sines + noise), L={L}",
-                      "peak_gbs": peak, "results": out}), flush=True)
+    line = {"workload": f"LeCo-Poly vs linear: {n} uint64 sine mixture (two sines + noise), L={L}",
+            "peak_gbs": peak, "results": out}
+    if not args.no_cpu_baseline:
+        # the oracle beside it: encode and decode of every 100th partition, one thread
+        import oracle
+
+        oracle.build()
+        smp = sample_partitions(v, args.sample_every)
+        cpu = {"kind": "oracle", "cores": 1,
+               "sample": f"every {args.sample_every}th {L}-value partition ({len(smp)} values), one thread"}
+        for name, model in (("linear", oracle.MODEL_LINEAR), ("poly", oracle.MODEL_POLY)):
+            t0 = time.perf_counter()
+            rec, words = oracle.encode_fixed(smp, L, model)
+            t1 = time.perf_counter()
+            d = oracle.decode(rec, words, len(smp))
+            t2 = time.perf_counter()
+            assert (d == smp).all()
+            cb = oracle.compressed_bytes(rec, words)
+            cpu[name] = {"encode_gbs": (8 * len(smp) + cb) / (t1 - t0) / 1e9,
+                         "decode_gbs": (cb + 8 * len(smp)) / (t2 - t1) / 1e9, "ratio": cb / (8 * len(smp))}
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
     return 0
 
 
