@@ -114,7 +114,8 @@ typedef struct {
   int32_t kind;            /* leco_part_kind */
   int32_t model;           /* leco_model */
   uint32_t part_size;      /* fixed L (0 for variable) */
-  uint64_t residual_bits;  /* sum over partitions of len * b */
+  uint64_t residual_bits;  /* bits of the stream: sum over partitions of len * b, plus 320 per
+                              polynomial partition (its coefficient block) */
   uint64_t device_bytes;   /* bytes the column holds on the device */
 } leco_stats;
 
