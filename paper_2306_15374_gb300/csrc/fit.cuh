@@ -402,6 +402,32 @@ __host__ __device__ __forceinline__ PolyAux poly_aux_from(const int64_t* K, cons
   return r;
 }
 
+// The cubic F(x) = c0 + c1 x + c2 x^2 + c3 x^3 (128-bit, from a PolyAux row) at x and its forward
+// differences over the stride h, each multiplied by 2^up modulo 2^128:
+// D1 = c1 h + c2 (2xh + h^2) + c3 (3x^2 h + 3x h^2 + h^3), D2 = c2 2h^2 + c3 (6x h^2 + 6h^3),
+// D3 = c3 6h^3 (x and h below 2^14 and 2^8 keep every bracket inside 64 bits). Stepping
+// F += D1, D1 += D2, D2 += D3 then gives F at x + h, x + 2h, ... exactly (modulo 2^128).
+struct PolySteps {
+  u128 F, D1, D2, D3;
+};
+
+__device__ __forceinline__ PolySteps poly_steps(const PolyAux& q, uint64_t x, uint64_t h, uint32_t up) {
+  u128 c[4];
+  for (int k = 0; k < 4; k++) c[k] = ((u128)q.a[k][1] << 64) | q.a[k][0];
+  PolySteps r;
+  r.F = (((c[3] * x + c[2]) * x + c[1]) * x + c[0]) << up;
+  r.D1 = (c[1] * h + c[2] * (2 * x * h + h * h) + c[3] * (3 * x * x * h + 3 * x * h * h + h * h * h)) << up;
+  r.D2 = (c[2] * (2 * h * h) + c[3] * (6 * x * h * h + 6 * h * h * h)) << up;
+  r.D3 = (c[3] * (6 * h * h * h)) << up;
+  return r;
+}
+
+__device__ __forceinline__ void poly_step(PolySteps& r) {
+  r.F += r.D1;
+  r.D1 += r.D2;
+  r.D2 += r.D3;
+}
+
 // one polynomial candidate's grid (step 2)
 struct PolyGrid {
   int64_t K[3];
@@ -556,21 +582,15 @@ __device__ PolyRange poly_ranges_warp(const void* __restrict__ values, int dtype
   const int32_t s = plan->PL.s, fallback = plan->PL.fallback;
   bool valid[2], fast[2];
   int32_t S[2];
-  u128 F[2], D1[2], D2[2], D3[2];
+  PolySteps Fd[2];
   for (int d = 0; d < 2; d++) {
     valid[d] = plan->G[d].valid != 0;
     fast[d] = valid[d] && plan->fast[d];
     S[d] = plan->G[d].S;
-    u128 c[4];
-    for (int k = 0; k < 4; k++) c[k] = valid[d] ? ((u128)plan->Q[d].a[k][1] << 64) | plan->Q[d].a[k][0] : 0;
-    const uint64_t x = lane, h = 32;
     // fast: carried times 2^(64-S) modulo 2^128, so that floor(F / 2^S) mod 2^64 (= floor(F / 2^S),
     // which the plan bounded inside int64) is the high half
     const uint32_t up = fast[d] ? 64u - (uint32_t)S[d] : 0u;
-    F[d] = (((c[3] * x + c[2]) * x + c[1]) * x + c[0]) << up;
-    D1[d] = (c[1] * h + c[2] * (2 * x * h + h * h) + c[3] * (3 * x * x * h + 3 * x * h * h + h * h * h)) << up;
-    D2[d] = (c[2] * (2 * h * h) + c[3] * (6 * x * h * h + 6 * h * h * h)) << up;
-    D3[d] = (c[3] * (6 * h * h * h)) << up;
+    Fd[d] = valid[d] ? poly_steps(plan->Q[d], lane, 32, up) : PolySteps{0, 0, 0, 0};
   }
   PolyRange R;
   int64_t lo = INT64_MAX, hi = INT64_MIN;
@@ -591,11 +611,11 @@ __device__ PolyRange poly_ranges_warp(const void* __restrict__ values, int dtype
     for (int d = 0; d < 2; d++) {
       if (!valid[d]) continue;
       if (fast[d]) {
-        const int64_t r = w - (int64_t)(uint64_t)(F[d] >> 64);
+        const int64_t r = w - (int64_t)(uint64_t)(Fd[d].F >> 64);
         plo[d] = min(plo[d], r);
         phi[d] = max(phi[d], r);
       } else {
-        const i128 r = (i128)w - ((i128)F[d] >> S[d]);
+        const i128 r = (i128)w - ((i128)Fd[d].F >> S[d]);
         if (r > (i128)INT64_MAX || r < (i128)INT64_MIN) {
           bad[d] = 1;
         } else {
@@ -603,9 +623,7 @@ __device__ PolyRange poly_ranges_warp(const void* __restrict__ values, int dtype
           phi[d] = max(phi[d], (int64_t)r);
         }
       }
-      F[d] += D1[d];
-      D1[d] += D2[d];
-      D2[d] += D3[d];
+      poly_step(Fd[d]);
     }
   }
   R.lo = warp_min_i64(lo);

@@ -488,24 +488,11 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
         // the thread's predictions T + (F(x) >> S) for x = tid, tid + blockDim, ... by forward
         // differences of the cubic F over that stride, carried times 2^(64-S) modulo 2^128 so that
         // the prediction's low 64 bits are the carried value's high half
-        const ulonglong2* row = reinterpret_cast<const ulonglong2*>(poly + p);
-        u128 c[4];
-        for (int k = 0; k < 4; k++) {
-          const ulonglong2 h = __ldg(row + k);
-          c[k] = ((u128)h.y << 64) | h.x;
-        }
-        const uint64_t x = threadIdx.x, h = blockDim.x;
-        const uint32_t up = 64u - ((uint32_t)w3_s(a.word3) & 63u);
-        u128 F = (((c[3] * x + c[2]) * x + c[1]) * x + c[0]) << up;
-        u128 D1 = (c[1] * h + c[2] * (2 * x * h + h * h) + c[3] * (3 * x * x * h + 3 * x * h * h + h * h * h)) << up;
-        u128 D2 = (c[2] * (2 * h * h) + c[3] * (6 * x * h * h + 6 * h * h * h)) << up;
-        const u128 D3 = (c[3] * (6 * h * h * h)) << up;
+        PolySteps Fd = poly_steps(poly[p], threadIdx.x, blockDim.x, 64u - ((uint32_t)w3_s(a.word3) & 63u));
         const uint64_t T = (uint64_t)a.A;
         for (uint32_t xx = threadIdx.x; xx < s.N; xx += blockDim.x) {
-          zs[xx] = zz_encode((int64_t)((uint64_t)staged_value(st, s.dtype, xx) - (T + (uint64_t)(F >> 64))));
-          F += D1;
-          D1 += D2;
-          D2 += D3;
+          zs[xx] = zz_encode((int64_t)((uint64_t)staged_value(st, s.dtype, xx) - (T + (uint64_t)(Fd.F >> 64))));
+          poly_step(Fd);
         }
       } else {
         for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
