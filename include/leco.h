@@ -175,12 +175,16 @@ leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype
  *   nwords_out host; receives the stream's word count, also when words_cap is too small.
  * Scratch lives in a fixed 12.6 MB __device__ array that every GPU loading the library holds
  * until exit; ceil(n / L) must not exceed 2^18 (INVALID_ARG otherwise). The first call on a
- * device looks up that array's device address (make it before any stream capture). All calls on
- * a device share the array, so calls whose GPU work overlaps (e.g. on different streams) race;
- * nothing of it needs clearing between calls. The call synchronizes `stream` once to size the
- * stream; INVALID_ARG when words_cap < *nwords_out (nothing packed then) or for LECO_MODEL_POLY
- * (constant and linear only), CUDA on a runtime failure. No cudaMalloc, cudaFree or allocating
- * library routine is called. */
+ * device looks up that array's device address; with CUDA's lazy module loading (the default) that
+ * first call is also when the driver loads the encode kernels and creates the array, a driver
+ * allocation of its own: make the first call on each device before any stream capture and before
+ * the caller's own pool reserves the device's memory. All calls on a device share the array, so
+ * calls whose GPU work overlaps (e.g. on different streams) race; nothing of it needs clearing
+ * between calls. The call synchronizes `stream` twice: once to size the stream, and once at the
+ * end to read back whether a staging copy of the packer gave up (then LECO_ERR_TIMEOUT: the words
+ * are incomplete). INVALID_ARG when words_cap < *nwords_out (nothing packed then) or for
+ * LECO_MODEL_POLY (constant and linear only), CUDA on a runtime failure. No cudaMalloc, cudaFree
+ * or allocating library routine is called. */
 leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t n, leco_dtype dtype, uint32_t L,
                                       leco_model model, void* d_records, void* d_words,
                                       uint64_t words_cap, uint64_t* nwords_out,

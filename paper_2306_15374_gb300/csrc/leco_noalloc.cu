@@ -89,5 +89,12 @@ extern "C" leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t 
   if (e == cudaSuccess)
     e = launch_pack(d_values, dtype, rec, aux, nullptr, nullptr, m, n, total, static_cast<uint64_t*>(d_words), nwords,
                     err, st);
-  return e == cudaSuccess ? LECO_OK : LECO_ERR_CUDA;
+  // A staging copy that gave up leaves part of the stream unwritten, and this call has no column
+  // whose status word could carry the flag to a later leco_sync: read it back here, before the
+  // next call's clear can erase it.
+  flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return LECO_ERR_CUDA;
+  return (flags & kStatTimeout) ? LECO_ERR_TIMEOUT : LECO_OK;
 }

@@ -350,6 +350,13 @@ def leco_encode_fixed_noalloc(values, L: int, records_out, words_out, model: int
     records_out: CUDA tensor of >= 32 * ceil(n / L) bytes; words_out: CUDA tensor whose byte size
     / 8 is the word capacity. Returns the stream's word count; raises LecoError (INVALID_ARG) when
     the capacity is too small, with the needed count in the exception's .nwords."""
+    n = values.numel()
+    m = (n + int(L) - 1) // int(L) if int(L) >= 1 else 0
+    for name, t in (("records_out", records_out), ("words_out", words_out)):
+        if not t.is_cuda or not t.is_contiguous() or t.device != values.device:
+            raise ValueError(f"{name} must be a contiguous CUDA tensor on the values' device")
+    if records_out.numel() * records_out.element_size() < 32 * m:
+        raise ValueError(f"records_out holds fewer than 32 * {m} bytes")
     nw = ctypes.c_uint64(0)
     cap = words_out.numel() * words_out.element_size() // 8
     st = lib().leco_encode_fixed_noalloc(_dev(values), values.numel(), _dtype_of(values), int(L), model,

@@ -475,7 +475,8 @@ def _brute_force_best(orc, v, model):
 
 def test_split_merge_vs_brute_force_optimum(orc):
     """Tiny inputs: enumerate all 2^(n-1) partitionings under the exact size function; the DP over
-    prefixes must match, and both greedy variants can only be >= the optimum."""
+    prefixes must match, and both greedy variants can only be >= the optimum (the merge rules
+    themselves are pinned by the hand-worked rounds below)."""
     g = W.rng(8)
     for trial in range(12):
         n = int(g.integers(2, 11))
@@ -489,7 +490,32 @@ def test_split_merge_vs_brute_force_optimum(orc):
             st = orc.var_partition(v, 0.03, variant=variant)
             got = sum(_sizes(orc, v, st, 1))
             assert got >= best
-            assert got <= best + 256 * n  # never worse than one partition per value beyond optimum
+
+
+def test_merge_rounds_worked_by_hand(orc):
+    """Both merge readings (§3.2.2) on eight values with the constant model, whose partition size is
+    S_M + len * bitlen(max - min) (FOR's width, pinned above), from singletons (256 bits each).
+    v = 0, 1, 3, 7, J, J+1, J+3, J+7 with J = 2^40.
+
+    Round reading: round 1 pair gains 254, 252, 250, 176, 254, 252, 250 (a pair of range d costs
+    256 + 2 bitlen(d)); the local maxima j = 0 and j = 4 merge: {0,1} {3} {7} {J,J+1} {J+3} {J+7}.
+    Round 2 gains 252, 250, 138, 252, 250 ({7,J,J+1} costs 256 + 3*40): j = 0 and j = 3 merge.
+    Round 3 gains 250, 102, 250: j = 0 and j = 2 merge into {0,1,3,7} and {J..J+7}, 268 bits each.
+    Round 4: the whole column costs 256 + 8 * bitlen(J + 7) = 584 > 536, gain -48: stop after three
+    merging rounds at starts [0, 4, 8], 536 bits.
+
+    Sequential reading: the open partition absorbs 1, 3, 7 (258 < 512, 262 < 514, 268 < 518), then
+    J as well (256 + 5*41 = 461 < 268 + 256) and everything after it (502, 543, 584 bits); the second
+    pass finds nothing: one partition of 584 bits, worse than the round reading here."""
+    J = 1 << 40
+    v = np.array([0, 1, 3, 7, J, J + 1, J + 3, J + 7], dtype=np.uint64)
+    singles = np.arange(9, dtype=np.uint64)
+    st, rounds = orc.var_merge_round(v, singles, orc.MODEL_CONSTANT)
+    assert st.tolist() == [0, 4, 8] and rounds == 3
+    assert sum(_sizes(orc, v, st, orc.MODEL_CONSTANT)) == 536
+    st, passes = orc.var_merge_seq(v, singles, orc.MODEL_CONSTANT)
+    assert st.tolist() == [0, 8] and passes == 2
+    assert sum(_sizes(orc, v, st, orc.MODEL_CONSTANT)) == 584
 
 
 # ----------------------------------------------------------------------------- partition-size search (§3.2.1)

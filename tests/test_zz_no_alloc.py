@@ -3,8 +3,9 @@
 That entry point serves callers that cannot call cudaMalloc (device memory owned by another
 allocator, or paths that cannot take an allocation's synchronization); its scratch is a fixed
 __device__ array shared by all calls. Here two calls in a row, on different inputs, must give the
-records and residual words of the allocating entry point byte for byte, and sizes past the fixed
-scratch must be refused. This file is collected last so a failure here comes after every other test.
+records and residual words of the allocating entry point byte for byte, the second call must leave
+the device's free memory unchanged, and sizes past the fixed scratch must be refused. This file is
+collected last so a failure here comes after every other test.
 """
 import numpy as np
 import pytest
@@ -47,8 +48,14 @@ def test_noalloc_matches_allocating_encode_twice(lc):
         m = (len(v) + L - 1) // L
         rec = torch.zeros(4 * max(m, 1), dtype=torch.int64, device="cuda")
         words = torch.full((len(want_words) // 8 + 64,), -1, dtype=torch.int64, device="cuda")
-        for _ in range(2):  # two calls in a row share the scratch array
-            nw = lc.leco_encode_fixed_noalloc(to_dev(v, bits), L, rec, words, model)
+        dv = to_dev(v, bits)
+        torch.cuda.synchronize()
+        for call in range(2):  # two calls in a row share the scratch array
+            free_before = torch.cuda.mem_get_info()[0]
+            nw = lc.leco_encode_fixed_noalloc(dv, L, rec, words, model)
+            torch.cuda.synchronize()
+            if call == 1:  # the first call may load kernels; the second must take no device memory
+                assert torch.cuda.mem_get_info()[0] == free_before
             assert nw * 8 == len(want_words)
             assert rec.cpu().numpy().tobytes()[: 32 * m] == want_rec
             assert words.cpu().numpy().tobytes()[: 8 * nw] == want_words
