@@ -1,18 +1,21 @@
 // Variable-length partitioning on the GPU (§3.2.2): split, then merge.
 //
 // Split: the sequence is cut into chunks of kChunk values (chunk edges always start a partition);
-// inside a chunk one thread grows partitions left to right: v_j joins the open partition [i, j)
+// inside a chunk one lane grows partitions left to right: v_j joins the open partition [i, j)
 // iff C = (j+1-i) D(v[i,j+1)) - (j-i) D(v[i,j)) <= tau * S_M and j - i < cap, where D is the
 // linear regressor's fast metric bitlen(max d - min d) over the inner differences d_k = w_k -
-// w_{k-1}. Starts go to a bitmap (the thread owns its chunk's words), then a popcount scan
-// compacts them.
+// w_{k-1}. A warp sweeps 32 chunks at once, one per lane, and stages their values through shared
+// memory in coalesced segments ahead of the lanes' dependency chains. Starts go to a bitmap (each
+// lane owns its chunk's words), then a popcount scan compacts them.
 //
 // Merge, round-synchronous: each round computes for every adjacent pair the size of the merged
-// partition with the full regressor (S_M + len * b; pairs sorted by length onto a thread, a warp or a
-// CTA each) and its gain over the two apart; every pair
+// partition with the full regressor (S_M + len * b) and its gain over the two apart; every pair
 // with a positive gain whose priority (gain, SplitMix64 of its start) beats both neighbouring
-// pairs merges, all at once. Pair sizes are cached: only pairs touching a partition merged in the
-// previous round are refitted. Rounds repeat until none merges.
+// pairs merges, all at once. Rounds repeat until none merges. Pair sizes are cached: only pairs
+// touching a partition merged in the previous round are refitted, and a refit needs one pass over
+// the pair's values, because every partition carries the moments of its values and two
+// partitions' moments combine exactly (see SpanStats). The fits of the final partitions are the
+// column's records, so the encoder does not fit them again.
 #include <math.h>
 
 #include <map>
@@ -31,83 +34,126 @@ cudaError_t scan_u64(const uint64_t* in, uint64_t count, uint64_t* out, uint64_t
 namespace {
 
 constexpr uint64_t kChunk = 1ull << 16;
-constexpr uint64_t kNone = ~0ull;        // no merged size (pair longer than the cap)
-constexpr uint32_t kLongPair = 1u << 14; // pairs longer than this are fitted by a whole CTA
+constexpr uint64_t kNone = ~0ull;  // no merged size (pair longer than the cap)
+constexpr uint32_t kFull = 0xffffffffu;
 
-// One chunk's greedy sweep. NARROW: every value of the chunk lies in (-2^62, 2^62) as int64, so the
-// differences and their running extremes fit 64 bits (their range below 2^64, taken unsigned);
-// otherwise 128-bit. The threshold test C <= tau S_M is done on integers: for an integer C and a
-// real t, C <= t exactly when C <= floor(t). Values are read eight at a time ahead of the sweep's
-// dependency chain.
-template <bool NARROW, typename T>
-__device__ __forceinline__ void split_chunk(const T* __restrict__ v, uint64_t a, uint64_t e, uint32_t cap,
-                                            int64_t tfloor, uint64_t* __restrict__ bitmap) {
-  using D = typename std::conditional<NARROW, int64_t, i128>::type;
-  uint64_t i = a;
-  uint64_t word = 1ull;  // position a opens a partition (a % 64 == 0)
-  uint64_t wi = a >> 6;
-  int64_t prev = (int64_t)v[a];
-  D dmax = 0, dmin = 0;
-  int cur = 0;
-  int64_t nxt[8];  // the next batch, loaded while the current one is swept
-#pragma unroll
-  for (int u = 0; u < 8; u++) nxt[u] = a + 1 + u < e ? (int64_t)__ldg(v + a + 1 + u) : 0;
-  for (uint64_t j0 = a + 1; j0 < e; j0 += 8) {
-    int64_t buf[8];
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      buf[u] = nxt[u];
-      nxt[u] = j0 + 8 + u < e ? (int64_t)__ldg(v + j0 + 8 + u) : 0;
+// One greedy step of the split at position j with value w (the previous value prev): returns true
+// when v_j joins the open partition [i, j). NARROW: the chunk's values lie in (-2^62, 2^62) as
+// int64, so differences and their running extremes fit 64 bits (their range below 2^64, taken
+// unsigned); otherwise 128-bit. The threshold test C <= tau S_M is done on integers: for an integer
+// C and a real t, C <= t exactly when C <= floor(t).
+template <typename D>
+__device__ __forceinline__ bool split_step(uint64_t j, int64_t w, int64_t prev, uint64_t& i, D& dmax, D& dmin,
+                                           int& cur, uint32_t cap, int64_t tfloor) {
+  bool take = (j - i) < cap;
+  D nmax = dmax, nmin = dmin;
+  int next = 0;
+  if (take) {
+    const D d = (D)w - (D)prev;
+    if (j == i + 1) {
+      nmax = d;
+      nmin = d;
+    } else {
+      nmax = d > nmax ? d : nmax;
+      nmin = d < nmin ? d : nmin;
     }
+    if (std::is_same<D, int64_t>::value)
+      next = bitlen_u64((uint64_t)nmax - (uint64_t)nmin);
+    else
+      next = bitlen_u128((u128)(nmax - nmin));
+    const int64_t C = (int64_t)(j + 1 - i) * next - (int64_t)(j - i) * cur;
+    take = C <= tfloor;
+  }
+  if (take) {
+    cur = next;
+    dmax = nmax;
+    dmin = nmin;
+  } else {
+    i = j;
+    cur = 0;
+    dmax = 0;
+    dmin = 0;
+  }
+  return take;
+}
+
+// Left-to-right split of 32 chunks per warp (lane l sweeps chunk 32 w + l). Segment k of every
+// chunk (positions k kSplitSeg .. + kSplitSeg) is loaded by the whole warp with coalesced loads one
+// segment ahead, transposed through shared memory (row x holds position x of the 32 chunks, padded
+// against bank conflicts), and then swept by each lane from shared memory while the next
+// segment's loads are in flight. A segment is one bitmap word per chunk.
+constexpr uint32_t kSplitSeg = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_split_staged(const T* __restrict__ v, uint64_t n, uint32_t cap, int64_t tfloor,
+                                                     const uint8_t* __restrict__ narrow, uint64_t* __restrict__ bitmap) {
+  __shared__ T ring[2][kSplitSeg][33];
+  const uint32_t lane = threadIdx.x;
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  const uint64_t c0 = (uint64_t)blockIdx.x * 32;
+  const uint64_t c = c0 + lane;
+  const bool has = c < nchunks;
+  const uint64_t a = c * kChunk;
+  const uint64_t e = has ? min(a + kChunk, n) : a;
+  const bool nar = has ? narrow[c] != 0 : true;
+  constexpr uint32_t nseg = (uint32_t)(kChunk / kSplitSeg);
+  T r[kSplitSeg];
+  // segment 0 into slot 0
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint64_t j = j0 + u;
-      if (j >= e) break;
-      if ((j & 63) == 0) {
-        bitmap[wi++] = word;
-        word = 0;
+  for (uint32_t u = 0; u < kSplitSeg; u++) {
+    const uint32_t cc = u >> 1, x = ((u & 1u) << 5) + lane;  // two loads per chunk
+    const uint64_t pos = (c0 + cc) * kChunk + x;
+    r[u] = pos < n ? __ldg(v + pos) : (T)0;
+  }
+#pragma unroll
+  for (uint32_t u = 0; u < kSplitSeg; u++) ring[0][((u & 1u) << 5) + lane][u >> 1] = r[u];
+  __syncwarp();
+  uint64_t i = a;
+  int64_t prev = 0;
+  int64_t dmax64 = 0, dmin64 = 0;
+  i128 dmax128 = 0, dmin128 = 0;
+  int cur = 0;
+  for (uint32_t k = 0; k < nseg; k++) {
+    const uint32_t slot = k & 1u;
+    if (k + 1 < nseg) {  // issue segment k + 1
+#pragma unroll
+      for (uint32_t u = 0; u < kSplitSeg; u++) {
+        const uint32_t cc = u >> 1, x = ((u & 1u) << 5) + lane;
+        const uint64_t pos = (c0 + cc) * kChunk + (uint64_t)(k + 1) * kSplitSeg + x;
+        r[u] = pos < n ? __ldg(v + pos) : (T)0;
       }
-      const int64_t w = buf[u];
-      bool take = (j - i) < cap;
-      D nmax = dmax, nmin = dmin;
-      int next = 0;
-      if (take) {
-        const D d = (D)w - (D)prev;
-        if (j == i + 1) {
-          nmax = d;
-          nmin = d;
-        } else {
-          nmax = d > nmax ? d : nmax;
-          nmin = d < nmin ? d : nmin;
+    }
+    const uint64_t base = a + (uint64_t)k * kSplitSeg;
+    uint64_t word = 0;
+    if (base < e) {
+      for (uint32_t x = 0; x < kSplitSeg; x++) {
+        const uint64_t j = base + x;
+        const int64_t w = (int64_t)ring[slot][x][lane];
+        if (j == a) {
+          word |= 1ull;  // the chunk's first position opens a partition
+        } else if (j < e) {
+          const bool take = nar ? split_step<int64_t>(j, w, prev, i, dmax64, dmin64, cur, cap, tfloor)
+                                : split_step<i128>(j, w, prev, i, dmax128, dmin128, cur, cap, tfloor);
+          if (!take) word |= 1ull << x;
         }
-        if (NARROW)
-          next = bitlen_u64((uint64_t)nmax - (uint64_t)nmin);
-        else
-          next = bitlen_u128((u128)(nmax - nmin));
-        const int64_t C = (int64_t)(j + 1 - i) * next - (int64_t)(j - i) * cur;
-        take = C <= tfloor;
+        prev = w;
       }
-      if (take) {
-        cur = next;
-        dmax = nmax;
-        dmin = nmin;
-      } else {
-        word |= 1ull << (j & 63);
-        i = j;
-        cur = 0;
-        dmax = 0;
-        dmin = 0;
-      }
-      prev = w;
+      bitmap[base >> 6] = word;
+    }
+    __syncwarp();
+    if (k + 1 < nseg) {
+#pragma unroll
+      for (uint32_t u = 0; u < kSplitSeg; u++) ring[slot ^ 1u][((u & 1u) << 5) + lane][u >> 1] = r[u];
+      __syncwarp();
     }
   }
-  bitmap[wi] = word;
 }
+
 
 // Seeded split (§3.2.2, selecting good starting positions): the greedy sweep over the count values
 // u_k = v[base + dir k] (dir = +1, or -1 to read them backwards); a partition opens at u-index k when
 // u_k is refused, and mark(k) records it (the first partition, at k = 0, is not marked). Same rule,
-// cap and integer threshold as split_chunk; values are read eight ahead of the dependency chain.
+// cap and integer threshold as split_step; values are read eight ahead of the dependency chain.
 template <bool NARROW, typename T, typename Mark>
 __device__ __forceinline__ void sweep_dir(const T* __restrict__ v, uint64_t base, int dir, uint64_t count, uint32_t cap,
                                           int64_t tfloor, Mark mark) {
@@ -230,28 +276,24 @@ __device__ __forceinline__ void split_chunk_seeded(const T* __restrict__ v, uint
   sweep_dir<NARROW>(v, seed, 1, e - seed, cap, tfloor, [&](uint64_t k) { set(seed + k); });
 }
 
-// seeds: nullptr for the left-to-right split, else each chunk's seed (k_chunk_seed)
+
+// the seeded split: chunk c's partitions grow from seeds[c] (k_chunk_seed) both ways; a thread per chunk
 template <typename T>
-__global__ void k_split(const T* __restrict__ values, uint64_t n, uint32_t cap, int64_t tfloor,
-                        const uint8_t* __restrict__ narrow, const uint64_t* __restrict__ seeds,
-                        uint64_t* __restrict__ bitmap) {
+__global__ void k_split_seeded(const T* __restrict__ values, uint64_t n, uint32_t cap, int64_t tfloor,
+                               const uint8_t* __restrict__ narrow, const uint64_t* __restrict__ seeds,
+                               uint64_t* __restrict__ bitmap) {
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
        c += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t a = c * kChunk;
     const uint64_t e = min(a + kChunk, n);
-    if (seeds) {
-      if (narrow[c])
-        split_chunk_seeded<true>(values, a, e, seeds[c], cap, tfloor, bitmap);
-      else
-        split_chunk_seeded<false>(values, a, e, seeds[c], cap, tfloor, bitmap);
-    } else if (narrow[c]) {
-      split_chunk<true>(values, a, e, cap, tfloor, bitmap);
-    } else {
-      split_chunk<false>(values, a, e, cap, tfloor, bitmap);
-    }
+    if (narrow[c])
+      split_chunk_seeded<true>(values, a, e, seeds[c], cap, tfloor, bitmap);
+    else
+      split_chunk_seeded<false>(values, a, e, seeds[c], cap, tfloor, bitmap);
   }
 }
+
 
 __global__ void k_popc(const uint64_t* __restrict__ bitmap, uint64_t nw, uint64_t* __restrict__ cnt) {
   for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nw;
@@ -272,92 +314,6 @@ __global__ void k_scatter_starts(const uint64_t* __restrict__ bitmap, uint64_t n
       bits &= bits - 1;
     }
     if (w == 0) starts[m] = n;
-  }
-}
-
-// Sizes S_M + len * b of spans [st[j], st[j + w]) (w = 1: partitions; w = 2: adjacent pairs) by the
-// full fit. The spans to fit are first sorted into three work lists by length, so that each is fitted
-// by a group of matching size: one thread for short spans (32 of them share a warp, and with it the
-// single-lane parameter solve), a warp for medium ones, a CTA for long ones. A list's order is free:
-// every span's size is independent of the others.
-constexpr uint32_t kTinySpan = 256;
-
-struct SpanLists {
-  uint64_t* tiny;       // [0, counts[0])
-  uint64_t* medium;     // [0, counts[1])
-  uint64_t* lng;        // [0, counts[2])
-  unsigned long long* counts;
-};
-
-// append j to list k with one atomic per warp and list
-__device__ __forceinline__ void list_push(const SpanLists& L, int k, bool take, uint64_t j) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t mask = __ballot_sync(0xffffffffu, take);
-  if (!mask) return;
-  const int leader = __ffs(mask) - 1;
-  unsigned long long base = 0;
-  if ((int)lane == leader) base = atomicAdd(&L.counts[k], (unsigned long long)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (take) {
-    uint64_t* list = k == 0 ? L.tiny : (k == 1 ? L.medium : L.lng);
-    list[base + __popc(mask & ((1u << lane) - 1u))] = j;
-  }
-}
-
-// dirty == nullptr: every span. A span longer than cap gets no fit (out[j] = kNone).
-__global__ void k_classify(const uint64_t* __restrict__ st, uint64_t count, uint32_t w, uint32_t cap,
-                           const uint8_t* __restrict__ dirty, uint64_t* __restrict__ out, SpanLists L) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x; j0 < count; j0 += stride) {
-    const uint64_t j = j0 + threadIdx.x;  // whole warps iterate together (list_push is warp-wide)
-    bool t = false, md = false, lg = false;
-    if (j < count && (!dirty || dirty[j])) {
-      const uint64_t len = st[j + w] - st[j];
-      if (len > cap)
-        out[j] = kNone;
-      else
-        (len <= kTinySpan ? t : (len <= kLongPair ? md : lg)) = true;
-    }
-    list_push(L, 0, t, j);
-    list_push(L, 1, md, j);
-    list_push(L, 2, lg, j);
-  }
-}
-
-__global__ void k_span_size_thread(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
-                                   uint32_t w, int model, SpanLists L, uint64_t* __restrict__ out) {
-  const uint64_t cnt = L.counts[0];
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t j = L.tiny[i];
-    const uint64_t a = st[j], len = st[j + w] - a;
-    const FitResult R = fit_range<1>(values, dtype, a, (uint32_t)len, model, 0, nullptr);
-    out[j] = kSmBits + len * (uint64_t)R.b;
-  }
-}
-
-__global__ void k_span_size_warp(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st,
-                                 uint32_t w, int model, SpanLists L, uint64_t* __restrict__ out) {
-  const uint64_t cnt = L.counts[1];
-  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t i = warp; i < cnt; i += nw) {
-    const uint64_t j = L.medium[i];
-    const uint64_t a = st[j], len = st[j + w] - a;
-    const FitResult R = fit_range<32>(values, dtype, a, (uint32_t)len, model, threadIdx.x & 31u, nullptr);
-    if ((threadIdx.x & 31u) == 0) out[j] = kSmBits + len * (uint64_t)R.b;
-  }
-}
-
-__global__ void __launch_bounds__(256)
-    k_span_size_block(const void* __restrict__ values, int dtype, const uint64_t* __restrict__ st, uint32_t w,
-                      int model, SpanLists L, uint64_t* __restrict__ out) {
-  __shared__ FitShared sm;
-  const uint64_t cnt = L.counts[2];
-  for (uint64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const uint64_t j = L.lng[i];
-    const uint64_t a = st[j], len = st[j + w] - a;
-    const FitResult R = fit_range<256>(values, dtype, a, (uint32_t)len, model, threadIdx.x, &sm);
-    if (threadIdx.x == 0) out[j] = kSmBits + len * (uint64_t)R.b;
   }
 }
 
@@ -395,6 +351,332 @@ __global__ void k_sample_sizes_warp(const void* __restrict__ values, int dtype, 
   if (lane == 0 && acc) atomicAdd(total, (unsigned long long)acc);
 }
 
+int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
+  const uint64_t need = (items + per_block - 1) / per_block;
+  const uint64_t cap = (uint64_t)sm_count() * max_blocks_per_sm;
+  return (int)(need < cap ? (need ? need : 1) : cap);
+}
+
+// ----------------------------------------------------------------------------------------- merge
+//
+// The moments of a span's values (w = the value as two's complement int64, x = the local index):
+// T0 = sum w, T1 = sum x w, and min and max of w. Two adjacent spans' moments combine exactly (the
+// right span's x shifts by the left span's length: T1 gains N_left T0_right), and they give the
+// least-squares moment S = sum (2x - (N-1)) w = 2 T1 - (N-1) T0 of the fit and its bounds, so a
+// refit needs one pass over the values: the residual range under the snapped line (none for the
+// constant model, whose residuals are the values themselves). Moments, partition fits and pair
+// fits live in slots indexed by a partition's first split partition ("orig"); a merge combines
+// the right partition's moments into the left one's slot.
+struct SpanStats {
+  i128 T0;
+  i128 T1;
+  int64_t mn;
+  int64_t mx;
+};
+
+// the record fields of a span's full fit
+struct SpanFit {
+  double theta0;
+  double theta1;
+  int32_t s;
+  uint32_t b;
+};
+
+// a pair too long for one warp: its residual range is reduced over pieces of kPiece values
+struct LongPair {
+  uint64_t j;  // pair index
+  uint64_t k;  // slot of its left partition
+  uint64_t a;  // first position
+  FitParams P;
+  uint32_t N;
+  uint32_t pad;
+};
+
+constexpr uint32_t kLaneSpan = 64;     // a lane fits spans up to this long on its own
+constexpr uint32_t kTinySpan = 256;    // size search: a thread per sampled partition up to this size
+constexpr uint32_t kWarpSpan = 4096;   // a warp fits longer pairs up to this long (split partitions: any)
+constexpr uint32_t kPiece = 2048;      // values per piece of a longer pair
+constexpr int kGroupBlock = 256;       // 8 warps, each taking 32 spans at a time
+constexpr uint32_t kStageBytes = 4096; // per warp: a group's values are staged when they fit
+
+__device__ __forceinline__ SpanStats combine_stats(const SpanStats& l, uint64_t nl, const SpanStats& r) {
+  SpanStats c;
+  c.T0 = l.T0 + r.T0;
+  c.T1 = l.T1 + r.T1 + (i128)nl * r.T0;
+  c.mn = min(l.mn, r.mn);
+  c.mx = max(l.mx, r.mx);
+  return c;
+}
+
+// reductions whose result every lane receives
+__device__ __forceinline__ int64_t xw_min(int64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ int64_t xw_max(int64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ uint64_t xw_min_u(uint64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, (uint64_t)__shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ uint64_t xw_max_u(uint64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ i128 xw_sum(i128 v) {
+  uint64_t lo = (uint64_t)v, hi = (uint64_t)((u128)v >> 64);
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t l2 = __shfl_xor_sync(kFull, lo, o);
+    const uint64_t h2 = __shfl_xor_sync(kFull, hi, o);
+    const uint64_t nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return (i128)(((u128)hi << 64) | lo);
+}
+
+// moments of the positions x, x + step, ... < N of the span whose first value is p[0]
+template <typename T>
+__device__ __forceinline__ SpanStats stats_part(const T* p, uint32_t x, uint32_t N, uint32_t step) {
+  SpanStats s;
+  s.T0 = 0;
+  s.T1 = 0;
+  s.mn = INT64_MAX;
+  s.mx = INT64_MIN;
+  for (; x < N; x += step) {
+    const int64_t w = (int64_t)p[x];
+    s.mn = min(s.mn, w);
+    s.mx = max(s.mx, w);
+    s.T0 += (i128)w;
+    s.T1 += (i128)w * (int64_t)x;
+  }
+  return s;
+}
+
+// residual range at the positions x, x + step, ... < N under the parameters P (fit.cuh, steps 4
+// and the fallback's widest zigzag residual), accumulated into lo, hi, zmax
+template <typename T>
+__device__ __forceinline__ void resid_part(const T* p, uint32_t x, uint32_t N, uint32_t step, const FitParams& P,
+                                           int64_t& lo, int64_t& hi, uint64_t& zmax) {
+  if (P.fallback) {
+    for (; x < N; x += step) zmax = max(zmax, zz_encode((int64_t)((uint64_t)p[x] - (uint64_t)P.fb_shift)));
+    return;
+  }
+  uint64_t F = (uint64_t)P.B * x;
+  const uint64_t dF = (uint64_t)P.B * step;
+  if (P.s >= 0) {
+    for (; x < N; x += step, F += dF) {
+      const int64_t r = (int64_t)p[x] - ((int64_t)F >> P.s);
+      lo = min(lo, r);
+      hi = max(hi, r);
+    }
+  } else {
+    for (; x < N; x += step, F += dF) {
+      const int64_t r = (int64_t)p[x] - (int64_t)(F << (-P.s));
+      lo = min(lo, r);
+      hi = max(hi, r);
+    }
+  }
+}
+
+__device__ __forceinline__ FitParams shfl_params(const FitParams& P, int src) {
+  FitParams q;
+  q.B = (int64_t)__shfl_sync(kFull, (unsigned long long)P.B, src);
+  q.fb_shift = (int64_t)__shfl_sync(kFull, (unsigned long long)P.fb_shift, src);
+  q.s = __shfl_sync(kFull, P.s, src);
+  q.fallback = __shfl_sync(kFull, P.fallback, src);
+  return q;
+}
+
+struct MergeWork {
+  LongPair* longs;
+  uint64_t* pieces;
+  unsigned long long* counters;  // [long pairs, pieces]
+  long long* lo;                 // per long pair
+  long long* hi;
+  unsigned long long* zmax;
+};
+
+// Sizes S_M + len * b of spans [st[j], st[j + W]) by the full fit: W = 1, every partition of the
+// split (its moments from a pass over its values, into stats[j], its fit into fit[j]); W = 2, the
+// dirty adjacent pairs (moments combined from stats[orig[j]] and stats[orig[j + 1]], the fit into
+// fit[orig[j]]). A warp takes 32 consecutive spans; when their values cover at most kStageBytes it
+// first stages them in shared memory with coalesced loads. A lane then fits its own span when it is
+// at most kLaneSpan long, the warp fits longer ones together, and pairs longer than kWarpSpan (not
+// staged) go to the piece list, where many warps share their residual pass.
+template <typename T, int W>
+__global__ void __launch_bounds__(kGroupBlock, 2)
+    k_span_groups(const T* __restrict__ v, const uint64_t* __restrict__ st, uint64_t count, uint32_t cap, int model,
+                  const uint8_t* __restrict__ dirty, const uint64_t* __restrict__ orig, SpanStats* __restrict__ stats,
+                  uint64_t* __restrict__ size_out, SpanFit* __restrict__ fit, MergeWork mw) {
+  __shared__ __align__(16) unsigned char stage_raw[kGroupBlock / 32][kStageBytes];
+  constexpr uint64_t kStageVals = kStageBytes / sizeof(T);
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  T* stage = reinterpret_cast<T*>(stage_raw[wib]);
+  const uint64_t ngroups = (count + 31) / 32;
+  const uint64_t gw = (uint64_t)gridDim.x * (kGroupBlock / 32);
+  for (uint64_t g = (uint64_t)blockIdx.x * (kGroupBlock / 32) + wib; g < ngroups; g += gw) {
+    const uint64_t j = g * 32 + lane;
+    bool act = j < count && (W == 1 || dirty[j]);
+    if (!__any_sync(kFull, act)) continue;
+    uint64_t a = 0, c = 0;
+    if (act) {
+      a = st[j];
+      c = st[j + W];
+      if (W == 2 && c - a > cap) {  // pairs beyond the cap never merge
+        size_out[j] = kNone;
+        act = false;
+      }
+    }
+    const uint32_t N = act ? (uint32_t)(c - a) : 0u;
+    const uint64_t ga = xw_min_u(act ? a : ~0ull), gc = xw_max_u(act ? c : 0ull);
+    const bool staged = ga != ~0ull && gc - ga <= kStageVals;
+    if (staged) {
+      for (uint64_t t = lane; t < gc - ga; t += 32) stage[t] = __ldg(v + ga + t);
+      __syncwarp();
+    }
+    const T* src = staged ? stage + (a - ga) : v + a;
+    // moments
+    SpanStats S;
+    S.T0 = S.T1 = 0;
+    S.mn = S.mx = 0;
+    if (W == 1) {
+      if (act && N <= kLaneSpan) S = stats_part(src, 0, N, 1);
+      uint32_t mask = __ballot_sync(kFull, act && N > kLaneSpan);
+      while (mask) {
+        const int sl = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint64_t as = __shfl_sync(kFull, a, sl);
+        const uint32_t Ns = __shfl_sync(kFull, N, sl);
+        const T* ps = staged ? stage + (as - ga) : v + as;
+        SpanStats q = stats_part(ps, lane, Ns, 32);
+        q.T0 = xw_sum(q.T0);
+        q.T1 = xw_sum(q.T1);
+        q.mn = xw_min(q.mn);
+        q.mx = xw_max(q.mx);
+        if ((int)lane == sl) S = q;
+      }
+    } else if (act) {
+      const uint64_t k0 = orig[j], k1 = orig[j + 1];
+      S = combine_stats(stats[k0], st[j + 1] - a, stats[k1]);
+    }
+    // parameters (fit.cuh steps 1-3)
+    const bool lin = model == LECO_MODEL_LINEAR && N >= 2;
+    FitParams P;
+    P.B = 0;
+    P.fb_shift = 0;
+    P.s = 0;
+    P.fallback = 0;
+    if (act) P = solve_params(lin ? 2 * S.T1 - (i128)(N - 1) * S.T0 : (i128)0, S.mx, S.mn, N, lin);
+    // residual range (step 4)
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    uint64_t zmax = 0;
+    const bool need = act && (lin || P.fallback);
+    if (act && !need) {  // constant model on its grid: the residuals are the values
+      lo = S.mn;
+      hi = S.mx;
+    }
+    const bool by_lane = need && N <= kLaneSpan;
+    const bool by_warp = need && N > kLaneSpan && (W == 1 || staged || N <= kWarpSpan);
+    const bool by_pieces = need && !by_lane && !by_warp;
+    if (by_lane) resid_part(src, 0, N, 1, P, lo, hi, zmax);
+    uint32_t mask = __ballot_sync(kFull, by_warp);
+    while (mask) {
+      const int sl = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const uint64_t as = __shfl_sync(kFull, a, sl);
+      const uint32_t Ns = __shfl_sync(kFull, N, sl);
+      const FitParams Ps = shfl_params(P, sl);
+      const T* ps = staged ? stage + (as - ga) : v + as;
+      int64_t l = INT64_MAX, h = INT64_MIN;
+      uint64_t z = 0;
+      resid_part(ps, lane, Ns, 32, Ps, l, h, z);
+      l = xw_min(l);
+      h = xw_max(h);
+      z = xw_max_u(z);
+      if ((int)lane == sl) {
+        lo = l;
+        hi = h;
+        zmax = z;
+      }
+    }
+    if (by_pieces) {
+      const uint32_t np = (N + kPiece - 1) / kPiece;
+      const unsigned long long li = atomicAdd(&mw.counters[0], 1ull);
+      const unsigned long long pb = atomicAdd(&mw.counters[1], (unsigned long long)np);
+      LongPair lp;
+      lp.j = j;
+      lp.k = orig[j];
+      lp.a = a;
+      lp.P = P;
+      lp.N = N;
+      lp.pad = 0;
+      mw.longs[li] = lp;
+      mw.lo[li] = INT64_MAX;
+      mw.hi[li] = INT64_MIN;
+      mw.zmax[li] = 0;
+      for (uint32_t q = 0; q < np; q++) mw.pieces[pb + q] = ((uint64_t)li << 16) | q;
+    }
+    if (act && !by_pieces) {  // steps 5-6
+      const FitResult R = finish_fit(P, lo, hi, zmax);
+      size_out[j] = kSmBits + (uint64_t)N * R.b;
+      const uint64_t slot = W == 1 ? j : orig[j];
+      SpanFit f;
+      f.theta0 = R.theta0;
+      f.theta1 = R.theta1;
+      f.s = R.s;
+      f.b = R.b;
+      fit[slot] = f;
+      if (W == 1) stats[j] = S;
+    }
+    __syncwarp();  // the stage is reused by the next group
+  }
+}
+
+// residual range of one piece of a long pair per warp, folded into the pair's range by atomics
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_pieces(const T* __restrict__ v, MergeWork mw) {
+  const uint64_t np = *(volatile unsigned long long*)&mw.counters[1];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t pi = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; pi < np; pi += nw) {
+    const uint64_t e = mw.pieces[pi];
+    const uint64_t li = e >> 16;
+    const uint32_t q = (uint32_t)(e & 0xFFFFu);
+    const LongPair L = mw.longs[li];
+    const uint32_t x0 = q * kPiece, x1 = min(x0 + kPiece, L.N);
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    uint64_t z = 0;
+    resid_part(v + L.a, x0 + lane, x1, 32, L.P, lo, hi, z);
+    lo = warp_min_i64(lo);
+    hi = warp_max_i64(hi);
+    z = warp_max_u64(z);
+    if (lane == 0) {
+      atomicMin(&mw.lo[li], (long long)lo);
+      atomicMax(&mw.hi[li], (long long)hi);
+      atomicMax(&mw.zmax[li], (unsigned long long)z);
+    }
+  }
+}
+
+// steps 5-6 of the long pairs
+__global__ void k_pair_finish(MergeWork mw, uint64_t* __restrict__ msz, SpanFit* __restrict__ fit) {
+  const uint64_t nl = *(volatile unsigned long long*)&mw.counters[0];
+  for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
+    const LongPair L = mw.longs[li];
+    const FitResult R = finish_fit(L.P, (int64_t)mw.lo[li], (int64_t)mw.hi[li], (uint64_t)mw.zmax[li]);
+    msz[L.j] = kSmBits + (uint64_t)L.N * R.b;
+    SpanFit f;
+    f.theta0 = R.theta0;
+    f.theta1 = R.theta1;
+    f.s = R.s;
+    f.b = R.b;
+    fit[L.k] = f;
+  }
+}
+
 __device__ __forceinline__ bool pair_gain(const uint64_t* sz, const uint64_t* msz, uint64_t j, int64_t* g) {
   if (msz[j] == kNone) return false;
   *g = (int64_t)(sz[j] + sz[j + 1]) - (int64_t)msz[j];
@@ -409,48 +691,56 @@ __device__ __forceinline__ bool beats(int64_t g1, uint64_t s1, int64_t g2, uint6
   return s1 < s2;
 }
 
+// sel[j]: pair j merges this round; keep[p]: partition p survives (it was not merged into its left
+// neighbour); *nsel counts the merging pairs
 __global__ void k_select(const uint64_t* __restrict__ st, const uint64_t* __restrict__ sz,
                          const uint64_t* __restrict__ msz, uint64_t m, uint8_t* __restrict__ sel,
-                         unsigned long long* __restrict__ nsel) {
+                         uint64_t* __restrict__ keep, unsigned long long* __restrict__ nsel) {
   uint32_t local = 0;
-  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j + 1 < m;
-       j += (uint64_t)gridDim.x * blockDim.x) {
-    int64_t g;
-    bool ok = pair_gain(sz, msz, j, &g) && g > 0;
-    if (ok && j > 0) {
-      int64_t gl;
-      if (pair_gain(sz, msz, j - 1, &gl) && !beats(g, st[j], gl, st[j - 1])) ok = false;
-    }
-    if (ok && j + 2 < m) {
-      int64_t gr;
-      if (pair_gain(sz, msz, j + 1, &gr) && !beats(g, st[j], gr, st[j + 1])) ok = false;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < m; j += (uint64_t)gridDim.x * blockDim.x) {
+    bool ok = false;
+    if (j + 1 < m) {
+      int64_t g;
+      ok = pair_gain(sz, msz, j, &g) && g > 0;
+      if (ok && j > 0) {
+        int64_t gl;
+        if (pair_gain(sz, msz, j - 1, &gl) && !beats(g, st[j], gl, st[j - 1])) ok = false;
+      }
+      if (ok && j + 2 < m) {
+        int64_t gr;
+        if (pair_gain(sz, msz, j + 1, &gr) && !beats(g, st[j], gr, st[j + 1])) ok = false;
+      }
     }
     sel[j] = ok ? 1 : 0;
     local += ok ? 1u : 0u;
+    // partition j + 1 is absorbed when pair j merges; partition 0 always survives
+    if (j + 1 < m) keep[j + 1] = ok ? 0ull : 1ull;
+    if (j == 0) keep[0] = 1ull;
   }
   local = (uint32_t)warp_sum_u64(local);
   if ((threadIdx.x & 31u) == 0 && local) atomicAdd(nsel, (unsigned long long)local);
 }
 
-// partition p survives unless it was merged into its left neighbour
-__global__ void k_keep(const uint8_t* __restrict__ sel, uint64_t m, uint64_t* __restrict__ keep) {
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
-       p += (uint64_t)gridDim.x * blockDim.x)
-    keep[p] = (p == 0 || !sel[p - 1]) ? 1ull : 0ull;
-}
-
+// the next round's arrays; a merged pair's moments and fit become its left partition's
 __global__ void k_compact(const uint64_t* __restrict__ st, const uint64_t* __restrict__ sz,
                           const uint64_t* __restrict__ msz, const uint8_t* __restrict__ sel,
-                          const uint64_t* __restrict__ newidx, uint64_t m, uint64_t n, uint64_t new_m,
-                          uint64_t* __restrict__ nst, uint64_t* __restrict__ nsz,
-                          uint64_t* __restrict__ nmsz, uint8_t* __restrict__ ndirty) {
+                          const uint64_t* __restrict__ newidx, const uint64_t* __restrict__ orig, uint64_t m,
+                          uint64_t n, uint64_t new_m, SpanStats* __restrict__ stats, SpanFit* __restrict__ fitres,
+                          const SpanFit* __restrict__ pairfit, uint64_t* __restrict__ nst, uint64_t* __restrict__ nsz,
+                          uint64_t* __restrict__ nmsz, uint8_t* __restrict__ ndirty, uint64_t* __restrict__ norig) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
        p += (uint64_t)gridDim.x * blockDim.x) {
     if (p > 0 && sel[p - 1]) continue;  // absorbed by p-1
     const uint64_t k = newidx[p];
     const bool mp = p + 1 < m && sel[p];
+    const uint64_t o = orig[p];
     nst[k] = st[p];
     nsz[k] = mp ? msz[p] : sz[p];
+    norig[k] = o;
+    if (mp) {
+      stats[o] = combine_stats(stats[o], st[p + 1] - st[p], stats[orig[p + 1]]);
+      fitres[o] = pairfit[o];
+    }
     const uint64_t q = mp ? p + 2 : p + 1;  // next surviving partition
     if (q < m) {
       const bool mq = q + 1 < m && sel[q];
@@ -462,43 +752,60 @@ __global__ void k_compact(const uint64_t* __restrict__ st, const uint64_t* __res
   }
 }
 
-__global__ void k_fill_u8(uint8_t* p, uint64_t count, uint8_t v) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    p[i] = v;
+// the column's records from the final partitions' fits (as k_fit writes them: offset 0, exact grid)
+__global__ void k_var_records(const uint64_t* __restrict__ st, const uint64_t* __restrict__ orig,
+                              const SpanFit* __restrict__ fitres, uint64_t m, Record* __restrict__ rec) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const SpanFit f = fitres[orig ? orig[p] : p];
+    Record r;
+    r.theta0 = f.theta0;
+    r.theta1 = f.theta1;
+    r.start = st[p];
+    r.word3 = make_w3(0, f.b, f.s, 1);
+    rec[p] = r;
+  }
 }
 
-int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
-  const uint64_t need = (items + per_block - 1) / per_block;
-  const uint64_t cap = (uint64_t)sm_count() * max_blocks_per_sm;
-  return (int)(need < cap ? (need ? need : 1) : cap);
+__global__ void k_iota(uint64_t* p, uint64_t count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = i;
 }
+
 
 template <typename T>
 cudaError_t dalloc(T** p, uint64_t elems, cudaStream_t st) {
   return dev_alloc((void**)p, (elems ? elems : 1) * sizeof(T), st);
 }
 
-// spans longer than kLongPair among those of a column of n values: partitions are disjoint, and
-// of adjacent pairs every other one is
-inline uint64_t long_span_cap(uint64_t n) { return 2 * (n / kLongPair + 1); }
+int group_grid(uint64_t count) {
+  const uint64_t groups = (count + 31) / 32;
+  return grid_for((groups + kGroupBlock / 32 - 1) / (kGroupBlock / 32), 1, 2);
+}
 
-// sizes of the `count` spans [st[j], st[j + w]) selected by dirty (nullptr: all) into out; the lists
-// hold `count` entries each (tiny, medium) and long_span_cap(n) (long)
-cudaError_t span_sizes(const void* values, int dtype, uint64_t n, const uint64_t* st, uint64_t count, uint32_t w,
-                       uint32_t cap, int model, const uint8_t* dirty, uint64_t* out, const SpanLists& L,
-                       cudaStream_t stm) {
+template <typename T>
+cudaError_t span_groups(const void* values, int W, const uint64_t* st, uint64_t count, uint32_t cap, int model,
+                        const uint8_t* dirty, const uint64_t* orig, SpanStats* stats, uint64_t* size_out, SpanFit* fit,
+                        const MergeWork& mw, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(L.counts, 0, 3 * sizeof(unsigned long long), stm);
-  if (e != cudaSuccess) return e;
-  k_classify<<<grid_for(count, 256, 8), 256, 0, stm>>>(st, count, w, cap, dirty, out, L);
-  k_span_size_thread<<<grid_for(count, 256, 8), 256, 0, stm>>>(values, dtype, st, w, model, L, out);
-  k_span_size_warp<<<grid_for(count * 32, 256, 8), 256, 0, stm>>>(values, dtype, st, w, model, L, out);
-  k_span_size_block<<<grid_for(long_span_cap(n), 1, 4), 256, 0, stm>>>(values, dtype, st, w, model, L, out);
+  const T* v = static_cast<const T*>(values);
+  if (W == 1)
+    k_span_groups<T, 1><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, orig, stats,
+                                                                  size_out, fit, mw);
+  else
+    k_span_groups<T, 2><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, orig, stats,
+                                                                  size_out, fit, mw);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pair_rounds_long(const void* values, const MergeWork& mw, uint64_t* msz, SpanFit* pairfit, cudaStream_t s) {
+  k_pair_pieces<T><<<sm_count() * 8, 256, 0, s>>>(static_cast<const T*>(values), mw);
+  k_pair_finish<<<sm_count() * 2, 256, 0, s>>>(mw, msz, pairfit);
   return cudaGetLastError();
 }
 
 }  // namespace
+
 
 // Fixed partition-size search (§3.2.1), in the reading the oracle states (R9): SplitMix64-placed
 // sample subsequences, an exponential phase over powers of two that ends after the first size above
@@ -594,161 +901,215 @@ cudaError_t search_partition_size(const void* values, int dtype, uint64_t n, int
   return e;
 }
 
-// Runs split + merge; writes m+1 starts to starts_out (capacity n+1) and m to *m_out.
-cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
-                          int model, bool seeded, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
+// Runs split + merge; writes m+1 starts to starts_out (capacity n+1) and m to *m_out. rec_out:
+// when non-null, receives m records (a new device allocation from the library pool; the caller
+// frees it) holding the full fit of every final partition, as the encoder's fit writes them.
+cudaError_t var_partition_fit(const void* values, int dtype, uint64_t n, double tau, uint32_t cap, int model,
+                              bool seeded, uint64_t* starts_out, uint64_t* m_out, Record** rec_out, cudaStream_t st) {
   *m_out = 0;
+  if (rec_out) *rec_out = nullptr;
   if (n == 0) {
     const uint64_t zero = 0;
     cudaError_t e = cudaMemcpyAsync(starts_out, &zero, 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
   }
+  const bool u32 = dtype == LECO_U32;
   const double thresh = tau * (double)kSmBits;
   const uint64_t nw = (n + 63) / 64;
-  uint64_t *bitmap = nullptr, *cnt = nullptr, *pos = nullptr, *scan_scratch = nullptr, *d_total = nullptr;
-  uint64_t* seeds = nullptr;
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  // C <= tau * S_M for an integer C: C <= floor(tau * S_M) (thresh >= 0, below 2^62 here)
+  const int64_t tfloor = thresh < 4.0e18 ? (int64_t)floor(thresh) : INT64_MAX;
+  uint64_t m = 0;
   cudaError_t e = cudaSuccess;
-  const uint64_t scan_elems = nw / 2048 + 2;
-#define LECO_TRY(x)          \
-  do {                       \
-    e = (x);                 \
-    if (e != cudaSuccess) goto done; \
-  } while (0)
-  {
-    LECO_TRY(dalloc(&bitmap, nw, st));
-    LECO_TRY(dalloc(&cnt, nw, st));
-    LECO_TRY(dalloc(&pos, nw, st));
-    LECO_TRY(dalloc(&scan_scratch, scan_elems + 1, st));
-    LECO_TRY(dalloc(&d_total, 1, st));
-    const uint64_t nchunks = (n + kChunk - 1) / kChunk;
-    // C <= tau * S_M for an integer C: C <= floor(tau * S_M) (thresh >= 0, below 2^62 here). The
-    // sweeps are serial per chunk, so each gets a warp of its own SM slot (one-warp blocks)
-    const int64_t tfloor = thresh < 4.0e18 ? (int64_t)floor(thresh) : INT64_MAX;
+  {  // split
+    uint64_t *bitmap = nullptr, *cnt = nullptr, *pos = nullptr, *scan_scratch = nullptr, *d_total = nullptr;
+    uint64_t* seeds = nullptr;
+    const uint64_t scan_elems = nw / 2048 + 2;
+    if (e == cudaSuccess) e = dalloc(&bitmap, nw, st);
+    if (e == cudaSuccess) e = dalloc(&cnt, nw, st);
+    if (e == cudaSuccess) e = dalloc(&pos, nw, st);
+    if (e == cudaSuccess) e = dalloc(&scan_scratch, scan_elems + 1, st);
+    if (e == cudaSuccess) e = dalloc(&d_total, 1, st);
+    if (e == cudaSuccess && seeded) e = dalloc(&seeds, nchunks, st);
     uint8_t* narrow = reinterpret_cast<uint8_t*>(cnt);  // scratch: cnt is not used until the popcount
-    if (seeded) LECO_TRY(dalloc(&seeds, nchunks, st));
-    if (dtype == LECO_U32) {
-      k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint32_t*>(values), n, narrow);
-      if (seeded)
-        k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint32_t*>(values), n, seeds);
-      k_split<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(static_cast<const uint32_t*>(values), n, cap, tfloor, narrow,
-                                                         seeds, bitmap);
-    } else {
-      k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint64_t*>(values), n, narrow);
-      if (seeded)
-        k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(static_cast<const uint64_t*>(values), n, seeds);
-      k_split<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(static_cast<const uint64_t*>(values), n, cap, tfloor, narrow,
-                                                         seeds, bitmap);
-    }
-    LECO_TRY(cudaGetLastError());
-    k_popc<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, cnt);
-    LECO_TRY(cudaGetLastError());
-    LECO_TRY(scan_u64(cnt, nw, pos, scan_scratch, d_total, st));
-    uint64_t m = 0;
-    LECO_TRY(cudaMemcpyAsync(&m, d_total, 8, cudaMemcpyDeviceToHost, st));
-    LECO_TRY(cudaStreamSynchronize(st));
-    k_scatter_starts<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, pos, n, m, starts_out);
-    LECO_TRY(cudaGetLastError());
-    cudaFreeAsync(cnt, st);
-    cnt = nullptr;
-    cudaFreeAsync(pos, st);
-    pos = nullptr;
-    cudaFreeAsync(bitmap, st);
-    bitmap = nullptr;
-    if (seeds) cudaFreeAsync(seeds, st);
-    seeds = nullptr;
-    cudaFreeAsync(scan_scratch, st);
-    scan_scratch = nullptr;
-
-    // merge state (ping-pong)
-    uint64_t *st_b = nullptr, *sz_a = nullptr, *sz_b = nullptr, *msz_a = nullptr, *msz_b = nullptr;
-    uint64_t *keep = nullptr, *newidx = nullptr, *scr = nullptr;
-    uint8_t *dirty_a = nullptr, *dirty_b = nullptr, *sel = nullptr;
-    unsigned long long* d_nsel = nullptr;
-    const uint64_t m0 = m;
-    const uint64_t scr_elems = m0 / 2048 + 2;
-    bool ok = true;
-    ok = ok && dalloc(&st_b, m0 + 1, st) == cudaSuccess;
-    ok = ok && dalloc(&sz_a, m0, st) == cudaSuccess && dalloc(&sz_b, m0, st) == cudaSuccess;
-    ok = ok && dalloc(&msz_a, m0, st) == cudaSuccess && dalloc(&msz_b, m0, st) == cudaSuccess;
-    ok = ok && dalloc(&keep, m0, st) == cudaSuccess && dalloc(&newidx, m0, st) == cudaSuccess;
-    ok = ok && dalloc(&scr, scr_elems + 1, st) == cudaSuccess;
-    ok = ok && dalloc(&dirty_a, m0, st) == cudaSuccess && dalloc(&dirty_b, m0, st) == cudaSuccess;
-    ok = ok && dalloc(&sel, m0, st) == cudaSuccess && dalloc(&d_nsel, 1, st) == cudaSuccess;
-    SpanLists lists;
-    lists.tiny = lists.medium = lists.lng = nullptr;
-    lists.counts = nullptr;
-    ok = ok && dalloc(&lists.tiny, m0, st) == cudaSuccess && dalloc(&lists.medium, m0, st) == cudaSuccess;
-    ok = ok && dalloc(&lists.lng, long_span_cap(n), st) == cudaSuccess && dalloc(&lists.counts, 3, st) == cudaSuccess;
-    uint64_t* cur_st = starts_out;
-    uint64_t* nxt_st = st_b;
-    if (ok && m > 1) {
-      e = span_sizes(values, dtype, n, cur_st, m, 1, ~0u, model, nullptr, sz_a, lists, st);
-      k_fill_u8<<<grid_for(m, 256, 8), 256, 0, st>>>(dirty_a, m, 1);
-      if (e == cudaSuccess) e = cudaGetLastError();
-      while (e == cudaSuccess && m > 1) {
-        e = span_sizes(values, dtype, n, cur_st, m - 1, 2, cap, model, dirty_a, msz_a, lists, st);
-        if (e != cudaSuccess) break;
-        cudaMemsetAsync(d_nsel, 0, 8, st);
-        k_select<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, m, sel, d_nsel);
-        unsigned long long nsel = 0;
-        e = cudaMemcpyAsync(&nsel, d_nsel, 8, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess || nsel == 0) break;
-        k_keep<<<grid_for(m, 256, 8), 256, 0, st>>>(sel, m, keep);
-        e = scan_u64(keep, m, newidx, scr, d_total, st);
-        if (e != cudaSuccess) break;
-        const uint64_t new_m = m - nsel;
-        k_compact<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, sel, newidx, m, n, new_m,
-                                                       nxt_st, sz_b, msz_b, dirty_b);
-        e = cudaGetLastError();
-        uint64_t* t64;
-        uint8_t* t8;
-        t64 = cur_st; cur_st = nxt_st; nxt_st = t64;
-        t64 = sz_a; sz_a = sz_b; sz_b = t64;
-        t64 = msz_a; msz_a = msz_b; msz_b = t64;
-        t8 = dirty_a; dirty_a = dirty_b; dirty_b = t8;
-        m = new_m;
+    if (e == cudaSuccess) {
+      const int wgrid = (int)((nchunks + 31) / 32);
+      if (u32) {
+        const uint32_t* v = static_cast<const uint32_t*>(values);
+        k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, narrow);
+        if (seeded) {
+          k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, seeds);
+          k_split_seeded<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(v, n, cap, tfloor, narrow, seeds, bitmap);
+        } else {
+          k_split_staged<<<wgrid, 32, 0, st>>>(v, n, cap, tfloor, narrow, bitmap);
+        }
+      } else {
+        const uint64_t* v = static_cast<const uint64_t*>(values);
+        k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, narrow);
+        if (seeded) {
+          k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, seeds);
+          k_split_seeded<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(v, n, cap, tfloor, narrow, seeds, bitmap);
+        } else {
+          k_split_staged<<<wgrid, 32, 0, st>>>(v, n, cap, tfloor, narrow, bitmap);
+        }
       }
-      if (e == cudaSuccess && cur_st != starts_out)
-        e = cudaMemcpyAsync(starts_out, cur_st, (m + 1) * 8, cudaMemcpyDeviceToDevice, st);
-    } else if (!ok) {
-      e = cudaErrorMemoryAllocation;
+      e = cudaGetLastError();
     }
+    if (e == cudaSuccess) {
+      k_popc<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, cnt);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = scan_u64(cnt, nw, pos, scan_scratch, d_total, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, d_total, 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    // st_b may be cur_st's partner; both are scratch except starts_out
-    cudaFreeAsync(cur_st == starts_out ? nxt_st : cur_st, st);
-    cudaFreeAsync(sz_a, st);
-    cudaFreeAsync(sz_b, st);
-    cudaFreeAsync(msz_a, st);
-    cudaFreeAsync(msz_b, st);
-    cudaFreeAsync(keep, st);
-    cudaFreeAsync(newidx, st);
-    cudaFreeAsync(scr, st);
-    cudaFreeAsync(dirty_a, st);
-    cudaFreeAsync(dirty_b, st);
-    cudaFreeAsync(sel, st);
-    cudaFreeAsync(d_nsel, st);
-    cudaFreeAsync(lists.tiny, st);
-    cudaFreeAsync(lists.medium, st);
-    cudaFreeAsync(lists.lng, st);
-    cudaFreeAsync(lists.counts, st);
-    if (e == cudaSuccess) *m_out = m;
+    if (e == cudaSuccess) {
+      k_scatter_starts<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, pos, n, m, starts_out);
+      e = cudaGetLastError();
+    }
+    for (uint64_t* p : {bitmap, cnt, pos, scan_scratch, d_total, seeds})
+      if (p) cudaFreeAsync(p, st);
   }
-done:
-  if (seeds) cudaFreeAsync(seeds, st);
-  if (bitmap) cudaFreeAsync(bitmap, st);
-  if (cnt) cudaFreeAsync(cnt, st);
-  if (pos) cudaFreeAsync(pos, st);
-  if (scan_scratch) cudaFreeAsync(scan_scratch, st);
-  if (d_total) cudaFreeAsync(d_total, st);
-#undef LECO_TRY
+  if (e != cudaSuccess) return e;
+
+  // merge state
+  const uint64_t m0 = m;
+  SpanStats* stats = nullptr;
+  SpanFit *fitres = nullptr, *pairfit = nullptr;
+  uint64_t *orig_a = nullptr, *orig_b = nullptr, *st_b = nullptr, *sz_a = nullptr, *sz_b = nullptr;
+  uint64_t *msz_a = nullptr, *msz_b = nullptr, *keep = nullptr, *newidx = nullptr, *scr = nullptr, *d_total = nullptr;
+  uint8_t *dirty_a = nullptr, *dirty_b = nullptr, *sel = nullptr;
+  unsigned long long* d_nsel = nullptr;
+  MergeWork mw;
+  mw.longs = nullptr;
+  mw.pieces = nullptr;
+  mw.counters = nullptr;
+  mw.lo = nullptr;
+  mw.hi = nullptr;
+  mw.zmax = nullptr;
+  const uint64_t long_cap = 2 * n / kWarpSpan + 2;
+  const uint64_t piece_cap = 2 * n / kPiece + long_cap + 2;
+  const uint64_t scr_elems = m0 / 2048 + 2;
+  if (e == cudaSuccess) e = dalloc(&stats, m0, st);
+  if (e == cudaSuccess) e = dalloc(&fitres, m0, st);
+  if (e == cudaSuccess) e = dalloc(&pairfit, m0, st);
+  if (e == cudaSuccess) e = dalloc(&orig_a, m0, st);
+  if (e == cudaSuccess) e = dalloc(&orig_b, m0, st);
+  if (e == cudaSuccess) e = dalloc(&st_b, m0 + 1, st);
+  if (e == cudaSuccess) e = dalloc(&sz_a, m0, st);
+  if (e == cudaSuccess) e = dalloc(&sz_b, m0, st);
+  if (e == cudaSuccess) e = dalloc(&msz_a, m0, st);
+  if (e == cudaSuccess) e = dalloc(&msz_b, m0, st);
+  if (e == cudaSuccess) e = dalloc(&keep, m0, st);
+  if (e == cudaSuccess) e = dalloc(&newidx, m0, st);
+  if (e == cudaSuccess) e = dalloc(&scr, scr_elems + 1, st);
+  if (e == cudaSuccess) e = dalloc(&d_total, 1, st);
+  if (e == cudaSuccess) e = dalloc(&dirty_a, m0, st);
+  if (e == cudaSuccess) e = dalloc(&dirty_b, m0, st);
+  if (e == cudaSuccess) e = dalloc(&sel, m0, st);
+  if (e == cudaSuccess) e = dalloc(&d_nsel, 1, st);
+  if (e == cudaSuccess) e = dalloc(&mw.longs, long_cap, st);
+  if (e == cudaSuccess) e = dalloc(&mw.pieces, piece_cap, st);
+  if (e == cudaSuccess) e = dalloc(&mw.counters, 2, st);
+  if (e == cudaSuccess) e = dalloc(&mw.lo, long_cap, st);
+  if (e == cudaSuccess) e = dalloc(&mw.hi, long_cap, st);
+  if (e == cudaSuccess) e = dalloc(&mw.zmax, long_cap, st);
+  uint64_t* cur_st = starts_out;
+  uint64_t* nxt_st = st_b;
+  // every split partition's moments, fit and size
+  if (e == cudaSuccess)
+    e = u32 ? span_groups<uint32_t>(values, 1, cur_st, m, cap, model, nullptr, nullptr, stats, sz_a, fitres, mw, st)
+            : span_groups<uint64_t>(values, 1, cur_st, m, cap, model, nullptr, nullptr, stats, sz_a, fitres, mw, st);
+  if (e == cudaSuccess) {
+    k_iota<<<grid_for(m, 256, 8), 256, 0, st>>>(orig_a, m);
+    e = cudaMemsetAsync(dirty_a, 1, m, st);
+  }
+  while (e == cudaSuccess && m > 1) {
+    e = cudaMemsetAsync(mw.counters, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+      e = u32 ? span_groups<uint32_t>(values, 2, cur_st, m - 1, cap, model, dirty_a, orig_a, stats, msz_a, pairfit,
+                                      mw, st)
+              : span_groups<uint64_t>(values, 2, cur_st, m - 1, cap, model, dirty_a, orig_a, stats, msz_a, pairfit,
+                                      mw, st);
+    if (e == cudaSuccess)
+      e = u32 ? pair_rounds_long<uint32_t>(values, mw, msz_a, pairfit, st)
+              : pair_rounds_long<uint64_t>(values, mw, msz_a, pairfit, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_nsel, 0, 8, st);
+    if (e != cudaSuccess) break;
+    k_select<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, m, sel, keep, d_nsel);
+    unsigned long long nsel = 0;
+    e = cudaMemcpyAsync(&nsel, d_nsel, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || nsel == 0) break;
+    e = scan_u64(keep, m, newidx, scr, d_total, st);
+    if (e != cudaSuccess) break;
+    const uint64_t new_m = m - nsel;
+    k_compact<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, sel, newidx, orig_a, m, n, new_m, stats,
+                                                   fitres, pairfit, nxt_st, sz_b, msz_b, dirty_b, orig_b);
+    e = cudaGetLastError();
+    std::swap(cur_st, nxt_st);
+    std::swap(sz_a, sz_b);
+    std::swap(msz_a, msz_b);
+    std::swap(dirty_a, dirty_b);
+    std::swap(orig_a, orig_b);
+    m = new_m;
+  }
+  if (e == cudaSuccess && rec_out) {
+    e = dalloc(rec_out, m, st);
+    if (e == cudaSuccess) {
+      k_var_records<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, orig_a, fitres, m, *rec_out);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && cur_st != starts_out)
+    e = cudaMemcpyAsync(starts_out, cur_st, (m + 1) * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(cur_st == starts_out ? nxt_st : cur_st, st);  // st_b, wherever it ended up
+  for (void* p : {(void*)stats, (void*)fitres, (void*)pairfit, (void*)orig_a, (void*)orig_b, (void*)sz_a,
+                  (void*)sz_b, (void*)msz_a, (void*)msz_b, (void*)keep, (void*)newidx, (void*)scr, (void*)d_total,
+                  (void*)dirty_a, (void*)dirty_b, (void*)sel, (void*)d_nsel, (void*)mw.longs, (void*)mw.pieces,
+                  (void*)mw.counters, (void*)mw.lo, (void*)mw.hi, (void*)mw.zmax})
+    if (p) cudaFreeAsync(p, st);
+  if (e != cudaSuccess && rec_out && *rec_out) {
+    cudaFreeAsync(*rec_out, st);
+    *rec_out = nullptr;
+  }
+  if (e == cudaSuccess) *m_out = m;
   return e;
+}
+
+cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap, int model, bool seeded,
+                          uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
+  return var_partition_fit(values, dtype, n, tau, cap, model, seeded, starts_out, m_out, nullptr, st);
 }
 
 cudaError_t var_partition(const void* values, int dtype, uint64_t n, double tau, uint32_t cap,
                           int model, uint64_t* starts_out, uint64_t* m_out, cudaStream_t st) {
-  return var_partition(values, dtype, n, tau, cap, model, false, starts_out, m_out, st);
+  return var_partition_fit(values, dtype, n, tau, cap, model, false, starts_out, m_out, nullptr, st);
+}
+
+namespace {
+// lenbits[p] = len_p * b_p and the widest b, from records whose fits are done (variable partitions)
+__global__ void k_lenbits(const Record* __restrict__ rec, const uint64_t* __restrict__ starts, uint64_t m,
+                          uint64_t* __restrict__ lenbits, uint32_t* __restrict__ max_b) {
+  uint32_t mb = 0;
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = w3_b(rec[p].word3);
+    lenbits[p] = (starts[p + 1] - starts[p]) * b;
+    mb = max(mb, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_down_sync(kFull, mb, o));
+  if ((threadIdx.x & 31u) == 0 && mb) atomicMax(max_b, mb);
+}
+}  // namespace
+
+cudaError_t launch_lenbits(const Record* rec, const uint64_t* starts, uint64_t m, uint64_t* lenbits, uint32_t* max_b,
+                           cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess || m == 0) return e;
+  k_lenbits<<<grid_for(m, 256, 8), 256, 0, st>>>(rec, starts, m, lenbits, max_b);
+  return cudaGetLastError();
 }
 
 }  // namespace leco
+

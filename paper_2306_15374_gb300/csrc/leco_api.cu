@@ -90,8 +90,9 @@ void release(leco_column* c, cudaStream_t st) {
   delete c;
 }
 
-// fit + offsets + pack of an already partitioned column (c->m, c->starts or c->L set)
-leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t st) {
+// fit + offsets + pack of an already partitioned column (c->m, c->starts or c->L set). prefit: the
+// records already hold every partition's fit (variable partitions fitted by the partitioner)
+leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t st, bool prefit = false) {
   const uint64_t m = c->m;
   const bool poly = c->model == LECO_MODEL_POLY;
   const uint64_t pc_elems = poly ? (sizeof(PolyCoef) / 8) * (m ? m : 1) : 0;
@@ -108,8 +109,11 @@ leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t
   uint64_t hres[2] = {0, 0};
   uint64_t& total = hres[0];
   uint32_t flags = 0;
-  e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, pcoef, d_maxb, c->status,
-                 st);
+  if (prefit)
+    e = launch_lenbits(c->rec, starts, m, lenbits, d_maxb, st);
+  else
+    e = launch_fit(d_values, c->dtype, c->n, starts, c->L, m, c->model, c->rec, lenbits, pcoef, d_maxb, c->status,
+                   st);
   if (e == cudaSuccess)
     e = launch_offsets(c->rec, lenbits, m, off_scr, offsets_scratch_elems(m), d_total, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hres, d_total, 16, cudaMemcpyDeviceToHost, st);
@@ -364,6 +368,7 @@ leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
   c->home = st;
   cudaGetDevice(&c->device);
   leco_status s = LECO_OK;
+  bool encode_prefit = false;
   if (policy.kind == LECO_PART_AUTO) {  // fixed partitions of the searched size (§3.2.1)
     uint32_t L = 1;
     s = leco_search_partition_size(d_values, n, dtype, model, policy.part_size, 0.01, 0, stream, &L, nullptr,
@@ -399,19 +404,28 @@ leco_status leco_encode(const void* d_values, uint64_t n, leco_dtype dtype,
       return from_cuda(e);
     }
     uint64_t m = 0;
-    s = leco_var_partition(d_values, n, dtype, policy, model, tmp, &m, stream);
+    // the partitioner's fits are the records of a constant or linear column
+    Record* prefit = nullptr;
+    const uint32_t cap = policy.part_size ? policy.part_size : kMaxPartLen;
+    s = from_cuda(var_partition_fit(d_values, dtype, n, policy.tau, cap, sizing_model(model),
+                                    policy.kind == LECO_PART_VAR_SEEDED, tmp, &m,
+                                    model == LECO_MODEL_POLY ? nullptr : &prefit, st));
     if (s == LECO_OK) {
       c->m = m;
       s = alloc_meta(c, st);
     }
     if (s == LECO_OK)
       s = from_cuda(cudaMemcpyAsync(c->starts, tmp, 8 * (m + 1), cudaMemcpyDeviceToDevice, st));
+    if (s == LECO_OK && prefit && m)
+      s = from_cuda(cudaMemcpyAsync(c->rec, prefit, sizeof(Record) * m, cudaMemcpyDeviceToDevice, st));
+    if (s == LECO_OK) encode_prefit = prefit != nullptr;
+    if (prefit) cudaFreeAsync(prefit, st);
     cudaFreeAsync(tmp, st);
   } else {
     delete c;
     return LECO_ERR_INVALID_ARG;
   }
-  if (s == LECO_OK) s = encode_partitions(c, d_values, st);
+  if (s == LECO_OK) s = encode_partitions(c, d_values, st, encode_prefit);
   if (s != LECO_OK) {
     release(c, st);
     return s;

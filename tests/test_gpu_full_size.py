@@ -86,10 +86,48 @@ def _check_queries(lc, col, v, dv, bits):
     assert lc.leco_sync(col) == lc.LECO_OK
 
 
+_CFG3 = {}
+
+
+def _cfg3(dist):
+    """The full variable-partition column, generated once per test session."""
+    if dist not in _CFG3:
+        _CFG3[dist] = W.cfg3(dist)
+    return _CFG3[dist]
+
+
+# Contiguous slices of the two full columns, each partitioned as a column of its own: 8M piecewise
+# values (about 120 chunks of 2^16 and, from the split's ~4M partitions, the merge's full round
+# count) and 16M timestamps (about 250 chunks, partitions merged across chunk edges).
+SLICES = [("a", 60_000_000, 8_000_000), ("b", 200_000_000, 16_000_000)]
+
+
+@pytest.mark.parametrize("dist,off,n", SLICES, ids=["piecewise_8M", "timestamps_16M"])
+def test_variable_partition_slice_matches_round_oracle(lc, dist, off, n):
+    """The whole boundary list of the GPU split/merge equals the oracle's round reading (§3.2.2,
+    chunked split and round-synchronous merge) on a multi-million-value slice; the column built on it
+    is lossless."""
+    import torch
+
+    v = _cfg3(dist)[off:off + n].copy()
+    bits = 64 if dist == "a" else 32
+    dv = to_dev(v, bits)
+    starts = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    m = lc.leco_var_partition(dv, starts, lc.variable(TAU), lc.LECO_MODEL_LINEAR)
+    got = from_dev(starts)[: m + 1]
+    want = oracle.var_partition(v, TAU, lc.LECO_MODEL_LINEAR, variant="round")
+    assert len(got) == len(want) and np.array_equal(got, want)
+    col = lc.leco_encode(dv, lc.variable(TAU), lc.LECO_MODEL_LINEAR)
+    out = torch.empty_like(dv)
+    lc.leco_decode_all(col, out)
+    assert torch.equal(out, dv)
+    col.free()
+
+
 @pytest.mark.parametrize("dist", ["a", "b"])
 def test_full_size_variable_partitions(lc, dist):
     """200M piecewise-linear uint64 / 500M uint32 timestamps, GPU split/merge at tau = 0.03."""
-    v = W.cfg3(dist)
+    v = _cfg3(dist)
     bits = 64 if dist == "a" else 32
     n = len(v)
     dv = to_dev(v, bits)

@@ -72,6 +72,10 @@ def test_noalloc_refuses_what_does_not_fit(lc):
     assert e.value.status == lc.LECO_ERR_INVALID_ARG and e.value.nwords > 4
     # more partitions than the fixed scratch holds (2^18)
     big = torch.zeros((1 << 18) + 1, dtype=torch.int64, device="cuda")
+    big_rec = torch.zeros(4 * big.numel(), dtype=torch.int64, device="cuda")
     with pytest.raises(lc.LecoError) as e:
-        lc.leco_encode_fixed_noalloc(big, 1, torch.zeros(1, dtype=torch.int64, device="cuda"), small)
+        lc.leco_encode_fixed_noalloc(big, 1, big_rec, small)
     assert e.value.status == lc.LECO_ERR_INVALID_ARG
+    # a records buffer too small for ceil(n / L) records is refused before the call
+    with pytest.raises(ValueError):
+        lc.leco_encode_fixed_noalloc(big, 1, torch.zeros(1, dtype=torch.int64, device="cuda"), small)
