@@ -57,15 +57,19 @@ __host__ __device__ __forceinline__ uint64_t divlu(uint64_t u1, uint64_t u0, uin
 }
 
 // floor(num / den) for den > 0, exactly. Divisors below 2^64 (every fit of a partition up to 2^21
-// values) take two native 64-bit divisions and one 128-by-64 long division; wider divisors use
-// the generic 128-bit routine, whose bit-serial latency would otherwise stall a whole CTA per
-// fitted partition.
+// values) take one native 64-bit division when |num| < 2^64 (the common case of short partitions),
+// else two native 64-bit divisions and one 128-by-64 long division; wider divisors use the generic
+// 128-bit routine, whose bit-serial latency would otherwise stall a whole CTA per fitted partition.
 __host__ __device__ __forceinline__ i128 floordiv_i128(i128 num, i128 den) {
   if ((den >> 64) == 0 && num != ((i128)1 << 127)) {
     const uint64_t d = (uint64_t)den;
     const bool neg = num < 0;
     const u128 u = neg ? (u128)0 - (u128)num : (u128)num;
     const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    if (hi == 0) {
+      const uint64_t q0 = lo / d, r0 = lo - q0 * d;
+      return neg ? -(i128)q0 - (r0 != 0 ? 1 : 0) : (i128)q0;
+    }
     const uint64_t qh = hi / d;
     uint64_t r = 0;
     const uint64_t ql = divlu(hi - qh * d, lo, d, &r);

@@ -77,6 +77,24 @@ __device__ __forceinline__ bool split_step(uint64_t j, int64_t w, int64_t prev, 
   return take;
 }
 
+// One step of the same rule for a narrow chunk, with positions relative to the chunk (below 2^17)
+// so that the cost C stays in 32 bits: a chunk's partition is at most 2^16 long and D <= 64, so
+// |C| < 2^23, and tf32 = min(floor(tau S_M), 2^31 - 1) decides C <= tau S_M exactly.
+__device__ __forceinline__ bool split_step_narrow(uint32_t jj, int64_t d, uint32_t& ii, int64_t& dmax, int64_t& dmin,
+                                                  int& cur, uint32_t cap, int32_t tf32) {
+  const uint32_t len = jj - ii;
+  int64_t nmax = max(dmax, d), nmin = min(dmin, d);
+  if (len == 1) nmax = nmin = d;
+  const int next = bitlen_u64((uint64_t)nmax - (uint64_t)nmin);
+  const int32_t C = (int32_t)(len + 1) * next - (int32_t)len * cur;
+  const bool take = len < cap && C <= tf32;
+  cur = take ? next : 0;
+  dmax = take ? nmax : 0;
+  dmin = take ? nmin : 0;
+  ii = take ? ii : jj;
+  return take;
+}
+
 // Left-to-right split of 32 chunks per warp (lane l sweeps chunk 32 w + l). Segment k of every
 // chunk (positions k kSplitSeg .. + kSplitSeg) is loaded by the whole warp with coalesced loads one
 // segment ahead, transposed through shared memory (row x holds position x of the 32 chunks, padded
@@ -94,22 +112,23 @@ __global__ void __launch_bounds__(32) k_split_staged(const T* __restrict__ v, ui
   const uint64_t c = c0 + lane;
   const bool has = c < nchunks;
   const uint64_t a = c * kChunk;
-  const uint64_t e = has ? min(a + kChunk, n) : a;
+  const uint32_t clen = has ? (uint32_t)(min(a + kChunk, n) - a) : 0u;  // the chunk's values
   const bool nar = has ? narrow[c] != 0 : true;
+  const int32_t tf32 = tfloor > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)tfloor;
   constexpr uint32_t nseg = (uint32_t)(kChunk / kSplitSeg);
   T r[kSplitSeg];
-  // segment 0 into slot 0
 #pragma unroll
-  for (uint32_t u = 0; u < kSplitSeg; u++) {
-    const uint32_t cc = u >> 1, x = ((u & 1u) << 5) + lane;  // two loads per chunk
+  for (uint32_t u = 0; u < kSplitSeg; u++) {  // segment 0 (two loads per chunk)
+    const uint32_t cc = u >> 1, x = ((u & 1u) << 5) + lane;
     const uint64_t pos = (c0 + cc) * kChunk + x;
     r[u] = pos < n ? __ldg(v + pos) : (T)0;
   }
 #pragma unroll
   for (uint32_t u = 0; u < kSplitSeg; u++) ring[0][((u & 1u) << 5) + lane][u >> 1] = r[u];
   __syncwarp();
-  uint64_t i = a;
-  int64_t prev = 0;
+  uint32_t ii = 0;  // open partition [ii, jj) relative to the chunk
+  uint64_t iw = a;  // the same, absolute (wide chunks)
+  int64_t prev = has ? (int64_t)ring[0][0][lane] : 0;
   int64_t dmax64 = 0, dmin64 = 0;
   i128 dmax128 = 0, dmin128 = 0;
   int cur = 0;
@@ -123,22 +142,25 @@ __global__ void __launch_bounds__(32) k_split_staged(const T* __restrict__ v, ui
         r[u] = pos < n ? __ldg(v + pos) : (T)0;
       }
     }
-    const uint64_t base = a + (uint64_t)k * kSplitSeg;
-    uint64_t word = 0;
-    if (base < e) {
-      for (uint32_t x = 0; x < kSplitSeg; x++) {
-        const uint64_t j = base + x;
-        const int64_t w = (int64_t)ring[slot][x][lane];
-        if (j == a) {
-          word |= 1ull;  // the chunk's first position opens a partition
-        } else if (j < e) {
-          const bool take = nar ? split_step<int64_t>(j, w, prev, i, dmax64, dmin64, cur, cap, tfloor)
-                                : split_step<i128>(j, w, prev, i, dmax128, dmin128, cur, cap, tfloor);
-          if (!take) word |= 1ull << x;
+    const uint32_t base = k * kSplitSeg;
+    if (base < clen) {
+      uint64_t word = k == 0 ? 1ull : 0ull;  // the chunk's first position opens a partition
+      const uint32_t x0 = k == 0 ? 1u : 0u;
+      const uint32_t xe = clen - base < kSplitSeg ? clen - base : kSplitSeg;
+      if (nar) {
+        for (uint32_t x = x0; x < xe; x++) {
+          const int64_t w = (int64_t)ring[slot][x][lane];
+          if (!split_step_narrow(base + x, w - prev, ii, dmax64, dmin64, cur, cap, tf32)) word |= 1ull << x;
+          prev = w;
         }
-        prev = w;
+      } else {
+        for (uint32_t x = x0; x < xe; x++) {
+          const int64_t w = (int64_t)ring[slot][x][lane];
+          if (!split_step<i128>(a + base + x, w, prev, iw, dmax128, dmin128, cur, cap, tfloor)) word |= 1ull << x;
+          prev = w;
+        }
       }
-      bitmap[base >> 6] = word;
+      bitmap[(a + base) >> 6] = word;
     }
     __syncwarp();
     if (k + 1 < nseg) {
@@ -148,7 +170,6 @@ __global__ void __launch_bounds__(32) k_split_staged(const T* __restrict__ v, ui
     }
   }
 }
-
 
 // Seeded split (§3.2.2, selecting good starting positions): the greedy sweep over the count values
 // u_k = v[base + dir k] (dir = +1, or -1 to read them backwards); a partition opens at u-index k when
@@ -364,22 +385,14 @@ int grid_for(uint64_t items, int per_block, int max_blocks_per_sm) {
 // right span's x shifts by the left span's length: T1 gains N_left T0_right), and they give the
 // least-squares moment S = sum (2x - (N-1)) w = 2 T1 - (N-1) T0 of the fit and its bounds, so a
 // refit needs one pass over the values: the residual range under the snapped line (none for the
-// constant model, whose residuals are the values themselves). Moments, partition fits and pair
-// fits live in slots indexed by a partition's first split partition ("orig"); a merge combines
-// the right partition's moments into the left one's slot.
+// constant model, whose residuals are the values themselves). The moments move with the partitions
+// when a round compacts them (a merged pair's are combined then), and the final partitions' fits
+// are taken once, from their moments, at the end.
 struct SpanStats {
   i128 T0;
   i128 T1;
   int64_t mn;
   int64_t mx;
-};
-
-// the record fields of a span's full fit
-struct SpanFit {
-  double theta0;
-  double theta1;
-  int32_t s;
-  uint32_t b;
 };
 
 // a pair too long for one warp: its residual range is reduced over pieces of kPiece values
@@ -394,6 +407,7 @@ struct LongPair {
 
 constexpr uint32_t kLaneSpan = 64;     // a lane fits spans up to this long on its own
 constexpr uint32_t kTinySpan = 256;    // size search: a thread per sampled partition up to this size
+constexpr uint32_t kTileSpan = 1024;   // eight lanes fit longer spans up to this long, four at a time
 constexpr uint32_t kWarpSpan = 4096;   // a warp fits longer pairs up to this long (split partitions: any)
 constexpr uint32_t kPiece = 2048;      // values per piece of a longer pair
 constexpr int kGroupBlock = 256;       // 8 warps, each taking 32 spans at a time
@@ -408,26 +422,31 @@ __device__ __forceinline__ SpanStats combine_stats(const SpanStats& l, uint64_t 
   return c;
 }
 
-// reductions whose result every lane receives
+// reductions over aligned tiles of TILE lanes (32: the warp) whose result every lane of the tile
+// receives
+template <int TILE = 32>
 __device__ __forceinline__ int64_t xw_min(int64_t v) {
-  for (int o = 16; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_xor_sync(kFull, v, o));
+  for (int o = TILE / 2; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_xor_sync(kFull, v, o));
   return v;
 }
+template <int TILE = 32>
 __device__ __forceinline__ int64_t xw_max(int64_t v) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(kFull, v, o));
+  for (int o = TILE / 2; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(kFull, v, o));
   return v;
 }
 __device__ __forceinline__ uint64_t xw_min_u(uint64_t v) {
   for (int o = 16; o > 0; o >>= 1) v = min(v, (uint64_t)__shfl_xor_sync(kFull, v, o));
   return v;
 }
+template <int TILE = 32>
 __device__ __forceinline__ uint64_t xw_max_u(uint64_t v) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(kFull, v, o));
+  for (int o = TILE / 2; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(kFull, v, o));
   return v;
 }
+template <int TILE = 32>
 __device__ __forceinline__ i128 xw_sum(i128 v) {
   uint64_t lo = (uint64_t)v, hi = (uint64_t)((u128)v >> 64);
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = TILE / 2; o > 0; o >>= 1) {
     const uint64_t l2 = __shfl_xor_sync(kFull, lo, o);
     const uint64_t h2 = __shfl_xor_sync(kFull, hi, o);
     const uint64_t nl = lo + l2;
@@ -445,6 +464,7 @@ __device__ __forceinline__ SpanStats stats_part(const T* p, uint32_t x, uint32_t
   s.T1 = 0;
   s.mn = INT64_MAX;
   s.mx = INT64_MIN;
+#pragma unroll 8
   for (; x < N; x += step) {
     const int64_t w = (int64_t)p[x];
     s.mn = min(s.mn, w);
@@ -461,18 +481,21 @@ template <typename T>
 __device__ __forceinline__ void resid_part(const T* p, uint32_t x, uint32_t N, uint32_t step, const FitParams& P,
                                            int64_t& lo, int64_t& hi, uint64_t& zmax) {
   if (P.fallback) {
+#pragma unroll 4
     for (; x < N; x += step) zmax = max(zmax, zz_encode((int64_t)((uint64_t)p[x] - (uint64_t)P.fb_shift)));
     return;
   }
   uint64_t F = (uint64_t)P.B * x;
   const uint64_t dF = (uint64_t)P.B * step;
   if (P.s >= 0) {
+#pragma unroll 8
     for (; x < N; x += step, F += dF) {
       const int64_t r = (int64_t)p[x] - ((int64_t)F >> P.s);
       lo = min(lo, r);
       hi = max(hi, r);
     }
   } else {
+#pragma unroll 4
     for (; x < N; x += step, F += dF) {
       const int64_t r = (int64_t)p[x] - (int64_t)(F << (-P.s));
       lo = min(lo, r);
@@ -490,6 +513,76 @@ __device__ __forceinline__ FitParams shfl_params(const FitParams& P, int src) {
   return q;
 }
 
+// Spans fitted cooperatively: the spans of the lanes set in mask, TILE lanes each (32 / TILE spans
+// at a time, in the order of their lanes). Each call hands every owning lane the reduced result of
+// its own span. a, N, P: the calling lane's span (its first position, length and parameters);
+// spans whose values are staged are read from the stage (first position ga), else from v.
+template <int TILE, typename T>
+__device__ __forceinline__ void coop_stats(uint32_t mask, const T* v, const T* stage, bool staged, uint64_t ga,
+                                           uint64_t a, uint32_t N, SpanStats& S) {
+  constexpr int NT = 32 / TILE;
+  const int lane = (int)(threadIdx.x & 31u), tile = lane / TILE, r = lane % TILE;
+  const int total = __popc(mask);
+  const bool mine = (mask >> lane) & 1u;
+  const int rank = __popc(mask & ((1u << lane) - 1u));
+  for (int it = 0; it * NT < total; it++) {
+    const int k = it * NT + tile;
+    const int sl = k < total ? (int)__fns(mask, 0, k + 1) : lane;
+    const uint64_t as = __shfl_sync(kFull, a, sl);
+    const uint32_t Ns = __shfl_sync(kFull, N, sl);
+    SpanStats q = stats_part(staged ? stage + (as - ga) : v + as, (uint32_t)r, k < total ? Ns : 0u, (uint32_t)TILE);
+    q.T0 = xw_sum<TILE>(q.T0);
+    q.T1 = xw_sum<TILE>(q.T1);
+    q.mn = xw_min<TILE>(q.mn);
+    q.mx = xw_max<TILE>(q.mx);
+    const bool take = mine && rank / NT == it;
+    const int src = take ? (rank % NT) * TILE : lane;
+    const uint64_t t0l = __shfl_sync(kFull, (uint64_t)q.T0, src), t0h = __shfl_sync(kFull, (uint64_t)((u128)q.T0 >> 64), src);
+    const uint64_t t1l = __shfl_sync(kFull, (uint64_t)q.T1, src), t1h = __shfl_sync(kFull, (uint64_t)((u128)q.T1 >> 64), src);
+    const int64_t mn = __shfl_sync(kFull, q.mn, src), mx = __shfl_sync(kFull, q.mx, src);
+    if (take) {
+      S.T0 = (i128)(((u128)t0h << 64) | t0l);
+      S.T1 = (i128)(((u128)t1h << 64) | t1l);
+      S.mn = mn;
+      S.mx = mx;
+    }
+  }
+}
+
+template <int TILE, typename T>
+__device__ __forceinline__ void coop_resid(uint32_t mask, const T* v, const T* stage, bool staged, uint64_t ga,
+                                           uint64_t a, uint32_t N, const FitParams& P, int64_t& lo, int64_t& hi,
+                                           uint64_t& zmax) {
+  constexpr int NT = 32 / TILE;
+  const int lane = (int)(threadIdx.x & 31u), tile = lane / TILE, r = lane % TILE;
+  const int total = __popc(mask);
+  const bool mine = (mask >> lane) & 1u;
+  const int rank = __popc(mask & ((1u << lane) - 1u));
+  for (int it = 0; it * NT < total; it++) {
+    const int k = it * NT + tile;
+    const int sl = k < total ? (int)__fns(mask, 0, k + 1) : lane;
+    const uint64_t as = __shfl_sync(kFull, a, sl);
+    const uint32_t Ns = __shfl_sync(kFull, N, sl);
+    const FitParams Ps = shfl_params(P, sl);
+    int64_t l = INT64_MAX, h = INT64_MIN;
+    uint64_t z = 0;
+    resid_part(staged ? stage + (as - ga) : v + as, (uint32_t)r, k < total ? Ns : 0u, (uint32_t)TILE, Ps, l, h, z);
+    l = xw_min<TILE>(l);
+    h = xw_max<TILE>(h);
+    z = xw_max_u<TILE>(z);
+    const bool take = mine && rank / NT == it;
+    const int src = take ? (rank % NT) * TILE : lane;
+    l = __shfl_sync(kFull, l, src);
+    h = __shfl_sync(kFull, h, src);
+    z = __shfl_sync(kFull, z, src);
+    if (take) {
+      lo = l;
+      hi = h;
+      zmax = z;
+    }
+  }
+}
+
 struct MergeWork {
   LongPair* longs;
   uint64_t* pieces;
@@ -499,18 +592,22 @@ struct MergeWork {
   unsigned long long* zmax;
 };
 
-// Sizes S_M + len * b of spans [st[j], st[j + W]) by the full fit: W = 1, every partition of the
-// split (its moments from a pass over its values, into stats[j], its fit into fit[j]); W = 2, the
-// dirty adjacent pairs (moments combined from stats[orig[j]] and stats[orig[j + 1]], the fit into
-// fit[orig[j]]). A warp takes 32 consecutive spans; when their values cover at most kStageBytes it
-// first stages them in shared memory with coalesced loads. A lane then fits its own span when it is
-// at most kLaneSpan long, the warp fits longer ones together, and pairs longer than kWarpSpan (not
-// staged) go to the piece list, where many warps share their residual pass.
-template <typename T, int W>
-__global__ void __launch_bounds__(kGroupBlock, 2)
+// Full fits of spans. MODE 1: every partition of the split (its moments from a pass over its
+// values, into stats[j]; size S_M + len * b into size_out[j]). MODE 2: the dirty adjacent pairs
+// [st[j], st[j + 2)) (moments combined from stats[j] and stats[j + 1]; merged size into
+// size_out[j]). MODE 3: the final partitions (moments stats[j]; record into rec[j], as the
+// encoder's fit writes it). A warp takes 32 consecutive spans; when their values cover at most
+// kStageBytes it first stages them in shared memory with coalesced loads. A lane then fits its own
+// span when it is at most kLaneSpan long, tiles of eight lanes fit spans up to kTileSpan, the warp
+// fits longer ones together, and spans longer than
+// kWarpSpan (modes 2 and 3, not staged) go to the piece list, where many warps share their residual
+// pass (k_pair_pieces, then k_pair_finish).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kGroupBlock, 3)
     k_span_groups(const T* __restrict__ v, const uint64_t* __restrict__ st, uint64_t count, uint32_t cap, int model,
-                  const uint8_t* __restrict__ dirty, const uint64_t* __restrict__ orig, SpanStats* __restrict__ stats,
-                  uint64_t* __restrict__ size_out, SpanFit* __restrict__ fit, MergeWork mw) {
+                  const uint8_t* __restrict__ dirty, SpanStats* __restrict__ stats, uint64_t* __restrict__ size_out,
+                  Record* __restrict__ rec, MergeWork mw) {
+  constexpr int W = MODE == 2 ? 2 : 1;
   __shared__ __align__(16) unsigned char stage_raw[kGroupBlock / 32][kStageBytes];
   constexpr uint64_t kStageVals = kStageBytes / sizeof(T);
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
@@ -519,7 +616,7 @@ __global__ void __launch_bounds__(kGroupBlock, 2)
   const uint64_t gw = (uint64_t)gridDim.x * (kGroupBlock / 32);
   for (uint64_t g = (uint64_t)blockIdx.x * (kGroupBlock / 32) + wib; g < ngroups; g += gw) {
     const uint64_t j = g * 32 + lane;
-    bool act = j < count && (W == 1 || dirty[j]);
+    bool act = j < count && (MODE != 2 || dirty[j]);
     if (!__any_sync(kFull, act)) continue;
     uint64_t a = 0, c = 0;
     if (act) {
@@ -542,25 +639,14 @@ __global__ void __launch_bounds__(kGroupBlock, 2)
     SpanStats S;
     S.T0 = S.T1 = 0;
     S.mn = S.mx = 0;
-    if (W == 1) {
+    if (MODE == 1) {
       if (act && N <= kLaneSpan) S = stats_part(src, 0, N, 1);
-      uint32_t mask = __ballot_sync(kFull, act && N > kLaneSpan);
-      while (mask) {
-        const int sl = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint64_t as = __shfl_sync(kFull, a, sl);
-        const uint32_t Ns = __shfl_sync(kFull, N, sl);
-        const T* ps = staged ? stage + (as - ga) : v + as;
-        SpanStats q = stats_part(ps, lane, Ns, 32);
-        q.T0 = xw_sum(q.T0);
-        q.T1 = xw_sum(q.T1);
-        q.mn = xw_min(q.mn);
-        q.mx = xw_max(q.mx);
-        if ((int)lane == sl) S = q;
-      }
+      coop_stats<8>(__ballot_sync(kFull, act && N > kLaneSpan && N <= kTileSpan), v, stage, staged, ga, a, N, S);
+      coop_stats<32>(__ballot_sync(kFull, act && N > kTileSpan), v, stage, staged, ga, a, N, S);
+    } else if (MODE == 2 && act) {
+      S = combine_stats(stats[j], st[j + 1] - a, stats[j + 1]);
     } else if (act) {
-      const uint64_t k0 = orig[j], k1 = orig[j + 1];
-      S = combine_stats(stats[k0], st[j + 1] - a, stats[k1]);
+      S = stats[j];
     }
     // parameters (fit.cuh steps 1-3)
     const bool lin = model == LECO_MODEL_LINEAR && N >= 2;
@@ -579,36 +665,18 @@ __global__ void __launch_bounds__(kGroupBlock, 2)
       hi = S.mx;
     }
     const bool by_lane = need && N <= kLaneSpan;
-    const bool by_warp = need && N > kLaneSpan && (W == 1 || staged || N <= kWarpSpan);
+    const bool by_warp = need && N > kLaneSpan && (MODE == 1 || staged || N <= kWarpSpan);
     const bool by_pieces = need && !by_lane && !by_warp;
     if (by_lane) resid_part(src, 0, N, 1, P, lo, hi, zmax);
-    uint32_t mask = __ballot_sync(kFull, by_warp);
-    while (mask) {
-      const int sl = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const uint64_t as = __shfl_sync(kFull, a, sl);
-      const uint32_t Ns = __shfl_sync(kFull, N, sl);
-      const FitParams Ps = shfl_params(P, sl);
-      const T* ps = staged ? stage + (as - ga) : v + as;
-      int64_t l = INT64_MAX, h = INT64_MIN;
-      uint64_t z = 0;
-      resid_part(ps, lane, Ns, 32, Ps, l, h, z);
-      l = xw_min(l);
-      h = xw_max(h);
-      z = xw_max_u(z);
-      if ((int)lane == sl) {
-        lo = l;
-        hi = h;
-        zmax = z;
-      }
-    }
+    coop_resid<8>(__ballot_sync(kFull, by_warp && N <= kTileSpan), v, stage, staged, ga, a, N, P, lo, hi, zmax);
+    coop_resid<32>(__ballot_sync(kFull, by_warp && N > kTileSpan), v, stage, staged, ga, a, N, P, lo, hi, zmax);
     if (by_pieces) {
       const uint32_t np = (N + kPiece - 1) / kPiece;
       const unsigned long long li = atomicAdd(&mw.counters[0], 1ull);
       const unsigned long long pb = atomicAdd(&mw.counters[1], (unsigned long long)np);
       LongPair lp;
       lp.j = j;
-      lp.k = orig[j];
+      lp.k = 0;
       lp.a = a;
       lp.P = P;
       lp.N = N;
@@ -621,15 +689,17 @@ __global__ void __launch_bounds__(kGroupBlock, 2)
     }
     if (act && !by_pieces) {  // steps 5-6
       const FitResult R = finish_fit(P, lo, hi, zmax);
-      size_out[j] = kSmBits + (uint64_t)N * R.b;
-      const uint64_t slot = W == 1 ? j : orig[j];
-      SpanFit f;
-      f.theta0 = R.theta0;
-      f.theta1 = R.theta1;
-      f.s = R.s;
-      f.b = R.b;
-      fit[slot] = f;
-      if (W == 1) stats[j] = S;
+      if (MODE == 3) {
+        Record r;
+        r.theta0 = R.theta0;
+        r.theta1 = R.theta1;
+        r.start = a;
+        r.word3 = make_w3(0, R.b, R.s, 1);
+        rec[j] = r;
+      } else {
+        size_out[j] = kSmBits + (uint64_t)N * R.b;
+      }
+      if (MODE == 1) stats[j] = S;
     }
     __syncwarp();  // the stage is reused by the next group
   }
@@ -661,19 +731,22 @@ __global__ void __launch_bounds__(256) k_pair_pieces(const T* __restrict__ v, Me
   }
 }
 
-// steps 5-6 of the long pairs
-__global__ void k_pair_finish(MergeWork mw, uint64_t* __restrict__ msz, SpanFit* __restrict__ fit) {
+// steps 5-6 of the long spans: their merged size (msz) or their record (rec)
+__global__ void k_pair_finish(MergeWork mw, uint64_t* __restrict__ msz, Record* __restrict__ rec) {
   const uint64_t nl = *(volatile unsigned long long*)&mw.counters[0];
   for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
     const LongPair L = mw.longs[li];
     const FitResult R = finish_fit(L.P, (int64_t)mw.lo[li], (int64_t)mw.hi[li], (uint64_t)mw.zmax[li]);
-    msz[L.j] = kSmBits + (uint64_t)L.N * R.b;
-    SpanFit f;
-    f.theta0 = R.theta0;
-    f.theta1 = R.theta1;
-    f.s = R.s;
-    f.b = R.b;
-    fit[L.k] = f;
+    if (rec) {
+      Record r;
+      r.theta0 = R.theta0;
+      r.theta1 = R.theta1;
+      r.start = L.a;
+      r.word3 = make_w3(0, R.b, R.s, 1);
+      rec[L.j] = r;
+    } else {
+      msz[L.j] = kSmBits + (uint64_t)L.N * R.b;
+    }
   }
 }
 
@@ -721,55 +794,39 @@ __global__ void k_select(const uint64_t* __restrict__ st, const uint64_t* __rest
   if ((threadIdx.x & 31u) == 0 && local) atomicAdd(nsel, (unsigned long long)local);
 }
 
-// the next round's arrays; a merged pair's moments and fit become its left partition's
+// the next round's arrays; a merged pair's moments are combined. Every load a partition needs is
+// issued before the first branch, so the loads of one thread overlap.
 __global__ void k_compact(const uint64_t* __restrict__ st, const uint64_t* __restrict__ sz,
                           const uint64_t* __restrict__ msz, const uint8_t* __restrict__ sel,
-                          const uint64_t* __restrict__ newidx, const uint64_t* __restrict__ orig, uint64_t m,
-                          uint64_t n, uint64_t new_m, SpanStats* __restrict__ stats, SpanFit* __restrict__ fitres,
-                          const SpanFit* __restrict__ pairfit, uint64_t* __restrict__ nst, uint64_t* __restrict__ nsz,
-                          uint64_t* __restrict__ nmsz, uint8_t* __restrict__ ndirty, uint64_t* __restrict__ norig) {
+                          const uint64_t* __restrict__ newidx, const SpanStats* __restrict__ stats, uint64_t m,
+                          uint64_t n, uint64_t new_m, uint64_t* __restrict__ nst, uint64_t* __restrict__ nsz,
+                          uint64_t* __restrict__ nmsz, uint8_t* __restrict__ ndirty, SpanStats* __restrict__ nstats) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m;
        p += (uint64_t)gridDim.x * blockDim.x) {
-    if (p > 0 && sel[p - 1]) continue;  // absorbed by p-1
-    const uint64_t k = newidx[p];
+    const bool absorbed = p > 0 && sel[p - 1];  // merged into p - 1
     const bool mp = p + 1 < m && sel[p];
-    const uint64_t o = orig[p];
-    nst[k] = st[p];
-    nsz[k] = mp ? msz[p] : sz[p];
-    norig[k] = o;
-    if (mp) {
-      stats[o] = combine_stats(stats[o], st[p + 1] - st[p], stats[orig[p + 1]]);
-      fitres[o] = pairfit[o];
-    }
+    const bool mq2 = p + 3 < m && sel[p + 2];  // the next survivor's pair when p merges
+    const bool mq1 = p + 2 < m && sel[p + 1];  // ... when it does not
+    const uint64_t k = newidx[p];
+    const uint64_t s0 = st[p];
+    const uint64_t szp = sz[p];
+    const uint64_t mszp = p + 1 < m ? msz[p] : 0;
+    const uint64_t s1 = p + 1 < m ? st[p + 1] : n;
+    if (absorbed) continue;
+    const SpanStats sp = stats[p];
+    nst[k] = s0;
+    nsz[k] = mp ? mszp : szp;
+    nstats[k] = mp ? combine_stats(sp, s1 - s0, stats[p + 1]) : sp;
     const uint64_t q = mp ? p + 2 : p + 1;  // next surviving partition
     if (q < m) {
-      const bool mq = q + 1 < m && sel[q];
-      const bool d = mp || mq;
+      const bool d = mp || (mp ? mq2 : mq1);
       ndirty[k] = d ? 1 : 0;
-      if (!d) nmsz[k] = msz[p];
+      if (!d) nmsz[k] = mszp;
     }
     if (k == 0) nst[new_m] = n;
   }
 }
 
-// the column's records from the final partitions' fits (as k_fit writes them: offset 0, exact grid)
-__global__ void k_var_records(const uint64_t* __restrict__ st, const uint64_t* __restrict__ orig,
-                              const SpanFit* __restrict__ fitres, uint64_t m, Record* __restrict__ rec) {
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
-    const SpanFit f = fitres[orig ? orig[p] : p];
-    Record r;
-    r.theta0 = f.theta0;
-    r.theta1 = f.theta1;
-    r.start = st[p];
-    r.word3 = make_w3(0, f.b, f.s, 1);
-    rec[p] = r;
-  }
-}
-
-__global__ void k_iota(uint64_t* p, uint64_t count) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
-    p[i] = i;
-}
 
 
 template <typename T>
@@ -779,28 +836,33 @@ cudaError_t dalloc(T** p, uint64_t elems, cudaStream_t st) {
 
 int group_grid(uint64_t count) {
   const uint64_t groups = (count + 31) / 32;
-  return grid_for((groups + kGroupBlock / 32 - 1) / (kGroupBlock / 32), 1, 2);
+  return grid_for((groups + kGroupBlock / 32 - 1) / (kGroupBlock / 32), 1, 3);
 }
 
+// one mode of k_span_groups over count spans, then (modes 2 and 3) the pieces of the long ones
 template <typename T>
-cudaError_t span_groups(const void* values, int W, const uint64_t* st, uint64_t count, uint32_t cap, int model,
-                        const uint8_t* dirty, const uint64_t* orig, SpanStats* stats, uint64_t* size_out, SpanFit* fit,
-                        const MergeWork& mw, cudaStream_t s) {
+cudaError_t span_groups(const void* values, int mode, const uint64_t* st, uint64_t count, uint32_t cap, int model,
+                        const uint8_t* dirty, SpanStats* stats, uint64_t* size_out, Record* rec, const MergeWork& mw,
+                        cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   const T* v = static_cast<const T*>(values);
-  if (W == 1)
-    k_span_groups<T, 1><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, orig, stats,
-                                                                  size_out, fit, mw);
+  if (mode != 1) {
+    const cudaError_t e = cudaMemsetAsync(mw.counters, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (mode == 1)
+    k_span_groups<T, 1><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, stats, size_out,
+                                                                  rec, mw);
+  else if (mode == 2)
+    k_span_groups<T, 2><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, stats, size_out,
+                                                                  rec, mw);
   else
-    k_span_groups<T, 2><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, orig, stats,
-                                                                  size_out, fit, mw);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t pair_rounds_long(const void* values, const MergeWork& mw, uint64_t* msz, SpanFit* pairfit, cudaStream_t s) {
-  k_pair_pieces<T><<<sm_count() * 8, 256, 0, s>>>(static_cast<const T*>(values), mw);
-  k_pair_finish<<<sm_count() * 2, 256, 0, s>>>(mw, msz, pairfit);
+    k_span_groups<T, 3><<<group_grid(count), kGroupBlock, 0, s>>>(v, st, count, cap, model, dirty, stats, size_out,
+                                                                  rec, mw);
+  if (mode != 1) {
+    k_pair_pieces<T><<<sm_count() * 8, 256, 0, s>>>(v, mw);
+    k_pair_finish<<<sm_count() * 2, 256, 0, s>>>(mw, size_out, mode == 3 ? rec : nullptr);
+  }
   return cudaGetLastError();
 }
 
@@ -974,9 +1036,8 @@ cudaError_t var_partition_fit(const void* values, int dtype, uint64_t n, double 
 
   // merge state
   const uint64_t m0 = m;
-  SpanStats* stats = nullptr;
-  SpanFit *fitres = nullptr, *pairfit = nullptr;
-  uint64_t *orig_a = nullptr, *orig_b = nullptr, *st_b = nullptr, *sz_a = nullptr, *sz_b = nullptr;
+  SpanStats *stats = nullptr, *stats_b = nullptr;
+  uint64_t *st_b = nullptr, *sz_a = nullptr, *sz_b = nullptr;
   uint64_t *msz_a = nullptr, *msz_b = nullptr, *keep = nullptr, *newidx = nullptr, *scr = nullptr, *d_total = nullptr;
   uint8_t *dirty_a = nullptr, *dirty_b = nullptr, *sel = nullptr;
   unsigned long long* d_nsel = nullptr;
@@ -991,10 +1052,7 @@ cudaError_t var_partition_fit(const void* values, int dtype, uint64_t n, double 
   const uint64_t piece_cap = 2 * n / kPiece + long_cap + 2;
   const uint64_t scr_elems = m0 / 2048 + 2;
   if (e == cudaSuccess) e = dalloc(&stats, m0, st);
-  if (e == cudaSuccess) e = dalloc(&fitres, m0, st);
-  if (e == cudaSuccess) e = dalloc(&pairfit, m0, st);
-  if (e == cudaSuccess) e = dalloc(&orig_a, m0, st);
-  if (e == cudaSuccess) e = dalloc(&orig_b, m0, st);
+  if (e == cudaSuccess) e = dalloc(&stats_b, m0, st);
   if (e == cudaSuccess) e = dalloc(&st_b, m0 + 1, st);
   if (e == cudaSuccess) e = dalloc(&sz_a, m0, st);
   if (e == cudaSuccess) e = dalloc(&sz_b, m0, st);
@@ -1018,22 +1076,12 @@ cudaError_t var_partition_fit(const void* values, int dtype, uint64_t n, double 
   uint64_t* nxt_st = st_b;
   // every split partition's moments, fit and size
   if (e == cudaSuccess)
-    e = u32 ? span_groups<uint32_t>(values, 1, cur_st, m, cap, model, nullptr, nullptr, stats, sz_a, fitres, mw, st)
-            : span_groups<uint64_t>(values, 1, cur_st, m, cap, model, nullptr, nullptr, stats, sz_a, fitres, mw, st);
-  if (e == cudaSuccess) {
-    k_iota<<<grid_for(m, 256, 8), 256, 0, st>>>(orig_a, m);
-    e = cudaMemsetAsync(dirty_a, 1, m, st);
-  }
+    e = u32 ? span_groups<uint32_t>(values, 1, cur_st, m, cap, model, nullptr, stats, sz_a, nullptr, mw, st)
+            : span_groups<uint64_t>(values, 1, cur_st, m, cap, model, nullptr, stats, sz_a, nullptr, mw, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dirty_a, 1, m, st);
   while (e == cudaSuccess && m > 1) {
-    e = cudaMemsetAsync(mw.counters, 0, 2 * sizeof(unsigned long long), st);
-    if (e == cudaSuccess)
-      e = u32 ? span_groups<uint32_t>(values, 2, cur_st, m - 1, cap, model, dirty_a, orig_a, stats, msz_a, pairfit,
-                                      mw, st)
-              : span_groups<uint64_t>(values, 2, cur_st, m - 1, cap, model, dirty_a, orig_a, stats, msz_a, pairfit,
-                                      mw, st);
-    if (e == cudaSuccess)
-      e = u32 ? pair_rounds_long<uint32_t>(values, mw, msz_a, pairfit, st)
-              : pair_rounds_long<uint64_t>(values, mw, msz_a, pairfit, st);
+    e = u32 ? span_groups<uint32_t>(values, 2, cur_st, m - 1, cap, model, dirty_a, stats, msz_a, nullptr, mw, st)
+            : span_groups<uint64_t>(values, 2, cur_st, m - 1, cap, model, dirty_a, stats, msz_a, nullptr, mw, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_nsel, 0, 8, st);
     if (e != cudaSuccess) break;
     k_select<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, m, sel, keep, d_nsel);
@@ -1044,28 +1092,27 @@ cudaError_t var_partition_fit(const void* values, int dtype, uint64_t n, double 
     e = scan_u64(keep, m, newidx, scr, d_total, st);
     if (e != cudaSuccess) break;
     const uint64_t new_m = m - nsel;
-    k_compact<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, sel, newidx, orig_a, m, n, new_m, stats,
-                                                   fitres, pairfit, nxt_st, sz_b, msz_b, dirty_b, orig_b);
+    k_compact<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, sz_a, msz_a, sel, newidx, stats, m, n, new_m, nxt_st,
+                                                   sz_b, msz_b, dirty_b, stats_b);
     e = cudaGetLastError();
     std::swap(cur_st, nxt_st);
     std::swap(sz_a, sz_b);
     std::swap(msz_a, msz_b);
     std::swap(dirty_a, dirty_b);
-    std::swap(orig_a, orig_b);
+    std::swap(stats, stats_b);
     m = new_m;
   }
   if (e == cudaSuccess && rec_out) {
-    e = dalloc(rec_out, m, st);
-    if (e == cudaSuccess) {
-      k_var_records<<<grid_for(m, 256, 8), 256, 0, st>>>(cur_st, orig_a, fitres, m, *rec_out);
-      e = cudaGetLastError();
-    }
+    e = dalloc(rec_out, m, st);  // the final partitions' fits from their moments
+    if (e == cudaSuccess)
+      e = u32 ? span_groups<uint32_t>(values, 3, cur_st, m, cap, model, nullptr, stats, nullptr, *rec_out, mw, st)
+              : span_groups<uint64_t>(values, 3, cur_st, m, cap, model, nullptr, stats, nullptr, *rec_out, mw, st);
   }
   if (e == cudaSuccess && cur_st != starts_out)
     e = cudaMemcpyAsync(starts_out, cur_st, (m + 1) * 8, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(cur_st == starts_out ? nxt_st : cur_st, st);  // st_b, wherever it ended up
-  for (void* p : {(void*)stats, (void*)fitres, (void*)pairfit, (void*)orig_a, (void*)orig_b, (void*)sz_a,
+  for (void* p : {(void*)stats, (void*)stats_b, (void*)sz_a,
                   (void*)sz_b, (void*)msz_a, (void*)msz_b, (void*)keep, (void*)newidx, (void*)scr, (void*)d_total,
                   (void*)dirty_a, (void*)dirty_b, (void*)sel, (void*)d_nsel, (void*)mw.longs, (void*)mw.pieces,
                   (void*)mw.counters, (void*)mw.lo, (void*)mw.hi, (void*)mw.zmax})
