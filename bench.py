@@ -1,18 +1,26 @@
 #!/usr/bin/env python3
 """LeCo hot-path benchmark on GB300.
 
-Workload: three 200M-value uint64 columns, fixed partitions of 4096, linear model, seeded and
-synthetic (linear + bounded noise; sorted Normal(2^40, 2^36); sorted 1e9 * LogNormal(0, 2)).
-Each column is encoded once (encode throughput is reported separately); the timed step then runs,
-for every column, the three query paths of the library: full decode, the fused filter-sum at ~1%
-selectivity, and 10M uniform random lookups. All inputs are resident in HBM and larger than L2.
+Headline workload (the metric's configuration): three 200M-value uint64 columns, fixed partitions
+of 4096, linear model, seeded and synthetic (linear + bounded noise; sorted Normal(2^40, 2^36);
+sorted 1e9 * LogNormal(0, 2)). Each column is encoded once (encode throughput is reported
+separately); the timed step then runs, for every column, the three query paths of the library:
+full decode, the fused filter-sum at ~1% selectivity, and 10M uniform random lookups. All inputs
+are resident in HBM and larger than L2.
 
-value = algorithmic bytes of one step / step time (GB/s); per-op figures follow in "ops".
+value = algorithmic bytes of one whole step (decode + lookups + filter-sum over the three
+columns) / step time, in GB/s; the full-decode figure alone is ops.decode and roofline.achieved.
 Algorithmic bytes, C = compressed bytes (32 per record + 8 per residual word):
   decode  C + 8 n          filter-sum  C + 24          lookups  k * (8 idx + 8 out + 32 sector)
 
---impl reference times the CPU oracle (one thread) on a bounded sample of the same columns: every
-100th partition, so the sample's encoding is exactly those partitions of the full encoding.
+After the headline (one GPU, unless --no-extra), the same run measures the other workloads and
+reports them under ops: the 1M-value fixed column with the whole oracle timed beside it
+(ops.cfg1_fix_1M), the two variable-partition columns (ops.cfg3_var), the 10,000-column batch
+(ops.cfg4_batch) and the serving loop with p50/p99 latency (ops.cfg5_serve).
+
+--impl reference times the CPU oracle (partition-parallel on the host cores) on a bounded sample of
+the same columns: every 100th partition, so the sample's encoding is exactly those partitions of
+the full encoding.
 """
 from __future__ import annotations
 
@@ -49,7 +57,11 @@ def parse_args():
     ap.add_argument("--batch-total", type=float, default=3e9)
     ap.add_argument("--serve-columns", type=int, default=2000)
     ap.add_argument("--serve-total", type=float, default=2.5e9)
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline only: skip the 1M, variable, batch and serving workloads")
+    ap.add_argument("--cpu-sample-every", type=int, default=20,
+                    help="CPU baseline sample of the headline columns: every k-th partition")
     ap.add_argument("--workload", choices=["fix", "var", "batch", "serve", "poly"], default="fix",
                     help="fix: the 3 x 200M fixed-partition columns (default); var: the variable-partition "
                          "columns (200M piecewise-linear uint64, 500M uint32 timestamps); batch: 10,000 columns; "
@@ -166,6 +178,27 @@ def host_cores() -> int:
         return max(1, os.cpu_count() or 1)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_run(cols, lookups_frac, reps=1, threads=1):
     """Time the oracle on prepared samples: decode, filter-sum and lookups of every sample piece.
     threads > 1 runs the pieces on a thread pool (the oracle is C behind ctypes, which releases the
@@ -228,6 +261,55 @@ def prepare_cpu_samples(columns, every, lookups, n, parts=1):
             pieces.append(dict(v=sv, rec=rec, words=words, idx=sel, lo=lo, hi=hi))
         out.append(dict(pieces=pieces, comp=comp, n=len(s), k=k))
     return out
+
+
+def timed_median(fn, reps=3):
+    """Median wall time of reps calls of fn (and fn's last result)."""
+    ts, r = [], None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = fn()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts), r
+
+
+def cpu_baseline_headline(args, columns, n):
+    """The oracle on the headline columns' sample (every cpu_sample_every-th partition), timed as the
+    median of 3 runs, partition-parallel on all host cores and on one thread; plus the oracle's
+    encode of the same sample."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    oracle.build()
+    cores = host_cores()
+    every = args.cpu_sample_every
+    samples = prepare_cpu_samples(columns, every, args.lookups, n, parts=cores)
+    b = cpu_oracle_run(samples, None, threads=cores)[0]
+    runs_all = sorted(cpu_oracle_run(samples, None, threads=cores)[1] for _ in range(3))
+    runs_one = sorted(cpu_oracle_run(samples, None, threads=1)[1] for _ in range(3))
+    b1 = b
+    pieces = [p for c in samples for p in c["pieces"]]
+    enc_bytes = sum(8 * len(p["v"]) for p in pieces) + sum(c["comp"] for c in samples)
+
+    def encode_all(threads):
+        def enc(p):
+            return oracle.encode_fixed(p["v"], L, oracle.MODEL_LINEAR)
+        if threads <= 1:
+            return [enc(p) for p in pieces]
+        with ThreadPoolExecutor(threads) as ex:
+            return list(ex.map(enc, pieces))
+
+    t_enc_all, _ = timed_median(lambda: encode_all(cores))
+    t_enc_one, _ = timed_median(lambda: encode_all(1))
+    nsamp = sum(c["n"] for c in samples)
+    return {"value": b / runs_all[1] / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": b1 / runs_one[1] / 1e9,
+            "encode_gbs": enc_bytes / t_enc_all / 1e9, "encode_single_thread_gbs": enc_bytes / t_enc_one / 1e9,
+            "runs": 3, "statistic": "median", "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"{nsamp} values: every {every}th 4096-value partition of each column; decode + filter-sum + "
+                      f"proportional lookups (value), encode (encode_gbs), partition-parallel on {cores} threads; "
+                      f"single_thread_*: the same on one thread; median of 3 runs each"}
 
 
 def run_reference(args):
@@ -441,20 +523,25 @@ def run_leco(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        oracle.build()
-        cores = host_cores()
-        samples = prepare_cpu_samples(columns, args.sample_every, args.lookups, n, parts=cores)
-        b1, t1 = cpu_oracle_run(samples, None, threads=1)
-        b, t = cpu_oracle_run(samples, None, threads=cores)
-        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-               "single_thread_value": b1 / t1 / 1e9,
-               "sample": f"{sum(c['n'] for c in samples)} values: every {args.sample_every}th "
-                         f"4096-value partition of each column; decode + filter-sum + proportional lookups, "
-                         f"partition-parallel on {cores} threads (single_thread_value: the same on one)"}
+        cpu = cpu_baseline_headline(args, columns, n)
 
     value = whole_job_gbs(step_b, world, ms)
+    for c in cols.values():
+        c.free()
+    cols.clear()
+    del out, outk, idxs, columns
+    if world == 1 and not args.no_extra:  # the other workloads, on the same GPU after the headline
+        torch.cuda.synchronize()
+        leco.leco_trim_memory()
+        torch.cuda.empty_cache()
+        for key, fn in (("cfg1_fix_1M", bench_fix1m), ("cfg3_var", bench_var), ("cfg4_batch", bench_batch),
+                        ("cfg5_serve", bench_serve)):
+            t_w = time.time()
+            ops_out[key] = fn(args, leco, dev, stream)
+            ops_out[key]["wall_s"] = time.time() - t_w
+            torch.cuda.synchronize()
+            leco.leco_trim_memory()
+            torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -467,8 +554,6 @@ def run_leco(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for c in cols.values():
-        c.free()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -516,25 +601,100 @@ def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
             "h2d_bytes_per_step": 3 * 8 * k, "d2h_bytes_per_step": 3 * (8 * n + 8 * k + 24)}
 
 
-def run_var(args):
-    """Variable partitions: GPU split/merge + encode (timed once per column), then decode, filter-sum
-    and 10M lookups per column, reported per op (not the default workload)."""
-    import numpy as np
+def gpu_setup():
     import torch
 
-    import workloads as W
     import paper_2306_15374_gb300 as pkg
 
     pkg.build()
     from paper_2306_15374_gb300 import leco
 
     torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()
+    return leco, torch.device("cuda", 0), torch.cuda.current_stream()
+
+
+def ev_timed(fn, stream, reps, warm=3):
+    """Average CUDA-event time (ms) of reps calls of fn after warm untimed ones."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_fix1m(args, leco, dev, stream):
+    """The 1M-value fixed-partition column (v_i = 1000 + 37 i + U{-500..500}, L = 1024, linear):
+    encode, full decode and 100k uniform lookups on the GPU, with the whole oracle timed beside it
+    (encode, decode and the same lookups on one host thread), and the encodings compared byte for
+    byte."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads as W
+
+    oracle.build()
+    L1, k = W.L_CFG1, 100_000
+    v = W.cfg1()
+    n = len(v)
+    dv = torch.from_numpy(v.view(np.int64)).to(dev)
+    idx = W.uniform_indices(k, n, seed=0, stream=2)
+    didx = torch.from_numpy(idx.view(np.int64)).to(dev)
+    o = torch.empty(n, dtype=torch.int64, device=dev)
+    ok_ = torch.empty(k, dtype=torch.int64, device=dev)
+    reps = 50
+    t_enc = ev_timed(lambda: leco.leco_encode(dv, leco.fixed(L1), leco.LECO_MODEL_LINEAR).free(), stream, 10, warm=2)
+    col = leco.leco_encode(dv, leco.fixed(L1), leco.LECO_MODEL_LINEAR)
+    st = col.stats()
+    comp = st["record_bytes"] + st["residual_bytes"]
+    t_dec = ev_timed(lambda: leco.leco_decode_all(col, o), stream, reps)
+    t_ra = ev_timed(lambda: leco.leco_random_access(col, didx, ok_), stream, reps)
+    exact = bool(torch.equal(o, dv)) and bool(torch.equal(ok_, dv[didx]))
+    rec_b, words_b, _ = leco.leco_column_export(col)
+    col.free()
+    t_oenc, (rec, words) = timed_median(lambda: oracle.encode_fixed(v, L1, oracle.MODEL_LINEAR))
+    t_odec, d = timed_median(lambda: oracle.decode(rec, words, n))
+    t_olook, (lk, _) = timed_median(lambda: oracle.lookup(rec, words, n, idx, L=L1))
+    exact = exact and bool((d == v).all()) and bool((lk == v[idx]).all())
+    enc_b, dec_b = 8 * n + comp, comp + 8 * n
+    return {
+        "workload": "1M uint64, v_i = 1000 + 37 i + U{-500..500} (seed 0), L = 1024, linear; 100k uniform lookups",
+        "ratio": comp / (8 * n), "compressed_bytes": comp, "encode_identical_to_oracle":
+            rec_b == rec.tobytes() and words_b == words.tobytes(), "results_exact": exact,
+        "gpu": {"encode_ms": t_enc, "encode_gbs": enc_b / (t_enc * 1e-3) / 1e9, "decode_ms": t_dec,
+                "decode_gbs": dec_b / (t_dec * 1e-3) / 1e9, "lookup_ms": t_ra,
+                "mlookups_s": k / (t_ra * 1e-3) / 1e6},
+        "oracle": {"kind": "oracle", "cores": 1, "sample": "the whole 1M-value column, median of 3 runs",
+                   "encode_ms": 1e3 * t_oenc, "encode_gbs": enc_b / t_oenc / 1e9, "decode_ms": 1e3 * t_odec,
+                   "decode_gbs": dec_b / t_odec / 1e9, "lookup_ms": 1e3 * t_olook,
+                   "mlookups_s": k / t_olook / 1e6},
+    }
+
+
+def bench_var(args, leco, dev, stream, sweep=False):
+    """Variable partitions (tau = args.tau): GPU split/merge + encode of the 200M piecewise-linear
+    uint64 column and the 500M uint32 timestamp column, then decode, filter-sum and 10M lookups per
+    column; the oracle beside it decodes, filters and looks up every 100th GPU partition (encoded
+    by the oracle with the same boundaries), on one host thread."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads as W
+
+    oracle.build()
     n_a = args.n
     n_b = int(args.n * 2.5)
     specs = [("piecewise_u64", lambda: W.cfg3("a", n_a), 64), ("timestamps_u32", lambda: W.cfg3("b", n_b), 32)]
     k = args.lookups
+    peak, _ = measured_peaks()
     out = {}
     for name, gen, bits in specs:
         v = gen()
@@ -543,15 +703,23 @@ def run_var(args):
             dv = torch.from_numpy(v.astype(np.uint32).view(np.int32)).to(dev)
         else:
             dv = torch.from_numpy(v.view(np.int64)).to(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        col = leco.leco_encode(dv, leco.variable(args.tau), leco.LECO_MODEL_LINEAR)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        enc_ms = e0.elapsed_time(e1)
+        vb = bits // 8
+
+        def var_encode(tau, seeded):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c = leco.leco_encode(dv, leco.variable(tau, seeded=seeded), leco.LECO_MODEL_LINEAR)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return c, a.elapsed_time(b)
+
+        c0, _ = var_encode(args.tau, False)  # warms the library's memory pool
+        c0.free()
+        col, enc_ms = var_encode(args.tau, False)
         fix = leco.leco_encode(dv, leco.fixed(4096), leco.LECO_MODEL_LINEAR)
         st, stf = col.stats(), fix.stats()
+        fix.free()
         comp = st["record_bytes"] + st["residual_bytes"] + 8 * (st["partitions"] + 1)
         tdt = torch.int32 if bits == 32 else torch.int64
         o = torch.empty(n, dtype=tdt, device=dev)
@@ -560,67 +728,75 @@ def run_var(args):
         res = torch.zeros(3, dtype=torch.int64, device=dev)
         lo, hi = W.filter_bounds(v)
         reps = max(3, min(args.steps, 50))
-
-        def timed(fn):
-            for _ in range(3):
-                fn()
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(reps):
-                fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b) / reps
-
-        t_dec = timed(lambda: leco.leco_decode_all(col, o))
+        t_dec = ev_timed(lambda: leco.leco_decode_all(col, o), stream, reps)
         ok = bool(torch.equal(o, dv))
-        t_fil = timed(lambda: leco.leco_filter_sum(col, lo, hi, res))
-        t_pru = timed(lambda: leco.leco_filter_sum(col, lo, hi, res, flags=leco.LECO_FILTER_PRUNE))
-        t_ra = timed(lambda: leco.leco_random_access(col, idx, ok_))
-        peak, _ = measured_peaks()
-        vb = bits // 8
-        out[name] = {
+        t_fil = ev_timed(lambda: leco.leco_filter_sum(col, lo, hi, res), stream, reps)
+        t_pru = ev_timed(lambda: leco.leco_filter_sum(col, lo, hi, res, flags=leco.LECO_FILTER_PRUNE), stream, reps)
+        t_ra = ev_timed(lambda: leco.leco_random_access(col, idx, ok_), stream, reps)
+        ok = ok and bool(torch.equal(ok_, dv[idx]))
+        r = {
             "n": n, "partitions": st["partitions"], "ratio": comp / (n * vb), "ratio_fixed_4096": stf["ratio"],
             "partition_encode_ms": enc_ms, "partition_encode_gbs": (n * vb + comp) / (enc_ms * 1e-3) / 1e9,
             "decode_ms": t_dec, "decode_gbs": (comp + n * vb) / (t_dec * 1e-3) / 1e9,
             "decode_frac_hbm": (comp + n * vb) / (t_dec * 1e-3) / 1e9 / peak, "decode_equals_input": ok,
             "filter_ms": t_fil, "filter_gbs": (comp + 24) / (t_fil * 1e-3) / 1e9,
+            "filter_frac_hbm": (comp + 24) / (t_fil * 1e-3) / 1e9 / peak,
             "filter_prune_ms": t_pru, "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6,
         }
-        def var_encode(tau, seeded):
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            c = leco.leco_encode(dv, leco.variable(tau, seeded=seeded), leco.LECO_MODEL_LINEAR)
-            b.record(stream)
-            torch.cuda.synchronize()
-            sc = c.stats()
-            cb = sc["record_bytes"] + sc["residual_bytes"] + 8 * (sc["partitions"] + 1)
-            c.free()
-            return {"tau": tau, "partitions": sc["partitions"], "ratio": cb / (n * vb),
-                    "partition_encode_ms": a.elapsed_time(b)}
+        # the oracle beside it: every 100th GPU partition, encoded with the same boundaries
+        _, _, starts_b = leco.leco_column_export(col)
+        starts = np.frombuffer(starts_b, dtype=np.uint64).astype(np.int64)
+        pick = np.arange(0, len(starts) - 1, 100)
+        sv = np.concatenate([v[starts[p]:starts[p + 1]] for p in pick])
+        sst = np.concatenate([[0], np.cumsum([starts[p + 1] - starts[p] for p in pick])]).astype(np.uint64)
+        ks = max(1, int(k * len(sv) / n))
+        sidx = W.uniform_indices(ks, len(sv), seed=12)
+        slo, shi = W.filter_bounds(sv)
+        t_oenc, (srec, swords) = timed_median(lambda: oracle.encode(sv, sst, oracle.MODEL_LINEAR))
+        t_odec, sd = timed_median(lambda: oracle.decode(srec, swords, len(sv), bits))
+        t_ofil, _ = timed_median(lambda: oracle.filter_sum(srec, swords, len(sv), slo, shi, bits))
+        t_olook, _ = timed_median(lambda: oracle.lookup(srec, swords, len(sv), sidx, L=0, dtype_bits=bits))
+        assert (sd == sv).all()
+        scomp = oracle.compressed_bytes(srec, swords)
+        r["oracle"] = {"kind": "oracle", "cores": 1, "sample": f"every 100th GPU partition ({len(sv)} values), "
+                       "encoded by the oracle with the same boundaries; median of 3 runs",
+                       "encode_gbs": (len(sv) * vb + scomp) / t_oenc / 1e9,
+                       "decode_gbs": (scomp + len(sv) * vb) / t_odec / 1e9,
+                       "filter_gbs": (scomp + 24) / t_ofil / 1e9, "mlookups_s": ks / t_olook / 1e6}
+        if sweep:
+            def var_stats(tau, seeded):
+                c, ms = var_encode(tau, seeded)
+                sc = c.stats()
+                cb = sc["record_bytes"] + sc["residual_bytes"] + 8 * (sc["partitions"] + 1)
+                c.free()
+                return {"tau": tau, "partitions": sc["partitions"], "ratio": cb / (n * vb),
+                        "partition_encode_ms": ms}
 
-        # the seeded split (each chunk grown from its smoothest point both ways, §3.2.2)
-        out[name]["seeded"] = var_encode(args.tau, True)
-        if args.tau_sweep:
-            # compression against tau (the partitioner's one knob, swept over the paper's range),
-            # left-to-right and seeded
-            sweep = []
-            for tau in [float(t) for t in args.tau_sweep.split(",")]:
-                r = var_encode(tau, False)
-                r["seeded"] = var_encode(tau, True)
-                sweep.append(r)
-            L_auto, _, n_eval = leco.leco_search_partition_size(dv, leco.LECO_MODEL_LINEAR)
-            auto = leco.leco_encode(dv, leco.auto(), leco.LECO_MODEL_LINEAR)
-            out[name]["tau_sweep"] = sweep
-            out[name]["fixed_searched_size"] = {"L": L_auto, "sizes_evaluated": n_eval, "ratio": auto.stats()["ratio"]}
-            auto.free()
-        for c in (col, fix):
-            c.free()
-        del dv, o
-    print(json.dumps({"workload": "LeCo-var tau=%g: 200M piecewise-linear uint64, 500M uint32 timestamps" % args.tau,
-                      "results": out}), flush=True)
+            # the seeded split (each chunk grown from its smoothest point both ways, §3.2.2)
+            r["seeded"] = var_stats(args.tau, True)
+            if args.tau_sweep:
+                # compression against tau (the partitioner's one knob, swept over the paper's range),
+                # left-to-right and seeded
+                tau_rows = []
+                for tau in [float(t) for t in args.tau_sweep.split(",")]:
+                    row = var_stats(tau, False)
+                    row["seeded"] = var_stats(tau, True)
+                    tau_rows.append(row)
+                L_auto, _, n_eval = leco.leco_search_partition_size(dv, leco.LECO_MODEL_LINEAR)
+                auto = leco.leco_encode(dv, leco.auto(), leco.LECO_MODEL_LINEAR)
+                r["tau_sweep"] = tau_rows
+                r["fixed_searched_size"] = {"L": L_auto, "sizes_evaluated": n_eval, "ratio": auto.stats()["ratio"]}
+                auto.free()
+        out[name] = r
+        col.free()
+        del dv, o, idx, ok_
+    return {"workload": "LeCo-var tau=%g: 200M piecewise-linear uint64, 500M uint32 timestamps" % args.tau,
+            "results": out}
+
+
+def run_var(args):
+    leco, dev, stream = gpu_setup()
+    print(json.dumps(bench_var(args, leco, dev, stream, sweep=True)), flush=True)
     return 0
 
 
@@ -729,23 +905,17 @@ def upload_columns(gen, spec, ncols, dev):
     return out
 
 
-def run_batch(args):
+def bench_batch(args, leco, dev, stream):
     """Batched form: 10,000 uint64 columns, lengths log-uniform in [1K, 10M] rescaled to 3B values,
     each linear + noise, sorted normal or sorted lognormal with its own seed, constant or linear
-    model (50/50), partition size 256/1024/4096. Encode and decode all columns in one pass (decode: one persistent launch, also as
-    a CUDA graph, with the autotuned scan shape) against one launch per column."""
-    import numpy as np
+    model (50/50), partition size 256/1024/4096. Encode and decode all columns in one pass (decode:
+    one persistent launch, also as a CUDA graph, with the autotuned scan shape) against one launch
+    per column."""
+    import numpy as np  # noqa: F401
     import torch
 
     import workloads as W
-    import paper_2306_15374_gb300 as pkg
 
-    pkg.build()
-    from paper_2306_15374_gb300 import leco
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()
     spec = W.batch_spec(args.batch_columns, int(args.batch_total))
     ncols = len(spec["lens"])
     lens = spec["lens"]
@@ -801,59 +971,63 @@ def run_batch(args):
     peak, _ = measured_peaks()
     dec_bytes = comp + 8 * total
     enc_bytes = 8 * total + comp
-    print(json.dumps({
+    res = {
         "workload": f"batched: {ncols} uint64 columns, {total} values (log-uniform 1K-10M rescaled; linear + noise, "
                     "sorted normal, sorted lognormal), L in {256,1024,4096}, constant/linear 50/50",
-        "results": {
-            "encode_batched_ms": t_benc, "encode_batched_gbs": enc_bytes / (t_benc * 1e-3) / 1e9,
-            "encode_per_column_ms": t_penc, "encode_speedup": t_penc / t_benc, "encode_identical": same,
-            "decode_plan_ms": t_plan, "decode_plan_gbs": dec_bytes / (t_plan * 1e-3) / 1e9,
-            "decode_plan_frac_hbm": dec_bytes / (t_plan * 1e-3) / 1e9 / peak,
-            "decode_graph_ms": t_graph, "decode_per_column_ms": t_pdec,
-            "decode_speedup_vs_per_column": t_pdec / t_graph, "decode_equals_input": ok,
-            "jobs": leco.leco_batch_plan_jobs(plan), "tuned_scan": tuned, "compressed_bytes": comp,
-            "kernel_launches": {"decode_plan": 1, "decode_per_column": ncols},
-        }}), flush=True)
+        "encode_batched_ms": t_benc, "encode_batched_gbs": enc_bytes / (t_benc * 1e-3) / 1e9,
+        "encode_per_column_ms": t_penc, "encode_speedup": t_penc / t_benc, "encode_identical": same,
+        "decode_plan_ms": t_plan, "decode_plan_gbs": dec_bytes / (t_plan * 1e-3) / 1e9,
+        "decode_plan_frac_hbm": dec_bytes / (t_plan * 1e-3) / 1e9 / peak,
+        "decode_graph_ms": t_graph, "decode_per_column_ms": t_pdec,
+        "decode_speedup_vs_per_column": t_pdec / t_graph, "decode_equals_input": ok,
+        "jobs": leco.leco_batch_plan_jobs(plan), "tuned_scan": tuned, "compressed_bytes": comp,
+        "kernel_launches": {"decode_plan": 1, "decode_per_column": ncols},
+    }
     plan.free()
+    for c in cols:
+        c.free()
+    del vals, outs
+    return res
+
+
+def run_batch(args):
+    leco, dev, stream = gpu_setup()
+    print(json.dumps(bench_batch(args, leco, dev, stream)), flush=True)
     return 0
 
 
-def run_serve(args):
+def bench_serve(args, leco, dev, stream):
     """Serving form: 2,000 resident uint64 columns (lengths log-uniform 100K-50M rescaled to 2.5B
-    values; half fixed L=4096 over linear + noise, half variable over piecewise-linear), admitted against a 40 GB budget; a Poisson stream of
-    requests (50% lookups of log-uniform 1-4096 indices, 50% range decodes of log-uniform 1K-1M
-    values) at several offered loads, continuous batching vs one launch per request. Also an
-    admission-stress run with the budget at half the resident size."""
-    import numpy as np
-    import torch
-
+    values; half fixed L=4096 over linear + noise, half variable over piecewise-linear), admitted
+    against a 40 GB budget; a Poisson stream of requests (50% lookups of log-uniform 1-4096 indices,
+    50% range decodes of log-uniform 1K-1M values) at several offered loads, continuous batching vs
+    one launch per request. Also an admission-stress run with the budget at half the resident size.
+    The columns are encoded once; each server gets copies rebuilt from their serialized form."""
     import workloads as W
-    import paper_2306_15374_gb300 as pkg
 
-    pkg.build()
-    from paper_2306_15374_gb300 import leco
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     spec = W.serve_spec(args.serve_columns, int(args.serve_total))
     ncols = len(spec["lens"])
+    t0 = time.time()
+    vals = upload_columns(W.serve_column, spec, ncols, dev)
+    t_gen = time.time() - t0
+    t0 = time.time()
+    blobs = []
+    for c in range(ncols):
+        pol = leco.variable(args.tau) if spec["variable"][c] else leco.fixed(4096)
+        col = leco.leco_encode(vals[c], pol, leco.LECO_MODEL_LINEAR)
+        blobs.append(leco.leco_serialize(col))
+        col.free()
+        vals[c] = None
+    t_enc = time.time() - t0
 
     def build_columns():
-        vals = upload_columns(W.serve_column, spec, ncols, dev)
-        out = []
-        for c in range(ncols):
-            pol = leco.variable(args.tau) if spec["variable"][c] else leco.fixed(4096)
-            out.append(leco.leco_encode(vals[c], pol, leco.LECO_MODEL_LINEAR))
-            vals[c] = None
-        return out
+        return [leco.leco_deserialize(b) for b in blobs]
 
     results = {}
-    build_s = resident = None
+    resident = None
     rates = None  # both modes are offered the same absolute loads: fractions of the batched saturation
     for mode, mb in (("continuous", 0), ("per_request", 1)):
-        t0 = time.time()
         cols = build_columns()
-        build_s = build_s or time.time() - t0
         resident = resident or sum(c.stats()["device_bytes"] for c in cols)
         s = leco.leco_server_create(int(40e9), max_batch_requests=mb, max_batch_values=1 << 24,
                                     max_batch_lookups=1 << 17)
@@ -893,10 +1067,16 @@ def run_serve(args):
     stress = {"budget_bytes": int(resident // 2), "admitted": admitted, "refused": refused,
               "resident_bytes": st["resident_bytes"], "reserved_bytes": st["reserved_bytes"]}
     s.destroy()
-    print(json.dumps({
-        "workload": f"serving: {ncols} resident uint64 columns, {int(spec['lens'].sum())} values, half fixed / half variable, "
-                    "budget 40 GB; Poisson requests, 50% lookups (1-4096), 50% ranges (1K-1M)",
-        "build_s": build_s, "resident_bytes": resident, "results": results, "admission_stress": stress}), flush=True)
+    return {
+        "workload": f"serving: {ncols} resident uint64 columns, {int(spec['lens'].sum())} values, half fixed / half "
+                    "variable, budget 40 GB; Poisson requests, 50% lookups (1-4096), 50% ranges (1K-1M)",
+        "generate_s": t_gen, "encode_s": t_enc, "resident_bytes": resident, "seconds_per_load": args.serve_seconds,
+        "results": results, "admission_stress": stress}
+
+
+def run_serve(args):
+    leco, dev, stream = gpu_setup()
+    print(json.dumps(bench_serve(args, leco, dev, stream)), flush=True)
     return 0
 
 

@@ -140,6 +140,16 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   return P;
 }
 
+// step 6 alone (one thread): the width b, without the binary64 parameters (sizing only)
+__device__ __forceinline__ uint32_t finish_width(const FitParams& P, int64_t lo, int64_t hi, uint64_t fb_maxzz) {
+  if (P.fallback) return (uint32_t)bitlen_u64(fb_maxzz);
+  const int s = P.s;
+  const i128 t = (i128)lo + (((i128)hi - (i128)lo + 1) / 2);
+  const i128 shift = s >= 0 ? t : (t >> (-s)) * ((i128)1 << (-s));
+  const int64_t lo2 = (int64_t)((i128)lo - shift), hi2 = (int64_t)((i128)hi - shift);
+  return (uint32_t)bitlen_u64(max(zz_encode(lo2), zz_encode(hi2)));
+}
+
 // steps 5-6 (one thread)
 __device__ FitResult finish_fit(const FitParams& P, int64_t lo, int64_t hi, uint64_t fb_maxzz) {
   FitResult R;

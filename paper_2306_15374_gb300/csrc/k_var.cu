@@ -688,8 +688,8 @@ __global__ void __launch_bounds__(kGroupBlock, 3)
       for (uint32_t q = 0; q < np; q++) mw.pieces[pb + q] = ((uint64_t)li << 16) | q;
     }
     if (act && !by_pieces) {  // steps 5-6
-      const FitResult R = finish_fit(P, lo, hi, zmax);
       if (MODE == 3) {
+        const FitResult R = finish_fit(P, lo, hi, zmax);
         Record r;
         r.theta0 = R.theta0;
         r.theta1 = R.theta1;
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(kGroupBlock, 3)
         r.word3 = make_w3(0, R.b, R.s, 1);
         rec[j] = r;
       } else {
-        size_out[j] = kSmBits + (uint64_t)N * R.b;
+        size_out[j] = kSmBits + (uint64_t)N * finish_width(P, lo, hi, zmax);
       }
       if (MODE == 1) stats[j] = S;
     }
@@ -736,8 +736,8 @@ __global__ void k_pair_finish(MergeWork mw, uint64_t* __restrict__ msz, Record* 
   const uint64_t nl = *(volatile unsigned long long*)&mw.counters[0];
   for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
     const LongPair L = mw.longs[li];
-    const FitResult R = finish_fit(L.P, (int64_t)mw.lo[li], (int64_t)mw.hi[li], (uint64_t)mw.zmax[li]);
     if (rec) {
+      const FitResult R = finish_fit(L.P, (int64_t)mw.lo[li], (int64_t)mw.hi[li], (uint64_t)mw.zmax[li]);
       Record r;
       r.theta0 = R.theta0;
       r.theta1 = R.theta1;
@@ -745,7 +745,7 @@ __global__ void k_pair_finish(MergeWork mw, uint64_t* __restrict__ msz, Record* 
       r.word3 = make_w3(0, R.b, R.s, 1);
       rec[L.j] = r;
     } else {
-      msz[L.j] = kSmBits + (uint64_t)L.N * R.b;
+      msz[L.j] = kSmBits + (uint64_t)L.N * finish_width(L.P, (int64_t)mw.lo[li], (int64_t)mw.hi[li], (uint64_t)mw.zmax[li]);
     }
   }
 }
