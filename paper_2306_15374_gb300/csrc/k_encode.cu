@@ -468,11 +468,13 @@ __device__ __forceinline__ uint64_t place64(uint64_t z, uint64_t f, uint64_t wb)
 
 // POLY: the column may hold polynomial partitions (a separate instantiation keeps the constant and
 // linear packer as small as before)
+// zofs: the partition's first value within a stage holding several partitions (the 32-bit
+// residual buffer is indexed like the stage)
 template <bool POLY>
 __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned char* st, unsigned char* ring,
                                                const Record* __restrict__ rec, const Aux* __restrict__ aux,
                                                const PolyCoef* __restrict__ pcoef, const PolyAux* __restrict__ poly,
-                                               uint64_t p, uint64_t* __restrict__ words) {
+                                               uint64_t p, uint64_t* __restrict__ words, uint32_t zofs = 0) {
   const Aux a = aux[p];
   const uint32_t b = w3_b(a.word3);
   const bool pl = POLY && w3_poly(a.word3) != 0;
@@ -482,7 +484,7 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
     // phase 1: residuals into shared memory (staged partitions only; others recompute per field)
     uint64_t* zs = nullptr;
     if (st && b) {
-      zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32)
+      zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32) + zofs
                                : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
       if (pl) {
         // the thread's predictions T + (F(x) >> S) for x = tid, tid + blockDim, ... by forward
@@ -572,15 +574,15 @@ __global__ void k_zero_bounds(const Aux* __restrict__ aux, uint64_t m, uint64_t 
 
 // ------------------------------------------------------------------------------ batched encode
 
-// one warp per partition of every column (the column by a search over part_base)
+// one warp per partition of every column (its column from the partition-column table)
 __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
-    k_fit_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base, uint32_t ncols,
-                uint64_t P, int dtype, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
-                uint32_t* __restrict__ max_b) {
+    k_fit_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
+                const uint32_t* __restrict__ part_col, uint64_t P, int dtype, Record* __restrict__ rec,
+                uint64_t* __restrict__ lenbits, uint32_t* __restrict__ max_b) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t nw = (uint64_t)gridDim.x * kFitWarps;
   for (uint64_t p = (uint64_t)blockIdx.x * kFitWarps + (threadIdx.x >> 5); p < P; p += nw) {
-    const uint32_t c = find_col(part_base, ncols, p);
+    const uint32_t c = part_col[p];
     const EncCol col = cols[c];
     if (col.model == LECO_MODEL_POLY) continue;  // fitted by the polynomial phases
     const uint64_t a = (p - part_base[c]) * (uint64_t)col.L;
@@ -602,10 +604,11 @@ __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
 // column-relative offsets from the global exclusive scan, and each column's total bits
 __global__ void k_set_offsets_multi(Record* __restrict__ rec, const uint64_t* __restrict__ off,
                                     const uint64_t* __restrict__ lenbits, const uint64_t* __restrict__ part_base,
-                                    uint32_t ncols, uint64_t P, uint64_t* __restrict__ col_bits) {
+                                    const uint32_t* __restrict__ part_col, uint64_t P,
+                                    uint64_t* __restrict__ col_bits) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P;
        p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = find_col(part_base, ncols, p);
+    const uint32_t c = part_col[p];
     const uint64_t base = off[part_base[c]];
     rec[p].word3 = (rec[p].word3 & ~kOffMask) | ((off[p] - base) & kOffMask);
     if (p + 1 == part_base[c + 1]) col_bits[c] = off[p] + lenbits[p] - base;
@@ -613,11 +616,12 @@ __global__ void k_set_offsets_multi(Record* __restrict__ rec, const uint64_t* __
 }
 
 __global__ void k_aux_multi(const Record* __restrict__ rec, const PolyCoef* __restrict__ pcoef,
-                            const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base, uint32_t ncols,
-                            uint64_t P, Aux* __restrict__ aux, PolyAux* __restrict__ poly) {
+                            const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
+                            const uint32_t* __restrict__ part_col, uint64_t P, Aux* __restrict__ aux,
+                            PolyAux* __restrict__ poly) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P;
        p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = find_col(part_base, ncols, p);
+    const uint32_t c = part_col[p];
     const Record r = rec[p];
     const uint64_t e = p + 1 < part_base[c + 1] ? rec[p + 1].start : cols[c].n;
     const uint64_t N = e > r.start ? e - r.start : 0;
@@ -628,41 +632,59 @@ __global__ void k_aux_multi(const Record* __restrict__ rec, const PolyCoef* __re
   }
 }
 
-// CTA per partition of every column (the column by a search over part_base)
+// CTA per pack item: a run of consecutive partitions of one column whose values fit one stage
+// (several short partitions share one staged copy), packed one partition after the other
 template <bool POLY>
 __global__ void __launch_bounds__(kPackBlock)
     k_pack_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
-                 const uint64_t* __restrict__ word_base, uint32_t ncols, uint64_t P, int dtype,
+                 const uint64_t* __restrict__ word_base, const PackItem* __restrict__ items, uint64_t nitems, int dtype,
                  const Record* __restrict__ rec, const Aux* __restrict__ aux, const PolyCoef* __restrict__ pcoef,
                  const PolyAux* __restrict__ poly, uint64_t* __restrict__ words, uint32_t* __restrict__ err) {
   __shared__ __align__(8) uint64_t full[1];
   extern __shared__ __align__(128) unsigned char ring[];
-  auto get = [&](uint64_t p) {
-    const uint32_t c = find_col(part_base, ncols, p);
+  auto get = [&](uint64_t it) {
+    const PackItem item = items[it];
+    const EncCol col = cols[item.c];
+    const uint64_t pe = item.p0 + item.k;
     PartSrc s;
-    s.values = cols[c].values;
-    s.n = cols[c].n;
-    s.a = aux[p].start;
-    s.N = (uint32_t)((p + 1 < part_base[c + 1] ? aux[p + 1].start : s.n) - s.a);
+    s.values = col.values;
+    s.n = col.n;
+    s.a = aux[item.p0].start;
+    s.N = (uint32_t)((pe < part_base[item.c + 1] ? aux[pe].start : s.n) - s.a);
     s.dtype = dtype;
     return s;
   };
-  auto body = [&](uint64_t p, const PartSrc& s, const unsigned char* st) {
-    const uint32_t c = find_col(part_base, ncols, p);
-    const uint64_t p0 = part_base[c];
-    pack_partition<POLY>(s, st, ring, rec + p0, aux + p0, POLY ? pcoef + p0 : nullptr, POLY ? poly + p0 : nullptr,
-                         p - p0, words + word_base[c]);
+  auto body = [&](uint64_t it, const PartSrc& si, const unsigned char* st) {
+    const PackItem item = items[it];
+    const uint64_t p0 = part_base[item.c];
+    const uint32_t vb = dtype == LECO_U32 ? 4u : 8u;
+    for (uint32_t q = 0; q < item.k; q++) {
+      const uint64_t p = item.p0 + q;
+      PartSrc s = si;
+      s.a = aux[p].start;
+      s.N = (uint32_t)((p + 1 < part_base[item.c + 1] ? aux[p + 1].start : si.n) - s.a);
+      const uint32_t zofs = (uint32_t)(s.a - si.a);
+      pack_partition<POLY>(s, st ? st + (size_t)zofs * vb : nullptr, ring, rec + p0, aux + p0,
+                           POLY ? pcoef + p0 : nullptr, POLY ? poly + p0 : nullptr, p - p0, words + word_base[item.c],
+                           zofs);
+    }
   };
-  for_each_staged<1>(P, pack_stage_cap(dtype), get, body, ring, full, err);
+  for_each_staged<1>(nitems, pack_stage_cap(dtype), get, body, ring, full, err);
+}
+
+__global__ void k_part_col(const uint64_t* __restrict__ part_base, uint32_t ncols, uint64_t P,
+                           uint32_t* __restrict__ part_col) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x)
+    part_col[p] = find_col(part_base, ncols, p);
 }
 
 // k_zero_bounds for every column: thread per partition, then each column's tail words
-__global__ void k_zero_bounds_multi(const Aux* __restrict__ aux, const uint64_t* __restrict__ part_base,
+__global__ void k_zero_bounds_multi(const Aux* __restrict__ aux, const uint32_t* __restrict__ part_col,
                                     const uint64_t* __restrict__ word_base, const uint64_t* __restrict__ col_bits,
                                     uint32_t ncols, uint64_t P, uint64_t* __restrict__ words) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P; p += stride) {
-    const uint32_t c = find_col(part_base, ncols, p);
+    const uint32_t c = part_col[p];
     words[word_base[c] + (part_first_bit(aux[p]) >> 6)] = 0;
   }
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < ncols; c += stride)
@@ -793,14 +815,20 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
-                             Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b, uint32_t* err,
-                             cudaStream_t st) {
+cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t P, uint32_t* part_col, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  k_part_col<<<grid_for(P, 256, 8), 256, 0, st>>>(part_base, ncols, P, part_col);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col, uint32_t ncols,
+                             uint64_t P, int dtype, Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b,
+                             uint32_t* err, cudaStream_t st) {
   (void)err;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t) * (ncols ? ncols : 1), st);
   if (e != cudaSuccess || P == 0) return e;
   const int grid = grid_for((P + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
-  k_fit_multi<<<grid, kFitBlock, 0, st>>>(cols, part_base, ncols, P, dtype, rec, lenbits, max_b);
+  k_fit_multi<<<grid, kFitBlock, 0, st>>>(cols, part_base, part_col, P, dtype, rec, lenbits, max_b);
   e = cudaGetLastError();
   if (e == cudaSuccess && pcoef)
     e = launch_poly_fit(BatchColumns{cols, part_base, ncols}, dtype, P, rec, lenbits, pcoef, max_b, st);
@@ -809,8 +837,9 @@ cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint
 
 uint64_t offsets_multi_scratch_elems(uint64_t P) { return P + (P + kPrefixTile - 1) / kPrefixTile + 2; }
 
-cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base, uint32_t ncols,
-                                 uint64_t P, uint64_t* scratch, uint64_t* col_bits, cudaStream_t st) {
+cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base,
+                                 const uint32_t* part_col, uint32_t ncols, uint64_t P, uint64_t* scratch,
+                                 uint64_t* col_bits, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(col_bits, 0, sizeof(uint64_t) * (ncols ? ncols : 1), st);
   if (e != cudaSuccess || P == 0) return e;
   uint64_t* off = scratch;
@@ -818,33 +847,36 @@ cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uin
   uint64_t* total = scratch + offsets_multi_scratch_elems(P) - 1;
   e = scan_u64(lenbits, P, off, tiles, total, st);
   if (e != cudaSuccess) return e;
-  k_set_offsets_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, off, lenbits, part_base, ncols, P, col_bits);
+  k_set_offsets_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, off, lenbits, part_base, part_col, P, col_bits);
   return cudaGetLastError();
 }
 
 cudaError_t launch_aux_multi(const Record* rec, const PolyCoef* pcoef, const EncCol* cols, const uint64_t* part_base,
-                             uint32_t ncols, uint64_t P, Aux* aux, PolyAux* poly, cudaStream_t st) {
+                             const uint32_t* part_col, uint64_t P, Aux* aux, PolyAux* poly, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
-  k_aux_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, pcoef, cols, part_base, ncols, P, aux, poly);
+  k_aux_multi<<<grid_for(P, 256, 8), 256, 0, st>>>(rec, pcoef, cols, part_base, part_col, P, aux, poly);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
-                              const uint64_t* col_bits, uint32_t ncols, uint64_t P, uint64_t W, int dtype,
-                              const Record* rec, const Aux* aux, const PolyCoef* pcoef, const PolyAux* poly,
-                              uint64_t* words, uint32_t* err, cudaStream_t st) {
+uint32_t pack_item_values() { return kStageData / 8; }
+
+cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col,
+                              const uint64_t* word_base, const uint64_t* col_bits, const PackItem* items,
+                              uint64_t nitems, uint32_t ncols, uint64_t P, uint64_t W, int dtype, const Record* rec,
+                              const Aux* aux, const PolyCoef* pcoef, const PolyAux* poly, uint64_t* words,
+                              uint32_t* err, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
-  k_zero_bounds_multi<<<grid_for(P > ncols ? P : ncols, 256, 8), 256, 0, st>>>(aux, part_base, word_base, col_bits,
+  k_zero_bounds_multi<<<grid_for(P > ncols ? P : ncols, 256, 8), 256, 0, st>>>(aux, part_col, word_base, col_bits,
                                                                                 ncols, P, words);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || P == 0) return e;
+  if (e != cudaSuccess || nitems == 0) return e;
   const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
   if (pcoef)
-    k_pack_multi<true><<<resident_grid(k_pack_multi<true>, kPackBlock, P, smem), kPackBlock, smem, st>>>(
-        cols, part_base, word_base, ncols, P, dtype, rec, aux, pcoef, poly, words, err);
+    k_pack_multi<true><<<resident_grid(k_pack_multi<true>, kPackBlock, nitems, smem), kPackBlock, smem, st>>>(
+        cols, part_base, word_base, items, nitems, dtype, rec, aux, pcoef, poly, words, err);
   else
-    k_pack_multi<false><<<resident_grid(k_pack_multi<false>, kPackBlock, P, smem), kPackBlock, smem, st>>>(
-        cols, part_base, word_base, ncols, P, dtype, rec, aux, nullptr, nullptr, words, err);
+    k_pack_multi<false><<<resident_grid(k_pack_multi<false>, kPackBlock, nitems, smem), kPackBlock, smem, st>>>(
+        cols, part_base, word_base, items, nitems, dtype, rec, aux, nullptr, nullptr, words, err);
   return cudaGetLastError();
 }
 

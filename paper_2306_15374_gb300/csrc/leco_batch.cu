@@ -307,6 +307,17 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
     tile_base[c + 1] = tile_base[c] + scan_tiles(n[c]);
   }
   const uint64_t P = part_base[ncols], T = tile_base[ncols];
+  // pack items: runs of consecutive partitions of one column that fit one staged copy
+  std::vector<PackItem> items;
+  items.reserve(P / 4 + ncols);
+  const uint64_t item_vals = pack_item_values();
+  for (uint32_t c = 0; c < ncols; c++) {
+    const uint64_t mc = part_base[c + 1] - part_base[c];
+    const uint64_t g = models[c] == LECO_MODEL_POLY ? 1 : (L[c] >= item_vals ? 1 : item_vals / L[c]);
+    for (uint64_t q = 0; q < mc; q += g)
+      items.push_back(PackItem{part_base[c] + q, c, (uint32_t)(mc - q < g ? mc - q : g)});
+  }
+  const uint64_t nitems = items.size();
   auto a256 = [](uint64_t x) { return (x + 255) & ~255ull; };
   // shared block 0: records | decode table | tile descriptors | status words | polynomial table
   const uint64_t rec_b = a256(32 * (P ? P : 1)), tiles_b = a256(sizeof(TileDesc) * (T ? T : 1));
@@ -315,11 +326,13 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   char* meta = nullptr;
   // scratch: lenbits | scan scratch | col_bits | max_b | polynomial blocks
   const uint64_t pc_words = any_poly ? (sizeof(PolyCoef) / 8) * (P ? P : 1) : 0;
-  const uint64_t scr_words = P + offsets_multi_scratch_elems(P) + 2 * (uint64_t)ncols + 8 + pc_words;
+  const uint64_t pcol_words = (P + 1) / 2 + 1;  // part_col, 32 bits per partition
+  const uint64_t scr_words = P + offsets_multi_scratch_elems(P) + 2 * (uint64_t)ncols + 8 + pc_words + pcol_words;
   uint64_t* scr = nullptr;
   EncCol* d_ec = nullptr;
   uint64_t* d_bases = nullptr;  // part_base | tile_base | word_base
   ColumnView* d_views = nullptr;
+  PackItem* d_items = nullptr;
   uint64_t* words = nullptr;
   leco_shared_blocks* sh = nullptr;
   std::vector<uint64_t> col_bits(ncols);
@@ -331,6 +344,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   if (e == cudaSuccess) e = dev_alloc((void**)&d_ec, sizeof(EncCol) * ncols, st);
   if (e == cudaSuccess) e = dev_alloc((void**)&d_bases, 8 * 3 * (uint64_t)(ncols + 1), st);
   if (e == cudaSuccess) e = dev_alloc((void**)&d_views, sizeof(ColumnView) * ncols, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&d_items, sizeof(PackItem) * (nitems ? nitems : 1), st);
   Record* rec = reinterpret_cast<Record*>(meta);
   Aux* aux = reinterpret_cast<Aux*>(meta + rec_b);
   TileDesc* tiles = reinterpret_cast<TileDesc*>(meta + 2 * rec_b);
@@ -340,7 +354,8 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   uint64_t* offs = scr + P;
   uint64_t* d_colbits = offs + offsets_multi_scratch_elems(P);
   uint32_t* d_maxb = reinterpret_cast<uint32_t*>(d_colbits + ncols);
-  PolyCoef* pcoef = any_poly ? reinterpret_cast<PolyCoef*>(scr + scr_words - pc_words) : nullptr;
+  PolyCoef* pcoef = any_poly ? reinterpret_cast<PolyCoef*>(scr + scr_words - pcol_words - pc_words) : nullptr;
+  uint32_t* part_col = reinterpret_cast<uint32_t*>(scr + scr_words - pcol_words);
   uint64_t* d_part = d_bases;
   uint64_t* d_tile = d_bases + (ncols + 1);
   uint64_t* d_word = d_bases + 2 * (ncols + 1);
@@ -348,9 +363,13 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_ec, ec.data(), sizeof(EncCol) * ncols, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_part, part_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_tile, tile_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nitems)
+    e = cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * nitems, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_part_col(d_part, ncols, P, part_col, st);
   // fit every partition of every column, then column-relative offsets and per-column totals
-  if (e == cudaSuccess) e = launch_fit_multi(d_ec, d_part, ncols, P, dtype, rec, lenbits, pcoef, d_maxb, status, st);
-  if (e == cudaSuccess) e = launch_offsets_multi(rec, lenbits, d_part, ncols, P, offs, d_colbits, st);
+  if (e == cudaSuccess)
+    e = launch_fit_multi(d_ec, d_part, part_col, ncols, P, dtype, rec, lenbits, pcoef, d_maxb, status, st);
+  if (e == cudaSuccess) e = launch_offsets_multi(rec, lenbits, d_part, part_col, ncols, P, offs, d_colbits, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(col_bits.data(), d_colbits, 8 * ncols, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(max_b.data(), d_maxb, 4 * ncols, cudaMemcpyDeviceToHost, st);
   uint32_t fit_flags = 0;
@@ -386,10 +405,11 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
     e = cudaMemcpyAsync(d_word, word_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_views, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = launch_aux_multi(rec, pcoef, d_ec, d_part, ncols, P, aux, poly, st);
+  if (e == cudaSuccess) e = launch_aux_multi(rec, pcoef, d_ec, d_part, part_col, P, aux, poly, st);
   if (e == cudaSuccess) e = launch_tile_desc_multi(d_views, d_tile, ncols, T, any_poly, tiles, st);
   if (e == cudaSuccess)
-    e = launch_pack_multi(d_ec, d_part, d_word, d_colbits, ncols, P, W, dtype, rec, aux, pcoef, poly, words, status, st);
+    e = launch_pack_multi(d_ec, d_part, part_col, d_word, d_colbits, d_items, nitems, ncols, P, W, dtype, rec, aux, pcoef,
+                          poly, words, status, st);
   if (e == cudaSuccess) {
     sh = new (std::nothrow) leco_shared_blocks();
     if (!sh) e = cudaErrorMemoryAllocation;
@@ -429,6 +449,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   cudaFreeAsync(d_ec, st);
   cudaFreeAsync(d_bases, st);
   cudaFreeAsync(d_views, st);
+  cudaFreeAsync(d_items, st);
   if (e != cudaSuccess) {
     for (uint32_t c = 0; c < ncols; c++) {
       delete out[c];

@@ -275,18 +275,30 @@ struct EncCol {
 // word_base / tile_base hold each column's first partition / word / scan tile (ncols + 1 entries)
 // pcoef / poly: as for one column, over all P partitions (nullptr when no column takes the
 // polynomial model; a polynomial column's partitions are fitted by the polynomial phases)
-cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, uint32_t ncols, uint64_t P, int dtype,
-                             Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b, uint32_t* err,
-                             cudaStream_t st);
+// part_col[p]: the column of global partition p (launch_part_col fills it once per batch)
+cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t P, uint32_t* part_col, cudaStream_t st);
+cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col, uint32_t ncols,
+                             uint64_t P, int dtype, Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b,
+                             uint32_t* err, cudaStream_t st);
 uint64_t offsets_multi_scratch_elems(uint64_t P);
-cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base, uint32_t ncols,
-                                 uint64_t P, uint64_t* scratch, uint64_t* col_bits, cudaStream_t st);
+cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base,
+                                 const uint32_t* part_col, uint32_t ncols, uint64_t P, uint64_t* scratch,
+                                 uint64_t* col_bits, cudaStream_t st);
 cudaError_t launch_aux_multi(const Record* rec, const PolyCoef* pcoef, const EncCol* cols, const uint64_t* part_base,
-                             uint32_t ncols, uint64_t P, Aux* aux, PolyAux* poly, cudaStream_t st);
-cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint64_t* word_base,
-                              const uint64_t* col_bits, uint32_t ncols, uint64_t P, uint64_t W, int dtype,
-                              const Record* rec, const Aux* aux, const PolyCoef* pcoef, const PolyAux* poly,
-                              uint64_t* words, uint32_t* err, cudaStream_t st);
+                             const uint32_t* part_col, uint64_t P, Aux* aux, PolyAux* poly, cudaStream_t st);
+// A pack item: k consecutive partitions p0 .. p0 + k - 1 (global indices) of column c, packed by one
+// CTA from one staged copy; at most pack_item_values() values, one partition for polynomial columns.
+struct PackItem {
+  uint64_t p0;
+  uint32_t c;
+  uint32_t k;
+};
+uint32_t pack_item_values();
+cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col,
+                              const uint64_t* word_base, const uint64_t* col_bits, const PackItem* items,
+                              uint64_t nitems, uint32_t ncols, uint64_t P, uint64_t W, int dtype, const Record* rec,
+                              const Aux* aux, const PolyCoef* pcoef, const PolyAux* poly, uint64_t* words,
+                              uint32_t* err, cudaStream_t st);
 // poly: some column has a polynomial table (its tiles then get the exact polynomial bounds)
 cudaError_t launch_tile_desc_multi(const ColumnView* views, const uint64_t* tile_base, uint32_t ncols, uint64_t T,
                                    bool poly, TileDesc* tiles, cudaStream_t st);
