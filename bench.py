@@ -512,10 +512,15 @@ def run_leco(args):
         "compressed_bytes": {d: comp[d] for d in DISTS},
         "ratio": {d: comp[d] / (8 * n) for d in DISTS},
     }
+    # execution-unit probes (a few ms each): the integer and binary64 rates the kernels' instruction
+    # mixes are held against
+    probes = {name: leco.leco_probe_throughput(kind) for kind, name in
+              ((0, "int32_shift_xor_add_ops_s"), (1, "int64_shift_xor_add_ops_s"), (2, "int32_and_funnel_ops_s"),
+               (3, "fp64_mul_add_ops_s"))}
     roofline = {"bound": "hbm", "kernel": "k_tilescan<decode u64> (full-column decode)", "achieved": dec_gbs,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": dec_gbs / peak,
                 "traffic": decode_traffic() if n == 200_000_000 else None,
-                "bytes_per_launch": dec_b / 3}
+                "bytes_per_launch": dec_b / 3, "unit_probes": probes}
 
     e2e = None
     if not args.no_e2e:

@@ -237,6 +237,15 @@ leco_status leco_search_partition_size(const void* d_values, uint64_t n, leco_dt
  * errors. Synchronizes `stream`. A systems facility; the paper has no counterpart. */
 leco_status leco_selftest_wait_timeout(uint32_t limit_us, leco_stream_t stream);
 
+/* Execution-unit throughput probe (a systems facility; the paper has no counterpart): runs many
+ * independent chains of one kind of operation on every SM of the current device and returns the
+ * measured rate in *ops_per_s. kind 0: 32-bit integer shift, xor and add (x = (x ^ (x >> 7)) + c,
+ * 3 ops per step); 1: the same in 64 bits (3 ops per step, each a 64-bit operation); 2: 32-bit
+ * funnel shift by a data-dependent amount (and + shift, 2 ops per step); 3: binary64 multiply and
+ * add without FMA (2 ops per step). Synchronizes `stream`; takes a few milliseconds. Errors:
+ * INVALID_ARG (NULL ops_per_s, kind outside 0..3), CUDA. */
+leco_status leco_probe_throughput(int32_t kind, double* ops_per_s, leco_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------ */
 /* Column metadata and lifetime */
 

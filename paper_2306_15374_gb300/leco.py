@@ -138,6 +138,7 @@ def lib() -> ctypes.CDLL:
         "leco_search_partition_size": (i32, [vp, u64, i32, i32, u32, ctypes.c_double, u64, vp,
                                              ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "leco_selftest_wait_timeout": (i32, [u32, vp]),
+        "leco_probe_throughput": (i32, [i32, ctypes.POINTER(ctypes.c_double), vp]),
         "leco_batch_plan_tune": (i32, [vp, vp, ctypes.POINTER(ScanConfig)]),
         "leco_batch_plan_free": (None, [vp]),
         "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
@@ -393,6 +394,16 @@ def leco_search_partition_size(values, model: int = 1, max_len: int = 0, sample_
                                             _stream(stream), ctypes.byref(L), ctypes.byref(bits), ctypes.byref(ne)),
            "leco_search_partition_size")
     return int(L.value), int(bits.value), int(ne.value)
+
+
+PROBE_KINDS = {0: "int32 shift+xor+add", 1: "int64 shift+xor+add", 2: "int32 and+funnel shift", 3: "fp64 mul+add"}
+
+
+def leco_probe_throughput(kind: int, stream=None) -> float:
+    """Measured operations per second of one execution-unit probe (kinds in PROBE_KINDS)."""
+    r = ctypes.c_double(0.0)
+    _check(lib().leco_probe_throughput(int(kind), ctypes.byref(r), _stream(stream)), "leco_probe_throughput")
+    return float(r.value)
 
 
 def leco_trim_memory() -> None:

@@ -94,3 +94,8 @@ def test_host_side_argument_errors(built):
         assert L.leco_var_partition(fake, 10, 1, pol, 1, fake, ctypes.byref(m_out), None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_encode(fake, 10, 1, leco.variable(2.0, seeded=True), 1, None, ctypes.byref(h)) == \
         leco.LECO_ERR_INVALID_ARG
+    # the execution-unit probe takes kinds 0..3 and an output pointer
+    r = ctypes.c_double(0.0)
+    assert L.leco_probe_throughput(4, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_probe_throughput(-1, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_probe_throughput(0, None, None) == leco.LECO_ERR_INVALID_ARG
