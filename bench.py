@@ -516,7 +516,7 @@ def run_leco(args):
     # mixes are held against
     probes = {name: leco.leco_probe_throughput(kind) for kind, name in
               ((0, "int32_shift_xor_add_ops_s"), (1, "int64_shift_xor_add_ops_s"), (2, "int32_and_funnel_ops_s"),
-               (3, "fp64_mul_add_ops_s"))}
+               (3, "fp64_mul_add_ops_s"), (4, "random_8B_reads_s"))}
     roofline = {"bound": "hbm", "kernel": "k_tilescan<decode u64> (full-column decode)", "achieved": dec_gbs,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": dec_gbs / peak,
                 "traffic": decode_traffic() if n == 200_000_000 else None,

@@ -242,8 +242,9 @@ leco_status leco_selftest_wait_timeout(uint32_t limit_us, leco_stream_t stream);
  * measured rate in *ops_per_s. kind 0: 32-bit integer shift, xor and add (x = (x ^ (x >> 7)) + c,
  * 3 ops per step); 1: the same in 64 bits (3 ops per step, each a 64-bit operation); 2: 32-bit
  * funnel shift by a data-dependent amount (and + shift, 2 ops per step); 3: binary64 multiply and
- * add without FMA (2 ops per step). Synchronizes `stream`; takes a few milliseconds. Errors:
- * INVALID_ARG (NULL ops_per_s, kind outside 0..3), CUDA. */
+ * add without FMA (2 ops per step); 4: random 8-byte reads from a 2 GiB buffer (one DRAM sector
+ * each; the buffer is allocated from the library's pool for the call). Synchronizes `stream`; takes
+ * a few milliseconds. Errors: INVALID_ARG (NULL ops_per_s, kind outside 0..4), OOM, CUDA. */
 leco_status leco_probe_throughput(int32_t kind, double* ops_per_s, leco_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------ */

@@ -67,6 +67,27 @@ __global__ void __launch_bounds__(kProbeBlock) k_probe(uint64_t iters, uint32_t 
   if (store) sink[t] = out;
 }
 
+// KIND 4: random 8-byte reads from a buffer far larger than L2 (nwords words): each step every
+// chain reads the word at a SplitMix64-scattered index that depends on the previous word read, so
+// the reads of one chain are serial and the chains of all threads are independent; the rate is one
+// random DRAM sector per read.
+__global__ void __launch_bounds__(kProbeBlock) k_probe_gather(const uint64_t* __restrict__ buf, uint64_t nwords,
+                                                               uint64_t iters, uint32_t seed, uint32_t store,
+                                                               uint64_t* sink) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  uint64_t h[kProbeChains];
+#pragma unroll
+  for (int u = 0; u < kProbeChains; u++) h[u] = splitmix64(t * kProbeChains + u + ((uint64_t)seed << 40));
+  for (uint64_t i = 0; i < iters; i++) {
+#pragma unroll
+    for (int u = 0; u < kProbeChains; u++) h[u] = splitmix64(h[u] ^ __ldg(buf + (h[u] % nwords)));
+  }
+  uint64_t out = 0;
+#pragma unroll
+  for (int u = 0; u < kProbeChains; u++) out += h[u];
+  if (store) sink[t] = out;
+}
+
 template <int KIND>
 cudaError_t run_probe(uint64_t iters, uint32_t seed, uint64_t* sink, int blocks, cudaStream_t st) {
   k_probe<KIND><<<blocks, kProbeBlock, 0, st>>>(iters, seed, 0u, sink);
@@ -87,10 +108,51 @@ cudaError_t probe_launch(int kind, uint64_t iters, uint32_t seed, uint64_t* sink
 
 using namespace leco;
 
+namespace {
+
+// kind 4: random gathers from a 2 GiB buffer (zeroed: the reads' values do not matter)
+leco_status probe_gather(double* ops_per_s, cudaStream_t st) {
+  const uint64_t nwords = (2ull << 30) / 8;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_probe_gather, kProbeBlock, 0) != cudaSuccess)
+    return LECO_ERR_CUDA;
+  const int blocks = sm_count() * (nb > 0 ? nb : 1);
+  uint64_t* buf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = dev_alloc((void**)&buf, 8 * nwords, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 8 * nwords, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const uint64_t iters = 64;
+  if (e == cudaSuccess) {
+    k_probe_gather<<<blocks, kProbeBlock, 0, st>>>(buf, nwords, iters / 8, 1, 0u, buf);  // warm-up
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    k_probe_gather<<<blocks, kProbeBlock, 0, st>>>(buf, nwords, iters, 2, 0u, buf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (buf) cudaFreeAsync(buf, st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return LECO_ERR_CUDA;
+  const double reads = (double)kProbeChains * (double)iters * (double)blocks * kProbeBlock;
+  *ops_per_s = ms > 0.f ? reads / (ms * 1e-3) : 0.0;
+  return LECO_OK;
+}
+
+}  // namespace
+
 extern "C" leco_status leco_probe_throughput(int32_t kind, double* ops_per_s, leco_stream_t stream) {
-  if (!ops_per_s || kind < 0 || kind > 3) return LECO_ERR_INVALID_ARG;
+  if (!ops_per_s || kind < 0 || kind > 4) return LECO_ERR_INVALID_ARG;
   *ops_per_s = 0.0;
   cudaStream_t st = (cudaStream_t)stream;
+  if (kind == 4) return probe_gather(ops_per_s, st);
   int nb = 0;
   cudaError_t e = cudaSuccess;
   switch (kind) {

@@ -396,7 +396,8 @@ def leco_search_partition_size(values, model: int = 1, max_len: int = 0, sample_
     return int(L.value), int(bits.value), int(ne.value)
 
 
-PROBE_KINDS = {0: "int32 shift+xor+add", 1: "int64 shift+xor+add", 2: "int32 and+funnel shift", 3: "fp64 mul+add"}
+PROBE_KINDS = {0: "int32 shift+xor+add", 1: "int64 shift+xor+add", 2: "int32 and+funnel shift", 3: "fp64 mul+add",
+               4: "random 8-byte reads"}
 
 
 def leco_probe_throughput(kind: int, stream=None) -> float:

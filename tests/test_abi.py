@@ -96,6 +96,6 @@ def test_host_side_argument_errors(built):
         leco.LECO_ERR_INVALID_ARG
     # the execution-unit probe takes kinds 0..3 and an output pointer
     r = ctypes.c_double(0.0)
-    assert L.leco_probe_throughput(4, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_probe_throughput(5, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_probe_throughput(-1, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_probe_throughput(0, None, None) == leco.LECO_ERR_INVALID_ARG
