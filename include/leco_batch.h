@@ -3,8 +3,8 @@
  *
  * The paper decodes one column at a time on one CPU thread (§4.2); these calls are this library's
  * systems layer around the same per-value decode of §3.3: many columns of uneven lengths decoded
- * by one persistent kernel launch (optionally a CUDA graph), and an autotuner that picks the scan
- * pipeline's shape. Conventions (device pointers, streams, ownership, errors) are those of leco.h.
+ * by one persistent kernel launch (optionally a CUDA graph) or encoded by one persistent fit and one
+ * persistent pack launch, and an autotuner that picks the scan pipeline's and the encode's shape. Conventions (device pointers, streams, ownership, errors) are those of leco.h.
  */
 #ifndef LECO_BATCH_H
 #define LECO_BATCH_H
@@ -77,14 +77,35 @@ leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_out
  * column c has n[c] values of `dtype` at d_vals[c] (device), model models[c] (constant, linear or
  * polynomial, mixed freely) and partition size L[c] (1 .. 2^24). Every stage runs over all columns
  * in one launch (fit, offset scan, decode table, tile descriptors, pack; the polynomial columns' fit
- * adds its four phases over all their partitions); one stream synchronization sizes the residual
- * streams. out[c]
+ * adds its four phases over all their partitions), in the shape the tuning table holds for `dtype`
+ * (leco_tune_batch_encode); one stream synchronization reads back the residual streams' sizes, which
+ * the allocation of the packed streams needs. out[c]
  * receives a column identical to leco_encode(d_vals[c], n[c], dtype, fixed(L[c]), models[c]);
  * the columns share their device blocks, which are released when the last of them is freed.
  * Errors: INVALID_ARG, OOM, CUDA (then no column is returned). */
 leco_status leco_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
                               const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
                               leco_column** out);
+
+/* Shape of the batched encode (a systems knob; the paper has no counterpart): values per pack item
+ * (1024, 2048 or 4096: a run of consecutive short partitions of one column that the packer stages
+ * with one copy and packs in one CTA) and fit CTAs per SM (2, 3 or 4: fewer keep more of each
+ * partition in L2 between the fit's two passes, more hide the exact solve's latency); ms is the
+ * measured time of the chosen shape (leco_tune_batch_encode only). */
+typedef struct {
+  uint32_t item_values;
+  uint32_t fit_ctas;
+  double ms;
+} leco_encode_config;
+
+/* Time leco_batch_encode of these columns (arguments as there) under every candidate shape (twice;
+ * the second pass counts), keep the fastest for later batched encodes of the same value width (the
+ * process-wide tuning table, saved and loaded with the scan configurations), and return it in
+ * *best. The encoded columns are freed; the result of every later encode is unchanged (byte for
+ * byte), only its speed. Synchronizes `stream`. Errors: INVALID_ARG, OOM, CUDA. */
+leco_status leco_tune_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                                   const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
+                                   leco_encode_config* best);
 
 #ifdef __cplusplus
 }

@@ -823,11 +823,12 @@ cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t 
 
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col, uint32_t ncols,
                              uint64_t P, int dtype, Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b,
-                             uint32_t* err, cudaStream_t st) {
+                             uint32_t* err, uint32_t fit_ctas, cudaStream_t st) {
   (void)err;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t) * (ncols ? ncols : 1), st);
   if (e != cudaSuccess || P == 0) return e;
-  const int grid = grid_for((P + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
+  const int ctas = fit_ctas >= 1 && fit_ctas <= (uint32_t)kFitCtasPerSm ? (int)fit_ctas : kFitCtasPerSm;
+  const int grid = grid_for((P + kFitWarps - 1) / kFitWarps, 1, ctas);
   k_fit_multi<<<grid, kFitBlock, 0, st>>>(cols, part_base, part_col, P, dtype, rec, lenbits, max_b);
   e = cudaGetLastError();
   if (e == cudaSuccess && pcoef)

@@ -280,9 +280,11 @@ leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_out
 
 // ------------------------------------------------------------------------------ batched encode
 
-extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
-                                         const uint32_t* L, uint32_t ncols, leco_dtype dtype,
-                                         leco_stream_t stream, leco_column** out) {
+namespace {
+
+leco_status batch_encode_cfg(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                             const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
+                             leco_column** out, EncodeConfig cfg) {
   if (!out || (ncols && (!d_vals || !n || !models || !L)) || (dtype != LECO_U32 && dtype != LECO_U64))
     return LECO_ERR_INVALID_ARG;
   for (uint32_t c = 0; c < ncols; c++) {
@@ -310,7 +312,8 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   // pack items: runs of consecutive partitions of one column that fit one staged copy
   std::vector<PackItem> items;
   items.reserve(P / 4 + ncols);
-  const uint64_t item_vals = pack_item_values();
+  const uint64_t item_vals = cfg.item_values >= 1 && cfg.item_values <= pack_item_values() ? cfg.item_values
+                                                                                           : pack_item_values();
   for (uint32_t c = 0; c < ncols; c++) {
     const uint64_t mc = part_base[c + 1] - part_base[c];
     const uint64_t g = models[c] == LECO_MODEL_POLY ? 1 : (L[c] >= item_vals ? 1 : item_vals / L[c]);
@@ -368,7 +371,7 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   if (e == cudaSuccess) e = launch_part_col(d_part, ncols, P, part_col, st);
   // fit every partition of every column, then column-relative offsets and per-column totals
   if (e == cudaSuccess)
-    e = launch_fit_multi(d_ec, d_part, part_col, ncols, P, dtype, rec, lenbits, pcoef, d_maxb, status, st);
+    e = launch_fit_multi(d_ec, d_part, part_col, ncols, P, dtype, rec, lenbits, pcoef, d_maxb, status, cfg.fit_ctas, st);
   if (e == cudaSuccess) e = launch_offsets_multi(rec, lenbits, d_part, part_col, ncols, P, offs, d_colbits, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(col_bits.data(), d_colbits, 8 * ncols, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(max_b.data(), d_maxb, 4 * ncols, cudaMemcpyDeviceToHost, st);
@@ -462,3 +465,59 @@ extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64
   }
   return LECO_OK;
 }
+
+}  // namespace
+
+extern "C" leco_status leco_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                                         const uint32_t* L, uint32_t ncols, leco_dtype dtype,
+                                         leco_stream_t stream, leco_column** out) {
+  return batch_encode_cfg(d_vals, n, models, L, ncols, dtype, stream, out, encode_config_lookup(dtype));
+}
+
+extern "C" leco_status leco_tune_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                                              const uint32_t* L, uint32_t ncols, leco_dtype dtype,
+                                              leco_stream_t stream, leco_encode_config* best) {
+  if (!best || (dtype != LECO_U32 && dtype != LECO_U64)) return LECO_ERR_INVALID_ARG;
+  if (ncols == 0) return LECO_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<leco_column*> cols(ncols, nullptr);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return LECO_ERR_CUDA;
+  }
+  leco_status s = LECO_OK;
+  EncodeConfig win{4096, 4};
+  float win_ms = -1.f;
+  const uint32_t items[3] = {1024, 2048, 4096}, ctas[3] = {2, 3, 4};
+  for (int rep = 0; rep < 2 && s == LECO_OK; rep++) {  // the first pass warms pools and modules
+    for (uint32_t iv : items)
+      for (uint32_t fc : ctas) {
+        if (s != LECO_OK) break;
+        const EncodeConfig cfg{iv, fc};
+        if (cudaEventRecord(e0, st) != cudaSuccess) s = LECO_ERR_CUDA;
+        if (s == LECO_OK) s = batch_encode_cfg(d_vals, n, models, L, ncols, dtype, stream, cols.data(), cfg);
+        if (s == LECO_OK && cudaEventRecord(e1, st) != cudaSuccess) s = LECO_ERR_CUDA;
+        if (s == LECO_OK && cudaEventSynchronize(e1) != cudaSuccess) s = LECO_ERR_CUDA;
+        float ms = 0.f;
+        if (s == LECO_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s = LECO_ERR_CUDA;
+        for (leco_column*& c : cols) {
+          leco_column_free_async(c, stream);
+          c = nullptr;
+        }
+        if (s == LECO_OK && rep == 1 && (win_ms < 0.f || ms < win_ms)) {
+          win_ms = ms;
+          win = cfg;
+        }
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != LECO_OK) return s;
+  encode_config_store(dtype, win);
+  best->item_values = win.item_values;
+  best->fit_ctas = win.fit_ctas;
+  best->ms = win_ms;
+  return cudaStreamSynchronize(st) == cudaSuccess ? LECO_OK : LECO_ERR_CUDA;
+}
+

@@ -279,7 +279,7 @@ struct EncCol {
 cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t P, uint32_t* part_col, cudaStream_t st);
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col, uint32_t ncols,
                              uint64_t P, int dtype, Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b,
-                             uint32_t* err, cudaStream_t st);
+                             uint32_t* err, uint32_t fit_ctas, cudaStream_t st);
 uint64_t offsets_multi_scratch_elems(uint64_t P);
 cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base,
                                  const uint32_t* part_col, uint32_t ncols, uint64_t P, uint64_t* scratch,
@@ -315,6 +315,16 @@ __device__ __forceinline__ uint32_t find_col(const uint64_t* __restrict__ base, 
   }
   return lo;
 }
+
+// Shape of the batched encode: values per pack item (a run of short partitions staged by one copy:
+// 1024, 2048 or 4096) and fit CTAs per SM (2, 3 or 4; fewer keep more of each partition in L2 for
+// the fit's second pass). Tuned per value width by leco_tune_batch_encode.
+struct EncodeConfig {
+  uint32_t item_values;
+  uint32_t fit_ctas;
+};
+EncodeConfig encode_config_lookup(int dtype);
+void encode_config_store(int dtype, EncodeConfig cfg);
 
 // tuning table (tune.cu): op 0 = decode, 1 = filter-sum; keyed by value width and widest partition
 ScanConfig scan_config_for(const ColumnView& c, int op);

@@ -1,6 +1,7 @@
-// Scan-pipeline tuning table: the configuration (stages in flight, consumer warps) each scan uses,
-// keyed by operation, value width and the column's widest partition (which sets the stage size).
-// Entries come from leco_tune_scan (timed candidates on a real column) or from a JSON file.
+// Tuning table: the configuration (stages in flight, consumer warps) each scan uses, keyed by
+// operation, value width and the column's widest partition (which sets the stage size), and the
+// batched encode's shape (values per pack item, fit CTAs per SM) per value width. Entries come from
+// leco_tune_scan / leco_tune_batch_encode (timed candidates on real data) or from a JSON file.
 #include <stdio.h>
 #include <string.h>
 
@@ -16,6 +17,7 @@ namespace {
 
 std::mutex g_mu;
 std::map<std::tuple<int, int, int>, ScanConfig> g_table;
+std::map<int, EncodeConfig> g_enc;  // batched encode shape per value width
 
 // 0: widest partition <= 8 bits, 1: <= 16, 2: <= 32, 3: wider
 int width_bucket(uint32_t stage_bytes) {
@@ -41,6 +43,18 @@ void scan_config_store(int op, int dtype, uint32_t stage_bytes, ScanConfig cfg) 
   g_table[std::make_tuple(op, dtype, width_bucket(stage_bytes))] = cfg;
 }
 
+EncodeConfig encode_config_lookup(int dtype) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_enc.find(dtype);
+  if (it != g_enc.end()) return it->second;
+  return EncodeConfig{4096, 4};  // untuned default: the largest items, four fit CTAs per SM
+}
+
+void encode_config_store(int dtype, EncodeConfig cfg) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_enc[dtype] = cfg;
+}
+
 int tune_table_save(const char* path) {
   std::lock_guard<std::mutex> lock(g_mu);
   FILE* f = fopen(path, "w");
@@ -51,6 +65,13 @@ int tune_table_save(const char* path) {
     fprintf(f, "%s\n  {\"op\": %d, \"dtype\": %d, \"width_bucket\": %d, \"stages\": %u, \"consumer_warps\": %u}",
             first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
             kv.second.stages, kv.second.consumer_warps);
+    first = false;
+  }
+  fprintf(f, "\n], \"encode_configs\": [");
+  first = true;
+  for (const auto& kv : g_enc) {
+    fprintf(f, "%s\n  {\"dtype\": %d, \"item_values\": %u, \"fit_ctas\": %u}", first ? "" : ",", kv.first,
+            kv.second.item_values, kv.second.fit_ctas);
     first = false;
   }
   fprintf(f, "\n]}\n");
@@ -68,6 +89,14 @@ int tune_table_load(const char* path) {
   while (fgets(line, sizeof(line), f)) {
     int op, dtype, wb;
     unsigned st, cw;
+    unsigned iv, fc;
+    const char* q = strstr(line, "{\"dtype\"");
+    if (q && sscanf(q, "{\"dtype\": %d, \"item_values\": %u, \"fit_ctas\": %u}", &dtype, &iv, &fc) == 3 &&
+        (iv == 1024 || iv == 2048 || iv == 4096) && fc >= 2 && fc <= 4) {
+      g_enc[dtype] = EncodeConfig{iv, fc};
+      n++;
+      continue;
+    }
     const char* p = strstr(line, "{\"op\"");
     if (!p) continue;
     if (sscanf(p, "{\"op\": %d, \"dtype\": %d, \"width_bucket\": %d, \"stages\": %u, \"consumer_warps\": %u}", &op,

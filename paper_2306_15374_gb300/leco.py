@@ -63,6 +63,10 @@ class ScanConfig(ctypes.Structure):
     _fields_ = [("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
 
+class EncodeConfig(ctypes.Structure):
+    _fields_ = [("item_values", ctypes.c_uint32), ("fit_ctas", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [
         ("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("max_batch_requests", ctypes.c_uint32),
@@ -144,6 +148,8 @@ def lib() -> ctypes.CDLL:
         "leco_batch_decode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp]),
         "leco_batch_encode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
                                     ctypes.POINTER(u32), u32, i32, vp, ctypes.POINTER(vp)]),
+        "leco_tune_batch_encode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
+                                         ctypes.POINTER(u32), u32, i32, vp, ctypes.POINTER(EncodeConfig)]),
         "leco_server_create": (i32, [ctypes.POINTER(ServerConfig), col_pp]),
         "leco_server_admit": (i32, [vp, vp, ctypes.POINTER(u32)]),
         "leco_server_admit_mock": (i32, [vp, u64, i32, u64, ctypes.POINTER(u32)]),
@@ -601,8 +607,7 @@ def leco_server_destroy(server: Server) -> None:
     server.destroy()
 
 
-def leco_batch_encode(values, models, Ls, stream=None) -> list:
-    """Fixed-partition encode of several columns (CUDA tensors of one width) in one pass."""
+def _batch_args(values, models, Ls):
     k = len(values)
     dt = _dtype_of(values[0]) if k else LECO_U64
     if any(_dtype_of(v) != dt for v in values):
@@ -611,6 +616,21 @@ def leco_batch_encode(values, models, Ls, stream=None) -> list:
     ns = (ctypes.c_uint64 * max(k, 1))(*[v.numel() for v in values])
     ms = (ctypes.c_int * max(k, 1))(*[int(m) for m in models])
     ls = (ctypes.c_uint32 * max(k, 1))(*[int(x) for x in Ls])
+    return k, dt, vals, ns, ms, ls
+
+
+def leco_tune_batch_encode(values, models, Ls, stream=None) -> dict:
+    """Time the batched encode's candidate shapes on these columns and keep the fastest (leco_batch.h)."""
+    k, dt, vals, ns, ms, ls = _batch_args(values, models, Ls)
+    cfg = EncodeConfig()
+    _check(lib().leco_tune_batch_encode(vals, ns, ms, ls, k, dt, _stream(stream), ctypes.byref(cfg)),
+           "leco_tune_batch_encode")
+    return {"item_values": cfg.item_values, "fit_ctas": cfg.fit_ctas, "ms": cfg.ms}
+
+
+def leco_batch_encode(values, models, Ls, stream=None) -> list:
+    """Fixed-partition encode of several columns (CUDA tensors of one width) in one pass."""
+    k, dt, vals, ns, ms, ls = _batch_args(values, models, Ls)
     out = (ctypes.c_void_p * max(k, 1))()
     _check(lib().leco_batch_encode(vals, ns, ms, ls, k, dt, _stream(stream), out), "leco_batch_encode")
     return [Column(ctypes.c_void_p(out[i])) for i in range(k)]

@@ -115,6 +115,28 @@ def test_batch_encode_matches_single_column_encode(lc, bits):
         assert (from_dev(out)[: len(v)] == v).all()
 
 
+def test_encode_tuner_keeps_results_identical(lc, tmp_path):
+    """Every batched-encode shape the tuner tries gives the same bytes; the chosen one is stored and
+    saved with the scan configurations."""
+    g = W.rng(29)
+    vals, models, Ls = [], [], []
+    for c in range(24):
+        n = int(np.exp(g.uniform(np.log(100), np.log(400_000))))
+        vals.append(W.linear_noise(n, 1 << 30, int(g.integers(0, 60)), int(g.integers(0, 3000)), seed=c))
+        models.append(c % 2)
+        Ls.append(int(g.choice([37, 256, 1024, 4096])))
+    dvals = [to_dev(v) for v in vals]
+    before = [lc.leco_column_export(c) for c in lc.leco_batch_encode(dvals, models, Ls)]
+    best = lc.leco_tune_batch_encode(dvals, models, Ls)
+    assert best["item_values"] in (1024, 2048, 4096) and best["fit_ctas"] in (2, 3, 4) and best["ms"] > 0
+    after = [lc.leco_column_export(c) for c in lc.leco_batch_encode(dvals, models, Ls)]
+    assert before == after
+    path = str(tmp_path / "tune_enc.json")
+    lc.leco_tune_save(path)
+    assert '"item_values"' in open(path).read()
+    lc.leco_tune_load(path)
+
+
 def test_tuner_keeps_results_identical(lc, tmp_path):
     import torch
 
