@@ -480,6 +480,48 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
   const bool pl = POLY && w3_poly(a.word3) != 0;
   const uint64_t off = w3_off(a.word3), endb = off + (uint64_t)s.N * b;
   const uint64_t off0 = pl ? off - kPolyBlockBits : off;  // first bit of the partition (its block)
+  if (!pl && st && b && w3_exact(a.word3)) {
+    // Staged partition on the integer grid (the common case). Phase 1: each thread steps its
+    // fixed-point prediction F = A + B x by B blockDim from one position to its next (no multiply).
+    // Phase 2: bit positions relative to the partition's first residual bit fit 32 bits (at most
+    // 2^24 fields of at most 64 bits).
+    uint64_t* zs = s.dtype == LECO_U32 ? reinterpret_cast<uint64_t*>(ring + kZzOffset32) + zofs
+                                       : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
+    const int32_t sr = w3_s(a.word3);
+    const uint32_t sh = sr > 0 ? (uint32_t)sr : 0u;
+    uint64_t F = (uint64_t)a.A + (uint64_t)a.B * threadIdx.x;
+    const uint64_t dF = (uint64_t)a.B * blockDim.x;
+    if (s.dtype == LECO_U32) {
+      const uint32_t* v = reinterpret_cast<const uint32_t*>(st);
+      for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x, F += dF)
+        zs[x] = zz_encode((int64_t)((uint64_t)v[x] - (uint64_t)((int64_t)F >> sh)));
+    } else {
+      const uint64_t* v = reinterpret_cast<const uint64_t*>(st);
+      for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x, F += dF)
+        zs[x] = zz_encode((int64_t)(v[x] - (uint64_t)((int64_t)F >> sh)));
+    }
+    __syncthreads();
+    const uint32_t lead = (uint32_t)(off & 63u);
+    const int32_t nbits = (int32_t)(s.N * b);
+    const uint64_t w0 = off >> 6, wl = (endb - 1) >> 6;
+    for (uint64_t w = w0 + threadIdx.x; w <= wl; w += blockDim.x) {
+      const int32_t r0 = (int32_t)((w - w0) << 6) - (int32_t)lead;  // the word's first bit, relative
+      const int32_t r1 = r0 + 64 < nbits ? r0 + 64 : nbits;
+      uint32_t x = r0 > 0 ? (uint32_t)r0 / b : 0u;
+      uint64_t acc = 0;
+      for (int32_t fr = (int32_t)(x * b); fr < r1; fr += (int32_t)b, x++) {
+        const uint64_t z = zs[x];
+        const int32_t d = fr - r0;
+        acc |= d >= 0 ? z << d : z >> (-d);
+      }
+      if (r0 >= 0 && r0 + 64 <= nbits)
+        words[w] = acc;
+      else
+        atomicOr((unsigned long long*)&words[w], (unsigned long long)acc);
+    }
+    __syncthreads();  // the stage buffer is refilled for the next partition
+    return;
+  }
   if (endb > off0) {
     // phase 1: residuals into shared memory (staged partitions only; others recompute per field)
     uint64_t* zs = nullptr;
@@ -672,6 +714,66 @@ __global__ void __launch_bounds__(kPackBlock)
   for_each_staged<1>(nitems, pack_stage_cap(dtype), get, body, ring, full, err);
 }
 
+// Pack items of one column with short partitions (variable partitions): a partition of at most
+// kItemWindow values joins the item of its predecessor when both start in the same kItemWindow-aligned
+// window of positions (so an item spans fewer than 2 kItemWindow values and fits one stage); a longer
+// partition is an item of its own. flag[p] = 1 where an item begins.
+constexpr uint64_t kItemWindow = 2048;
+
+__global__ void k_item_flags(const Aux* __restrict__ aux, uint64_t m, uint64_t n, uint64_t* __restrict__ flag) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = aux[p].start, e = p + 1 < m ? aux[p + 1].start : n;
+    bool begin = p == 0 || e - s > kItemWindow;
+    if (!begin) {
+      const uint64_t s0 = aux[p - 1].start;
+      begin = s - s0 > kItemWindow || (s / kItemWindow) != (s0 / kItemWindow);
+    }
+    flag[p] = begin ? 1ull : 0ull;
+  }
+}
+
+// item_start[idx[p]] = p for every item-beginning partition p, and item_start[nitems] = m
+__global__ void k_item_starts(const uint64_t* __restrict__ flag, const uint64_t* __restrict__ idx, uint64_t m,
+                              const uint64_t* __restrict__ nitems, uint64_t* __restrict__ item_start) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    if (flag[p]) item_start[idx[p]] = p;
+    if (p == 0) item_start[*nitems] = m;
+  }
+}
+
+// CTA per item of one column (constant and linear partitions): one staged copy for the item's
+// partitions, packed one after the other; the item count is read on the device
+__global__ void __launch_bounds__(kPackBlock)
+    k_pack_items(const void* __restrict__ values, int dtype, const Record* __restrict__ rec,
+                 const Aux* __restrict__ aux, uint64_t m, uint64_t n, const uint64_t* __restrict__ item_start,
+                 const uint64_t* __restrict__ nitems_d, uint64_t* __restrict__ words, uint32_t* __restrict__ err) {
+  __shared__ __align__(8) uint64_t full[1];
+  extern __shared__ __align__(128) unsigned char ring[];
+  const uint64_t nitems = *nitems_d;
+  auto get = [&](uint64_t it) {
+    const uint64_t p0 = item_start[it], pe = item_start[it + 1];
+    PartSrc s;
+    s.values = values;
+    s.n = n;
+    s.a = aux[p0].start;
+    s.N = (uint32_t)((pe < m ? aux[pe].start : n) - s.a);
+    s.dtype = dtype;
+    return s;
+  };
+  auto body = [&](uint64_t it, const PartSrc& si, const unsigned char* st) {
+    const uint64_t p0 = item_start[it], pe = item_start[it + 1];
+    const uint32_t vb = dtype == LECO_U32 ? 4u : 8u;
+    for (uint64_t p = p0; p < pe; p++) {
+      PartSrc s = si;
+      s.a = aux[p].start;
+      s.N = (uint32_t)((p + 1 < m ? aux[p + 1].start : n) - s.a);
+      const uint32_t zofs = (uint32_t)(s.a - si.a);
+      pack_partition<false>(s, st ? st + (size_t)zofs * vb : nullptr, ring, rec, aux, nullptr, nullptr, p, words, zofs);
+    }
+  };
+  for_each_staged<1>(nitems, pack_stage_cap(dtype), get, body, ring, full, err);
+}
+
 __global__ void k_part_col(const uint64_t* __restrict__ part_base, uint32_t ncols, uint64_t P,
                            uint32_t* __restrict__ part_col) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x)
@@ -813,6 +915,42 @@ cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const 
     k_pack<false><<<resident_grid(k_pack<false>, kPackBlock, m, smem), kPackBlock, smem, st>>>(
         values, dtype, rec, aux, nullptr, nullptr, m, n, words, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pack_var(const void* values, int dtype, const Record* rec, const Aux* aux, uint64_t m, uint64_t n,
+                            uint64_t total_bits, uint64_t* words, uint64_t nwords, uint32_t* err, cudaStream_t st) {
+  if (nwords == 0) return cudaSuccess;
+  const uint64_t tail = total_bits >> 6;
+  k_zero_bounds<<<grid_for(m + (nwords > tail ? nwords - tail : 0), 256, 8), 256, 0, st>>>(aux, m, total_bits, nwords,
+                                                                                         words);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || m == 0) return e;
+  // flags | indices | item starts (m + 1) | scan scratch | item count
+  const uint64_t scr_elems = m / 2048 + 2;
+  uint64_t* buf = nullptr;
+  e = dev_alloc((void**)&buf, 8 * (3 * m + 1 + scr_elems + 2), st);
+  if (e != cudaSuccess) return e;
+  uint64_t* flag = buf;
+  uint64_t* idx = buf + m;
+  uint64_t* item_start = buf + 2 * m;
+  uint64_t* scr = item_start + m + 1;
+  uint64_t* nitems = scr + scr_elems + 1;
+  k_item_flags<<<grid_for(m, 256, 8), 256, 0, st>>>(aux, m, n, flag);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = scan_u64(flag, m, idx, scr, nitems, st);
+  if (e == cudaSuccess) {
+    k_item_starts<<<grid_for(m, 256, 8), 256, 0, st>>>(flag, idx, m, nitems, item_start);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const uint32_t smem = dtype == LECO_U32 ? kPackSmem32 : kPackSmem64;
+    // every item holds at least one partition: m bounds the count the grid is sized for
+    k_pack_items<<<resident_grid(k_pack_items, kPackBlock, m, smem), kPackBlock, smem, st>>>(
+        values, dtype, rec, aux, m, n, item_start, nitems, words, err);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(buf, st);
+  return e;
 }
 
 cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t P, uint32_t* part_col, cudaStream_t st) {

@@ -134,9 +134,13 @@ leco_status encode_partitions(leco_column* c, const void* d_values, cudaStream_t
   }
   if (e == cudaSuccess) e = launch_build_aux(c->rec, pcoef, m, c->n, c->aux, c->poly, c->status, st);
   if (e == cudaSuccess) e = launch_tile_desc(view_of(c), c->tiles, st);
-  if (e == cudaSuccess)
-    e = launch_pack(d_values, c->dtype, c->rec, c->aux, pcoef, c->poly, m, c->n, total, c->words, c->nwords,
-                    c->status, st);
+  if (e == cudaSuccess) {
+    if (c->kind == LECO_PART_VAR && !poly)
+      e = launch_pack_var(d_values, c->dtype, c->rec, c->aux, m, c->n, total, c->words, c->nwords, c->status, st);
+    else
+      e = launch_pack(d_values, c->dtype, c->rec, c->aux, pcoef, c->poly, m, c->n, total, c->words, c->nwords,
+                      c->status, st);
+  }
   cudaFreeAsync(scr, st);
   if (e == cudaErrorInvalidValue) return LECO_ERR_INVALID_ARG;
   return from_cuda(e);

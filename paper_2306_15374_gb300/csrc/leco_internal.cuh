@@ -345,6 +345,10 @@ cudaError_t launch_build_aux(const Record* rec, const PolyCoef* pcoef, uint64_t 
 cudaError_t launch_pack(const void* values, int dtype, const Record* rec, const Aux* aux, const PolyCoef* pcoef,
                         const PolyAux* poly, uint64_t m, uint64_t n, uint64_t total_bits, uint64_t* words,
                         uint64_t nwords, uint32_t* err, cudaStream_t st);
+// the same for a column of constant and linear partitions of any lengths (variable partitions):
+// short partitions that start in one 2048-position window share one staged copy
+cudaError_t launch_pack_var(const void* values, int dtype, const Record* rec, const Aux* aux, uint64_t m, uint64_t n,
+                            uint64_t total_bits, uint64_t* words, uint64_t nwords, uint32_t* err, cudaStream_t st);
 
 // scans (k_scan.cu) and lookups (k_decode.cu)
 cudaError_t launch_tile_desc(const ColumnView& c, TileDesc* tiles, cudaStream_t st);
