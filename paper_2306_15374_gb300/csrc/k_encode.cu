@@ -857,7 +857,10 @@ cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t
   if (e != cudaSuccess || m == 0) return e;
   if (model == LECO_MODEL_POLY) return launch_poly_fit(OneColumn{values, n, starts, L}, dtype, m, rec, lenbits, pcoef,
                                                         max_b, st);
-  const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, kFitCtasPerSm);
+  // fit CTAs per SM: the encode shape of the tuning table for this value width (fewer keep more of
+  // each partition in L2 between the two passes)
+  const uint32_t fc = encode_config_lookup(dtype).fit_ctas;
+  const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, fc >= 1 && fc <= (uint32_t)kFitCtasPerSm ? (int)fc : kFitCtasPerSm);
   k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
   return cudaGetLastError();
 }
