@@ -733,6 +733,8 @@ def bench_var(args, leco, dev, stream, sweep=False):
         res = torch.zeros(3, dtype=torch.int64, device=dev)
         lo, hi = W.filter_bounds(v)
         reps = max(3, min(args.steps, 50))
+        # the library's scan tuner picks stages x consumer warps for this column's shape
+        tuned = {"decode": leco.leco_tune_scan(col, 0), "filter": leco.leco_tune_scan(col, 1, lo, hi)}
         t_dec = ev_timed(lambda: leco.leco_decode_all(col, o), stream, reps)
         ok = bool(torch.equal(o, dv))
         t_fil = ev_timed(lambda: leco.leco_filter_sum(col, lo, hi, res), stream, reps)
@@ -746,7 +748,7 @@ def bench_var(args, leco, dev, stream, sweep=False):
             "decode_frac_hbm": (comp + n * vb) / (t_dec * 1e-3) / 1e9 / peak, "decode_equals_input": ok,
             "filter_ms": t_fil, "filter_gbs": (comp + 24) / (t_fil * 1e-3) / 1e9,
             "filter_frac_hbm": (comp + 24) / (t_fil * 1e-3) / 1e9 / peak,
-            "filter_prune_ms": t_pru, "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6,
+            "filter_prune_ms": t_pru, "lookup_ms": t_ra, "mlookups_s": k / (t_ra * 1e-3) / 1e6, "tuned_scan": tuned,
         }
         # the oracle beside it: every 100th GPU partition, encoded with the same boundaries
         _, _, starts_b = leco.leco_column_export(col)

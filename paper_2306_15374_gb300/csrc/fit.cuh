@@ -109,7 +109,8 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   const i128 D = lin ? (i128)N * ((i128)N * (i128)N - 1) : (i128)1;
   const i128 sixS = lin ? 6 * S : (i128)0;
   const i128 a6 = sixS < 0 ? -sixS : sixS;
-  const i128 Q = floordiv_i128(a6 + D - 1, D);  // ceil(|6S| / D)
+  // ceil(|6S| / D); without a division for the constant model (0) and for two values (D = 6: |S|)
+  const i128 Q = !lin ? (i128)0 : (N == 2 ? (S < 0 ? -S : S) : floordiv_i128(a6 + D - 1, D));
   const i128 amx = mx < 0 ? -(i128)mx : (i128)mx;
   const i128 amn = mn < 0 ? -(i128)mn : (i128)mn;
   const i128 M = amx > amn ? amx : amn;
@@ -127,7 +128,9 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   int s = 52 - eU;
   if (s > 52) s = 52;
   i128 B = 0;
-  if (lin) {
+  if (lin && N == 2) {  // q = S exactly: B = S 2^s, or round(S / 2^-s) half up by a shift
+    B = s >= 0 ? S * ((i128)1 << s) : (2 * S + ((i128)1 << (-s))) >> (1 - s);
+  } else if (lin) {
     if (s >= 0)
       B = round_half_up_i128(sixS * ((i128)1 << s), D);
     else

@@ -469,12 +469,22 @@ __device__ __forceinline__ uint64_t place64(uint64_t z, uint64_t f, uint64_t wb)
 // POLY: the column may hold polynomial partitions (a separate instantiation keeps the constant and
 // linear packer as small as before)
 // zofs: the partition's first value within a stage holding several partitions (the 32-bit
-// residual buffer is indexed like the stage)
-template <bool POLY>
+// residual buffer is indexed like the stage). WARP: one warp packs the partition (the CTA's warps
+// take different partitions of one staged item, whose residual buffers and full output words are
+// disjoint), otherwise the whole CTA.
+template <bool POLY, bool WARP = false>
 __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned char* st, unsigned char* ring,
                                                const Record* __restrict__ rec, const Aux* __restrict__ aux,
                                                const PolyCoef* __restrict__ pcoef, const PolyAux* __restrict__ poly,
                                                uint64_t p, uint64_t* __restrict__ words, uint32_t zofs = 0) {
+  const uint32_t t = WARP ? (threadIdx.x & 31u) : threadIdx.x;
+  const uint32_t G = WARP ? 32u : blockDim.x;
+  auto gsync = [] {
+    if (WARP)
+      __syncwarp();
+    else
+      __syncthreads();
+  };
   const Aux a = aux[p];
   const uint32_t b = w3_b(a.word3);
   const bool pl = POLY && w3_poly(a.word3) != 0;
@@ -489,22 +499,22 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
                                        : const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(st));
     const int32_t sr = w3_s(a.word3);
     const uint32_t sh = sr > 0 ? (uint32_t)sr : 0u;
-    uint64_t F = (uint64_t)a.A + (uint64_t)a.B * threadIdx.x;
-    const uint64_t dF = (uint64_t)a.B * blockDim.x;
+    uint64_t F = (uint64_t)a.A + (uint64_t)a.B * t;
+    const uint64_t dF = (uint64_t)a.B * G;
     if (s.dtype == LECO_U32) {
       const uint32_t* v = reinterpret_cast<const uint32_t*>(st);
-      for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x, F += dF)
+      for (uint32_t x = t; x < s.N; x += G, F += dF)
         zs[x] = zz_encode((int64_t)((uint64_t)v[x] - (uint64_t)((int64_t)F >> sh)));
     } else {
       const uint64_t* v = reinterpret_cast<const uint64_t*>(st);
-      for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x, F += dF)
+      for (uint32_t x = t; x < s.N; x += G, F += dF)
         zs[x] = zz_encode((int64_t)(v[x] - (uint64_t)((int64_t)F >> sh)));
     }
-    __syncthreads();
+    gsync();
     const uint32_t lead = (uint32_t)(off & 63u);
     const int32_t nbits = (int32_t)(s.N * b);
     const uint64_t w0 = off >> 6, wl = (endb - 1) >> 6;
-    for (uint64_t w = w0 + threadIdx.x; w <= wl; w += blockDim.x) {
+    for (uint64_t w = w0 + t; w <= wl; w += G) {
       const int32_t r0 = (int32_t)((w - w0) << 6) - (int32_t)lead;  // the word's first bit, relative
       const int32_t r1 = r0 + 64 < nbits ? r0 + 64 : nbits;
       uint32_t x = r0 > 0 ? (uint32_t)r0 / b : 0u;
@@ -519,7 +529,7 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
       else
         atomicOr((unsigned long long*)&words[w], (unsigned long long)acc);
     }
-    __syncthreads();  // the stage buffer is refilled for the next partition
+    gsync();  // the stage buffer is refilled for the next partition
     return;
   }
   if (endb > off0) {
@@ -532,20 +542,20 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
         // the thread's predictions T + (F(x) >> S) for x = tid, tid + blockDim, ... by forward
         // differences of the cubic F over that stride, carried times 2^(64-S) modulo 2^128 so that
         // the prediction's low 64 bits are the carried value's high half
-        PolySteps Fd = poly_steps(poly[p], threadIdx.x, blockDim.x, 64u - ((uint32_t)w3_s(a.word3) & 63u));
+        PolySteps Fd = poly_steps(poly[p], t, G, 64u - ((uint32_t)w3_s(a.word3) & 63u));
         const uint64_t T = (uint64_t)a.A;
-        for (uint32_t xx = threadIdx.x; xx < s.N; xx += blockDim.x) {
+        for (uint32_t xx = t; xx < s.N; xx += G) {
           zs[xx] = zz_encode((int64_t)((uint64_t)staged_value(st, s.dtype, xx) - (T + (uint64_t)(Fd.F >> 64))));
           poly_step(Fd);
         }
       } else {
-        for (uint32_t x = threadIdx.x; x < s.N; x += blockDim.x)
+        for (uint32_t x = t; x < s.N; x += G)
           zs[x] = residual_at<POLY>(rec, poly, a, p, x, (uint64_t)staged_value(st, s.dtype, x));
       }
-      __syncthreads();
+      gsync();
     }
     // phase 2: output words of [off0, endb): the polynomial block's five words, then the fields
-    for (uint64_t w = (off0 >> 6) + threadIdx.x; w <= ((endb - 1) >> 6); w += blockDim.x) {
+    for (uint64_t w = (off0 >> 6) + t; w <= ((endb - 1) >> 6); w += G) {
       const uint64_t wb = w << 6;
       const uint64_t lo = wb > off0 ? wb : off0, hi = wb + 64 < endb ? wb + 64 : endb;
       uint64_t acc = 0;
@@ -569,7 +579,7 @@ __device__ __forceinline__ void pack_partition(const PartSrc& s, const unsigned 
         atomicOr((unsigned long long*)&words[w], (unsigned long long)acc);
     }
   }
-  __syncthreads();  // the stage buffer is refilled for the next partition
+  gsync();  // the stage buffer is refilled for the next partition
 }
 
 constexpr int kPackBlock = 128;
@@ -763,13 +773,24 @@ __global__ void __launch_bounds__(kPackBlock)
   auto body = [&](uint64_t it, const PartSrc& si, const unsigned char* st) {
     const uint64_t p0 = item_start[it], pe = item_start[it + 1];
     const uint32_t vb = dtype == LECO_U32 ? 4u : 8u;
-    for (uint64_t p = p0; p < pe; p++) {
+    auto part = [&](uint64_t p) {
       PartSrc s = si;
       s.a = aux[p].start;
       s.N = (uint32_t)((p + 1 < m ? aux[p + 1].start : n) - s.a);
-      const uint32_t zofs = (uint32_t)(s.a - si.a);
-      pack_partition<false>(s, st ? st + (size_t)zofs * vb : nullptr, ring, rec, aux, nullptr, nullptr, p, words, zofs);
+      return s;
+    };
+    if (pe - p0 == 1) {  // a long partition: the whole CTA
+      pack_partition<false>(part(p0), st, ring, rec, aux, nullptr, nullptr, p0, words, 0);
+      return;
     }
+    // short partitions: a warp each, the CTA's warps side by side
+    for (uint64_t p = p0 + (threadIdx.x >> 5); p < pe; p += kPackBlock / 32) {
+      const PartSrc s = part(p);
+      const uint32_t zofs = (uint32_t)(s.a - si.a);
+      pack_partition<false, true>(s, st ? st + (size_t)zofs * vb : nullptr, ring, rec, aux, nullptr, nullptr, p, words,
+                                  zofs);
+    }
+    __syncthreads();  // the stage buffer is refilled for the next item
   };
   for_each_staged<1>(nitems, pack_stage_cap(dtype), get, body, ring, full, err);
 }

@@ -183,6 +183,9 @@ __device__ __forceinline__ int64_t unzigzag32(uint32_t z) {
   return (int64_t)(int32_t)((z >> 1) ^ (0u - (z & 1u)));
 }
 
+// the same residual mod 2^32
+__device__ __forceinline__ uint32_t unzigzag_u32(uint32_t z) { return (z >> 1) ^ (0u - (z & 1u)); }
+
 struct Acc {
   uint64_t cnt = 0, lo = 0, hi = 0;
   __device__ __forceinline__ void add(uint64_t v) {
@@ -229,14 +232,15 @@ __device__ __forceinline__ uint64_t value_at(const ScanArgs& g, const uint32_t* 
   return (uint64_t)pred + (uint64_t)zz_decode(z);
 }
 
-// Tight loop over ng whole 32-value groups of one exact partition (the common case). Lane j
-// handles positions i0 + j + 32 k; its fixed-point prediction F and bit position step by 32 B and
-// 32 b. Filter runs are classified once by their model bounds: missed runs cost nothing, runs
-// certainly inside are summed without the compare.
+// Tight loop over ng whole 32-value groups of one exact partition (the common case), then a
+// partial group whose first `tail` lanes hold the partition's (or the warp range's) last values.
+// Lane j handles positions i0 + j + 32 k; its fixed-point prediction F and bit position step by
+// 32 B and 32 b. Filter runs are classified once by their model bounds: missed runs cost nothing,
+// runs certainly inside are summed without the compare.
 template <int MODE, bool WIDE>
 __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const uint32_t* words,
-                                           const Aux& a, uint64_t i0, uint32_t ng, uint64_t bit_base,
-                                           uint32_t lane, int cls) {
+                                           const Aux& a, uint64_t i0, uint32_t ng, uint32_t tail,
+                                           uint64_t bit_base, uint32_t lane, int cls) {
   const uint32_t b = w3_b(a.word3);
   int32_t sh = w3_s(a.word3);
   sh = (sh > 0 ? sh : 0) & 63;
@@ -257,21 +261,30 @@ __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const ui
       F += B32;
       bit += b32;
     }
+    if (lane < tail) {
+      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
+      *o = (uint64_t)(((int64_t)F >> sh) + r);
+    }
   } else if (MODE == kDecode32) {
     uint32_t* o = reinterpret_cast<uint32_t*>(g.out) + (i0 + lane - g.begin);
 #pragma unroll 4
     for (uint32_t k = 0; k < ng; k++) {
-      const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
-      *o = (uint32_t)(uint64_t)((int64_t)F >> sh) + (uint32_t)r;  // floor: arithmetic shift
+      const uint32_t r = WIDE ? (uint32_t)zz_decode(field64(words, bit, mask64)) : unzigzag_u32(field32(words, bit, mask32));
+      *o = (uint32_t)(uint64_t)((int64_t)F >> sh) + r;  // floor: arithmetic shift
       o += 32;
       F += B32;
       bit += b32;
     }
+    if (lane < tail) {
+      const uint32_t r = WIDE ? (uint32_t)zz_decode(field64(words, bit, mask64)) : unzigzag_u32(field32(words, bit, mask32));
+      *o = (uint32_t)(uint64_t)((int64_t)F >> sh) + r;
+    }
   } else {
     const uint64_t vmask = g.c.dtype == LECO_U32 ? 0xFFFFFFFFull : ~0ull;
     if (cls == 1) return;
+    const uint32_t steps = ng + (lane < tail ? 1u : 0u);
     if (cls == 2) {
-      for (uint32_t k = 0; k < ng; k++) {
+      for (uint32_t k = 0; k < steps; k++) {
         const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
         acc.add((uint64_t)(((int64_t)F >> sh) + r) & vmask);
         F += B32;
@@ -279,7 +292,7 @@ __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const ui
       }
       return;
     }
-    for (uint32_t k = 0; k < ng; k++) {
+    for (uint32_t k = 0; k < steps; k++) {
       const int64_t r = WIDE ? zz_decode(field64(words, bit, mask64)) : unzigzag32(field32(words, bit, mask32));
       const uint64_t v = (uint64_t)(((int64_t)F >> sh) + r) & vmask;
       if (v >= g.lo && v <= g.hi) acc.add(v);
@@ -376,17 +389,20 @@ __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, 
     const uint64_t run_end = min(qend, wend);
     const uint32_t ng = (uint32_t)((run_end - gp) >> 5);
     if (ng && w3_exact(a.word3)) {
+      // the whole run, its last partial group included: the next run starts at the partition's
+      // end, so no group straddles a partition edge
+      const uint32_t tail = (uint32_t)(run_end - gp) & 31u;
       int cls = (int)mt.cls;
       if (MODE == kFilter && cls == 0 && !(g.flags & LECO_FILTER_DECODE_ALL)) {
         uint64_t vlo = 0, vhi = 0;
-        const int kind = part_bounds(c.dtype, a, gp - a.start, gp + 32ull * ng - 1 - a.start, &vlo, &vhi);
+        const int kind = part_bounds(c.dtype, a, gp - a.start, run_end - 1 - a.start, &vlo, &vhi);
         cls = classify(kind, vlo, vhi, g.lo, g.hi);
       }
       if (w3_b(a.word3) > 32)
-        run_groups<MODE, true>(g, acc, words, a, gp, ng, mt.bit_base, lane, cls);
+        run_groups<MODE, true>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
       else
-        run_groups<MODE, false>(g, acc, words, a, gp, ng, mt.bit_base, lane, cls);
-      gp += 32ull * ng;
+        run_groups<MODE, false>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
+      gp = run_end;
     } else if (POLY && ng && w3_poly(a.word3)) {
       if (w3_b(a.word3) > 32)
         run_groups_poly<MODE, true>(g, acc, words, a, q, gp, ng, mt.bit_base, lane);

@@ -1,12 +1,12 @@
 // Variable-length partitioning on the GPU (§3.2.2): split, then merge.
 //
 // Split: the sequence is cut into chunks of kChunk values (chunk edges always start a partition);
-// inside a chunk one lane grows partitions left to right: v_j joins the open partition [i, j)
-// iff C = (j+1-i) D(v[i,j+1)) - (j-i) D(v[i,j)) <= tau * S_M and j - i < cap, where D is the
-// linear regressor's fast metric bitlen(max d - min d) over the inner differences d_k = w_k -
-// w_{k-1}. A warp sweeps 32 chunks at once, one per lane, and stages their values through shared
-// memory in coalesced segments ahead of the lanes' dependency chains. Starts go to a bitmap (each
-// lane owns its chunk's words), then a popcount scan compacts them.
+// inside a chunk partitions grow left to right: v_j joins the open partition [i, j) iff
+// C = (j+1-i) D(v[i,j+1)) - (j-i) D(v[i,j)) <= tau * S_M and j - i < cap, where D is the linear
+// regressor's fast metric bitlen(max d - min d) over the inner differences d_k = w_k - w_{k-1}. A
+// warp takes a chunk and tests 32 candidates per step (prefix scans of the extremes, a ballot for
+// the first refusal). Starts go to a bitmap (each warp owns its chunk's words), then a popcount
+// scan compacts them.
 //
 // Merge, round-synchronous: each round computes for every adjacent pair the size of the merged
 // partition with the full regressor (S_M + len * b) and its gain over the two apart; every pair
@@ -35,6 +35,7 @@ cudaError_t scan_u64(const uint64_t* in, uint64_t count, uint64_t* out, uint64_t
 namespace {
 
 constexpr uint64_t kChunk = 1ull << 16;
+constexpr uint8_t kChunkNarrow = 1, kChunkLanes = 2;  // chunk classes (k_chunk_class)
 constexpr uint64_t kNone = ~0ull;  // no merged size (pair longer than the cap)
 
 // One greedy step of the split at position j with value w (the previous value prev): returns true
@@ -95,25 +96,28 @@ __device__ __forceinline__ bool split_step_narrow(uint32_t jj, int64_t d, uint32
   return take;
 }
 
-// Left-to-right split of 32 chunks per warp (lane l sweeps chunk 32 w + l). Segment k of every
-// chunk (positions k kSplitSeg .. + kSplitSeg) is loaded by the whole warp with coalesced loads one
-// segment ahead, transposed through shared memory (row x holds position x of the 32 chunks, padded
-// against bank conflicts), and then swept by each lane from shared memory while the next
-// segment's loads are in flight. A segment is one bitmap word per chunk.
+// Left-to-right split of 32 chunks per warp (lane l sweeps chunk 32 w + l), for the chunks whose
+// class has kChunkLanes (dense cuts, or values beyond the narrow range); a warp without such a
+// chunk returns at once. Segment k of every chunk (positions k kSplitSeg .. + kSplitSeg) is loaded
+// by the whole warp with coalesced loads one segment ahead, transposed through shared memory (row x
+// holds position x of the 32 chunks, padded against bank conflicts), and then swept by each lane
+// from shared memory while the next segment's loads are in flight. A segment is one bitmap word per
+// chunk.
 constexpr uint32_t kSplitSeg = 64;
 
 template <typename T>
-__global__ void __launch_bounds__(32) k_split_staged(const T* __restrict__ v, uint64_t n, uint32_t cap, int64_t tfloor,
-                                                     const uint8_t* __restrict__ narrow, uint64_t* __restrict__ bitmap) {
+__global__ void __launch_bounds__(32) k_split_lanes(const T* __restrict__ v, uint64_t n, uint32_t cap, int64_t tfloor,
+                                                    const uint8_t* __restrict__ cls, uint64_t* __restrict__ bitmap) {
   __shared__ T ring[2][kSplitSeg][33];
   const uint32_t lane = threadIdx.x;
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   const uint64_t c0 = (uint64_t)blockIdx.x * 32;
   const uint64_t c = c0 + lane;
-  const bool has = c < nchunks;
+  const bool has = c < nchunks && (cls[c] & kChunkLanes);
+  if (!__any_sync(0xffffffffu, has)) return;
   const uint64_t a = c * kChunk;
   const uint32_t clen = has ? (uint32_t)(min(a + kChunk, n) - a) : 0u;  // the chunk's values
-  const bool nar = has ? narrow[c] != 0 : true;
+  const bool nar = has ? (cls[c] & kChunkNarrow) != 0 : true;
   const int32_t tf32 = tfloor > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)tfloor;
   constexpr uint32_t nseg = (uint32_t)(kChunk / kSplitSeg);
   T r[kSplitSeg];
@@ -169,6 +173,115 @@ __global__ void __launch_bounds__(32) k_split_staged(const T* __restrict__ v, ui
       __syncwarp();
     }
   }
+}
+
+// Warp-cooperative split, a warp per chunk, with the result of split_step's left-to-right sweep. From
+// the open partition [i, j0) the warp tests the 32 candidates j = j0 .. j0 + 31 at once, lane l
+// assuming that every candidate before it joined: the running extremes of the differences are the
+// carried ones combined with an inclusive max / min scan over the lanes, the fast metric of [i, j)
+// is the previous lane's metric of [i, j + 1) (the carried one for lane 0), and C follows as in
+// split_step, in 32 bits: a chunk's partition is at most 2^16 long and the metric at most 64, so
+// |C| < 2^23, and tf32 = min(floor(tau S_M), 2^31 - 1) decides C <= tau S_M exactly. The first
+// refused candidate (a ballot) opens the next partition and the warp
+// restarts after it; when none is refused the last lane's state carries over 32 positions on. A
+// partition of length len costs about len / 32 + 1 steps instead of len dependent steps, which pays
+// where partitions are long: the chunks whose class lacks kChunkLanes (narrow, few cuts). The warp
+// stages its chunk through a two-block shared-memory ring, one block of loads ahead.
+constexpr uint32_t kSplitWarps = 4;
+constexpr uint32_t kSplitBlk = 256;  // values per staged block (8 per lane)
+
+// bitmap must be zero on entry: a warp stores only its chunk's words that hold a start
+template <typename T>
+__global__ void __launch_bounds__(32 * kSplitWarps)
+    k_split_warp(const T* __restrict__ v, uint64_t n, uint32_t cap, int64_t tfloor, const uint8_t* __restrict__ cls,
+                 uint64_t* __restrict__ bitmap) {
+  constexpr uint32_t kRing = 2 * kSplitBlk, kMask = kRing - 1;
+  __shared__ T ring[kSplitWarps][kRing];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  const uint64_t c = (uint64_t)blockIdx.x * kSplitWarps + wid;
+  if (c >= nchunks || (cls[c] & kChunkLanes)) return;  // the whole warp: no block-wide barrier follows
+  const uint64_t a = c * kChunk;
+  const uint32_t clen = (uint32_t)(min(a + kChunk, n) - a);
+  uint64_t* bm = bitmap + (a >> 6);
+  T* rg = ring[wid];
+  const int32_t tf32 = tfloor > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)tfloor;
+  T pre[kSplitBlk / 32];
+  auto fetch = [&](uint32_t base) {
+#pragma unroll
+    for (uint32_t u = 0; u < kSplitBlk / 32; u++) {
+      const uint32_t x = base + u * 32 + lane;
+      pre[u] = x < clen ? __ldg(v + a + x) : (T)0;
+    }
+  };
+  auto commit = [&](uint32_t base) {
+#pragma unroll
+    for (uint32_t u = 0; u < kSplitBlk / 32; u++) rg[(base + u * 32 + lane) & kMask] = pre[u];
+  };
+  fetch(0);
+  commit(0);
+  uint32_t filled = kSplitBlk;  // ring holds positions [filled - kRing, filled)
+  fetch(filled);
+  __syncwarp();
+  uint32_t i = 0, j0 = 1;                          // open partition [i, j0), next candidate j0
+  int64_t cmax = INT64_MIN, cmin = INT64_MAX;      // extremes of its differences (none yet)
+  int ccur = 0;                                    // fast metric of [i, j0)
+  uint32_t wi = 0;
+  uint64_t word = 1;                               // bitmap word wi (the chunk start opens a partition)
+  while (j0 < clen) {
+    while (j0 + 32 > filled && filled < clen) {
+      // the slot written held [filled - kRing, filled - kSplitBlk), all below j0 - 1
+      __syncwarp();
+      commit(filled);
+      filled += kSplitBlk;
+      fetch(filled);
+      __syncwarp();
+    }
+    const uint32_t j = j0 + lane;
+    const bool valid = j < clen;
+    const int64_t d = valid ? (int64_t)rg[j & kMask] - (int64_t)rg[(j - 1) & kMask] : 0;
+    auto cut = [&](uint32_t at) {  // position `at` opens a partition (warp-uniform)
+      if ((at >> 6) != wi) {
+        if (lane == 0) bm[wi] = word;
+        wi = at >> 6;
+        word = 0;
+      }
+      word |= 1ull << (at & 63u);
+      cmax = INT64_MIN;
+      cmin = INT64_MAX;
+      ccur = 0;
+      i = at;
+    };
+    int64_t pmax = d, pmin = d;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const int64_t tmax = __shfl_up_sync(0xffffffffu, pmax, o);
+      const int64_t tmin = __shfl_up_sync(0xffffffffu, pmin, o);
+      if (lane >= o) {
+        pmax = tmax > pmax ? tmax : pmax;
+        pmin = tmin < pmin ? tmin : pmin;
+      }
+    }
+    const int64_t nmax = cmax > pmax ? cmax : pmax, nmin = cmin < pmin ? cmin : pmin;
+    const int next = bitlen_u64((uint64_t)nmax - (uint64_t)nmin);
+    int cur = __shfl_up_sync(0xffffffffu, next, 1);
+    if (lane == 0) cur = ccur;
+    const uint32_t len = j - i;
+    const int32_t C = (int32_t)(len + 1) * next - (int32_t)len * cur;
+    const uint32_t rej = __ballot_sync(0xffffffffu, valid && !(len < cap && C <= tf32));
+    if (rej == 0) {
+      const uint32_t last = clen - 1 - j0 < 31u ? clen - 1 - j0 : 31u;
+      cmax = __shfl_sync(0xffffffffu, nmax, last);
+      cmin = __shfl_sync(0xffffffffu, nmin, last);
+      ccur = __shfl_sync(0xffffffffu, next, last);
+      j0 += 32;
+    } else {
+      const uint32_t at = j0 + (uint32_t)(__ffs(rej) - 1);
+      cut(at);
+      j0 = at + 1;
+    }
+  }
+  if (lane == 0) bm[wi] = word;
 }
 
 // Seeded split (§3.2.2, selecting good starting positions): the greedy sweep over the count values
@@ -265,21 +378,37 @@ __global__ void __launch_bounds__(256) k_chunk_seed(const T* __restrict__ v, uin
   }
 }
 
-// narrow[c] = every value of chunk c lies in (-2^62, 2^62) as int64 (a CTA per chunk)
+// cls[c] for chunk c (a CTA per chunk): kChunkNarrow when every value lies in (-2^62, 2^62) as
+// int64; kChunkLanes when the chunk goes to the one-lane-per-chunk sweep: values beyond that range,
+// or cuts expected densely. A two-value partition [i, i + 2) refuses v_{i+2} exactly when
+// 3 bitlen(|second difference|) > floor(tau S_M) (C = 3 D - 2 * 0), so the share of positions with
+// such a second difference estimates how many partitions stay that short; above 1 in 12 the
+// per-lane sweep (about one dependent step per position) beats the warp's (one step per partition).
 template <typename T>
-__global__ void k_chunk_narrow(const T* __restrict__ v, uint64_t n, uint8_t* __restrict__ narrow) {
+__global__ void k_chunk_class(const T* __restrict__ v, uint64_t n, int64_t tfloor, uint8_t* __restrict__ cls) {
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   const int64_t lim = (int64_t)1 << 62;
   for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const uint64_t a = c * kChunk, e = min(a + kChunk, n);
+    __shared__ unsigned int tot;
+    if (threadIdx.x == 0) tot = 0;
     int bad = 0;
-    if (sizeof(T) == 8)
-      for (uint64_t j = a + threadIdx.x; j < e; j += blockDim.x) {
-        const int64_t w = (int64_t)__ldg(v + j);
-        bad |= (w <= -lim || w >= lim) ? 1 : 0;
+    unsigned int sharp = 0;
+    for (uint64_t j = a + threadIdx.x; j < e; j += blockDim.x) {
+      const int64_t w = (int64_t)__ldg(v + j);
+      if (sizeof(T) == 8) bad |= (w <= -lim || w >= lim) ? 1 : 0;
+      if (j > a && j + 1 < e) {  // wrapping arithmetic: an estimate only
+        const uint64_t d2 = (uint64_t)(int64_t)__ldg(v + j + 1) - 2 * (uint64_t)w + (uint64_t)(int64_t)__ldg(v + j - 1);
+        const uint64_t mag = (int64_t)d2 < 0 ? 0 - d2 : d2;
+        sharp += 3 * (int64_t)bitlen_u64(mag) > tfloor ? 1u : 0u;
       }
+    }
     bad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) narrow[c] = bad ? 0 : 1;
+    if (sharp) atomicAdd(&tot, sharp);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      cls[c] = (uint8_t)((bad ? 0 : kChunkNarrow) | ((bad || 12ull * tot > e - a) ? kChunkLanes : 0));
+    __syncthreads();  // tot is reset for the next chunk
   }
 }
 
@@ -301,14 +430,14 @@ __device__ __forceinline__ void split_chunk_seeded(const T* __restrict__ v, uint
 // the seeded split: chunk c's partitions grow from seeds[c] (k_chunk_seed) both ways; a thread per chunk
 template <typename T>
 __global__ void k_split_seeded(const T* __restrict__ values, uint64_t n, uint32_t cap, int64_t tfloor,
-                               const uint8_t* __restrict__ narrow, const uint64_t* __restrict__ seeds,
+                               const uint8_t* __restrict__ cls, const uint64_t* __restrict__ seeds,
                                uint64_t* __restrict__ bitmap) {
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
        c += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t a = c * kChunk;
     const uint64_t e = min(a + kChunk, n);
-    if (narrow[c])
+    if (cls[c] & kChunkNarrow)
       split_chunk_seeded<true>(values, a, e, seeds[c], cap, tfloor, bitmap);
     else
       split_chunk_seeded<false>(values, a, e, seeds[c], cap, tfloor, bitmap);
@@ -815,29 +944,37 @@ cudaError_t var_partition_fit(const void* values, int dtype, uint64_t n, double 
     if (e == cudaSuccess) e = dalloc(&scan_scratch, scan_elems + 1, st);
     if (e == cudaSuccess) e = dalloc(&d_total, 1, st);
     if (e == cudaSuccess && seeded) e = dalloc(&seeds, nchunks, st);
-    uint8_t* narrow = reinterpret_cast<uint8_t*>(cnt);  // scratch: cnt is not used until the popcount
+    uint8_t* cls = reinterpret_cast<uint8_t*>(cnt);  // chunk classes; cnt is not used until the popcount
     if (e == cudaSuccess) {
-      const int wgrid = (int)((nchunks + 31) / 32);
+      const int wgrid = (int)((nchunks + kSplitWarps - 1) / kSplitWarps);
       if (u32) {
         const uint32_t* v = static_cast<const uint32_t*>(values);
-        k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, narrow);
+        k_chunk_class<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, tfloor, cls);
         if (seeded) {
           k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, seeds);
-          k_split_seeded<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(v, n, cap, tfloor, narrow, seeds, bitmap);
+          k_split_seeded<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(v, n, cap, tfloor, cls, seeds, bitmap);
         } else {
-          k_split_staged<<<wgrid, 32, 0, st>>>(v, n, cap, tfloor, narrow, bitmap);
+          e = cudaMemsetAsync(bitmap, 0, 8 * nw, st);
+          if (e == cudaSuccess) {
+            k_split_lanes<<<(int)((nchunks + 31) / 32), 32, 0, st>>>(v, n, cap, tfloor, cls, bitmap);
+            k_split_warp<<<wgrid, 32 * kSplitWarps, 0, st>>>(v, n, cap, tfloor, cls, bitmap);
+          }
         }
       } else {
         const uint64_t* v = static_cast<const uint64_t*>(values);
-        k_chunk_narrow<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, narrow);
+        k_chunk_class<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, tfloor, cls);
         if (seeded) {
           k_chunk_seed<<<grid_for(nchunks, 1, 8), 256, 0, st>>>(v, n, seeds);
-          k_split_seeded<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(v, n, cap, tfloor, narrow, seeds, bitmap);
+          k_split_seeded<<<grid_for(nchunks, 32, 32), 32, 0, st>>>(v, n, cap, tfloor, cls, seeds, bitmap);
         } else {
-          k_split_staged<<<wgrid, 32, 0, st>>>(v, n, cap, tfloor, narrow, bitmap);
+          e = cudaMemsetAsync(bitmap, 0, 8 * nw, st);
+          if (e == cudaSuccess) {
+            k_split_lanes<<<(int)((nchunks + 31) / 32), 32, 0, st>>>(v, n, cap, tfloor, cls, bitmap);
+            k_split_warp<<<wgrid, 32 * kSplitWarps, 0, st>>>(v, n, cap, tfloor, cls, bitmap);
+          }
         }
       }
-      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
       k_popc<<<grid_for(nw, 256, 8), 256, 0, st>>>(bitmap, nw, cnt);
