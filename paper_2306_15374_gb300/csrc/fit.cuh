@@ -211,7 +211,7 @@ __device__ __forceinline__ void fit_pass1(const T* __restrict__ v, uint32_t N, b
       const uint32_t xe = N - x0 > 64u * GROUP ? x0 + 64u * GROUP : N;
       int64_t acc_hi = 0, acc_lo = 0;
       int32_t u = (int32_t)(2 * (int64_t)x0 - nm1);
-#pragma unroll 4
+#pragma unroll 8
       for (uint32_t x = x0; x < xe; x += GROUP, u += 2 * GROUP) {
         const int64_t w = (int64_t)__ldg(v + x);
         mx = max(mx, w);
@@ -222,7 +222,7 @@ __device__ __forceinline__ void fit_pass1(const T* __restrict__ v, uint32_t N, b
       S += (i128)acc_hi * ((i128)1 << 32) + (i128)acc_lo;
     }
   } else {
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t x = rank; x < N; x += GROUP) {
       const int64_t w = (int64_t)__ldg(v + x);
       mx = max(mx, w);
@@ -243,7 +243,7 @@ __device__ __forceinline__ void fit_pass2(const T* __restrict__ v, uint32_t N, i
   uint64_t F = (uint64_t)B * rank;
   const uint64_t dF = (uint64_t)B * GROUP;
   if (s >= 0) {
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t x = rank; x < N; x += GROUP, F += dF) {
       const int64_t r = (int64_t)__ldg(v + x) - ((int64_t)F >> s);
       lo = min(lo, r);

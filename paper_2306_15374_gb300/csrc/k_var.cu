@@ -36,6 +36,8 @@ namespace {
 
 constexpr uint64_t kChunk = 1ull << 16;
 constexpr uint8_t kChunkNarrow = 1, kChunkLanes = 2;  // chunk classes (k_chunk_class)
+constexpr uint32_t kClassSample = 8192;               // positions per chunk that estimate its cut density,
+constexpr uint32_t kClassWindows = 8;                 // in this many windows spread over the chunk
 constexpr uint64_t kNone = ~0ull;  // no merged size (pair longer than the cap)
 
 // One greedy step of the split at position j with value w (the previous value prev): returns true
@@ -252,14 +254,47 @@ __global__ void __launch_bounds__(32 * kSplitWarps)
       ccur = 0;
       i = at;
     };
+    // Whole window at once: when its differences leave the metric D of [i, j0) unchanged (D only
+    // grows with the range), every candidate's C is (len + 1) D - len D = D, so the window joins
+    // when D <= floor(tau S_M) and the cap allows. Differences that fit 32 bits use warp reductions
+    // (and 32-bit scans below).
+    const bool small = __all_sync(0xffffffffu, d >= INT32_MIN && d <= INT32_MAX);
+    if (small) {
+      const int32_t wmax = __reduce_max_sync(0xffffffffu, valid ? (int32_t)d : INT32_MIN);
+      const int32_t wmin = __reduce_min_sync(0xffffffffu, valid ? (int32_t)d : INT32_MAX);
+      const int64_t amax = cmax > (int64_t)wmax ? cmax : (int64_t)wmax;
+      const int64_t amin = cmin < (int64_t)wmin ? cmin : (int64_t)wmin;
+      const uint32_t jl = (clen - j0 < 32u ? clen : j0 + 32) - 1;  // the window's last candidate
+      if (bitlen_u64((uint64_t)amax - (uint64_t)amin) == ccur && ccur <= tf32 && jl - i < cap) {
+        cmax = amax;
+        cmin = amin;
+        j0 = jl + 1;
+        continue;
+      }
+    }
     int64_t pmax = d, pmin = d;
+    if (small) {
+      int32_t a = (int32_t)d, b = (int32_t)d;
 #pragma unroll
-    for (uint32_t o = 1; o < 32; o <<= 1) {
-      const int64_t tmax = __shfl_up_sync(0xffffffffu, pmax, o);
-      const int64_t tmin = __shfl_up_sync(0xffffffffu, pmin, o);
-      if (lane >= o) {
-        pmax = tmax > pmax ? tmax : pmax;
-        pmin = tmin < pmin ? tmin : pmin;
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const int32_t ta = __shfl_up_sync(0xffffffffu, a, o);
+        const int32_t tb = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) {
+          a = ta > a ? ta : a;
+          b = tb < b ? tb : b;
+        }
+      }
+      pmax = a;
+      pmin = b;
+    } else {
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const int64_t tmax = __shfl_up_sync(0xffffffffu, pmax, o);
+        const int64_t tmin = __shfl_up_sync(0xffffffffu, pmin, o);
+        if (lane >= o) {
+          pmax = tmax > pmax ? tmax : pmax;
+          pmin = tmin < pmin ? tmin : pmin;
+        }
       }
     }
     const int64_t nmax = cmax > pmax ? cmax : pmax, nmin = cmin < pmin ? cmin : pmin;
@@ -382,33 +417,52 @@ __global__ void __launch_bounds__(256) k_chunk_seed(const T* __restrict__ v, uin
 // int64; kChunkLanes when the chunk goes to the one-lane-per-chunk sweep: values beyond that range,
 // or cuts expected densely. A two-value partition [i, i + 2) refuses v_{i+2} exactly when
 // 3 bitlen(|second difference|) > floor(tau S_M) (C = 3 D - 2 * 0), so the share of positions with
-// such a second difference estimates how many partitions stay that short; above 1 in 12 the
-// per-lane sweep (about one dependent step per position) beats the warp's (one step per partition).
+// such a second difference estimates how many partitions stay that short; above 1 in 12 in any of
+// the sampled windows (the chunk's slowest part sets its sweep time) the per-lane sweep (about one
+// dependent step per position) beats the warp's (one step per partition). The class changes only
+// the speed.
 template <typename T>
 __global__ void k_chunk_class(const T* __restrict__ v, uint64_t n, int64_t tfloor, uint8_t* __restrict__ cls) {
+  constexpr uint32_t kWin = kClassSample / kClassWindows;  // positions per sampled window
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   const int64_t lim = (int64_t)1 << 62;
+  __shared__ unsigned int sharp[kClassWindows];
   for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const uint64_t a = c * kChunk, e = min(a + kChunk, n);
-    __shared__ unsigned int tot;
-    if (threadIdx.x == 0) tot = 0;
+    if (threadIdx.x < kClassWindows) sharp[threadIdx.x] = 0;
+    __syncthreads();
     int bad = 0;
-    unsigned int sharp = 0;
-    for (uint64_t j = a + threadIdx.x; j < e; j += blockDim.x) {
-      const int64_t w = (int64_t)__ldg(v + j);
-      if (sizeof(T) == 8) bad |= (w <= -lim || w >= lim) ? 1 : 0;
-      if (j > a && j + 1 < e) {  // wrapping arithmetic: an estimate only
-        const uint64_t d2 = (uint64_t)(int64_t)__ldg(v + j + 1) - 2 * (uint64_t)w + (uint64_t)(int64_t)__ldg(v + j - 1);
-        const uint64_t mag = (int64_t)d2 < 0 ? 0 - d2 : d2;
-        sharp += 3 * (int64_t)bitlen_u64(mag) > tfloor ? 1u : 0u;
+    if (sizeof(T) == 8)
+      for (uint64_t j = a + threadIdx.x; j < e; j += blockDim.x) {
+        const int64_t w = (int64_t)__ldg(v + j);
+        bad |= (w <= -lim || w >= lim) ? 1 : 0;
       }
+    // kClassWindows windows of kWin positions spread evenly over the chunk (a warp's 32 positions
+    // fall in one window); wrapping arithmetic: an estimate only
+    for (uint32_t k = threadIdx.x; k < kClassSample; k += blockDim.x) {
+      const uint32_t s = k / kWin;
+      const uint64_t j = a + (uint64_t)s * (kChunk / kClassWindows) + (k % kWin);
+      bool sh = false;
+      if (j > a && j + 1 < e) {
+        const uint64_t d2 = (uint64_t)(int64_t)__ldg(v + j + 1) - 2 * (uint64_t)(int64_t)__ldg(v + j) +
+                            (uint64_t)(int64_t)__ldg(v + j - 1);
+        const uint64_t mag = (int64_t)d2 < 0 ? 0 - d2 : d2;
+        sh = 3 * (int64_t)bitlen_u64(mag) > tfloor;
+      }
+      const unsigned int cnt = __popc(__ballot_sync(0xffffffffu, sh));
+      if ((threadIdx.x & 31u) == 0 && cnt) atomicAdd(&sharp[s], cnt);
     }
     bad = __syncthreads_or(bad);
-    if (sharp) atomicAdd(&tot, sharp);
-    __syncthreads();
-    if (threadIdx.x == 0)
-      cls[c] = (uint8_t)((bad ? 0 : kChunkNarrow) | ((bad || 12ull * tot > e - a) ? kChunkLanes : 0));
-    __syncthreads();  // tot is reset for the next chunk
+    if (threadIdx.x == 0) {
+      bool lanes = bad != 0;
+      for (uint32_t s = 0; s < kClassWindows; s++) {
+        const uint64_t w0 = a + (uint64_t)s * (kChunk / kClassWindows);
+        const uint64_t wl = w0 < e ? min((uint64_t)kWin, e - w0) : 0;
+        lanes = lanes || 12ull * sharp[s] > wl;
+      }
+      cls[c] = (uint8_t)((bad ? 0 : kChunkNarrow) | (lanes ? kChunkLanes : 0));
+    }
+    __syncthreads();  // sharp is reset for the next chunk
   }
 }
 
