@@ -106,7 +106,8 @@ struct FitResult {
 // step 1-3 (one thread): parameters from the reduced moments
 __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bool lin) {
   FitParams P;
-  const i128 D = lin ? (i128)N * ((i128)N * (i128)N - 1) : (i128)1;
+  // N (N^2 - 1) as a 64 x 64 -> 128-bit product (N^2 fits 64 bits)
+  const i128 D = lin ? (i128)((u128)(uint64_t)N * ((uint64_t)N * N - 1)) : (i128)1;
   const i128 sixS = lin ? 6 * S : (i128)0;
   const i128 a6 = sixS < 0 ? -sixS : sixS;
   // ceil(|6S| / D); without a division for the constant model (0) and for two values (D = 6: |S|)
@@ -114,10 +115,12 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   const i128 amx = mx < 0 ? -(i128)mx : (i128)mx;
   const i128 amn = mn < 0 ? -(i128)mn : (i128)mn;
   const i128 M = amx > amn ? amx : amn;
-  const i128 U = M + ((i128)mx - (i128)mn) + (Q + 1) * (i128)N + 4;
-  const int eU = bitlen_u128((u128)U);
+  // (Q + 1) N as a 64 x 64 -> 128-bit product; Q >= 2^62 already puts U above 2^62 (the fallback)
+  const bool huge = (Q >> 62) != 0;
+  const i128 U = M + ((i128)mx - (i128)mn) + (huge ? (i128)0 : (i128)((u128)(uint64_t)(Q + 1) * N)) + 4;
+  const int eU = huge ? 127 : bitlen_u128((u128)U);
   if (eU > 62) {
-    const i128 t = (i128)mn + (((i128)mx - (i128)mn + 1) / 2);
+    const i128 t = (i128)mn + (((i128)mx - (i128)mn + 1) >> 1);  // >= 1: the shift is the halving
     const i128 tg = t >> 11;  // floor(t / 2^11)
     P.fallback = 1;
     P.s = -11;
@@ -147,7 +150,7 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
 __device__ __forceinline__ uint32_t finish_width(const FitParams& P, int64_t lo, int64_t hi, uint64_t fb_maxzz) {
   if (P.fallback) return (uint32_t)bitlen_u64(fb_maxzz);
   const int s = P.s;
-  const i128 t = (i128)lo + (((i128)hi - (i128)lo + 1) / 2);
+  const i128 t = (i128)lo + (((i128)hi - (i128)lo + 1) >> 1);
   const i128 shift = s >= 0 ? t : (t >> (-s)) * ((i128)1 << (-s));
   const int64_t lo2 = (int64_t)((i128)lo - shift), hi2 = (int64_t)((i128)hi - shift);
   return (uint32_t)bitlen_u64(max(zz_encode(lo2), zz_encode(hi2)));
@@ -164,7 +167,7 @@ __device__ FitResult finish_fit(const FitParams& P, int64_t lo, int64_t hi, uint
     return R;
   }
   const int s = P.s;
-  const i128 t = (i128)lo + (((i128)hi - (i128)lo + 1) / 2);
+  const i128 t = (i128)lo + (((i128)hi - (i128)lo + 1) >> 1);
   i128 shift, A;
   if (s >= 0) {
     shift = t;
@@ -672,7 +675,7 @@ __device__ FitChoice poly_choose(const PolyMom& M, const PolyPlan& P, const Poly
   }
   for (int d = 0; d < 2; d++) {
     if (!P.G[d].valid || R.bad[d]) continue;
-    const i128 t = (i128)R.plo[d] + (((i128)R.phi[d] - (i128)R.plo[d] + 1) / 2);
+    const i128 t = (i128)R.plo[d] + (((i128)R.phi[d] - (i128)R.plo[d] + 1) >> 1);
     const uint64_t z = max(zz_encode((int64_t)((i128)R.plo[d] - t)), zz_encode((int64_t)((i128)R.phi[d] - t)));
     const uint32_t b = (uint32_t)bitlen_u64(z);
     const uint64_t size = kSmBits + kPolyBlockBits + (uint64_t)N * b;

@@ -363,7 +363,11 @@ __device__ __forceinline__ void run_groups_poly(const ScanArgs& g, Acc& acc, con
   }
 }
 
-template <int MODE, bool POLY>
+// TAIL: an exact run goes to its end, its last group partial, and the next run starts at the
+// partition's edge (columns whose partition edges fall anywhere); otherwise a run stops at its last
+// whole group and a group across an edge is decoded position by position (fixed partitions of a
+// multiple of 32 values, whose edges meet the warp ranges' 32-value grid).
+template <int MODE, bool POLY, bool TAIL>
 __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, const uint32_t* words,
                              const Aux* saux, Acc& acc, uint32_t per_warp) {
   const ColumnView& c = g.c;
@@ -389,20 +393,19 @@ __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, 
     const uint64_t run_end = min(qend, wend);
     const uint32_t ng = (uint32_t)((run_end - gp) >> 5);
     if (ng && w3_exact(a.word3)) {
-      // the whole run, its last partial group included: the next run starts at the partition's
-      // end, so no group straddles a partition edge
-      const uint32_t tail = (uint32_t)(run_end - gp) & 31u;
+      const uint32_t tail = TAIL ? (uint32_t)(run_end - gp) & 31u : 0u;
+      const uint64_t last_x = (TAIL ? run_end : gp + 32ull * ng) - 1 - a.start;
       int cls = (int)mt.cls;
       if (MODE == kFilter && cls == 0 && !(g.flags & LECO_FILTER_DECODE_ALL)) {
         uint64_t vlo = 0, vhi = 0;
-        const int kind = part_bounds(c.dtype, a, gp - a.start, run_end - 1 - a.start, &vlo, &vhi);
+        const int kind = part_bounds(c.dtype, a, gp - a.start, last_x, &vlo, &vhi);
         cls = classify(kind, vlo, vhi, g.lo, g.hi);
       }
       if (w3_b(a.word3) > 32)
         run_groups<MODE, true>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
       else
         run_groups<MODE, false>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
-      gp = run_end;
+      gp = TAIL ? run_end : gp + 32ull * ng;
     } else if (POLY && ng && w3_poly(a.word3)) {
       if (w3_b(a.word3) > 32)
         run_groups_poly<MODE, true>(g, acc, words, a, q, gp, ng, mt.bit_base, lane);
@@ -446,7 +449,7 @@ __device__ __forceinline__ TileMeta meta_from(const TileDesc& d, int mode, const
 // POLY: the column (or a column of the batch) may hold polynomial partitions, decoded by their own
 // loop (a separate instantiation, so that constant and linear columns keep the smaller register
 // budget).
-template <int MODE, int CW, bool MULTI, bool POLY>
+template <int MODE, int CW, bool MULTI, bool POLY, bool TAIL>
 __global__ void __launch_bounds__((CW + 1) * 32)
     k_tilescan(const ScanArgs g0, const ColumnView* __restrict__ cols, const BatchItem* __restrict__ items,
                uint64_t nitems, uint32_t nst, uint32_t stage_bytes) {
@@ -569,11 +572,11 @@ __global__ void __launch_bounds__((CW + 1) * 32)
         const Aux* saux = reinterpret_cast<const Aux*>(base + stage_bytes);
         if (MODE == kDecodeAny) {
           if (g.c.dtype == LECO_U32)
-            process_tile<kDecode32, POLY>(g, tile, mt, words, saux, acc, per_warp);
+            process_tile<kDecode32, POLY, TAIL>(g, tile, mt, words, saux, acc, per_warp);
           else
-            process_tile<kDecode64, POLY>(g, tile, mt, words, saux, acc, per_warp);
+            process_tile<kDecode64, POLY, TAIL>(g, tile, mt, words, saux, acc, per_warp);
         } else {
-          process_tile<MODE, POLY>(g, tile, mt, words, saux, acc, per_warp);
+          process_tile<MODE, POLY, TAIL>(g, tile, mt, words, saux, acc, per_warp);
         }
       }
       __syncwarp();
@@ -803,12 +806,12 @@ __global__ void k_tile_desc_multi(const ColumnView* __restrict__ views, const ui
   }
 }
 
-template <int MODE, int CW, bool MULTI, bool POLY>
+template <int MODE, int CW, bool MULTI, bool POLY, bool TAIL>
 cudaError_t launch_scan_cfg(const ScanArgs& g, const ColumnView* cols, const BatchItem* items,
                             uint64_t nitems, uint32_t stage_bytes, ScanConfig cfg, cudaStream_t st) {
   const uint32_t nst = cfg.stages < 2 ? 2u : (cfg.stages > (uint32_t)kMaxStages ? (uint32_t)kMaxStages : cfg.stages);
   const uint32_t smem = kCtrlBytes + nst * (stage_bytes + kAuxBytes);
-  auto kern = k_tilescan<MODE, CW, MULTI, POLY>;
+  auto kern = k_tilescan<MODE, CW, MULTI, POLY, TAIL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
@@ -824,17 +827,24 @@ cudaError_t launch_scan_cfg(const ScanArgs& g, const ColumnView* cols, const Bat
 
 // poly: the column (a single-column scan: it has a polynomial table) or some column of the batch
 // may hold polynomial partitions
+// (a multi-column scan, and a column with polynomial partitions, always end runs at partition edges)
 template <int MODE, bool MULTI>
 cudaError_t launch_scan(const ScanArgs& g, const ColumnView* cols, const BatchItem* items, uint64_t nitems,
                         uint32_t stage_bytes, ScanConfig cfg, bool poly, cudaStream_t st) {
   if (poly) {
     if (cfg.consumer_warps == 4)
-      return launch_scan_cfg<MODE, 4, MULTI, true>(g, cols, items, nitems, stage_bytes, cfg, st);
-    return launch_scan_cfg<MODE, 8, MULTI, true>(g, cols, items, nitems, stage_bytes, cfg, st);
+      return launch_scan_cfg<MODE, 4, MULTI, true, true>(g, cols, items, nitems, stage_bytes, cfg, st);
+    return launch_scan_cfg<MODE, 8, MULTI, true, true>(g, cols, items, nitems, stage_bytes, cfg, st);
+  }
+  const bool grid32 = !MULTI && !g.c.starts && g.c.L % 32 == 0;  // every partition edge on the 32-value grid
+  if (grid32) {
+    if (cfg.consumer_warps == 4)
+      return launch_scan_cfg<MODE, 4, MULTI, false, false>(g, cols, items, nitems, stage_bytes, cfg, st);
+    return launch_scan_cfg<MODE, 8, MULTI, false, false>(g, cols, items, nitems, stage_bytes, cfg, st);
   }
   if (cfg.consumer_warps == 4)
-    return launch_scan_cfg<MODE, 4, MULTI, false>(g, cols, items, nitems, stage_bytes, cfg, st);
-  return launch_scan_cfg<MODE, 8, MULTI, false>(g, cols, items, nitems, stage_bytes, cfg, st);
+    return launch_scan_cfg<MODE, 4, MULTI, false, true>(g, cols, items, nitems, stage_bytes, cfg, st);
+  return launch_scan_cfg<MODE, 8, MULTI, false, true>(g, cols, items, nitems, stage_bytes, cfg, st);
 }
 
 // One CTA waits on an mbarrier that nothing arrives at: the bounded wait must give up after limit_ns
