@@ -108,7 +108,7 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   FitParams P;
   // N (N^2 - 1) as a 64 x 64 -> 128-bit product (N^2 fits 64 bits)
   const i128 D = lin ? (i128)((u128)(uint64_t)N * ((uint64_t)N * N - 1)) : (i128)1;
-  const i128 sixS = lin ? 6 * S : (i128)0;
+  const i128 sixS = lin ? mul_i128_u64(S, 6) : (i128)0;
   const i128 a6 = sixS < 0 ? -sixS : sixS;
   // ceil(|6S| / D); without a division for the constant model (0) and for two values (D = 6: |S|)
   const i128 Q = !lin ? (i128)0 : (N == 2 ? (S < 0 ? -S : S) : floordiv_i128(a6 + D - 1, D));
@@ -132,12 +132,12 @@ __device__ FitParams solve_params(i128 S, int64_t mx, int64_t mn, uint32_t N, bo
   if (s > 52) s = 52;
   i128 B = 0;
   if (lin && N == 2) {  // q = S exactly: B = S 2^s, or round(S / 2^-s) half up by a shift
-    B = s >= 0 ? S * ((i128)1 << s) : (2 * S + ((i128)1 << (-s))) >> (1 - s);
+    B = s >= 0 ? (i128)((u128)S << s) : (2 * S + ((i128)1 << (-s))) >> (1 - s);
   } else if (lin) {
     if (s >= 0)
-      B = round_half_up_i128(sixS * ((i128)1 << s), D);
+      B = round_half_up_i128((i128)((u128)sixS << s), D);  // sixS 2^s
     else
-      B = round_half_up_i128(sixS, D * ((i128)1 << (-s)));
+      B = round_half_up_i128(sixS, (i128)((u128)D << (-s)));
   }
   P.fallback = 0;
   P.s = s;

@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(kGroupBlock, 3)
     P.fb_shift = 0;
     P.s = 0;
     P.fallback = 0;
-    if (act) P = solve_params(lin ? 2 * S.T1 - (i128)(N - 1) * S.T0 : (i128)0, S.mx, S.mn, N, lin);
+    if (act) P = solve_params(lin ? 2 * S.T1 - mul_i128_u64(S.T0, N - 1) : (i128)0, S.mx, S.mn, N, lin);
     // residual range (step 4)
     int64_t lo = INT64_MAX, hi = INT64_MIN;
     uint64_t zmax = 0;

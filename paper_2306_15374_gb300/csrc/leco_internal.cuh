@@ -185,6 +185,16 @@ __device__ __forceinline__ uint64_t load_value(const void* __restrict__ v, int d
 }
 
 __device__ __forceinline__ int bitlen_u64(uint64_t x) { return 64 - __clzll((long long)x); }
+// exact 128-bit products from 64-bit multiplies (the generic 128 x 128-bit product is not needed
+// when one factor has 64 bits): a * b for int64 a, b; a * b mod 2^128 for a 128-bit a, unsigned b
+__device__ __forceinline__ i128 mul_s64(int64_t a, int64_t b) {
+  return (i128)(((u128)(uint64_t)__mul64hi(a, b) << 64) | (u128)((uint64_t)a * (uint64_t)b));
+}
+__device__ __forceinline__ i128 mul_i128_u64(i128 a, uint64_t b) {
+  const uint64_t al = (uint64_t)a, ah = (uint64_t)((u128)a >> 64);
+  return (i128)(((u128)(__umul64hi(al, b) + ah * b) << 64) | (u128)(al * b));
+}
+
 __device__ __forceinline__ int bitlen_u128(u128 x) {
   const uint64_t hi = (uint64_t)(x >> 64);
   return hi ? 128 - __clzll((long long)hi) : bitlen_u64((uint64_t)x);

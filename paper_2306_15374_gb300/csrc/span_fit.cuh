@@ -25,7 +25,7 @@ struct SpanStats {
 __device__ __forceinline__ SpanStats combine_stats(const SpanStats& l, uint64_t nl, const SpanStats& r) {
   SpanStats c;
   c.T0 = l.T0 + r.T0;
-  c.T1 = l.T1 + r.T1 + (i128)nl * r.T0;
+  c.T1 = l.T1 + r.T1 + mul_i128_u64(r.T0, nl);
   c.mn = min(l.mn, r.mn);
   c.mx = max(l.mx, r.mx);
   return c;
@@ -79,7 +79,7 @@ __device__ __forceinline__ SpanStats stats_part(const T* p, uint32_t x, uint32_t
     s.mn = min(s.mn, w);
     s.mx = max(s.mx, w);
     s.T0 += (i128)w;
-    s.T1 += (i128)w * (int64_t)x;
+    s.T1 += mul_s64(w, (int64_t)x);
   }
   return s;
 }
