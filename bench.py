@@ -74,8 +74,8 @@ def parse_args():
 KSCAN_SRCS = [os.path.join(ROOT, "paper_2306_15374_gb300", "csrc", f) for f in ("k_scan.cu", "leco_internal.cuh", "tma.cuh")]
 # DRAM read + write per decode launch from one ncu capture of this workload (mean of columns a, b, c;
 # see profiles/k_tilescan_decode_filter_fix200M.md), valid only for the kernel sources it was taken on.
-DECODE_TRAFFIC = {"sha256": "64372303df54eb9e042ad419159bc3c880bd61b38aeaf6f1418dd9a724d8ba29",
-                  "bytes_per_launch": (1894107392 + 1973501952 + 1845167872) / 3}
+DECODE_TRAFFIC = {"sha256": "c5bc739e9d9415b8ed6d54cc8c9f0bfd31bf95fb0df1a9d78f56142a7ca52120",
+                  "bytes_per_launch": (1893680640 + 1972998144 + 1845286144) / 3}
 
 
 def decode_traffic():

@@ -685,7 +685,7 @@ __global__ void k_aux_multi(const Record* __restrict__ rec, const PolyCoef* __re
 }
 
 // CTA per pack item: a run of consecutive partitions of one column whose values fit one stage
-// (several short partitions share one staged copy), packed one partition after the other
+// (several short partitions share one staged copy, and a warp packs each of them)
 template <bool POLY>
 __global__ void __launch_bounds__(kPackBlock)
     k_pack_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
@@ -710,16 +710,28 @@ __global__ void __launch_bounds__(kPackBlock)
     const PackItem item = items[it];
     const uint64_t p0 = part_base[item.c];
     const uint32_t vb = dtype == LECO_U32 ? 4u : 8u;
-    for (uint32_t q = 0; q < item.k; q++) {
-      const uint64_t p = item.p0 + q;
+    auto part = [&](uint64_t p) {
       PartSrc s = si;
       s.a = aux[p].start;
       s.N = (uint32_t)((p + 1 < part_base[item.c + 1] ? aux[p + 1].start : si.n) - s.a);
-      const uint32_t zofs = (uint32_t)(s.a - si.a);
-      pack_partition<POLY>(s, st ? st + (size_t)zofs * vb : nullptr, ring, rec + p0, aux + p0,
-                           POLY ? pcoef + p0 : nullptr, POLY ? poly + p0 : nullptr, p - p0, words + word_base[item.c],
-                           zofs);
+      return s;
+    };
+    if (item.k == 1) {  // one partition: the whole CTA
+      pack_partition<POLY>(part(item.p0), st, ring, rec + p0, aux + p0, POLY ? pcoef + p0 : nullptr,
+                           POLY ? poly + p0 : nullptr, item.p0 - p0, words + word_base[item.c], 0);
+      return;
     }
+    // several short partitions: a warp each, the CTA's warps side by side (their residual buffers
+    // and whole output words are disjoint)
+    for (uint32_t q = threadIdx.x >> 5; q < item.k; q += kPackBlock / 32) {
+      const uint64_t p = item.p0 + q;
+      const PartSrc s = part(p);
+      const uint32_t zofs = (uint32_t)(s.a - si.a);
+      pack_partition<POLY, true>(s, st ? st + (size_t)zofs * vb : nullptr, ring, rec + p0, aux + p0,
+                                 POLY ? pcoef + p0 : nullptr, POLY ? poly + p0 : nullptr, p - p0,
+                                 words + word_base[item.c], zofs);
+    }
+    __syncthreads();  // the stage buffer is refilled for the next item
   };
   for_each_staged<1>(nitems, pack_stage_cap(dtype), get, body, ring, full, err);
 }
