@@ -263,9 +263,18 @@ __device__ __forceinline__ void fit_pass2(const T* __restrict__ v, uint32_t N, i
   *hi_out = hi;
 }
 
+// barrier of a fitting group wider than a warp: the CTA (bar_id < 0) or named barrier bar_id over
+// the group's nthreads threads (several groups in one CTA)
+__device__ __forceinline__ void group_sync(int bar_id, uint32_t nthreads) {
+  if (bar_id < 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+}
+
 template <int GROUP>
 __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint64_t a, uint32_t N,
-                               int model, uint32_t rank, FitShared* sm) {
+                               int model, uint32_t rank, FitShared* sm, int bar_id = -1) {
   const bool lin = model == LECO_MODEL_LINEAR && N >= 2;
   const bool u32 = dtype == LECO_U32;
   const uint32_t* v32 = static_cast<const uint32_t*>(values) + a;
@@ -298,7 +307,7 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
       sm->mx[wid] = mx;
       sm->mn[wid] = mn;
     }
-    __syncthreads();
+    group_sync(bar_id, GROUP);
     if (rank == 0) {
       for (int k = 1; k < GROUP / 32; k++) {
         S += sm->S[k];
@@ -307,7 +316,7 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
       }
       sm->P = solve_params(S, mx, mn, N, lin);
     }
-    __syncthreads();
+    group_sync(bar_id, GROUP);
     P = sm->P;
   }
 
@@ -346,7 +355,7 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
       sm->mn[wid] = lo;
       sm->zmax[wid] = zmax;
     }
-    __syncthreads();
+    group_sync(bar_id, GROUP);
     if (rank == 0) {
       for (int k = 1; k < GROUP / 32; k++) {
         hi = max(hi, sm->mx[k]);
@@ -355,9 +364,9 @@ __device__ FitResult fit_range(const void* __restrict__ values, int dtype, uint6
       }
       sm->R = finish_fit(P, lo, hi, zmax);
     }
-    __syncthreads();
+    group_sync(bar_id, GROUP);
     R = sm->R;
-    __syncthreads();  // sm is reused by the next partition
+    group_sync(bar_id, GROUP);  // sm is reused by the next partition
   }
   return R;
 }

@@ -162,6 +162,35 @@ __global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
   }
 }
 
+// Two warps per partition (four partitions per 256-thread CTA, each pair of warps synchronised by its
+// own named barrier): as many warps stream as with one warp per partition, but half as many
+// partitions are in flight, so the second pass finds the partition in L2 instead of DRAM.
+constexpr int kFitPairs = kFitBlock / 64;
+
+__global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
+    k_fit_pairs(const void* __restrict__ values, int dtype, uint64_t n, const uint64_t* __restrict__ starts,
+                uint32_t L, uint64_t m, int model, Record* __restrict__ rec, uint64_t* __restrict__ lenbits,
+                uint32_t* __restrict__ max_b) {
+  __shared__ FitShared sm[kFitPairs];
+  const uint32_t g = threadIdx.x >> 6, rank = threadIdx.x & 63u;
+  const uint64_t ng = (uint64_t)gridDim.x * kFitPairs;
+  for (uint64_t p = (uint64_t)blockIdx.x * kFitPairs + g; p < m; p += ng) {
+    const uint64_t a = part_begin(starts, L, n, p);
+    const uint32_t N = (uint32_t)(part_begin(starts, L, n, p + 1) - a);
+    const FitResult R = fit_range<64>(values, dtype, a, N, model, rank, &sm[g], 1 + (int)g);
+    if (rank == 0) {
+      Record r;
+      r.theta0 = R.theta0;
+      r.theta1 = R.theta1;
+      r.start = a;
+      r.word3 = make_w3(0, R.b, R.s, 1);
+      rec[p] = r;
+      lenbits[p] = (uint64_t)N * R.b;
+      if (R.b) atomicMax(max_b, R.b);
+    }
+  }
+}
+
 // The polynomial model (fit.cuh): four phases over all partitions, each its own kernel. Phases 1
 // and 3 read the values (a warp per partition), phases 2 and 4 are a thread per partition. A map
 // says where partition p's values are: one column (OneColumn), or the polynomial columns of a
@@ -893,8 +922,16 @@ cudaError_t launch_fit(const void* values, int dtype, uint64_t n, const uint64_t
   // fit CTAs per SM: the encode shape of the tuning table for this value width (fewer keep more of
   // each partition in L2 between the two passes)
   const uint32_t fc = encode_config_lookup(dtype).fit_ctas;
-  const int grid = grid_for((m + kFitWarps - 1) / kFitWarps, 1, fc >= 1 && fc <= (uint32_t)kFitCtasPerSm ? (int)fc : kFitCtasPerSm);
-  k_fit<<<grid, kFitBlock, 0, st>>>(values, dtype, n, starts, L, m, model, rec, lenbits, max_b);
+  const int ctas = fc >= 1 && fc <= (uint32_t)kFitCtasPerSm ? (int)fc : kFitCtasPerSm;
+  // partitions of at least 1024 values: two warps each (the second pass then stays in L2)
+  if (!starts && L >= 1024) {
+    k_fit_pairs<<<grid_for((m + kFitPairs - 1) / kFitPairs, 1, ctas), kFitBlock, 0, st>>>(values, dtype, n, starts,
+                                                                                        L, m, model, rec, lenbits,
+                                                                                        max_b);
+    return cudaGetLastError();
+  }
+  k_fit<<<grid_for((m + kFitWarps - 1) / kFitWarps, 1, ctas), kFitBlock, 0, st>>>(values, dtype, n, starts, L, m,
+                                                                                  model, rec, lenbits, max_b);
   return cudaGetLastError();
 }
 
