@@ -237,7 +237,7 @@ __device__ __forceinline__ uint64_t value_at(const ScanArgs& g, const uint32_t* 
 // Lane j handles positions i0 + j + 32 k; its fixed-point prediction F and bit position step by
 // 32 B and 32 b. Filter runs are classified once by their model bounds: missed runs cost nothing,
 // runs certainly inside are summed without the compare.
-template <int MODE, bool WIDE>
+template <int MODE, bool WIDE, bool ZERO_B>
 __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const uint32_t* words,
                                            const Aux& a, uint64_t i0, uint32_t ng, uint32_t tail,
                                            uint64_t bit_base, uint32_t lane, int cls) {
@@ -251,6 +251,19 @@ __device__ __forceinline__ void run_groups(const ScanArgs& g, Acc& acc, const ui
   const uint32_t b32 = 32u * b;
   const uint64_t mask64 = low_mask(b);
   const uint32_t mask32 = (uint32_t)mask64;
+  if (ZERO_B && (MODE == kDecode64 || MODE == kDecode32) && b == 0) {
+    // every residual is zero: the values are the predictions (columns with short partitions, where
+    // such runs are common)
+    const uint32_t steps = ng + (lane < tail ? 1u : 0u);
+    if (MODE == kDecode64) {
+      uint64_t* o = reinterpret_cast<uint64_t*>(g.out) + (i0 + lane - g.begin);
+      for (uint32_t k = 0; k < steps; k++, o += 32, F += B32) *o = (uint64_t)((int64_t)F >> sh);
+    } else {
+      uint32_t* o = reinterpret_cast<uint32_t*>(g.out) + (i0 + lane - g.begin);
+      for (uint32_t k = 0; k < steps; k++, o += 32, F += B32) *o = (uint32_t)(uint64_t)((int64_t)F >> sh);
+    }
+    return;
+  }
   if (MODE == kDecode64) {
     uint64_t* o = reinterpret_cast<uint64_t*>(g.out) + (i0 + lane - g.begin);
 #pragma unroll 4
@@ -402,9 +415,9 @@ __device__ void process_tile(const ScanArgs& g, uint64_t t, const TileMeta& mt, 
         cls = classify(kind, vlo, vhi, g.lo, g.hi);
       }
       if (w3_b(a.word3) > 32)
-        run_groups<MODE, true>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
+        run_groups<MODE, true, false>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
       else
-        run_groups<MODE, false>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
+        run_groups<MODE, false, TAIL>(g, acc, words, a, gp, ng, tail, mt.bit_base, lane, cls);
       gp = TAIL ? run_end : gp + 32ull * ng;
     } else if (POLY && ng && w3_poly(a.word3)) {
       if (w3_b(a.word3) > 32)
