@@ -124,6 +124,27 @@ def test_variable_partition_slice_matches_round_oracle(lc, dist, off, n):
     col.free()
 
 
+# Slices of the full columns where the oracle's sequential merge finishes in seconds (two 2M-value
+# timestamp slices, ~1-2 s each) or tens of seconds (one 500K-value piecewise slice).
+SEQ_SLICES = [("b", 33_703_774, 2_000_000), ("b", 285_115_043, 2_000_000), ("a", 114_217_773, 500_000)]
+
+
+@pytest.mark.parametrize("dist,off,n", SEQ_SLICES, ids=["timestamps_2M_a", "timestamps_2M_b", "piecewise_500K"])
+def test_variable_partition_slice_within_2pct_of_sequential_merge(lc, dist, off, n):
+    """The compressed size of the GPU partitioning of a slice (the round reading, §3.2.2) is within
+    2% of the oracle's sequential split/merge (one best pair merged at a time) on the same slice."""
+    v = _cfg3(dist)[off:off + n].copy()
+    bits = 64 if dist == "a" else 32
+    col = lc.leco_encode(to_dev(v, bits), lc.variable(TAU), lc.LECO_MODEL_LINEAR)
+    rec_b, words_b, _ = lc.leco_column_export(col)
+    col.free()
+    gpu_bytes = len(rec_b) + len(words_b)
+    seq = oracle.var_partition(v, TAU, lc.LECO_MODEL_LINEAR, variant="seq")
+    srec, swords = oracle.encode(v, seq, lc.LECO_MODEL_LINEAR)
+    seq_bytes = oracle.compressed_bytes(srec, swords)
+    assert gpu_bytes <= 1.02 * seq_bytes, (gpu_bytes, seq_bytes)
+
+
 @pytest.mark.parametrize("dist", ["a", "b"])
 def test_full_size_variable_partitions(lc, dist):
     """200M piecewise-linear uint64 / 500M uint32 timestamps, GPU split/merge at tau = 0.03."""
