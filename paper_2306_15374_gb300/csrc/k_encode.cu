@@ -655,8 +655,9 @@ __global__ void k_zero_bounds(const Aux* __restrict__ aux, uint64_t m, uint64_t 
 
 // ------------------------------------------------------------------------------ batched encode
 
-// one warp per partition of every column (its column from the partition-column table)
-__global__ void __launch_bounds__(kFitBlock, kFitCtasPerSm)
+// one warp per partition of every column (its column from the partition-column table); registers
+// for 3 CTAs per SM (4 spilled, and the encode tuner then keeps 3)
+__global__ void __launch_bounds__(kFitBlock, 3)
     k_fit_multi(const EncCol* __restrict__ cols, const uint64_t* __restrict__ part_base,
                 const uint32_t* __restrict__ part_col, uint64_t P, int dtype, Record* __restrict__ rec,
                 uint64_t* __restrict__ lenbits, uint32_t* __restrict__ max_b) {
