@@ -219,6 +219,7 @@ VAR_CASES = [
     ("timestamps_200k", lambda: W.timestamps_u32(200_000, seed=5), 32),
     ("adversarial_20k", lambda: W.adversarial_u64(20_000, seed=3), 64),
     ("cfg1_150k", lambda: W.cfg1(150_000), 64),
+    ("mixed_chunks_394k", lambda: W.mixed_chunks_u64(seed=6), 64),
 ]
 
 

@@ -164,6 +164,26 @@ def runs(n: int, run_len: int, seed: int = 0) -> np.ndarray:
     return np.repeat(vals, run_len)[:n]
 
 
+def mixed_chunks_u64(seed: int = 0, chunk: int = 1 << 16) -> np.ndarray:
+    """Six chunk-sized regions of different shape and a partial seventh, so that one column holds
+    both split schedules and the decoder's zero-width runs: smooth (a line), noisy (noise 2^20),
+    smooth with a noisy middle window, a line with rare jumps, constant runs, values near 2^63 (a
+    chunk whose values leave (-2^62, 2^62)), then 1000 values of a line."""
+    g = rng(seed, 10)
+    i = np.arange(chunk, dtype=np.int64)
+    parts = [
+        1_000_000 + 37 * i,
+        5_000_000 + 1000 * i + g.integers(-(1 << 20), (1 << 20) + 1, size=chunk),
+        9_000_000 + 11 * i + np.where((i >= 40_000) & (i < 41_000), g.integers(0, 1 << 18, size=chunk), 0),
+        20_000_000 + 1000 * i + np.cumsum((g.random(chunk) < 0.002) * g.integers(1, 100_000, size=chunk)),
+        np.repeat(g.integers(0, 1 << 30, size=chunk // 700 + 1), 700)[:chunk],
+    ]
+    out = [p.astype(np.uint64) for p in parts]
+    out.append(((1 << 63) - (1 << 40) + 3 * i + g.integers(0, 8, size=chunk)).astype(np.uint64))
+    out.append((7 + 5 * np.arange(1000, dtype=np.int64)).astype(np.uint64))
+    return np.concatenate(out)
+
+
 # ----------------------------------------------------------------------------- queries
 
 def uniform_indices(k: int, n: int, seed: int = 0, stream: int = 2) -> np.ndarray:
