@@ -916,7 +916,8 @@ def bench_batch(args, leco, dev, stream):
     """Batched form: 10,000 uint64 columns, lengths log-uniform in [1K, 10M] rescaled to 3B values,
     each linear + noise, sorted normal or sorted lognormal with its own seed, constant or linear
     model (50/50), partition size 256/1024/4096. Encode and decode all columns in one pass (decode:
-    one persistent launch, also as a CUDA graph, with the autotuned scan shape) against one launch
+    one persistent launch, also as a CUDA graph, with the autotuned scan shape; encode: the library
+    call, and a prepared plan replayed as one CUDA graph) against one launch
     per column."""
     import numpy as np  # noqa: F401
     import torch
@@ -962,6 +963,19 @@ def bench_batch(args, leco, dev, stream):
         return [leco.Column(ctypes.c_void_p(p_out[i])) for i in range(k_)]
 
     t_benc, cols = ev_time(lib_encode)
+    # the same encode prepared once and replayed as one CUDA graph (stream offsets on the device, no
+    # host round trip); its result is then copied out into columns at their exact size
+    eplan = leco.leco_batch_encode_plan_create(vals, models, Ls)
+    reserved = leco.leco_batch_encode_plan_reserved_bytes(eplan)
+    leco.leco_batch_encode_plan_run(eplan)
+    t_genc, _ = ev_time(lambda: leco.leco_batch_encode_plan_run(eplan), 3)
+    t_take, gcols = ev_time(lambda: leco.leco_batch_encode_plan_columns(eplan))
+    same_graph = all(leco.leco_column_export(a) == leco.leco_column_export(b)
+                     for a, b in zip(gcols[:: max(1, ncols // 50)], cols[:: max(1, ncols // 50)]))
+    for c in gcols:
+        c.free()
+    eplan.free()
+    del gcols
 
     def per_col_encode():
         return [leco.leco_encode(v, leco.fixed(L), m) for v, L, m in zip(vals, Ls, models)]
@@ -1001,13 +1015,16 @@ def bench_batch(args, leco, dev, stream):
         "encode_batched_ms": t_benc, "encode_batched_gbs": enc_bytes / (t_benc * 1e-3) / 1e9,
         "encode_batched_python_call_ms": t_py,
         "encode_per_column_ms": t_penc, "encode_speedup": t_penc / t_benc, "encode_identical": same,
+        "encode_graph_ms": t_genc, "encode_graph_gbs": enc_bytes / (t_genc * 1e-3) / 1e9,
+        "encode_graph_speedup_vs_per_column": t_penc / t_genc, "encode_graph_identical": same_graph,
+        "encode_graph_columns_ms": t_take, "encode_graph_reserved_bytes": reserved,
         "decode_plan_ms": t_plan, "decode_plan_gbs": dec_bytes / (t_plan * 1e-3) / 1e9,
         "decode_plan_frac_hbm": dec_bytes / (t_plan * 1e-3) / 1e9 / peak,
         "decode_graph_ms": t_graph, "decode_per_column_ms": t_pdec,
         "decode_speedup_vs_per_column": t_pdec / t_graph, "decode_equals_input": ok,
         "jobs": leco.leco_batch_plan_jobs(plan), "tuned_scan": tuned, "tuned_encode": enc_tuned,
         "compressed_bytes": comp,
-        "kernel_launches": {"decode_plan": 1, "decode_per_column": ncols},
+        "kernel_launches": {"decode_plan": 1, "decode_per_column": ncols, "encode_graph": 1},
     }
     plan.free()
     for c in cols:

@@ -4,7 +4,7 @@
  * The paper decodes one column at a time on one CPU thread (§4.2); these calls are this library's
  * systems layer around the same per-value decode of §3.3: many columns of uneven lengths decoded
  * by one persistent kernel launch (optionally a CUDA graph) or encoded by one persistent fit and one
- * persistent pack launch, and an autotuner that picks the scan pipeline's and the encode's shape. Conventions (device pointers, streams, ownership, errors) are those of leco.h.
+ * persistent pack launch (optionally a prepared plan replayed as one CUDA graph), and an autotuner that picks the scan pipeline's and the encode's shape. Conventions (device pointers, streams, ownership, errors) are those of leco.h.
  */
 #ifndef LECO_BATCH_H
 #define LECO_BATCH_H
@@ -106,6 +106,42 @@ typedef struct {
 leco_status leco_tune_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
                                    const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
                                    leco_encode_config* best);
+
+/* A prepared batched encode replayed as one CUDA graph (§3.2.1 partitions, §3.1 fit, §3.3 packing,
+ * as leco_batch_encode; the batching itself is this library's systems layer). Creation does the
+ * host work once: the columns' tables and pack items go to the device, the plan reserves its device
+ * blocks (records, decode table, tile descriptors, fit scratch, and words for the widest stream each
+ * column could have: 64 bits per value plus a polynomial coefficient block per partition that could
+ * hold one), and the launches from the fit to the pack are captured in a CUDA graph in the encode
+ * shape the tuning table holds for `dtype`. Each run is then one graph launch with no host round
+ * trip: the streams' offsets are computed on the device, each column's stream placed right after the
+ * previous one in the reserved words. Arguments as for leco_batch_encode, except that ncols must be
+ * at least 1 and every n[c] below 2^41. The graph holds the pointers d_vals[c]: those buffers must
+ * stay allocated while the plan lives, and each run encodes their contents at the time it runs.
+ * Synchronizes `stream` once. Errors: INVALID_ARG, OOM (the reservation did not fit), CUDA. */
+typedef struct leco_batch_encode_plan leco_batch_encode_plan;
+
+leco_status leco_batch_encode_plan_create(const void* const* d_vals, const uint64_t* n, const leco_model* models,
+                                          const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
+                                          leco_batch_encode_plan** out);
+
+/* One launch of the plan's graph on `stream`: every column is encoded into the plan's blocks,
+ * replacing the previous run's result. Runs that overlap on the device race on those blocks. */
+leco_status leco_batch_encode_plan_run(leco_batch_encode_plan* plan, leco_stream_t stream);
+
+/* Synchronize `stream` (the stream of the last run), then copy the last run's result out into
+ * ncols new columns, out[c] identical to leco_batch_encode's out[c] for the same values: one block
+ * of the records, decode table and tile descriptors and one of the packed streams at their exact
+ * size, shared by the columns and released when the last of them is freed. The plan is unchanged
+ * and may run again. Errors: INVALID_ARG, OOM, TIMEOUT (a bounded wait inside the run gave up; the
+ * streams are incomplete and no column is returned), CUDA. */
+leco_status leco_batch_encode_plan_columns(leco_batch_encode_plan* plan, leco_stream_t stream, leco_column** out);
+
+/* Device bytes the plan holds (its tables, scratch and reserved words); 0 for NULL. */
+uint64_t leco_batch_encode_plan_reserved_bytes(const leco_batch_encode_plan* plan);
+
+/* Waits for the device, then releases the plan's blocks and graph. NULL is ignored. */
+void leco_batch_encode_plan_free(leco_batch_encode_plan* plan);
 
 #ifdef __cplusplus
 }

@@ -843,6 +843,34 @@ __global__ void k_part_col(const uint64_t* __restrict__ part_base, uint32_t ncol
     part_col[p] = find_col(part_base, ncols, p);
 }
 
+// exclusive prefix sum of the columns' stream words: each thread sums a contiguous run of columns,
+// the CTA scans the run totals, then each thread writes its run's bases
+constexpr int kWordBaseBlock = 1024;
+__global__ void __launch_bounds__(kWordBaseBlock)
+    k_word_bases(const uint64_t* __restrict__ col_bits, uint32_t ncols, uint64_t* __restrict__ word_base) {
+  __shared__ uint64_t run[kWordBaseBlock];
+  const uint32_t t = threadIdx.x;
+  const uint64_t per = ((uint64_t)ncols + kWordBaseBlock - 1) / kWordBaseBlock;
+  const uint32_t c0 = (uint32_t)min((uint64_t)t * per, (uint64_t)ncols);
+  const uint32_t c1 = (uint32_t)min((uint64_t)c0 + per, (uint64_t)ncols);
+  uint64_t s = 0;
+  for (uint32_t c = c0; c < c1; c++) s += stream_words(col_bits[c]);
+  run[t] = s;
+  __syncthreads();
+  for (uint32_t d = 1; d < kWordBaseBlock; d <<= 1) {
+    const uint64_t add = t >= d ? run[t - d] : 0;
+    __syncthreads();
+    run[t] += add;
+    __syncthreads();
+  }
+  uint64_t base = run[t] - s;
+  for (uint32_t c = c0; c < c1; c++) {
+    word_base[c] = base;
+    base += stream_words(col_bits[c]);
+  }
+  if (t == kWordBaseBlock - 1) word_base[ncols] = run[t];
+}
+
 // k_zero_bounds for every column: thread per partition, then each column's tail words
 __global__ void k_zero_bounds_multi(const Aux* __restrict__ aux, const uint32_t* __restrict__ part_col,
                                     const uint64_t* __restrict__ word_base, const uint64_t* __restrict__ col_bits,
@@ -887,13 +915,14 @@ int resident_grid(K kern, int block, uint64_t work, uint32_t smem) {
   return (int)(work < cap ? work : cap);
 }
 
-// the four polynomial phases over partitions [0, m) of the map, with their scratch
+// the four polynomial phases over partitions [0, m) of the map, with their scratch (given: at least
+// poly_fit_scratch_bytes(m) bytes the caller owns; nullptr: taken from the pool and released)
 template <typename Map>
 cudaError_t launch_poly_fit(const Map& map, int dtype, uint64_t m, Record* rec, uint64_t* lenbits, PolyCoef* pcoef,
-                            uint32_t* max_b, cudaStream_t st) {
+                            uint32_t* max_b, cudaStream_t st, void* given = nullptr) {
   const uint64_t bm = (sizeof(PolyMom) * m + 255) & ~255ull, bp = (sizeof(PolyPlan) * m + 255) & ~255ull;
-  char* scr = nullptr;
-  cudaError_t e = dev_alloc((void**)&scr, bm + bp + sizeof(PolyRange) * m, st);
+  char* scr = static_cast<char*>(given);
+  cudaError_t e = given ? cudaSuccess : dev_alloc((void**)&scr, bm + bp + sizeof(PolyRange) * m, st);
   if (e != cudaSuccess) return e;
   PolyMom* mom = reinterpret_cast<PolyMom*>(scr);
   PolyPlan* plan = reinterpret_cast<PolyPlan*>(scr + bm);
@@ -907,7 +936,7 @@ cudaError_t launch_poly_fit(const Map& map, int dtype, uint64_t m, Record* rec, 
   k_poly_ranges<Map><<<grid_for(wb, 1, nb), kFitBlock, 0, st>>>(map, dtype, m, plan, rng);
   k_poly_choose<Map><<<grid_for(m, 128, 8), 128, 0, st>>>(map, m, mom, plan, rng, rec, lenbits, pcoef, max_b);
   e = cudaGetLastError();
-  cudaFreeAsync(scr, st);
+  if (!given) cudaFreeAsync(scr, st);
   return e;
 }
 
@@ -1033,9 +1062,13 @@ cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t 
   return cudaGetLastError();
 }
 
+uint64_t poly_fit_scratch_bytes(uint64_t m) {
+  return ((sizeof(PolyMom) * m + 255) & ~255ull) + ((sizeof(PolyPlan) * m + 255) & ~255ull) + sizeof(PolyRange) * m;
+}
+
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col, uint32_t ncols,
                              uint64_t P, int dtype, Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b,
-                             uint32_t* err, uint32_t fit_ctas, cudaStream_t st) {
+                             uint32_t* err, uint32_t fit_ctas, cudaStream_t st, void* poly_scratch) {
   (void)err;
   cudaError_t e = cudaMemsetAsync(max_b, 0, sizeof(uint32_t) * (ncols ? ncols : 1), st);
   if (e != cudaSuccess || P == 0) return e;
@@ -1044,7 +1077,7 @@ cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, cons
   k_fit_multi<<<grid, kFitBlock, 0, st>>>(cols, part_base, part_col, P, dtype, rec, lenbits, max_b);
   e = cudaGetLastError();
   if (e == cudaSuccess && pcoef)
-    e = launch_poly_fit(BatchColumns{cols, part_base, ncols}, dtype, P, rec, lenbits, pcoef, max_b, st);
+    e = launch_poly_fit(BatchColumns{cols, part_base, ncols}, dtype, P, rec, lenbits, pcoef, max_b, st, poly_scratch);
   return e;
 }
 
@@ -1072,6 +1105,11 @@ cudaError_t launch_aux_multi(const Record* rec, const PolyCoef* pcoef, const Enc
 }
 
 uint32_t pack_item_values() { return kStageData / 8; }
+
+cudaError_t launch_word_bases(const uint64_t* col_bits, uint32_t ncols, uint64_t* word_base, cudaStream_t st) {
+  k_word_bases<<<1, kWordBaseBlock, 0, st>>>(col_bits, ncols, word_base);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col,
                               const uint64_t* word_base, const uint64_t* col_bits, const PackItem* items,

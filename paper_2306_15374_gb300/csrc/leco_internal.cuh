@@ -287,9 +287,12 @@ struct EncCol {
 // polynomial model; a polynomial column's partitions are fitted by the polynomial phases)
 // part_col[p]: the column of global partition p (launch_part_col fills it once per batch)
 cudaError_t launch_part_col(const uint64_t* part_base, uint32_t ncols, uint64_t P, uint32_t* part_col, cudaStream_t st);
+// poly_scratch: poly_fit_scratch_bytes(P) caller-owned bytes for the polynomial phases, or nullptr
+// (then taken from the library pool for the call)
+uint64_t poly_fit_scratch_bytes(uint64_t m);
 cudaError_t launch_fit_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col, uint32_t ncols,
                              uint64_t P, int dtype, Record* rec, uint64_t* lenbits, PolyCoef* pcoef, uint32_t* max_b,
-                             uint32_t* err, uint32_t fit_ctas, cudaStream_t st);
+                             uint32_t* err, uint32_t fit_ctas, cudaStream_t st, void* poly_scratch = nullptr);
 uint64_t offsets_multi_scratch_elems(uint64_t P);
 cudaError_t launch_offsets_multi(Record* rec, const uint64_t* lenbits, const uint64_t* part_base,
                                  const uint32_t* part_col, uint32_t ncols, uint64_t P, uint64_t* scratch,
@@ -304,6 +307,9 @@ struct PackItem {
   uint32_t k;
 };
 uint32_t pack_item_values();
+// word_base[c] = sum of stream_words(col_bits[k]) over k < c, for c = 0 .. ncols, on the device (one
+// CTA): each column's packed stream placed right after the previous one
+cudaError_t launch_word_bases(const uint64_t* col_bits, uint32_t ncols, uint64_t* word_base, cudaStream_t st);
 cudaError_t launch_pack_multi(const EncCol* cols, const uint64_t* part_base, const uint32_t* part_col,
                               const uint64_t* word_base, const uint64_t* col_bits, const PackItem* items,
                               uint64_t nitems, uint32_t ncols, uint64_t P, uint64_t W, int dtype, const Record* rec,

@@ -150,6 +150,12 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(u32), u32, i32, vp, ctypes.POINTER(vp)]),
         "leco_tune_batch_encode": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
                                          ctypes.POINTER(u32), u32, i32, vp, ctypes.POINTER(EncodeConfig)]),
+        "leco_batch_encode_plan_create": (i32, [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(i32),
+                                                ctypes.POINTER(u32), u32, i32, vp, col_pp]),
+        "leco_batch_encode_plan_run": (i32, [vp, vp]),
+        "leco_batch_encode_plan_columns": (i32, [vp, vp, ctypes.POINTER(vp)]),
+        "leco_batch_encode_plan_reserved_bytes": (u64, [vp]),
+        "leco_batch_encode_plan_free": (None, [vp]),
         "leco_server_create": (i32, [ctypes.POINTER(ServerConfig), col_pp]),
         "leco_server_admit": (i32, [vp, vp, ctypes.POINTER(u32)]),
         "leco_server_admit_mock": (i32, [vp, u64, i32, u64, ctypes.POINTER(u32)]),
@@ -634,3 +640,56 @@ def leco_batch_encode(values, models, Ls, stream=None) -> list:
     out = (ctypes.c_void_p * max(k, 1))()
     _check(lib().leco_batch_encode(vals, ns, ms, ls, k, dt, _stream(stream), out), "leco_batch_encode")
     return [Column(ctypes.c_void_p(out[i])) for i in range(k)]
+
+
+class BatchEncodePlan:
+    """Owning handle of a leco_batch_encode_plan; keeps the input tensors its graph reads alive."""
+
+    def __init__(self, handle, values):
+        self._h = handle
+        self._values = list(values)
+        self.ncols = len(self._values)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("batch encode plan already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().leco_batch_encode_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def leco_batch_encode_plan_create(values, models, Ls, stream=None) -> BatchEncodePlan:
+    """Prepare the batched encode of these columns as one CUDA graph (leco_batch.h)."""
+    k, dt, vals, ns, ms, ls = _batch_args(values, models, Ls)
+    h = ctypes.c_void_p()
+    _check(lib().leco_batch_encode_plan_create(vals, ns, ms, ls, k, dt, _stream(stream), ctypes.byref(h)),
+           "leco_batch_encode_plan_create")
+    return BatchEncodePlan(h, values)
+
+
+def leco_batch_encode_plan_run(plan: BatchEncodePlan, stream=None) -> None:
+    _check(lib().leco_batch_encode_plan_run(plan.handle, _stream(stream)), "leco_batch_encode_plan_run")
+
+
+def leco_batch_encode_plan_columns(plan: BatchEncodePlan, stream=None) -> list:
+    out = (ctypes.c_void_p * max(plan.ncols, 1))()
+    _check(lib().leco_batch_encode_plan_columns(plan.handle, _stream(stream), out), "leco_batch_encode_plan_columns")
+    return [Column(ctypes.c_void_p(out[i])) for i in range(plan.ncols)]
+
+
+def leco_batch_encode_plan_reserved_bytes(plan: BatchEncodePlan) -> int:
+    return int(lib().leco_batch_encode_plan_reserved_bytes(plan.handle))
+
+
+def leco_batch_encode_plan_free(plan: BatchEncodePlan) -> None:
+    plan.free()

@@ -88,6 +88,15 @@ def test_host_side_argument_errors(built):
     ns, models, Ls = (ctypes.c_uint64 * 1)(10), (ctypes.c_int * 1)(3), (ctypes.c_uint32 * 1)(16)
     outs = (ctypes.c_void_p * 1)()
     assert L.leco_batch_encode(vals, ns, models, Ls, 1, 1, None, outs) == leco.LECO_ERR_INVALID_ARG
+    # the graph-replayed batched encode: same argument checks, at least one column, NULL plans refused
+    assert L.leco_batch_encode_plan_create(vals, ns, models, Ls, 1, 1, None, ctypes.byref(h)) == \
+        leco.LECO_ERR_INVALID_ARG
+    assert L.leco_batch_encode_plan_create(vals, ns, models, Ls, 0, 1, None, ctypes.byref(h)) == \
+        leco.LECO_ERR_INVALID_ARG
+    assert L.leco_batch_encode_plan_run(None, None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_batch_encode_plan_columns(None, None, outs) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_batch_encode_plan_reserved_bytes(None) == 0
+    L.leco_batch_encode_plan_free(None)
     # variable partitioning takes the variable kinds (plain or seeded) and tau in [0, 1]
     m_out = ctypes.c_uint64(0)
     for pol in (leco.fixed(16), leco.auto(), leco.variable(1.5), leco.variable(-0.1, seeded=True)):

@@ -115,6 +115,58 @@ def test_batch_encode_matches_single_column_encode(lc, bits):
         assert (from_dev(out)[: len(v)] == v).all()
 
 
+@pytest.mark.parametrize("bits", [64, 32])
+def test_batch_encode_plan_graph_matches_batch_encode(lc, bits):
+    """The batched encode prepared once and replayed as one CUDA graph: each run's columns are byte
+    for byte those of leco_batch_encode on the same values (constant, linear and polynomial models,
+    empty, tiny and multi-tile columns); a run after the inputs change in place encodes the new
+    contents; the columns taken out stay valid after the plan runs again and after it is freed."""
+    import torch
+
+    g = W.rng(41 + bits)
+    models, Ls, lens = [], [], []
+    for c in range(36):
+        lens.append(int(np.exp(g.uniform(0, np.log(150_000)))) if c % 8 else 0)
+        models.append(c % 3)
+        Ls.append(int(g.choice([1, 37, 256, 1024, 4096])))
+
+    def values(seed):
+        out = []
+        for c, n in enumerate(lens):
+            if bits == 32:
+                out.append(W.timestamps_u32(n, seed=seed + c))
+            elif c % 2:
+                out.append(W.linear_noise(n, 1 << 30, int(g.integers(0, 60)), int(g.integers(0, 3000)), seed=seed + c))
+            else:
+                out.append(W.adversarial_u64(n, seed=seed + c))
+        return out
+
+    vals = values(100)
+    dvals = [to_dev(v, bits) for v in vals]
+    plan = lc.leco_batch_encode_plan_create(dvals, models, Ls)
+    assert lc.leco_batch_encode_plan_reserved_bytes(plan) >= sum(8 * n for n in lens)
+    kept = []
+    for rnd in range(2):
+        if rnd == 1:  # same shapes, new contents, same device buffers
+            vals = values(900)
+            for dv, v in zip(dvals, vals):
+                dv.copy_(to_dev(v, bits))
+        lc.leco_batch_encode_plan_run(plan)
+        cols = lc.leco_batch_encode_plan_columns(plan)
+        refs = lc.leco_batch_encode(dvals, models, Ls)
+        for v, col, ref in zip(vals, cols, refs):
+            assert lc.leco_column_export(col) == lc.leco_column_export(ref)
+            assert lc.leco_serialize(col) == lc.leco_serialize(ref)
+        kept.append((vals, cols))
+    plan.free()
+    for vs, cols in kept:
+        for v, col in zip(vs, cols):
+            out = torch.empty(max(len(v), 1), dtype=torch.int32 if bits == 32 else torch.int64, device="cuda")
+            lc.leco_decode_all(col, out)
+            assert lc.leco_sync(col) == lc.LECO_OK
+            assert (from_dev(out)[: len(v)] == v).all()
+
+
 def test_encode_tuner_keeps_results_identical(lc, tmp_path):
     """Every batched-encode shape the tuner tries gives the same bytes; the chosen one is stored and
     saved with the scan configurations."""
