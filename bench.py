@@ -13,6 +13,10 @@ columns) / step time, in GB/s; the full-decode figure alone is ops.decode and ro
 Algorithmic bytes, C = compressed bytes (32 per record + 8 per residual word):
   decode  C + 8 n          filter-sum  C + 24          lookups  k * (8 idx + 8 out + 32 sector)
 
+e2e: the same step through the public API with pinned host buffers (indices in, every result out),
+the copies on their own streams so one column's results leave while the next column is decoded;
+e2e.host_link_gbs is the link's copy-engine bandwidth measured in the same run, which bounds it.
+
 After the headline (one GPU, unless --no-extra), the same run measures the other workloads and
 reports them under ops: the 1M-value fixed column with the whole oracle timed beside it
 (ops.cfg1_fix_1M), the two variable-partition columns (ops.cfg3_var), the 10,000-column batch
@@ -564,36 +568,78 @@ def run_leco(args):
     return 0
 
 
+def host_link_gbs(dev, nbytes=1 << 30, reps=3):
+    """Copy-engine bandwidth of the host link (pinned host memory): device->host and host->device
+    GB/s for one nbytes copy, best of reps. Every e2e step moves its results over this link."""
+    import torch
+
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d.fill_(1)
+    best = {}
+    for name, (dst, src) in (("d2h", (h, d)), ("h2d", (d, h))):
+        ts = []
+        for _ in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        best[name] = nbytes / (min(ts[1:]) * 1e-3) / 1e9
+    del h, d
+    return best
+
+
 def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
     """Same step through the public API with host buffers: lookup indices copied in from pinned
-    memory, decoded columns, lookup results and sums copied back to pinned memory."""
+    memory, decoded columns, lookup results and sums copied back to pinned memory. The copies run
+    on their own streams: the device->host copy of one column's results overlaps the next column's
+    decode, filter and lookups (two device result buffers in turn), and the indices of all three
+    columns are copied in up front."""
     import numpy as np
     import torch
 
     import workloads as W
 
     h_idx = {d: torch.from_numpy(W.uniform_indices(k, n, seed=ord(d)).view(np.int64)).pin_memory() for d in DISTS}
-    h_out = torch.empty(n, dtype=torch.int64).pin_memory()
-    h_outk = torch.empty(k, dtype=torch.int64).pin_memory()
-    h_res = torch.empty(3, dtype=torch.int64).pin_memory()
-    d_idx = torch.empty(k, dtype=torch.int64, device=dev)
-    out = torch.empty(n, dtype=torch.int64, device=dev)
-    outk = torch.empty(k, dtype=torch.int64, device=dev)
-    res = torch.zeros(3, dtype=torch.int64, device=dev)
+    h_out = {d: torch.empty(n, dtype=torch.int64).pin_memory() for d in DISTS}
+    h_outk = {d: torch.empty(k, dtype=torch.int64).pin_memory() for d in DISTS}
+    h_res = {d: torch.empty(3, dtype=torch.int64).pin_memory() for d in DISTS}
+    d_idx = {d: torch.empty(k, dtype=torch.int64, device=dev) for d in DISTS}
+    out = [torch.empty(n, dtype=torch.int64, device=dev) for _ in range(2)]
+    outk = [torch.empty(k, dtype=torch.int64, device=dev) for _ in range(2)]
+    res = [torch.zeros(3, dtype=torch.int64, device=dev) for _ in range(2)]
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    comp_s = torch.cuda.current_stream()
 
     def step():
-        for d in DISTS:
-            d_idx.copy_(h_idx[d], non_blocking=True)
-            leco.leco_decode_all(cols[d], out)
-            leco.leco_filter_sum(cols[d], bounds[d][0], bounds[d][1], res)
-            leco.leco_random_access(cols[d], d_idx, outk)
-            h_out.copy_(out, non_blocking=True)
-            h_outk.copy_(outk, non_blocking=True)
-            h_res.copy_(res, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        s_in.wait_stream(comp_s)
+        with torch.cuda.stream(s_in):
+            for d in DISTS:
+                d_idx[d].copy_(h_idx[d], non_blocking=True)
+        comp_s.wait_stream(s_in)
+        freed = [None, None]
+        for j, d in enumerate(DISTS):
+            b = j % 2
+            if freed[b] is not None:
+                comp_s.wait_event(freed[b])  # the copy out of this buffer's previous column is done
+            leco.leco_decode_all(cols[d], out[b])
+            leco.leco_filter_sum(cols[d], bounds[d][0], bounds[d][1], res[b])
+            leco.leco_random_access(cols[d], d_idx[d], outk[b])
+            s_out.wait_stream(comp_s)
+            with torch.cuda.stream(s_out):
+                h_out[d].copy_(out[b], non_blocking=True)
+                h_outk[d].copy_(outk[b], non_blocking=True)
+                h_res[d].copy_(res[b], non_blocking=True)
+                freed[b] = torch.cuda.Event()
+                freed[b].record(s_out)
+        comp_s.wait_stream(s_out)
+        comp_s.synchronize()
 
     for _ in range(max(1, args.warmup)):
         step()
+    link = host_link_gbs(dev)
     steps = max(1, min(args.steps, 5))
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -602,8 +648,10 @@ def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
+    d2h = 3 * (8 * n + 8 * k + 24)
     return {"value": step_b / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": 3 * 8 * k, "d2h_bytes_per_step": 3 * (8 * n + 8 * k + 24)}
+            "h2d_bytes_per_step": 3 * 8 * k, "d2h_bytes_per_step": d2h,
+            "host_link_gbs": link, "d2h_frac_of_link": d2h / (ms * 1e-3) / 1e9 / link["d2h"]}
 
 
 def gpu_setup():

@@ -202,7 +202,8 @@ struct FitShared {
 // u_x = 2x - (N-1), where w is the value as two's complement int64. S equals
 // sum u_x (w_x - w_0) because the u_x sum to zero. Each term is split as u w_hi 2^32 + u w_lo with
 // 32 x 32 -> 64-bit products, accumulated in 64 bits over at most 64 terms (|u| < 2^24: each
-// partial stays below 2^62), then folded into 128 bits.
+// partial stays below 2^62), then folded into 128 bits. Pairs of warps on one partition (GROUP 64,
+// partitions of 1024+ values) keep sixteen loads in flight per lane, other groups eight.
 template <int GROUP, typename T>
 __device__ __forceinline__ void fit_pass1(const T* __restrict__ v, uint32_t N, bool lin, uint32_t rank, i128* S_out,
                                           int64_t* mx_out, int64_t* mn_out) {
@@ -214,7 +215,7 @@ __device__ __forceinline__ void fit_pass1(const T* __restrict__ v, uint32_t N, b
       const uint32_t xe = N - x0 > 64u * GROUP ? x0 + 64u * GROUP : N;
       int64_t acc_hi = 0, acc_lo = 0;
       int32_t u = (int32_t)(2 * (int64_t)x0 - nm1);
-#pragma unroll 8
+#pragma unroll (GROUP == 64 ? 16 : 8)
       for (uint32_t x = x0; x < xe; x += GROUP, u += 2 * GROUP) {
         const int64_t w = (int64_t)__ldg(v + x);
         mx = max(mx, w);
@@ -246,7 +247,7 @@ __device__ __forceinline__ void fit_pass2(const T* __restrict__ v, uint32_t N, i
   uint64_t F = (uint64_t)B * rank;
   const uint64_t dF = (uint64_t)B * GROUP;
   if (s >= 0) {
-#pragma unroll 8
+#pragma unroll (GROUP == 64 ? 16 : 8)
     for (uint32_t x = rank; x < N; x += GROUP, F += dF) {
       const int64_t r = (int64_t)__ldg(v + x) - ((int64_t)F >> s);
       lo = min(lo, r);
