@@ -191,7 +191,8 @@ def _generate(gen, spec, ncols, keep):
 
 def test_full_size_batch(lc):
     """10,000 columns, 3B values: one batched encode (byte-identical to the oracle on sampled
-    columns) and one persistent decode launch and its CUDA graph (equal to the input)."""
+    columns), the same encode replayed as one CUDA graph (identical to it), and one persistent
+    decode launch and its CUDA graph (equal to the input)."""
     import torch
 
     spec = W.batch_spec()
@@ -206,6 +207,17 @@ def test_full_size_batch(lc):
         rec_b, words_b, _ = lc.leco_column_export(cols[c])
         rec, words = oracle.encode_fixed(v, Ls[c], models[c])
         assert rec_b == rec.tobytes() and words_b == words.tobytes(), c
+    # the same batch prepared once and replayed as one CUDA graph: the sampled columns byte for byte,
+    # every column the same size
+    eplan = lc.leco_batch_encode_plan_create(dvals, models, Ls)
+    lc.leco_batch_encode_plan_run(eplan)
+    gcols = lc.leco_batch_encode_plan_columns(eplan)
+    eplan.free()
+    for c in host:
+        assert lc.leco_column_export(gcols[c]) == lc.leco_column_export(cols[c]), c
+    assert all(a.stats()["residual_bytes"] == b.stats()["residual_bytes"] for a, b in zip(gcols, cols))
+    for c in gcols:
+        c.free()
     outs = [torch.empty_like(d) for d in dvals]
     plan = lc.leco_batch_plan_create(cols, outs)
     for runner in (lc.leco_batch_plan_run, lc.leco_batch_plan_run_graph):
