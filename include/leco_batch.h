@@ -133,8 +133,9 @@ leco_status leco_batch_encode_plan_run(leco_batch_encode_plan* plan, leco_stream
  * ncols new columns, out[c] identical to leco_batch_encode's out[c] for the same values: one block
  * of the records, decode table and tile descriptors and one of the packed streams at their exact
  * size, shared by the columns and released when the last of them is freed. The plan is unchanged
- * and may run again. Errors: INVALID_ARG, OOM, TIMEOUT (a bounded wait inside the run gave up; the
- * streams are incomplete and no column is returned), CUDA. */
+ * and may run again. Errors: INVALID_ARG (also before the plan's first run), OOM, TIMEOUT (a
+ * bounded wait inside the run gave up; the streams are incomplete and no column is returned),
+ * CUDA. */
 leco_status leco_batch_encode_plan_columns(leco_batch_encode_plan* plan, leco_stream_t stream, leco_column** out);
 
 /* Device bytes the plan holds (its tables, scratch and reserved words); 0 for NULL. */

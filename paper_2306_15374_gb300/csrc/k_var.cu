@@ -153,7 +153,52 @@ __global__ void __launch_bounds__(32) k_split_lanes(const T* __restrict__ v, uin
       uint64_t word = k == 0 ? 1ull : 0ull;  // the chunk's first position opens a partition
       const uint32_t x0 = k == 0 ? 1u : 0u;
       const uint32_t xe = clen - base < kSplitSeg ? clen - base : kSplitSeg;
-      if (nar) {
+      bool d32 = false;  // a whole segment whose differences, and the open partition's extremes, fit int32
+      if (nar && x0 == 0 && xe == kSplitSeg) {
+        d32 = dmax64 >= INT32_MIN && dmax64 <= INT32_MAX && dmin64 >= INT32_MIN && dmin64 <= INT32_MAX;
+        int64_t p = prev;
+#pragma unroll 8
+        for (uint32_t x = 0; x < kSplitSeg; x++) {
+          const int64_t w = (int64_t)ring[slot][x][lane];
+          const int64_t d = w - p;
+          d32 = d32 && d >= INT32_MIN && d <= INT32_MAX;
+          p = w;
+        }
+      }
+      if (d32) {
+        // the same steps in 32 bits: the extremes' difference stays below 2^32, so its bit length
+        // (and every decision) is that of the 64-bit step
+        int32_t mx = (int32_t)dmax64, mn = (int32_t)dmin64;
+        uint32_t pw = (uint32_t)prev;
+#pragma unroll 8
+        for (uint32_t x = 0; x < kSplitSeg; x++) {
+          const uint32_t w = (uint32_t)ring[slot][x][lane];
+          const int32_t d = (int32_t)(w - pw);
+          pw = w;
+          const uint32_t len = base + x - ii;
+          int32_t nmax = max(mx, d), nmin = min(mn, d);
+          if (len == 1) nmax = nmin = d;
+          const int next = 32 - __clz((int)((uint32_t)nmax - (uint32_t)nmin));
+          const int32_t C = (int32_t)(len + 1) * next - (int32_t)len * cur;
+          const bool take = len < cap && C <= tf32;
+          cur = take ? next : 0;
+          mx = take ? nmax : 0;
+          mn = take ? nmin : 0;
+          ii = take ? ii : base + x;
+          if (!take) word |= 1ull << x;
+        }
+        dmax64 = mx;
+        dmin64 = mn;
+        prev = (int64_t)ring[slot][kSplitSeg - 1][lane];
+      } else if (nar && x0 == 0 && xe == kSplitSeg) {
+        // a whole segment: unrolled, so that the shared-memory reads run ahead of the step chain
+#pragma unroll 8
+        for (uint32_t x = 0; x < kSplitSeg; x++) {
+          const int64_t w = (int64_t)ring[slot][x][lane];
+          if (!split_step_narrow(base + x, w - prev, ii, dmax64, dmin64, cur, cap, tf32)) word |= 1ull << x;
+          prev = w;
+        }
+      } else if (nar) {
         for (uint32_t x = x0; x < xe; x++) {
           const int64_t w = (int64_t)ring[slot][x][lane];
           if (!split_step_narrow(base + x, w - prev, ii, dmax64, dmin64, cur, cap, tf32)) word |= 1ull << x;

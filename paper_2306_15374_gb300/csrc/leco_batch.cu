@@ -536,6 +536,7 @@ struct leco_batch_encode_plan {
   PackItem* d_items = nullptr;
   uint64_t* words = nullptr;
   uint64_t words_cap = 0;  // 64-bit words reserved for the packed streams
+  uint64_t runs = 0;       // graph launches so far
   cudaStream_t capture = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -708,7 +709,9 @@ extern "C" leco_status leco_batch_encode_plan_create(const void* const* d_vals, 
 
 extern "C" leco_status leco_batch_encode_plan_run(leco_batch_encode_plan* plan, leco_stream_t stream) {
   if (!plan || !plan->exec) return LECO_ERR_INVALID_ARG;
-  return from_cuda(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+  const cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
+  if (e == cudaSuccess) plan->runs++;
+  return from_cuda(e);
 }
 
 extern "C" leco_status leco_batch_encode_plan_columns(leco_batch_encode_plan* plan, leco_stream_t stream,
@@ -717,6 +720,7 @@ extern "C" leco_status leco_batch_encode_plan_columns(leco_batch_encode_plan* pl
   const EncBatch& B = *plan->B;
   const uint32_t ncols = B.ncols;
   for (uint32_t c = 0; c < ncols; c++) out[c] = nullptr;
+  if (plan->runs == 0) return LECO_ERR_INVALID_ARG;  // nothing encoded yet
   cudaStream_t st = (cudaStream_t)stream;
   const EncPtrs p = enc_ptrs(B, plan->meta, plan->scr);
   std::vector<uint64_t> col_bits(ncols), word_base(ncols + 1);

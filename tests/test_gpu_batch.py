@@ -145,6 +145,8 @@ def test_batch_encode_plan_graph_matches_batch_encode(lc, bits):
     dvals = [to_dev(v, bits) for v in vals]
     plan = lc.leco_batch_encode_plan_create(dvals, models, Ls)
     assert lc.leco_batch_encode_plan_reserved_bytes(plan) >= sum(8 * n for n in lens)
+    with pytest.raises(lc.LecoError):  # nothing encoded before the first run
+        lc.leco_batch_encode_plan_columns(plan)
     kept = []
     for rnd in range(2):
         if rnd == 1:  # same shapes, new contents, same device buffers
