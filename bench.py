@@ -528,7 +528,7 @@ def run_leco(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b)
+        e2e = run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b, columns)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -591,7 +591,7 @@ def host_link_gbs(dev, nbytes=1 << 30, reps=3):
     return best
 
 
-def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
+def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b, columns):
     """Same step through the public API with host buffers: lookup indices copied in from pinned
     memory, decoded columns, lookup results and sums copied back to pinned memory. The copies run
     on their own streams: the device->host copy of one column's results overlaps the next column's
@@ -648,10 +648,22 @@ def run_e2e(args, leco, cols, comp, bounds, n, k, dev, stream, step_b):
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
+    # outside the timed region: the host buffers hold every column's decoded values, its lookups and
+    # its filter-sum (the copy streams delivered the right bytes)
+    ok = True
+    for d in DISTS:
+        v = columns[d]
+        ok = ok and np.array_equal(h_out[d].numpy().view(np.uint64), v)
+        ok = ok and np.array_equal(h_outk[d].numpy().view(np.uint64), v[h_idx[d].numpy().view(np.uint64)])
+        leco.leco_filter_sum(cols[d], bounds[d][0], bounds[d][1], res[0])
+        ok = ok and torch.equal(res[0].cpu(), h_res[d])
+    if not ok:
+        print("e2e: host results differ from the columns", file=sys.stderr)
     d2h = 3 * (8 * n + 8 * k + 24)
     return {"value": step_b / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
             "h2d_bytes_per_step": 3 * 8 * k, "d2h_bytes_per_step": d2h,
-            "host_link_gbs": link, "d2h_frac_of_link": d2h / (ms * 1e-3) / 1e9 / link["d2h"]}
+            "host_link_gbs": link, "d2h_frac_of_link": d2h / (ms * 1e-3) / 1e9 / link["d2h"],
+            "results_verified": bool(ok)}
 
 
 def gpu_setup():
