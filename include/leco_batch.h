@@ -31,7 +31,11 @@ typedef struct {
 leco_status leco_tune_scan(const leco_column* col, uint32_t op, uint64_t lo, uint64_t hi,
                            leco_stream_t stream, leco_scan_config* best);
 
-/* Write / read the tuning table as JSON (host file path). */
+/* Write / read the tuning table as JSON (host file path; host-only, no CUDA call). Save writes every
+ * entry, one per line. Load merges the file's entries into the process-wide table, keeping those
+ * that name a candidate the tuners can pick (scan: 2..8 stages, 4 or 8 consumer warps; batched
+ * encode: 1024, 2048 or 4096 values per pack item, 2..4 fit CTAs per SM) and skipping the rest.
+ * Errors: INVALID_ARG for a NULL path or a file that cannot be opened. */
 leco_status leco_tune_save(const char* path);
 leco_status leco_tune_load(const char* path);
 

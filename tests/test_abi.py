@@ -103,8 +103,51 @@ def test_host_side_argument_errors(built):
         assert L.leco_var_partition(fake, 10, 1, pol, 1, fake, ctypes.byref(m_out), None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_encode(fake, 10, 1, leco.variable(2.0, seeded=True), 1, None, ctypes.byref(h)) == \
         leco.LECO_ERR_INVALID_ARG
-    # the execution-unit probe takes kinds 0..3 and an output pointer
+    # the execution-unit probe takes kinds 0..4 and an output pointer
     r = ctypes.c_double(0.0)
     assert L.leco_probe_throughput(5, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_probe_throughput(-1, ctypes.byref(r), None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_probe_throughput(0, None, None) == leco.LECO_ERR_INVALID_ARG
+
+
+def test_tuning_table_file_round_trip(built, tmp_path):
+    """The tuning table's file form is host-only: load merges the entries that name a candidate
+    the tuners can pick (2..8 stages with 4 or 8 consumer warps; 1024/2048/4096 values per pack
+    item with 2..4 fit CTAs per SM) and skips the rest, save writes the whole table back as JSON.
+    The keys used here (operation 7, dtype 99) name no scan or encode the library runs."""
+    import json
+
+    from paper_2306_15374_gb300 import leco
+
+    L = leco.lib()
+    src = tmp_path / "in.json"
+    src.write_text(
+        '{"scan_configs": [\n'
+        '  {"op": 7, "dtype": 99, "width_bucket": 0, "stages": 3, "consumer_warps": 8},\n'
+        '  {"op": 7, "dtype": 99, "width_bucket": 1, "stages": 9, "consumer_warps": 4},\n'
+        '  {"op": 7, "dtype": 99, "width_bucket": 2, "stages": 2, "consumer_warps": 6},\n'
+        '  {"op": 7, "dtype": 99, "width_bucket": 3, "stages": 8, "consumer_warps": 4}\n'
+        '], "encode_configs": [\n'
+        '  {"dtype": 99, "item_values": 2048, "fit_ctas": 3},\n'
+        '  {"dtype": 98, "item_values": 3000, "fit_ctas": 3},\n'
+        '  {"dtype": 97, "item_values": 1024, "fit_ctas": 5}\n'
+        ']}\n')
+    assert L.leco_tune_load(str(src).encode()) == leco.LECO_OK
+    out = tmp_path / "out.json"
+    assert L.leco_tune_save(str(out).encode()) == leco.LECO_OK
+    table = json.loads(out.read_text())
+    mine = {(e["op"], e["dtype"], e["width_bucket"]): (e["stages"], e["consumer_warps"])
+            for e in table["scan_configs"] if e["dtype"] == 99}
+    assert mine == {(7, 99, 0): (3, 8), (7, 99, 3): (8, 4)}
+    enc = {e["dtype"]: (e["item_values"], e["fit_ctas"]) for e in table["encode_configs"] if e["dtype"] >= 97}
+    assert enc == {99: (2048, 3)}
+    # the saved file loads back to the same table
+    assert L.leco_tune_load(str(out).encode()) == leco.LECO_OK
+    again = tmp_path / "again.json"
+    assert L.leco_tune_save(str(again).encode()) == leco.LECO_OK
+    assert json.loads(again.read_text()) == table
+    # a file that cannot be opened, or no path at all, is refused
+    assert L.leco_tune_load(str(tmp_path / "missing.json").encode()) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_tune_load(None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_tune_save(None) == leco.LECO_ERR_INVALID_ARG
+    assert L.leco_tune_save(str(tmp_path / "no" / "dir.json").encode()) == leco.LECO_ERR_INVALID_ARG
