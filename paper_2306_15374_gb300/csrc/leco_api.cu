@@ -510,7 +510,9 @@ leco_status leco_sync(const leco_column* col, leco_stream_t stream) {
   if (e != cudaSuccess) return LECO_ERR_CUDA;
   uint32_t flags = 0;
   e = cudaMemcpy(&flags, col->status, 4, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && flags) e = cudaMemset(col->status, 0, 4);
+  // cleared in stream order and waited for, so a later call on any stream cannot have its flag erased
+  if (e == cudaSuccess && flags) e = cudaMemsetAsync(col->status, 0, 4, (cudaStream_t)stream);
+  if (e == cudaSuccess && flags) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return LECO_ERR_CUDA;
   if (flags & kStatIndexRange) return LECO_ERR_INDEX_RANGE;
   if (flags & kStatCorrupt) return LECO_ERR_CORRUPT;

@@ -157,6 +157,10 @@ leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* 
     e = cudaMemcpy(p->d_cols, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !items.empty())
     e = cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  // the memset and the copies from pageable memory ran on the legacy stream, and a copy may return
+  // before its DMA lands: wait for them, so a run on any stream (non-blocking ones included) finds
+  // the tables in place
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   if (e != cudaSuccess) {
     plan_release(p);
     return from_cuda(e);
@@ -249,7 +253,10 @@ leco_status leco_batch_plan_sync(leco_batch_plan* plan, leco_stream_t stream) {
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LECO_ERR_CUDA;
   uint32_t flags = 0;
   if (cudaMemcpy(&flags, plan->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LECO_ERR_CUDA;
-  if (flags && cudaMemset(plan->d_status, 0, 4) != cudaSuccess) return LECO_ERR_CUDA;
+  // cleared in stream order and waited for, so a later run on any stream cannot have its flag erased
+  if (flags && (cudaMemsetAsync(plan->d_status, 0, 4, (cudaStream_t)stream) != cudaSuccess ||
+                cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess))
+    return LECO_ERR_CUDA;
   if (flags & kStatTimeout) return LECO_ERR_TIMEOUT;
   if (flags & kStatCorrupt) return LECO_ERR_CORRUPT;
   if (flags & kStatIndexRange) return LECO_ERR_INDEX_RANGE;
@@ -681,16 +688,22 @@ extern "C" leco_status leco_batch_encode_plan_create(const void* const* d_vals, 
   if (e == cudaSuccess) e = cudaMalloc((void**)&pl->words, 8 * cap);
   const EncPtrs p = enc_ptrs(B, pl->meta, pl->scr);
   const std::vector<ColumnView> views = enc_views(B, p, n, L);
-  if (e == cudaSuccess) e = cudaMemcpy(pl->d_ec, B.ec.data(), sizeof(EncCol) * ncols, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(pl->d_bases, B.part_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice);
+  // the tables go in order on the caller's stream, ahead of the partition-column kernel that reads
+  // them; the stream is synchronized below, before any graph run
+  const cudaStream_t cst = (cudaStream_t)stream;
   if (e == cudaSuccess)
-    e = cudaMemcpy(pl->d_bases + (ncols + 1), B.tile_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(pl->d_ec, B.ec.data(), sizeof(EncCol) * ncols, cudaMemcpyHostToDevice, cst);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(pl->d_bases, B.part_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, cst);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(pl->d_bases + (ncols + 1), B.tile_base.data(), 8 * (ncols + 1), cudaMemcpyHostToDevice, cst);
   if (e == cudaSuccess && nitems)
-    e = cudaMemcpy(pl->d_items, B.items.data(), sizeof(PackItem) * nitems, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(pl->d_views, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(pl->d_items, B.items.data(), sizeof(PackItem) * nitems, cudaMemcpyHostToDevice, cst);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(pl->d_views, views.data(), sizeof(ColumnView) * ncols, cudaMemcpyHostToDevice, cst);
   // the partition -> column table depends on the shapes only: filled once, outside the graph
-  if (e == cudaSuccess) e = launch_part_col(pl->d_bases, ncols, B.P, p.part_col, (cudaStream_t)stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = launch_part_col(pl->d_bases, ncols, B.P, p.part_col, cst);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cst);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(pl->capture, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {

@@ -435,7 +435,10 @@ leco_status admit_common(leco_server* s, leco_column* col, uint64_t n, int dtype
   if (id >= s->cols.size()) return LECO_ERR_BUDGET;
   if (col) {
     s->h_views[id] = view_of(col);
-    if (cudaMemcpy(s->d_views + id, &s->h_views[id], sizeof(ColumnView), cudaMemcpyHostToDevice) != cudaSuccess)
+    // a copy from pageable memory may return before its DMA lands, and the serving streams are
+    // non-blocking: wait for the legacy stream, so the first batch that names this column finds it
+    if (cudaMemcpy(s->d_views + id, &s->h_views[id], sizeof(ColumnView), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess)
       return LECO_ERR_CUDA;
     s->stage_bytes = std::max(s->stage_bytes, col->stage_bytes);
     s->poly = s->poly || col->poly != nullptr;
