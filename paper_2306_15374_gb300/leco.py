@@ -213,6 +213,18 @@ def _dev(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _room(t, nbytes: int, what: str) -> None:
+    """A device buffer the call writes must hold nbytes: the library cannot see its size, and a
+    short one would be written past its end on the device."""
+    if t is not None and t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{what}: buffer of {t.numel() * t.element_size()} bytes, needs {nbytes}")
+
+
+def _indices(t, what: str) -> None:
+    if t.element_size() != 8:
+        raise ValueError(f"{what}: indices must be 8-byte integers, got {t.dtype}")
+
+
 def _check(status: int, what: str):
     if status != LECO_OK:
         raise LecoError(status, what)
@@ -223,6 +235,7 @@ class Column:
 
     def __init__(self, handle: ctypes.c_void_p):
         self._h = handle
+        self._shape = None  # (n, value bytes), read once: a column is immutable after encode
 
     @property
     def handle(self) -> ctypes.c_void_p:
@@ -259,6 +272,13 @@ class Column:
     def dtype(self) -> int:
         return self.stats()["dtype"]
 
+    def shape(self) -> tuple:
+        """(values, bytes per value) of the column."""
+        if self._shape is None:
+            st = self.stats()
+            self._shape = (int(st["n"]), 4 if st["dtype"] == LECO_U32 else 8)
+        return self._shape
+
 
 # ------------------------------------------------------------------------------ entry points
 
@@ -283,6 +303,7 @@ def leco_var_partition(values, starts_out, policy: PartitionPolicy, model: int =
                        stream=None) -> int:
     """Split + merge on the device; starts_out (int64 CUDA tensor of n+1) gets m+1 starts; returns m."""
     m = ctypes.c_uint64(0)
+    _room(starts_out, 8 * (values.numel() + 1), "leco_var_partition")
     _check(lib().leco_var_partition(_dev(values), values.numel(), _dtype_of(values), policy, model,
                                     _dev(starts_out), ctypes.byref(m), _stream(stream)),
            "leco_var_partition")
@@ -299,21 +320,27 @@ def leco_encode_with_starts(values, starts, m: int, model: int = LECO_MODEL_LINE
 
 
 def leco_decode_all(col: Column, out, stream=None) -> None:
+    n, vb = col.shape()
+    _room(out, n * vb, "leco_decode_all")
     _check(lib().leco_decode_all(col.handle, _dev(out), _stream(stream)), "leco_decode_all")
 
 
 def leco_decode_range(col: Column, begin: int, count: int, out, stream=None) -> None:
+    _room(out, int(count) * col.shape()[1], "leco_decode_range")
     _check(lib().leco_decode_range(col.handle, int(begin), int(count), _dev(out), _stream(stream)),
            "leco_decode_range")
 
 
 def leco_random_access(col: Column, idx, out, stream=None) -> None:
+    _indices(idx, "leco_random_access")
+    _room(out, idx.numel() * col.shape()[1], "leco_random_access")
     _check(lib().leco_random_access(col.handle, _dev(idx), idx.numel(), _dev(out), _stream(stream)),
            "leco_random_access")
 
 
 def leco_filter_sum(col: Column, lo: int, hi: int, out, flags: int = 0, stream=None) -> None:
     """out: CUDA tensor of >= 3 int64 (count, sum_lo, sum_hi)."""
+    _room(out, 24, "leco_filter_sum")
     _check(lib().leco_filter_sum(col.handle, int(lo), int(hi), int(flags), _dev(out), _stream(stream)),
            "leco_filter_sum")
 

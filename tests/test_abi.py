@@ -151,3 +151,45 @@ def test_tuning_table_file_round_trip(built, tmp_path):
     assert L.leco_tune_load(None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_tune_save(None) == leco.LECO_ERR_INVALID_ARG
     assert L.leco_tune_save(str(tmp_path / "no" / "dir.json").encode()) == leco.LECO_ERR_INVALID_ARG
+
+
+def test_binding_refuses_short_output_buffers(built):
+    """The library cannot see a device buffer's size, so the binding checks every buffer a call
+    writes before the call: a short one would otherwise be written past its end on the device.
+    The column here is a stand-in whose size is set by hand; its handle is never passed on."""
+    import ctypes
+
+    import torch
+
+    from paper_2306_15374_gb300 import leco
+
+    col = leco.Column(ctypes.c_void_p(1))
+    try:
+        col._shape = (1000, 8)
+        i64 = torch.int64
+        with pytest.raises(ValueError, match="needs 8000"):
+            leco.leco_decode_all(col, torch.empty(999, dtype=i64))
+        with pytest.raises(ValueError, match="needs 800"):
+            leco.leco_decode_range(col, 10, 100, torch.empty(99, dtype=i64))
+        with pytest.raises(ValueError, match="8-byte"):
+            leco.leco_random_access(col, torch.zeros(50, dtype=torch.int32), torch.empty(50, dtype=i64))
+        with pytest.raises(ValueError, match="needs 400"):
+            leco.leco_random_access(col, torch.zeros(50, dtype=i64), torch.empty(49, dtype=i64))
+        with pytest.raises(ValueError, match="needs 24"):
+            leco.leco_filter_sum(col, 0, 1, torch.empty(2, dtype=i64))
+        with pytest.raises(ValueError, match="needs 808"):
+            leco.leco_var_partition(torch.zeros(100, dtype=i64), torch.empty(100, dtype=i64), leco.variable(0.1))
+        # buffers of the right size pass the checks and stop only at the device check (these are
+        # host tensors); a 32-bit column needs 4 bytes per value
+        for call in (lambda: leco.leco_decode_all(col, torch.empty(1000, dtype=i64)),
+                     lambda: leco.leco_random_access(col, torch.zeros(50, dtype=i64), torch.empty(50, dtype=i64)),
+                     lambda: leco.leco_filter_sum(col, 0, 1, torch.empty(3, dtype=i64))):
+            with pytest.raises(ValueError, match="CUDA tensor"):
+                call()
+        col._shape = (1000, 4)
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            leco.leco_decode_all(col, torch.empty(1000, dtype=torch.int32))
+        with pytest.raises(ValueError, match="needs 4000"):
+            leco.leco_decode_all(col, torch.empty(999, dtype=torch.int32))
+    finally:
+        col._h = None  # the stand-in handle is not a column: nothing to free
