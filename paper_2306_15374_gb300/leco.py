@@ -467,6 +467,18 @@ def _ptrs(outs):
     return (ctypes.c_void_p * max(len(outs), 1))(*[o.data_ptr() for o in outs])
 
 
+def _outs_room(cols, outs, what: str) -> None:
+    """outs[c] receives every value of cols[c]: one contiguous device buffer of at least n * value
+    bytes per column."""
+    if len(outs) != len(cols):
+        raise ValueError(f"{what}: {len(cols)} columns but {len(outs)} outputs")
+    for c, o in zip(cols, outs):
+        n, vb = c.shape()
+        _room(o, n * vb, what)
+        if not o.is_cuda or not o.is_contiguous():
+            raise ValueError(f"{what}: outputs must be contiguous CUDA tensors")
+
+
 class BatchPlan:
     """Owning handle of a leco_batch_plan; keeps its columns and outputs alive."""
 
@@ -492,6 +504,7 @@ class BatchPlan:
 
 
 def leco_batch_plan_create(cols, outs) -> BatchPlan:
+    _outs_room(cols, outs, "leco_batch_plan_create")
     h = ctypes.c_void_p()
     _check(lib().leco_batch_plan_create(_handles(cols), _ptrs(outs), len(cols), ctypes.byref(h)),
            "leco_batch_plan_create")
@@ -527,6 +540,7 @@ def leco_batch_plan_free(plan: BatchPlan) -> None:
 
 
 def leco_batch_decode(cols, outs, stream=None) -> None:
+    _outs_room(cols, outs, "leco_batch_decode")
     _check(lib().leco_batch_decode(_handles(cols), _ptrs(outs), len(cols), _stream(stream)), "leco_batch_decode")
 
 
@@ -536,6 +550,7 @@ class Server:
     def __init__(self, handle):
         self._h = handle
         self._pending = {}
+        self._width = {}  # bytes per value of each admitted column, for the output checks
 
     @property
     def handle(self):
@@ -548,6 +563,7 @@ class Server:
             lib().leco_server_destroy(self._h)
             self._h = None
             self._pending.clear()
+            self._width.clear()
 
     def __del__(self):
         try:
@@ -569,8 +585,10 @@ def leco_server_create(budget_bytes: int, max_inflight: int = 0, max_batch_reque
 def leco_server_admit(server: Server, col: Column) -> int:
     """The server takes ownership of the column (the Column handle is emptied)."""
     cid = ctypes.c_uint32(0)
+    vb = col.shape()[1]
     _check(lib().leco_server_admit(server.handle, col.handle, ctypes.byref(cid)), "leco_server_admit")
     col._h = None
+    server._width[int(cid.value)] = vb
     return int(cid.value)
 
 
@@ -578,11 +596,26 @@ def leco_server_admit_mock(server: Server, n: int, dtype: int, nbytes: int) -> i
     cid = ctypes.c_uint32(0)
     _check(lib().leco_server_admit_mock(server.handle, int(n), int(dtype), int(nbytes), ctypes.byref(cid)),
            "leco_server_admit_mock")
+    server._width[int(cid.value)] = 4 if int(dtype) == LECO_U32 else 8
     return int(cid.value)
 
 
 def leco_server_evict(server: Server, col_id: int) -> None:
     _check(lib().leco_server_evict(server.handle, int(col_id)), "leco_server_evict")
+    server._width.pop(int(col_id), None)
+
+
+def _host_room(server: Server, col_id: int, out, count: int, what: str) -> None:
+    """The server writes count values of the column's width into out, a host array it cannot
+    size: a short or non-contiguous one would be written past its end. Unknown columns are left to
+    the library, which refuses them."""
+    vb = server._width.get(int(col_id))
+    if vb is None:
+        return
+    if not out.flags["C_CONTIGUOUS"] or not out.flags["WRITEABLE"]:
+        raise ValueError(f"{what}: out must be a writable C-contiguous array")
+    if out.nbytes < int(count) * vb:
+        raise ValueError(f"{what}: out of {out.nbytes} bytes, needs {int(count) * vb}")
 
 
 def leco_server_submit_lookup(server: Server, col_id: int, idx, out) -> int:
@@ -590,6 +623,7 @@ def leco_server_submit_lookup(server: Server, col_id: int, idx, out) -> int:
     import numpy as np
 
     idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    _host_room(server, col_id, out, idx.size, "leco_server_submit_lookup")
     rid = ctypes.c_uint64(0)
     _check(lib().leco_server_submit_lookup(server.handle, int(col_id), idx.ctypes.data_as(ctypes.c_void_p), idx.size,
                                            out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid)),
@@ -599,6 +633,7 @@ def leco_server_submit_lookup(server: Server, col_id: int, idx, out) -> int:
 
 
 def leco_server_submit_range(server: Server, col_id: int, begin: int, count: int, out) -> int:
+    _host_room(server, col_id, out, count, "leco_server_submit_range")
     rid = ctypes.c_uint64(0)
     _check(lib().leco_server_submit_range(server.handle, int(col_id), int(begin), int(count),
                                           out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid)),

@@ -191,5 +191,13 @@ def test_binding_refuses_short_output_buffers(built):
             leco.leco_decode_all(col, torch.empty(1000, dtype=torch.int32))
         with pytest.raises(ValueError, match="needs 4000"):
             leco.leco_decode_all(col, torch.empty(999, dtype=torch.int32))
+        # batched decode: one output per column, each holding that column's values
+        for fn in (leco.leco_batch_decode, leco.leco_batch_plan_create):
+            with pytest.raises(ValueError, match="2 columns but 1 outputs"):
+                fn([col, col], [torch.empty(1000, dtype=torch.int32)])
+            with pytest.raises(ValueError, match="needs 4000"):
+                fn([col, col], [torch.empty(999, dtype=torch.int32), torch.empty(1000, dtype=torch.int32)])
+            with pytest.raises(ValueError, match="CUDA tensors"):
+                fn([col], [torch.empty(1000, dtype=torch.int32)])
     finally:
         col._h = None  # the stand-in handle is not a column: nothing to free

@@ -164,3 +164,38 @@ def test_concurrent_submitters_and_poisson_driver(lc):
     st = lc.leco_server_stats_get(s)
     assert sent > 100 and st["completed"] == sent and st["failed"] == 0
     s.destroy()
+
+
+def test_binding_refuses_short_host_outputs(lc):
+    """The server writes each request's values, at the column's width, into the caller's host array:
+    the binding refuses an array that is too short, strided or read-only before the request is
+    queued; an array of exactly the right size is served."""
+    s = lc.leco_server_create(1 << 30, mock=True)
+    a = lc.leco_server_admit_mock(s, 1000, lc.LECO_U64, 10)
+    b = lc.leco_server_admit_mock(s, 1000, lc.LECO_U32, 10)
+    idx = np.array([1, 2, 3, 4], dtype=np.uint64)
+    with pytest.raises(ValueError, match="needs 32"):
+        lc.leco_server_submit_lookup(s, a, idx, np.zeros(3, dtype=np.uint64))
+    with pytest.raises(ValueError, match="needs 32"):
+        lc.leco_server_submit_lookup(s, a, idx, np.zeros(4, dtype=np.uint32))  # 32-bit slots, 64-bit column
+    with pytest.raises(ValueError, match="needs 80"):
+        lc.leco_server_submit_range(s, a, 0, 10, np.zeros(9, dtype=np.uint64))
+    with pytest.raises(ValueError, match="contiguous"):
+        lc.leco_server_submit_range(s, a, 0, 10, np.zeros(20, dtype=np.uint64)[::2])
+    ro = np.zeros(10, dtype=np.uint64)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError, match="writable"):
+        lc.leco_server_submit_range(s, a, 0, 10, ro)
+    # exact sizes: 4 x 4 bytes for the 32-bit column, 10 x 8 for the 64-bit one
+    out32, out64 = np.zeros(4, dtype=np.uint32), np.zeros(10, dtype=np.uint64)
+    r1 = lc.leco_server_submit_lookup(s, b, idx, out32)
+    r2 = lc.leco_server_submit_range(s, a, 5, 10, out64)
+    assert lc.leco_server_wait(s, r1) == lc.LECO_OK and lc.leco_server_wait(s, r2) == lc.LECO_OK
+    assert out32.tolist() == [mock_value(b, int(i), 32) for i in idx]
+    assert out64.tolist() == [mock_value(a, i, 64) for i in range(5, 15)]
+    # after eviction the id is unknown: the library refuses it
+    lc.leco_server_evict(s, a)
+    with pytest.raises(lc.LecoError) as e:
+        lc.leco_server_submit_range(s, a, 0, 1, np.zeros(1, dtype=np.uint64))
+    assert e.value.status == lc.LECO_ERR_INVALID_ARG
+    s.destroy()
