@@ -312,6 +312,9 @@ def leco_var_partition(values, starts_out, policy: PartitionPolicy, model: int =
 
 def leco_encode_with_starts(values, starts, m: int, model: int = LECO_MODEL_LINEAR,
                             stream=None) -> Column:
+    _indices(starts, "leco_encode_with_starts")
+    if starts.numel() < int(m) + 1:
+        raise ValueError(f"leco_encode_with_starts: {starts.numel()} starts, needs m + 1 = {int(m) + 1}")
     h = ctypes.c_void_p()
     _check(lib().leco_encode_with_starts(_dev(values), values.numel(), _dtype_of(values), _dev(starts),
                                          int(m), model, _stream(stream), ctypes.byref(h)),
@@ -677,10 +680,12 @@ def leco_server_destroy(server: Server) -> None:
 
 def _batch_args(values, models, Ls):
     k = len(values)
+    if len(models) != k or len(Ls) != k:
+        raise ValueError(f"{k} columns but {len(models)} models and {len(Ls)} partition sizes")
     dt = _dtype_of(values[0]) if k else LECO_U64
     if any(_dtype_of(v) != dt for v in values):
         raise ValueError("all columns of a batched encode must have the same value width")
-    vals = (ctypes.c_void_p * max(k, 1))(*[v.data_ptr() for v in values])
+    vals = (ctypes.c_void_p * max(k, 1))(*[_dev(v).value or 0 for v in values])
     ns = (ctypes.c_uint64 * max(k, 1))(*[v.numel() for v in values])
     ms = (ctypes.c_int * max(k, 1))(*[int(m) for m in models])
     ls = (ctypes.c_uint32 * max(k, 1))(*[int(x) for x in Ls])

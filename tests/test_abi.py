@@ -201,3 +201,22 @@ def test_binding_refuses_short_output_buffers(built):
                 fn([col], [torch.empty(1000, dtype=torch.int32)])
     finally:
         col._h = None  # the stand-in handle is not a column: nothing to free
+
+
+def test_binding_checks_encode_arguments(built):
+    """Batched encodes take one model and one partition size per column and device tensors only;
+    given starts are 8-byte and hold m + 1 entries (the library reads that many)."""
+    import torch
+
+    from paper_2306_15374_gb300 import leco
+
+    v = torch.zeros(100, dtype=torch.int64)
+    for fn in (leco.leco_batch_encode, leco.leco_batch_encode_plan_create, leco.leco_tune_batch_encode):
+        with pytest.raises(ValueError, match="1 columns but 2 models and 1 partition sizes"):
+            fn([v], [1, 1], [16])
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            fn([v], [1], [16])
+    with pytest.raises(ValueError, match="8-byte"):
+        leco.leco_encode_with_starts(v, torch.tensor([0, 100], dtype=torch.int32), 1)
+    with pytest.raises(ValueError, match="needs m \\+ 1 = 3"):
+        leco.leco_encode_with_starts(v, torch.tensor([0, 100], dtype=torch.int64), 2)
