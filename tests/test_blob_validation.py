@@ -168,3 +168,52 @@ def test_partition_longer_than_the_length_cap(lc):
         words = np.zeros(2, dtype=U64)
         blob = make_blob(rec, words, n, 0, 1, 1, 1, starts=np.array([0, n], dtype=U64))
         assert (_status(lc, blob) == lc.LECO_ERR_CORRUPT) == want_corrupt
+
+
+def test_polynomial_blocks_must_be_evaluable(lc, orc):
+    """A polynomial partition's 320-bit block (T, K1..K3, exponent word) is checked on the host:
+    exponents at most 62 in the low three bytes, |K_j| <= 2^61, and the exponent spread behind each
+    nonzero K_j within the room its Gram term leaves in 124 bits (49, 34 and 20 for j = 1, 2, 3).
+    A spread exactly at the room passes; one more is refused."""
+    POLY = 2
+    v = W.sine_mixture(20_000, seed=9)
+    rec, words = orc.encode_fixed(v, 1000, POLY)
+    n = len(v)
+    poly = np.flatnonzero(orc.rec_poly(rec["word3"]))
+    assert poly.size
+    big0 = int.from_bytes(words.tobytes(), "little")
+
+    def field(pos):
+        return (big0 >> pos) & ((1 << 64) - 1)
+
+    def blob(fields):
+        big = big0
+        for pos, value in fields.items():
+            big = (big & ~(((1 << 64) - 1) << pos)) | ((value & ((1 << 64) - 1)) << pos)
+        w = np.frombuffer(big.to_bytes(8 * len(words), "little"), dtype=U64).copy()
+        return make_blob(rec, w, n, 1000, 1, 0, POLY)
+
+    assert _status(lc, blob({})) != lc.LECO_ERR_CORRUPT
+    # a partition whose block has a nonzero K_j, for each j that has one somewhere
+    room = (49, 34, 20)
+    tested = set()
+    for p in poly:
+        off = int(orc.rec_offset(rec["word3"][int(p)]))
+        E = field(off + 256)
+        assert _status(lc, blob({off + 256: E | (1 << 30)})) == lc.LECO_ERR_CORRUPT  # bits above the exponents
+        assert _status(lc, blob({off + 256: (E & ~0xFF) | 63})) == lc.LECO_ERR_CORRUPT  # exponent 63
+        assert _status(lc, blob({off + 64: 1 << 62})) == lc.LECO_ERR_CORRUPT  # |K1| > 2^61
+        assert _status(lc, blob({off + 64: -(1 << 62)})) == lc.LECO_ERR_CORRUPT
+        assert _status(lc, blob({off + 64: 1 << 61})) != lc.LECO_ERR_CORRUPT  # |K1| = 2^61 is allowed
+        for j in range(3):
+            if j in tested or field(off + 64 * (j + 1)) == 0:
+                continue
+            tested.add(j)
+            for spread, corrupt in ((room[j], False), (room[j] + 1, True)):
+                # s_j = 0 and the other two exponents = spread: S - s_j = spread; every other term
+                # has S - s_i = 0
+                e = sum((0 if i == j else spread) << (8 * i) for i in range(3))
+                assert (_status(lc, blob({off + 256: e})) == lc.LECO_ERR_CORRUPT) == corrupt, (j, spread)
+        if len(tested) == 3:
+            break
+    assert tested == {0, 1, 2}  # every Gram term is used by some partition of this column
