@@ -319,6 +319,41 @@ def test_empty_column(orc):
     assert orc.filter_sum(rec, words, 0, 0, (1 << 64) - 1) == (0, 0)
 
 
+def test_model_bound_pruning_of_section_5_1(orc):
+    """§5.1.1's pruning bound on the oracle's encodings: every value lies within the signed b-bit
+    range around its prediction (pred(k) - 2^(b-1) <= v_k < pred(k) + 2^(b-1)), the prediction
+    never decreases inside a partition with theta1 >= 0, so once pred(k) - 2^(b-1) > alpha every
+    later value of that partition is above alpha and a less-than filter may stop there. Predictions
+    are recomputed with Python floats (binary64, one rounding per operation), not by the oracle."""
+    cols = [W.cfg1(20_000), W.sorted_lognormal(20_000, 1e9, 2.0, seed=3),
+            W.piecewise_linear(20_000, segments=12, mean_len=1500, max_k=50, seed=5),
+            W.linear_noise(20_000, 1 << 40, -977, 5000, seed=8)]  # decreasing: theta1 < 0
+    skipped = 0
+    for v in cols:
+        for L in (256, 1000):
+            rec, words = orc.encode_fixed(v, L, orc.MODEL_LINEAR)
+            assert (orc.decode(rec, words, v.size) == v).all()
+            widths = orc.rec_width(rec["word3"])
+            for p in range(len(rec)):
+                a = int(rec["start"][p])
+                seg = [int(x) for x in v[a:min(a + L, v.size)]]
+                t0, t1, b = float(rec["theta0"][p]), float(rec["theta1"][p]), int(widths[p])
+                pred = [math.floor(t1 * float(k) + t0) for k in range(len(seg))]
+                half = 1 << (b - 1) if b else 0
+                for k, x in enumerate(seg):
+                    r = s64(x - pred[k])
+                    assert (-half <= r < half) if b else r == 0, (p, k)
+                if t1 < 0:
+                    continue
+                assert all(pred[k] <= pred[k + 1] for k in range(len(seg) - 1))
+                alpha = seg[len(seg) // 2]  # a predicate v < alpha that cuts the partition
+                stop = next((k for k in range(len(seg)) if pred[k] - half > alpha), None)
+                if stop is not None:
+                    assert all(x > alpha for x in seg[stop:])
+                    skipped += len(seg) - stop
+    assert skipped > 0  # the bound does prune on these inputs
+
+
 def test_lookup_and_filter_sum_brute_force(orc):
     for v, L in ((W.cfg1(30000), 1024), (W.adversarial_u64(5000), 64),
                  (W.sorted_lognormal(8000, 1e9, 2.0, seed=9), 4096)):
