@@ -72,3 +72,21 @@ def test_variable_partitions_tile_and_are_lossless(orc, data, bits, tau):
     assert (np.diff(starts.astype(np.int64)) > 0).all() or v.size == 0
     rec, words = orc.encode(v, starts, orc.MODEL_LINEAR)
     _check_queries(orc, rec, words, v, bits, 0, data.draw)
+
+
+@settings(max_examples=60, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(data=st.data(), bits=st.sampled_from([64, 32]), L=st.sampled_from([63, 64, 65, 128, 300]))
+def test_polynomial_model_is_lossless(orc, data, bits, L):
+    """The per-partition choice among constant, linear, quadratic and cubic (§3.1, §4) on arbitrary
+    columns, also sampled smooth ones where higher degrees win: lossless, with lookups and sums."""
+    if data.draw(st.booleans()):
+        v = data.draw(columns(bits))
+    else:  # an integer cubic plus small noise: the polynomial candidates apply
+        n = data.draw(st.integers(0, 400))
+        c = [data.draw(st.integers(-50, 50)) for _ in range(4)]
+        noise = data.draw(st.lists(st.integers(0, 3), min_size=n, max_size=n))
+        top = (1 << bits) - 1
+        v = np.array([(c[0] * i ** 3 + c[1] * i ** 2 + c[2] * i + (1 << (bits - 2)) + noise[i]) & top
+                      for i in range(n)], dtype=np.uint64)
+    rec, words = orc.encode_fixed(v, L, 2)
+    _check_queries(orc, rec, words, v, bits, L, data.draw)
