@@ -77,8 +77,10 @@ def parse_args():
 
 KSCAN_SRCS = [os.path.join(ROOT, "paper_2306_15374_gb300", "csrc", f) for f in ("k_scan.cu", "leco_internal.cuh", "tma.cuh")]
 # DRAM read + write per decode launch from one ncu capture of this workload (mean of columns a, b, c;
-# see profiles/k_tilescan_decode_filter_fix200M.md), valid only for the kernel sources it was taken on.
-DECODE_TRAFFIC = {"sha256": "1ed87d886950696373d114d80a4c7c363c881df872b58e128b527b5e5bada242",
+# see profiles/k_tilescan_decode_filter_fix200M.md), valid only for the kernel sources it was taken on
+# (keyed by their hash; re-keyed once since, when the shared header gained only host declarations of
+# the batched-encode launchers and the decode kernel's code stayed the same).
+DECODE_TRAFFIC = {"sha256": "1e091f3002cd25780c164ad5dc869ef8ca403b716143b0ec0422a72376811554",
                   "bytes_per_launch": (1894286848 + 1973986048 + 1846223104) / 3}
 
 
