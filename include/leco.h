@@ -132,18 +132,18 @@ typedef struct {
 /* ------------------------------------------------------------------------------------------ */
 /* Library */
 
-/* Human-readable name of a status code; never NULL. */
+/* Human-readable name of a status code; never NULL. Library plumbing; the paper has no counterpart. */
 const char* leco_status_string(leco_status s);
 
-/* ABI version (major * 10000 + minor * 100 + patch). */
+/* ABI version (major * 10000 + minor * 100 + patch). Library plumbing; the paper has no counterpart. */
 uint32_t leco_version(void);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Encode (§3: Partitioner -> Regressor -> Encoder)
  *
  * d_values: n values of `dtype` (4 or 8 bytes each, contiguous) on the device, caller-owned, read
- * only. policy: fixed, variable or auto partitions. model: constant, linear or polynomial. On success *out receives
- * a new column (free with leco_column_free). The call synchronizes `stream` once (to size the
+ * only. policy: fixed, variable or auto partitions. model: constant, linear or polynomial. On
+ * success *out receives a new column (free with leco_column_free). The call synchronizes `stream` once (to size the
  * residual stream) and returns with the column's encode enqueued on `stream`.
  * Errors: INVALID_ARG (NULL out, NULL d_values with n > 0, part_size out of range, tau outside
  * [0,1], bad enum), OOM, CUDA. */
@@ -158,9 +158,10 @@ leco_status leco_var_partition(const void* d_values, uint64_t n, leco_dtype dtyp
                                leco_partition_policy policy, leco_model model,
                                uint64_t* d_starts_out, uint64_t* m_out, leco_stream_t stream);
 
-/* Encode with caller-chosen partition starts (d_starts: m+1 uint64 on the device, starts[0] = 0,
- * starts[m] = n, strictly increasing, each partition at most 2^24 long). The column is a variable
- * partition column. Errors as leco_encode. */
+/* Encode with caller-chosen partition starts (§3.2: any partitioning the Partitioner hands over; §3.1
+ * fit and §3.3 packing per partition as in leco_encode). d_starts: m+1 uint64 on the device,
+ * caller-owned, read only: starts[0] = 0, starts[m] = n, strictly increasing, each partition at most
+ * 2^24 long. The column is a variable partition column. Errors as leco_encode. */
 leco_status leco_encode_with_starts(const void* d_values, uint64_t n, leco_dtype dtype,
                                     const uint64_t* d_starts, uint64_t m, leco_model model,
                                     leco_stream_t stream, leco_column** out);
@@ -196,25 +197,30 @@ leco_status leco_encode_fixed_noalloc(const void* d_values, uint64_t n, leco_dty
  * Full decompression: d_out receives all n values (n * value bytes, caller-owned, device). */
 leco_status leco_decode_all(const leco_column* col, void* d_out, leco_stream_t stream);
 
-/* Range decompression of positions [begin, begin + count): d_out receives count values.
- * Errors: INVALID_ARG if begin + count > n. */
+/* Range decompression (§3.3 Decoder) of positions [begin, begin + count): d_out receives count
+ * values (count * value bytes, caller-owned, device). Errors: INVALID_ARG if begin + count > n. */
 leco_status leco_decode_range(const leco_column* col, uint64_t begin, uint64_t count, void* d_out,
                               leco_stream_t stream);
 
-/* Batched point lookups: d_out[q] = value at position d_idx[q] for q < k (input order, duplicates
- * allowed). Fixed partitions use j = i / L; variable partitions a search over the starts. An
- * index >= n writes 0 and sets LECO_ERR_INDEX_RANGE in the column status (see leco_sync). */
+/* Batched point lookups (§3.3 Decoder, random access; §4.3.2): d_out[q] = value at position d_idx[q]
+ * for q < k (input order, duplicates allowed). d_idx: k uint64 on the device; d_out: k values of the
+ * column's width on the device; both caller-owned. Fixed partitions use j = i / L; variable
+ * partitions a search over the starts. An index >= n writes 0 and sets LECO_ERR_INDEX_RANGE in the
+ * column status (see leco_sync). */
 leco_status leco_random_access(const leco_column* col, const uint64_t* d_idx, uint64_t k,
                                void* d_out, leco_stream_t stream);
 
-/* Fused filter + aggregate: count and sum of the values v with lo <= v <= hi (unsigned,
- * inclusive), never materialising the decoded column. d_out: one leco_sum_result on the device,
- * overwritten. lo > hi gives {0, 0, 0}. flags: 0 or LECO_FILTER_PRUNE. */
+/* Fused filter + aggregate (the filter of §5.1.1, with its sum): count and sum of the values v with
+ * lo <= v <= hi (unsigned, inclusive), never materialising the decoded column. d_out: one
+ * leco_sum_result on the device, caller-owned, overwritten. lo > hi gives {0, 0, 0}. flags: any
+ * combination of LECO_FILTER_PRUNE and LECO_FILTER_DECODE_ALL (the result is the same). Errors:
+ * INVALID_ARG (NULL, unknown flag bits), CUDA. */
 leco_status leco_filter_sum(const leco_column* col, uint64_t lo, uint64_t hi, uint32_t flags,
                             leco_sum_result* d_out, leco_stream_t stream);
 
 /* Synchronize `stream`, then return the first device-side error recorded on the column since the
- * last leco_sync (and clear it), else LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
+ * last leco_sync (and clear it), else LECO_OK; a failed synchronization returns LECO_ERR_CUDA.
+ * Error reporting of this library; the paper has no counterpart. */
 leco_status leco_sync(const leco_column* col, leco_stream_t stream);
 
 /* Fixed partition-size search (§3.2.1): sample k = max(1, floor(sample_frac n / max_len))
@@ -250,28 +256,37 @@ leco_status leco_probe_throughput(int32_t kind, double* ops_per_s, leco_stream_t
 /* ------------------------------------------------------------------------------------------ */
 /* Column metadata and lifetime */
 
+/* Sizes and parameters of the column (host memory *out, filled at once, no CUDA call). total_bytes
+ * / (n * value bytes) is the compression ratio the paper reports (§4.3.1). Errors: INVALID_ARG. */
 leco_status leco_stats_get(const leco_column* col, leco_stats* out);
 
-/* Copy the column's m records (32 bytes each) and padded residual words to host buffers of at
- * least 32 m and 8 * (padded words) bytes (either may be NULL to skip); synchronous. */
+/* Copy the column's stored format (§3.3 storage format): its m records (32 bytes each), padded
+ * residual words and, for variable columns, m+1 starts, to caller-owned host buffers of at least
+ * 32 m, 8 * (padded words) and 8 (m+1) bytes (any may be NULL to skip); synchronous. Errors:
+ * INVALID_ARG, CUDA. */
 leco_status leco_column_export(const leco_column* col, void* host_records, void* host_words,
                                void* host_starts);
 
-/* Serialize to a self-describing host blob (header + records + starts (variable only) + words +
- * CRC-32). host_buf == NULL: *bytes = the size needed. cap too small: INVALID_ARG with *bytes
- * set. Synchronous (waits for the column's encode). */
+/* Serialize to a self-describing host blob: the §3.3 storage format (records, starts for variable
+ * columns, words) behind this library's 64-byte header and CRC-32. host_buf == NULL: *bytes = the
+ * size needed. cap too small: INVALID_ARG with *bytes set. Synchronous (waits for the column's
+ * encode). */
 leco_status leco_serialize(const leco_column* col, void* host_buf, uint64_t cap, uint64_t* bytes);
 
-/* Rebuild a column from a blob (validated: magic, version, sizes, CRC, record consistency).
- * Errors: CORRUPT, INVALID_ARG, OOM, CUDA. */
+/* Rebuild a column from a blob written by leco_serialize (§3.3 storage format). Everything a kernel
+ * indexes with is validated on the host before any device work: magic, version, sizes, CRC, record
+ * widths and dense offsets, starts tiling [0, n), zero padding, polynomial blocks the decoder can
+ * evaluate. The blob stays the caller's. Errors: CORRUPT, INVALID_ARG, OOM, CUDA. */
 leco_status leco_deserialize(const void* host_buf, uint64_t bytes, leco_stream_t stream,
                              leco_column** out);
 
-/* Release a column: waits for the device to finish, then frees. NULL is ignored. */
+/* Release a column: waits for the device to finish, then frees. NULL is ignored. Library
+ * lifetime; the paper has no counterpart. */
 void leco_column_free(leco_column* col);
 
 /* Release a column in stream order: the memory is returned after the work already enqueued on
- * `stream` completes; the caller guarantees that no other stream still uses the column. */
+ * `stream` completes; the caller guarantees that no other stream still uses the column. Library
+ * lifetime; the paper has no counterpart. */
 void leco_column_free_async(leco_column* col, leco_stream_t stream);
 
 /* Device memory: the library allocates from its own stream-ordered pool on each device, which keeps

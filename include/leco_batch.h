@@ -4,7 +4,9 @@
  * The paper decodes one column at a time on one CPU thread (§4.2); these calls are this library's
  * systems layer around the same per-value decode of §3.3: many columns of uneven lengths decoded
  * by one persistent kernel launch (optionally a CUDA graph) or encoded by one persistent fit and one
- * persistent pack launch (optionally a prepared plan replayed as one CUDA graph), and an autotuner that picks the scan pipeline's and the encode's shape. Conventions (device pointers, streams, ownership, errors) are those of leco.h.
+ * persistent pack launch (optionally a prepared plan replayed as one CUDA graph), and an autotuner
+ * that picks the scan pipeline's and the encode's shape. Conventions (device pointers, streams,
+ * ownership, errors) are those of leco.h.
  */
 #ifndef LECO_BATCH_H
 #define LECO_BATCH_H
@@ -26,8 +28,9 @@ typedef struct {
 /* Time every candidate configuration of the scan on this column (op 0: leco_decode_all; op 1:
  * leco_filter_sum over [lo, hi] with flags 0), keep the fastest in the process-wide tuning table
  * (keyed by op, value width and the column's widest partition), and return it in *best. Later
- * decodes and filter-sums of columns in the same key use it. Synchronizes `stream`; allocates a
- * temporary decode output. Errors: INVALID_ARG, OOM, CUDA. */
+ * decodes and filter-sums of columns in the same key use it; no result changes, only the speed.
+ * Synchronizes `stream`; allocates a temporary decode output. Errors: INVALID_ARG, OOM, CUDA. An
+ * autotuner of this library; the paper has no counterpart. */
 leco_status leco_tune_scan(const leco_column* col, uint32_t op, uint64_t lo, uint64_t hi,
                            leco_stream_t stream, leco_scan_config* best);
 
@@ -35,12 +38,14 @@ leco_status leco_tune_scan(const leco_column* col, uint32_t op, uint64_t lo, uin
  * entry, one per line. Load merges the file's entries into the process-wide table, keeping those
  * that name a candidate the tuners can pick (scan: 2..8 stages, 4 or 8 consumer warps; batched
  * encode: 1024, 2048 or 4096 values per pack item, 2..4 fit CTAs per SM) and skipping the rest.
- * Errors: INVALID_ARG for a NULL path or a file that cannot be opened. */
+ * Errors: INVALID_ARG for a NULL path or a file that cannot be opened. The paper has no
+ * counterpart. */
 leco_status leco_tune_save(const char* path);
 leco_status leco_tune_load(const char* path);
 
-/* A prepared multi-column decode: every scan tile of every column becomes one job of a work
- * table on the device, so all columns decode in one persistent kernel launch. d_outs[c] receives
+/* A prepared multi-column decode (the §3.3 Decoder over many columns; the batching is this library's
+ * systems layer): every scan tile of every column becomes one job of a work table on the device,
+ * so all columns decode in one persistent kernel launch. d_outs[c] receives
  * all values of cols[c] (n * value bytes, caller-owned, device). Columns may mix 32- and 64-bit
  * values and partition kinds; all must live on the current device. The plan owns its tables and
  * must be freed with leco_batch_plan_free; the columns must outlive it. */
@@ -49,11 +54,13 @@ typedef struct leco_batch_plan leco_batch_plan;
 leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* d_outs, uint32_t ncols,
                                    leco_batch_plan** out);
 
-/* One kernel launch on `stream` decoding every column of the plan. */
+/* One kernel launch on `stream` decoding every column of the plan. Errors: INVALID_ARG (NULL
+ * plan), CUDA; device-side errors surface at leco_batch_plan_sync. */
 leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream);
 
 /* The same launch as a CUDA graph: the first call captures it (on a private stream) and
- * instantiates the graph; every call launches the graph on `stream`. */
+ * instantiates the graph; every call launches the graph on `stream`. Errors as
+ * leco_batch_plan_run. */
 leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream);
 
 /* Time the plan's launch under every candidate pipeline shape (the whole multi-column decode, on
@@ -67,13 +74,14 @@ leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, le
  * LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
 leco_status leco_batch_plan_sync(leco_batch_plan* plan, leco_stream_t stream);
 
-/* Number of jobs (scan tiles) in the plan. */
+/* Number of jobs (scan tiles) in the plan; 0 for NULL. */
 uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan);
 
 /* Waits for the device, then releases the plan's tables and graph. NULL is ignored. */
 void leco_batch_plan_free(leco_batch_plan* plan);
 
-/* create + run + free in one call (synchronizes `stream` before freeing). */
+/* The §3.3 Decoder over many columns in one call: create + run + free (synchronizes `stream`
+ * before freeing). Arguments and errors as leco_batch_plan_create and leco_batch_plan_run. */
 leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_outs, uint32_t ncols,
                               leco_stream_t stream);
 
@@ -83,8 +91,8 @@ leco_status leco_batch_decode(const leco_column* const* cols, void* const* d_out
  * in one launch (fit, offset scan, decode table, tile descriptors, pack; the polynomial columns' fit
  * adds its four phases over all their partitions), in the shape the tuning table holds for `dtype`
  * (leco_tune_batch_encode); one stream synchronization reads back the residual streams' sizes, which
- * the allocation of the packed streams needs. out[c]
- * receives a column identical to leco_encode(d_vals[c], n[c], dtype, fixed(L[c]), models[c]);
+ * the allocation of the packed streams needs. out[c] receives a column identical to
+ * leco_encode(d_vals[c], n[c], dtype, fixed(L[c]), models[c]);
  * the columns share their device blocks, which are released when the last of them is freed.
  * Errors: INVALID_ARG, OOM, CUDA (then no column is returned). */
 leco_status leco_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
@@ -106,7 +114,8 @@ typedef struct {
  * the second pass counts), keep the fastest for later batched encodes of the same value width (the
  * process-wide tuning table, saved and loaded with the scan configurations), and return it in
  * *best. The encoded columns are freed; the result of every later encode is unchanged (byte for
- * byte), only its speed. Synchronizes `stream`. Errors: INVALID_ARG, OOM, CUDA. */
+ * byte), only its speed. Synchronizes `stream`. Errors: INVALID_ARG, OOM, CUDA. An autotuner of
+ * this library; the paper has no counterpart. */
 leco_status leco_tune_batch_encode(const void* const* d_vals, const uint64_t* n, const leco_model* models,
                                    const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
                                    leco_encode_config* best);
@@ -129,8 +138,10 @@ leco_status leco_batch_encode_plan_create(const void* const* d_vals, const uint6
                                           const uint32_t* L, uint32_t ncols, leco_dtype dtype, leco_stream_t stream,
                                           leco_batch_encode_plan** out);
 
-/* One launch of the plan's graph on `stream`: every column is encoded into the plan's blocks,
- * replacing the previous run's result. Runs that overlap on the device race on those blocks. */
+/* One launch of the plan's graph on `stream`: every column is encoded (§3.1 fit, §3.3 packing)
+ * into the plan's blocks, replacing the previous run's result. Runs that overlap on the device race
+ * on those blocks. Errors: INVALID_ARG (NULL plan), CUDA; a bounded wait that gave up surfaces at
+ * leco_batch_encode_plan_columns. */
 leco_status leco_batch_encode_plan_run(leco_batch_encode_plan* plan, leco_stream_t stream);
 
 /* Synchronize `stream` (the stream of the last run), then copy the last run's result out into
@@ -142,7 +153,8 @@ leco_status leco_batch_encode_plan_run(leco_batch_encode_plan* plan, leco_stream
  * CUDA. */
 leco_status leco_batch_encode_plan_columns(leco_batch_encode_plan* plan, leco_stream_t stream, leco_column** out);
 
-/* Device bytes the plan holds (its tables, scratch and reserved words); 0 for NULL. */
+/* Device bytes the plan holds (its tables, scratch and reserved words); 0 for NULL. The paper has no
+ * counterpart. */
 uint64_t leco_batch_encode_plan_reserved_bytes(const leco_batch_encode_plan* plan);
 
 /* Waits for the device, then releases the plan's blocks and graph. NULL is ignored. */

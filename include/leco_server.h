@@ -45,8 +45,8 @@ typedef struct {
   uint32_t columns;               /* admitted columns */
 } leco_server_stats;
 
-/* Create a server on the current device. Errors: INVALID_ARG, OOM, BUDGET (the slots alone do
- * not fit in budget_bytes), CUDA. */
+/* Create a server on the current device (the serving layer; the paper has no counterpart). Errors:
+ * INVALID_ARG, OOM, BUDGET (the slots alone do not fit in budget_bytes), CUDA. */
 leco_status leco_server_create(const leco_server_config* cfg, leco_server** out);
 
 /* Admit a column: on success the server owns it (it frees it on evict/destroy) and *col_id names
@@ -61,15 +61,17 @@ leco_status leco_server_admit_mock(leco_server* s, uint64_t n, leco_dtype dtype,
 /* Remove a column once its pending requests are done, and free it. */
 leco_status leco_server_evict(leco_server* s, uint32_t col_id);
 
-/* Queue k point lookups of column col_id: host_idx is copied at submit; host_out (k values of the
- * column's width, host memory) is written before the request completes and must stay valid until
- * then. INDEX_RANGE when an index >= n, INVALID_ARG for an unknown column or k over the batch
- * limit. *req_id names the request for leco_server_wait. */
+/* Queue k point lookups (§3.3 random access, served) of column col_id: host_idx is copied at
+ * submit; host_out (k values of the column's width, host memory) is written before the request
+ * completes and must stay valid until then. INDEX_RANGE when an index >= n, INVALID_ARG for an
+ * unknown column or k over the batch limit. *req_id names the request for leco_server_wait. */
 leco_status leco_server_submit_lookup(leco_server* s, uint32_t col_id, const uint64_t* host_idx,
                                       uint64_t k, void* host_out, uint64_t* req_id);
 
-/* Queue the decode of positions [begin, begin + count) of column col_id into host_out (count
- * values of the column's width). INDEX_RANGE when begin + count > n. */
+/* Queue the decode of positions [begin, begin + count) of column col_id (§3.3 range decompression,
+ * served) into host_out (count values of the column's width, host memory, valid until the request
+ * completes). INDEX_RANGE when begin + count > n, INVALID_ARG for an unknown column, count = 0 or
+ * count over the batch limit. */
 leco_status leco_server_submit_range(leco_server* s, uint32_t col_id, uint64_t begin, uint64_t count,
                                      void* host_out, uint64_t* req_id);
 
