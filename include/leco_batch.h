@@ -55,29 +55,34 @@ leco_status leco_batch_plan_create(const leco_column* const* cols, void* const* 
                                    leco_batch_plan** out);
 
 /* One kernel launch on `stream` decoding every column of the plan. Errors: INVALID_ARG (NULL
- * plan), CUDA; device-side errors surface at leco_batch_plan_sync. */
+ * plan), CUDA; device-side errors surface at leco_batch_plan_sync.
+ * Batching layer; the paper has no counterpart. */
 leco_status leco_batch_plan_run(leco_batch_plan* plan, leco_stream_t stream);
 
 /* The same launch as a CUDA graph: the first call captures it (on a private stream) and
  * instantiates the graph; every call launches the graph on `stream`. Errors as
- * leco_batch_plan_run. */
+ * leco_batch_plan_run. Batching layer; the paper has no counterpart. */
 leco_status leco_batch_plan_run_graph(leco_batch_plan* plan, leco_stream_t stream);
 
 /* Time the plan's launch under every candidate pipeline shape (the whole multi-column decode, on
  * `stream`, writing the plan's outputs) and keep the fastest for this plan's later runs; a graph
  * captured with another shape is captured again on its next run. The process-wide table of
- * leco_tune_scan is not changed. Synchronizes `stream`. Errors: INVALID_ARG, CUDA. */
+ * leco_tune_scan is not changed. Synchronizes `stream`. Errors: INVALID_ARG, CUDA.
+ * Batching layer; the paper has no counterpart. */
 leco_status leco_batch_plan_tune(leco_batch_plan* plan, leco_stream_t stream, leco_scan_config* best);
 
 /* Synchronize `stream`, then return the first device-side error the plan's runs recorded since the
  * last call (LECO_ERR_TIMEOUT when a bounded wait inside the decode gave up) and clear it, else
- * LECO_OK; a failed synchronization returns LECO_ERR_CUDA. */
+ * LECO_OK; a failed synchronization returns LECO_ERR_CUDA.
+ * Batching layer; the paper has no counterpart. */
 leco_status leco_batch_plan_sync(leco_batch_plan* plan, leco_stream_t stream);
 
-/* Number of jobs (scan tiles) in the plan; 0 for NULL. */
+/* Number of jobs (scan tiles) in the plan; 0 for NULL.
+ * Batching layer; the paper has no counterpart. */
 uint64_t leco_batch_plan_jobs(const leco_batch_plan* plan);
 
-/* Waits for the device, then releases the plan's tables and graph. NULL is ignored. */
+/* Waits for the device, then releases the plan's tables and graph. NULL is ignored.
+ * Batching layer; the paper has no counterpart. */
 void leco_batch_plan_free(leco_batch_plan* plan);
 
 /* The §3.3 Decoder over many columns in one call: create + run + free (synchronizes `stream`
@@ -150,14 +155,15 @@ leco_status leco_batch_encode_plan_run(leco_batch_encode_plan* plan, leco_stream
  * size, shared by the columns and released when the last of them is freed. The plan is unchanged
  * and may run again. Errors: INVALID_ARG (also before the plan's first run), OOM, TIMEOUT (a
  * bounded wait inside the run gave up; the streams are incomplete and no column is returned),
- * CUDA. */
+ * CUDA. Batching layer; the paper has no counterpart. */
 leco_status leco_batch_encode_plan_columns(leco_batch_encode_plan* plan, leco_stream_t stream, leco_column** out);
 
 /* Device bytes the plan holds (its tables, scratch and reserved words); 0 for NULL. The paper has no
  * counterpart. */
 uint64_t leco_batch_encode_plan_reserved_bytes(const leco_batch_encode_plan* plan);
 
-/* Waits for the device, then releases the plan's blocks and graph. NULL is ignored. */
+/* Waits for the device, then releases the plan's blocks and graph. NULL is ignored.
+ * Batching layer; the paper has no counterpart. */
 void leco_batch_encode_plan_free(leco_batch_encode_plan* plan);
 
 #ifdef __cplusplus

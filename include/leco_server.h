@@ -51,14 +51,16 @@ leco_status leco_server_create(const leco_server_config* cfg, leco_server** out)
 
 /* Admit a column: on success the server owns it (it frees it on evict/destroy) and *col_id names
  * it in requests. BUDGET when resident + reserved + the column's device bytes > budget (the
- * caller keeps the column then). */
+ * caller keeps the column then). Serving layer; the paper has no counterpart. */
 leco_status leco_server_admit(leco_server* s, leco_column* col, uint32_t* col_id);
 
-/* Mock executor only: admit a column of n values of `dtype` occupying `bytes` (no device data). */
+/* Mock executor only: admit a column of n values of `dtype` occupying `bytes` (no device data).
+ * Serving layer; the paper has no counterpart. */
 leco_status leco_server_admit_mock(leco_server* s, uint64_t n, leco_dtype dtype, uint64_t bytes,
                                    uint32_t* col_id);
 
-/* Remove a column once its pending requests are done, and free it. */
+/* Remove a column once its pending requests are done, and free it.
+ * Serving layer; the paper has no counterpart. */
 leco_status leco_server_evict(leco_server* s, uint32_t col_id);
 
 /* Queue k point lookups (§3.3 random access, served) of column col_id: host_idx is copied at
@@ -76,22 +78,28 @@ leco_status leco_server_submit_range(leco_server* s, uint32_t col_id, uint64_t b
                                      void* host_out, uint64_t* req_id);
 
 /* Wait up to timeout_ms for request req_id; on completion *result is its status and the request is
- * forgotten. TIMEOUT if still pending, INVALID_ARG for an unknown id. */
+ * forgotten. TIMEOUT if still pending, INVALID_ARG for an unknown id.
+ * Serving layer; the paper has no counterpart. */
 leco_status leco_server_wait(leco_server* s, uint64_t req_id, uint32_t timeout_ms, leco_status* result);
 
 /* Drive the server with a Poisson stream of requests for `seconds` at `rate` requests/s (seeded):
  * each request picks a column uniformly among `ncols` ids, then with probability lookup_frac is a
  * lookup of log-uniform 1..max_lookup uniform indices, else a range decode of log-uniform
  * min_range..max_range positions at a uniform start (clipped to the column). Output buffers are
- * the driver's own. Returns when every submitted request completed; *submitted = requests sent. */
+ * the driver's own. Returns when every submitted request completed; *submitted = requests sent.
+ * Serving layer; the paper has no counterpart. */
 leco_status leco_server_drive_poisson(leco_server* s, const uint32_t* col_ids, uint32_t ncols, double rate,
                                       double seconds, uint64_t seed, double lookup_frac, uint64_t max_lookup,
                                       uint64_t min_range, uint64_t max_range, uint64_t* submitted);
 
+/* Counters and latency percentiles since creation or the last reset (*out: host memory); reset
+ * clears them and restarts the clock. Errors: INVALID_ARG. Serving layer; the paper has no
+ * counterpart. */
 leco_status leco_server_stats_get(leco_server* s, leco_server_stats* out);
 leco_status leco_server_reset_stats(leco_server* s);
 
-/* Finish queued requests, stop the threads, free the admitted columns and the slots. */
+/* Finish queued requests, stop the threads, free the admitted columns and the slots.
+ * Serving layer; the paper has no counterpart. */
 void leco_server_destroy(leco_server* s);
 
 #ifdef __cplusplus
