@@ -220,3 +220,17 @@ def test_binding_checks_encode_arguments(built):
         leco.leco_encode_with_starts(v, torch.tensor([0, 100], dtype=torch.int32), 1)
     with pytest.raises(ValueError, match="needs m \\+ 1 = 3"):
         leco.leco_encode_with_starts(v, torch.tensor([0, 100], dtype=torch.int64), 2)
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration's comment (the nearest one above it) names the section of the paper it
+    follows, or says that the paper has no counterpart (library plumbing, batching, serving)."""
+    missing = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        for m in re.finditer(r"\n(?:leco_status|void|uint64_t|uint32_t|const char\*)\s+(leco_[a-z0-9_]+)\s*\(", text):
+            end = text.rfind("*/", 0, m.start())
+            comment = text[text.rfind("/*", 0, end):end] if end >= 0 else ""
+            if "§" not in comment and "counterpart" not in comment:
+                missing.append(f"{os.path.basename(h)}:{m.group(1)}")
+    assert not missing, missing
