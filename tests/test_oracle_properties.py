@@ -90,3 +90,26 @@ def test_polynomial_model_is_lossless(orc, data, bits, L):
                       for i in range(n)], dtype=np.uint64)
     rec, words = orc.encode_fixed(v, L, 2)
     _check_queries(orc, rec, words, v, bits, L, data.draw)
+
+
+@settings(max_examples=80, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(data=st.data(), bits=st.sampled_from([64, 32]), model=st.sampled_from([0, 1, 2]),
+       L=st.sampled_from([1, 5, 64, 100, 300]))
+def test_partition_size_is_what_the_encoder_stores(orc, data, bits, model, L):
+    """The size the partitioner minimises (§3.2.2: the model's bits plus len * b) is what the encoder
+    stores for that partition: the 256-bit record, len * b residual bits, and the 320-bit coefficient
+    block of a polynomial partition; and the stream's offsets add up to those bits."""
+    v = data.draw(columns(bits))
+    rec, words = orc.encode_fixed(v, L, model)
+    b = orc.rec_width(rec["word3"])
+    poly = orc.rec_poly(rec["word3"])
+    off = orc.rec_offset(rec["word3"])
+    total = 0
+    for p in range(len(rec)):
+        a = int(rec["start"][p])
+        e = min(a + L, v.size)
+        stored = (e - a) * int(b[p]) + (320 if poly[p] else 0)
+        assert int(off[p]) == total
+        total += stored
+        assert orc.partition_size_bits(v[a:e], model) == 256 + stored
+    assert len(words) == orc.words_for_bits(total)
